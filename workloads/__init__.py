@@ -1,0 +1,271 @@
+"""Seeded synthetic workloads for Array-OL repetitive tasks.
+
+This module only *describes* tasks and *draws* their inputs.  It holds none of
+the method's arithmetic (no tiler address generation, no filtering, no
+products): both the CPU oracle (``oracle/``) and the CUDA binding
+(``paper_1105_4424_gb300``) consume the plain dictionaries built here, each in
+its own code.
+
+A task is a dict::
+
+    {"rep":      (R_0, ..., R_{q-1}),               # repetition space
+     "elem":     "copy" | "fir" | "matmul",         # elementary task
+     "inputs":   [port, ...],                       # 1 (copy, fir) or 2 (matmul)
+     "outputs":  [port],                            # exactly 1
+     "taps":     float32 ndarray (m, T) or None}    # FIR tap bank
+
+and a port is ``{"shape", "dtype", "origin", "paving", "fitting", "pattern"}``
+with ``paving`` a d x q and ``fitting`` a d x p nested tuple (d = array rank,
+p = pattern rank).  Arrays are dense and row-major.
+
+All random draws use ``numpy.random.Generator(PCG64(seed))`` in the fixed
+order stated in each builder's docstring.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "rng", "port", "task", "fir_row_task", "downscale_chain",
+    "config0", "config1", "config2", "config3", "config4",
+    "bf16_round", "bf16_bits_to_f32", "random_tiler_task",
+]
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def port(shape, origin, paving, fitting, pattern, dtype="f32"):
+    d = len(shape)
+    paving = tuple(tuple(int(v) for v in row) for row in paving)
+    fitting = tuple(tuple(int(v) for v in row) for row in fitting)
+    assert len(origin) == d and len(paving) == d and len(fitting) == d
+    return {"shape": tuple(int(v) for v in shape), "dtype": dtype,
+            "origin": tuple(int(v) for v in origin), "paving": paving,
+            "fitting": fitting, "pattern": tuple(int(v) for v in pattern)}
+
+
+def task(rep, elem, inputs, outputs, taps=None):
+    return {"rep": tuple(int(v) for v in rep), "elem": elem,
+            "inputs": list(inputs), "outputs": list(outputs),
+            "taps": None if taps is None else np.ascontiguousarray(taps, dtype=np.float32)}
+
+
+def fir_row_task(height, width, T, m, step, taps):
+    """Row FIR downscaler on an (height, width) array.
+
+    Input tiler: origin 0, paving [[1,0],[0,step]], fitting [[0],[1]],
+    pattern (T,), repetition space (height, ceil(width/step)); the last
+    pattern of a row wraps around the right edge (modulo the array shape).
+    Output tiler: (height, m*ceil(width/step)), paving [[1,0],[0,m]],
+    fitting [[0],[1]], pattern (m,), which partitions the output array.
+    """
+    reps = -(-width // step)
+    inp = port((height, width), (0, 0), ((1, 0), (0, step)), ((0,), (1,)), (T,))
+    out = port((height, m * reps), (0, 0), ((1, 0), (0, m)), ((0,), (1,)), (m,))
+    return task((height, reps), "fir", [inp], [out], taps)
+
+
+def downscale_chain(frames, height, width, taps_h, taps_v, step_h=8, step_v=8):
+    """Horizontal then vertical FIR downscaler on rank-3 (frames, height, width).
+
+    The frame dimension enters every tiler as an extra array dimension and an
+    extra repetition dimension with paving 1 and fitting 0.  The horizontal
+    pass tiles along the last dimension, the vertical pass is the same form
+    transposed onto the middle dimension.  The horizontal output array is the
+    vertical input array (one shared allocation between the two tasks).
+    """
+    mh, th = taps_h.shape
+    mv, tv = taps_v.shape
+    assert width % step_h == 0 and height % step_v == 0
+    wr = width // step_h
+    mid_w = wr * mh
+    hr = height // step_v
+    out_h = hr * mv
+    t_h = task(
+        (frames, height, wr), "fir",
+        [port((frames, height, width), (0, 0, 0),
+              ((1, 0, 0), (0, 1, 0), (0, 0, step_h)), ((0,), (0,), (1,)), (th,))],
+        [port((frames, height, mid_w), (0, 0, 0),
+              ((1, 0, 0), (0, 1, 0), (0, 0, mh)), ((0,), (0,), (1,)), (mh,))],
+        taps_h)
+    t_v = task(
+        (frames, hr, mid_w), "fir",
+        [port((frames, height, mid_w), (0, 0, 0),
+              ((1, 0, 0), (0, step_v, 0), (0, 0, 1)), ((0,), (1,), (0,)), (tv,))],
+        [port((frames, out_h, mid_w), (0, 0, 0),
+              ((1, 0, 0), (0, mv, 0), (0, 0, 1)), ((0,), (1,), (0,)), (mv,))],
+        taps_v)
+    return [t_h, t_v]
+
+
+def _taps(g, m, T):
+    return (g.standard_normal((m, T), dtype=np.float64) / T).astype(np.float32)
+
+
+def config0(seed=0):
+    """64x64 float32 U[0,1) -> 8-tap/3-output FIR, step 4, wrap -> 64x48.
+
+    Draw order: X (64x64), then taps H (3x8) ~ N(0,1)/8, j-major.
+    """
+    g = rng(seed)
+    x = g.random((64, 64), dtype=np.float32)
+    H = _taps(g, 3, 8)
+    inp = port((64, 64), (0, 0), ((1, 0), (0, 4)), ((0,), (1,)), (8,))
+    out = port((64, 48), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))
+    return task((64, 16), "fir", [inp], [out], H), [x]
+
+
+def config1(seed=0, frames=64, height=1080, width=1920):
+    """Two chained 8->3 FIR downscalers on frames x height x width float32.
+
+    Draw order: X (frames, height, width) U[0,1), taps_h (3x8), taps_v (3x8).
+    """
+    g = rng(seed)
+    x = g.random((frames, height, width), dtype=np.float32)
+    Hh = _taps(g, 3, 8)
+    Hv = _taps(g, 3, 8)
+    return downscale_chain(frames, height, width, Hh, Hv), [x]
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """float32 -> bfloat16 bit patterns (uint16), round to nearest even."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    nan = np.isnan(x)
+    bias = ((u >> 16) & 1) + 0x7FFF
+    b = ((u + bias) >> 16).astype(np.uint16)
+    b[nan] = 0x7FC0
+    return b
+
+
+def bf16_bits_to_f32(b: np.ndarray) -> np.ndarray:
+    return (np.ascontiguousarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def matmul_task(M, N, K, tile_m=128, tile_n=128):
+    """C (M,N) f32 = A (M,K) bf16 . B (K,N) bf16 as a repetitive task.
+
+    Repetition space (M/tile_m, N/tile_n); A's tiler fetches the tile_m x K row
+    panel (paving [[tile_m,0],[0,0]], fitting identity), B's tiler the
+    K x tile_n column panel (paving [[0,0],[0,tile_n]]), C's tiler the
+    tile_m x tile_n tile (paving diag(tile_m, tile_n)), a partition of C.
+    """
+    assert M % tile_m == 0 and N % tile_n == 0
+    eye = ((1, 0), (0, 1))
+    a = port((M, K), (0, 0), ((tile_m, 0), (0, 0)), eye, (tile_m, K), "bf16")
+    b = port((K, N), (0, 0), ((0, 0), (0, tile_n)), eye, (K, tile_n), "bf16")
+    c = port((M, N), (0, 0), ((tile_m, 0), (0, tile_n)), eye, (tile_m, tile_n), "f32")
+    return task((M // tile_m, N // tile_n), "matmul", [a, b], [c])
+
+
+def config2(seed=0, M=4096, N=4096, K=4096):
+    """Matmul task; A then B drawn N(0,1) as float32, rounded to bf16 (RNE).
+
+    Returns (task, [A_bits, B_bits]) with uint16 bfloat16 bit patterns.
+    """
+    g = rng(seed)
+    a = bf16_round(g.standard_normal((M, K), dtype=np.float32))
+    b = bf16_round(g.standard_normal((K, N), dtype=np.float32))
+    return matmul_task(M, N, K), [a, b]
+
+
+def config3_params(seed=0, n=512, lo=32, hi=2048):
+    """Per-instance parameters of the uneven batch, drawn in this order for
+    each instance: height, width ~ round(exp(U(ln lo, ln hi))); T ~ U{3..32};
+    m ~ U{1..floor(T/2)}; step ~ U{m..T}."""
+    g = rng(seed)
+    params = []
+    for _ in range(n):
+        h = int(round(math.exp(g.uniform(math.log(lo), math.log(hi)))))
+        w = int(round(math.exp(g.uniform(math.log(lo), math.log(hi)))))
+        T = int(g.integers(3, 33))
+        m = int(g.integers(1, T // 2 + 1))
+        step = int(g.integers(m, T + 1))
+        params.append((h, w, T, m, step))
+    return params, g
+
+
+def config3(seed=0, n=512, lo=32, hi=2048):
+    """512 independent row-FIR instances of uneven size (see config3_params).
+
+    After all parameters, for each instance in order: taps (m x T) ~ N(0,1)/T,
+    then X (height x width) U[0,1).
+    """
+    params, g = config3_params(seed, n, lo, hi)
+    tasks, xs = [], []
+    for (h, w, T, m, step) in params:
+        H = _taps(g, m, T)
+        x = g.random((h, w), dtype=np.float32)
+        tasks.append(fir_row_task(h, w, T, m, step, H))
+        xs.append(x)
+    return tasks, xs
+
+
+def config4(seed=0, frames=16, height=1080, width=1920):
+    """Forward + backward of the downscaler chain; loss = sum(W * out).
+
+    Draw order: X, taps_h, taps_v, then W ~ N(0,1) with the output shape.
+    """
+    g = rng(seed)
+    x = g.random((frames, height, width), dtype=np.float32)
+    Hh = _taps(g, 3, 8)
+    Hv = _taps(g, 3, 8)
+    chain = downscale_chain(frames, height, width, Hh, Hv)
+    out_shape = chain[1]["outputs"][0]["shape"]
+    w = g.standard_normal(out_shape, dtype=np.float32)
+    return chain, [x], w
+
+
+def random_tiler_task(g: np.random.Generator, elem="copy", max_side=12,
+                      max_rank=3, max_abs=6):
+    """A random small task: random input tiler (negative origin, paving and
+    fitting entries allowed, overlaps and wrap-around allowed) and an output
+    tiler that partitions its array by construction.
+
+    The output array's dimensions are a random permutation of the repetition
+    dimensions and the output pattern dimensions; with probability 1/2 the
+    last repetition dimension is merged with the (rank-1) output pattern into
+    one array dimension of size R*m (paving m, fitting 1), as in a downscaler.
+    """
+    q = int(g.integers(1, 3))
+    R = tuple(int(v) for v in g.integers(1, 6, size=q))
+    d = int(g.integers(1, max_rank + 1))
+    shape = tuple(int(v) for v in g.integers(1, max_side + 1, size=d))
+    p = 1 if elem == "fir" else int(g.integers(1, 3))
+    S = tuple(int(v) for v in g.integers(1, 5, size=p))
+    origin = tuple(int(v) for v in g.integers(-3 * max_abs, 3 * max_abs + 1, size=d))
+    paving = tuple(tuple(int(v) for v in g.integers(-max_abs, max_abs + 1, size=q)) for _ in range(d))
+    fitting = tuple(tuple(int(v) for v in g.integers(-max_abs, max_abs + 1, size=p)) for _ in range(d))
+    inp = port(shape, origin, paving, fitting, S)
+    T = int(np.prod(S))
+    if elem == "fir":
+        m = int(g.integers(1, T + 1))
+        S_out = (m,)
+        taps = _taps(g, m, T)
+    else:
+        S_out = S
+        taps = None
+    p_out = len(S_out)
+    merge = (p_out == 1) and bool(g.integers(0, 2))
+    if merge:
+        dims = [("r", k) for k in range(q - 1)] + [("m", 0)]
+    else:
+        dims = [("r", k) for k in range(q)] + [("s", k) for k in range(p_out)]
+    perm = g.permutation(len(dims))
+    dims = [dims[i] for i in perm]
+    oshape, opav, ofit = [], [], []
+    for kind, k in dims:
+        prow, frow = [0] * q, [0] * p_out
+        if kind == "r":
+            oshape.append(R[k]); prow[k] = 1
+        elif kind == "s":
+            oshape.append(S_out[k]); frow[k] = 1
+        else:
+            oshape.append(R[q - 1] * S_out[0]); prow[q - 1] = S_out[0]; frow[0] = 1
+        opav.append(tuple(prow)); ofit.append(tuple(frow))
+    oorigin = tuple(int(v) for v in g.integers(-max_abs, max_abs + 1, size=len(oshape)))
+    out = port(tuple(oshape), oorigin, tuple(opav), tuple(ofit), S_out)
+    return task(R, elem, [inp], [out], taps)
