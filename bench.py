@@ -1,0 +1,402 @@
+"""Benchmark of the Array-OL repetitive-task library on GB300.
+
+Headline step: the two chained 8->3 FIR downscalers (horizontal then vertical)
+on 64 float32 frames of 1080x1920 -> 64 x 405 x 720, one fused kernel launch
+through the C ABI.  Metric: tiler elements per second (pattern elements
+gathered + elements scattered, both tasks) and the fraction of the measured
+HBM copy bandwidth reached by the kernel on its algorithmic bytes (input read
+once, output written once).  The same JSON line also reports the batched
+uneven workload (512 tasks, one graph launch vs one launch per task), the
+backward pass (fwd+bwd over fwd, 16 frames) and the tensor-core matmul task
+(4096^3 bf16 -> f32).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs its own 64 frames (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+FRAMES, HEIGHT, WIDTH = 64, 1080, 1920
+METRIC = "tiler elems/s (fused 2-task FIR downscaler chain)"
+UNIT = "elems/s"
+WORKLOAD = "downscale chain 64x1080x1920 f32 -> 64x405x720 (8-tap->3 FIR, step 8, both axes)"
+L2_BYTES = 126 * 1024 * 1024
+
+
+def chain_units(frames, height=HEIGHT, width=WIDTH):
+    """Tiler elements of one pass of the chain: gathered + scattered, both tasks."""
+    wr, hr = width // 8, height // 8
+    gathered = frames * height * wr * 8 + frames * hr * (wr * 3) * 8
+    scattered = frames * height * wr * 3 + frames * hr * 3 * wr * 3
+    return gathered + scattered
+
+
+def chain_bytes(frames, height=HEIGHT, width=WIDTH):
+    """Algorithmic bytes of the fused chain: X read once, Y written once."""
+    return 4 * frames * height * width + 4 * frames * (height // 8 * 3) * (width // 8 * 3)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------- rank aggregation
+
+def aggregate(elapsed_ms_per_rank, units_per_rank, steps):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    t = max(elapsed_ms_per_rank)
+    total = sum(units_per_rank)
+    return total / (t / 1e3), t / steps
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def dist_max(value, world):
+    if world == 1:
+        return [value]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    out = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(out, t)
+    return [float(o.item()) for o in out]
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------- measurements
+
+def time_loop(fn, steps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def time_each_flushed(fn, reps, stream, flush):
+    """Per-iteration CUDA-event times with an L2 flush (a 256 MB write)
+    between iterations, outside the timed events."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts
+
+
+def bench_batched(A, torch, stream, flush, reps):
+    tasks, xs = W.config3()
+    b = A.Batch(tasks)
+    ins = [torch.from_numpy(x).cuda() for x in xs]
+    outs = b.empty_outputs()
+    cfg = b.tune(ins, outs)
+    for _ in range(3):
+        b.run(ins, outs)
+        b.run_per_task(ins, outs)
+    batched = time_each_flushed(lambda: b.run(ins, outs), reps, stream, flush)
+    per_task = time_each_flushed(lambda: b.run_per_task(ins, outs), reps, stream, flush)
+    nbytes = sum(4 * x.size for x in xs) + sum(4 * int(np.prod(t["outputs"][0]["shape"])) for t in tasks)
+    units = sum(t["rep"][0] * t["rep"][1] * (t["inputs"][0]["pattern"][0] + t["outputs"][0]["pattern"][0])
+                for t in tasks)
+    tb, tp = statistics.median(batched), statistics.median(per_task)
+    return {"tasks": len(tasks), "unique_bytes": nbytes, "tiler_elems": units,
+            "batched_ms": tb, "per_task_ms": tp, "speedup": tp / tb,
+            "batched_gbs": nbytes / (tb * 1e-3) / 1e9, "batched_elems_per_s": units / (tb * 1e-3),
+            "launches_batched": 1, "launches_per_task": len(tasks), "autotuned": cfg}
+
+
+def bench_backward(A, torch, stream, flush, reps):
+    chain, (x,), w = W.config4()
+    c = A.Chain(chain)
+    xd = torch.from_numpy(x).cuda()
+    wd = torch.from_numpy(w).cuda()
+    y = c.run([xd])
+    gx = torch.empty_like(xd)
+    gt = torch.empty(48, device="cuda")
+    for _ in range(3):
+        c.run([xd], y)
+        c.backward(wd, [xd], gx, gt)
+        c.fwd_bwd([xd], wd, y, gx, gt)
+    fwd = statistics.median(time_each_flushed(lambda: c.run([xd], y), reps, stream, flush))
+    bwd = statistics.median(time_each_flushed(lambda: c.backward(wd, [xd], gx, gt), reps, stream, flush))
+
+    def both():
+        c.run([xd], y)
+        c.backward(wd, [xd], gx, gt)
+    fb = statistics.median(time_each_flushed(both, reps, stream, flush))
+    fused = statistics.median(time_each_flushed(lambda: c.fwd_bwd([xd], wd, y, gx, gt), reps, stream, flush))
+    fb_bytes = 4 * (x.size + w.size) + 4 * x.size   # bwd reads X and dY, writes dX
+    return {"frames": 16, "fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_ms": fb, "ratio": fb / fwd,
+            "fused_fwd_bwd_ms": fused, "fused_ratio": fused / fwd,
+            "fwd_gbs": chain_bytes(16) / (fwd * 1e-3) / 1e9, "bwd_gbs": fb_bytes / (bwd * 1e-3) / 1e9}
+
+
+def bench_matmul(A, torch, stream, flush, reps, peak_tf):
+    tk, (a, b) = W.config2()
+    t = A.Task(tk)
+    ad = torch.from_numpy(a.view(np.int16)).cuda().view(torch.bfloat16)
+    bd = torch.from_numpy(b.view(np.int16)).cuda().view(torch.bfloat16)
+    c = t.run([ad, bd])
+    for _ in range(3):
+        t.run([ad, bd], c)
+    t.sync_status()
+    ms = statistics.median(time_each_flushed(lambda: t.run([ad, bd], c), reps, stream, flush))
+    ref = statistics.median(time_each_flushed(lambda: torch.matmul(ad, bd), reps, stream, flush))
+    flops = 2.0 * 4096 ** 3
+    return {"mnk": [4096, 4096, 4096], "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+            "frac_of_bf16_peak": flops / (ms * 1e-3) / 1e12 / peak_tf,
+            "torch_matmul_bf16_out_ms": ref, "torch_tflops": flops / (ref * 1e-3) / 1e12}
+
+
+def bench_config0(A, torch, stream, reps):
+    tk, (x,) = W.config0()
+    t = A.Task(tk)
+    xd = torch.from_numpy(x).cuda()
+    y = t.run([xd])
+    for _ in range(10):
+        t.run([xd], y)
+    ms = time_loop(lambda: t.run([xd], y), reps, stream) / reps
+    return {"us_per_call": ms * 1e3}
+
+
+def cpu_baseline_chain(max_seconds=12.0):
+    """The C oracle, as it stands, on a bounded sample of the chain workload
+    (whole frames of 1080x1920), on all host cores."""
+    from oracle import cpu_ref as C
+    frames = 1
+    g = W.rng(1)
+    while True:
+        chain, (x,) = W.config1(seed=1, frames=frames)
+        t0 = time.perf_counter()
+        C.run_chain(chain, [x])
+        dt = time.perf_counter() - t0
+        if dt * 2 > max_seconds or frames >= FRAMES:
+            break
+        frames = min(FRAMES, max(frames * 2, int(frames * max_seconds / max(dt, 1e-3) / 2)))
+    del g
+    return {"value": chain_units(frames) / dt, "unit": UNIT, "cores": C.threads(), "kind": "oracle",
+            "sample": f"{frames} of 64 frames (1080x1920), full chain, float64 accumulation",
+            "seconds": dt}
+
+
+# -------------------------------------------------------------- main arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import cpu_ref as C
+    frames = 2
+    chain, (x,) = W.config1(seed=1, frames=frames)
+    for _ in range(args.warmup):
+        C.run_chain(chain, [x])
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        C.run_chain(chain, [x])
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    value = chain_units(frames) * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_frames": frames},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": C.threads(), "kind": "oracle",
+                             "sample": f"{frames} of 64 frames per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import paper_1105_4424_gb300 as A
+    hbm, bf16, bf16_sus, peak_kind = measured_peaks()
+    stream = torch.cuda.current_stream()
+
+    chain, (x,) = W.config1(seed=rank)
+    c = A.Chain(chain)
+    xd = torch.from_numpy(x).cuda()
+    y = c.run([xd])
+    units = chain_units(FRAMES)
+    nbytes = chain_bytes(FRAMES)
+
+    with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            c.run([xd], y)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        ms = time_loop(lambda: c.run([xd], y), args.steps, stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    all_ms = dist_max(ms, world)
+    value, ms_per_step = aggregate(all_ms, [units] * world, args.steps)
+    kernel_ms = ms / args.steps                      # one kernel launch per step
+    achieved = nbytes / (kernel_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with page-locked host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty(tuple(chain[-1]["outputs"][0]["shape"]), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        c.run_host([xh], yh)
+    e2e_steps = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        c.run_host([xh], yh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    all_e2e = dist_max(e2e_s * 1e3, world)
+    e2e_value = units * world / (max(all_e2e) * 1e-3)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_gpu": FRAMES, "tiler_elems_per_step_per_gpu": units,
+                       "unique_bytes_per_step_per_gpu": nbytes,
+                       "l2": "inputs (531 MB per step) exceed L2 (126 MB): no flush; extras flush L2 with a 256 MB write",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": "downscale_fwd_kernel", "achieved": achieved, "peak": hbm,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
+                    "d2h_bytes_per_step": int(yh.numel() * 4), "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_extras:
+        flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+        reps = max(5, min(args.steps, 20))
+        line["config0"] = bench_config0(A, torch, stream, 200)
+        line["batched"] = bench_batched(A, torch, stream, flush, reps)
+        line["fwd_bwd"] = bench_backward(A, torch, stream, flush, reps)
+        line["matmul"] = bench_matmul(A, torch, stream, flush, reps, bf16)
+        del flush
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_chain()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="headline only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,246 @@
+/*
+ * arol.h — C ABI of the GB300 Array-OL repetitive-task library.
+ *
+ * A repetitive task (MARTE Repetitive Structure Modeling, named in Sec. 3 of
+ * Rodrigues, Guyomarc'h and Dekeyser 2011; "repetitive and thus potentially
+ * parallel" tasks mapped onto GPU processors, Sec. 7) runs one elementary task
+ * per point r of a repetition space R.  Its ports are arrays whose shape and
+ * element type come from the flow ports (Sec. 5: dimAllocation and
+ * typeAllocation; Sec. 6.3: direction — input ports are read-only).  A tiler
+ * connects a port to the repetition space: for repetition r and pattern index i
+ * it names the array element
+ *
+ *     e(r, i) = (origin + paving . r + fitting . i) mod shape
+ *
+ * componentwise with a Euclidean mod (result in [0, shape_k)).  Input tilers
+ * gather patterns, the elementary task maps them, the output tiler scatters
+ * the result and must write every element of its array exactly once.
+ *
+ * Conventions for every entry point
+ *  - Arrays are dense and row-major (last dimension contiguous).  Array and
+ *    pattern pointers passed to run calls are DEVICE pointers owned by the
+ *    caller; the library never frees them.  The only host-pointer entry point
+ *    is arol_task_run_host.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued asynchronously on it; the call returns after
+ *    enqueueing (arol_task_run_host is the exception: it synchronizes).
+ *  - Every call returns an arol_status and, on failure, records a message
+ *    readable with arol_last_error (thread-local).  No C++ exception crosses
+ *    the ABI.  A failed call enqueues nothing.
+ *  - Handles (arol_task, arol_batch) own copies of their descriptors, taps and
+ *    any scratch or staging memory they allocate; destroy them with
+ *    arol_task_destroy / arol_batch_destroy after the streams they were used
+ *    on have finished.
+ *  - Calls on one handle must not run concurrently from several host threads.
+ */
+#ifndef AROL_H
+#define AROL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AROL_VERSION 100            /* 1.0.0 */
+#define AROL_MAX_RANK 4             /* array rank and repetition-space rank */
+#define AROL_MAX_PATTERN_RANK 2     /* pattern rank */
+#define AROL_MAX_FIR_M 32           /* outputs per pattern of a FIR bank */
+#define AROL_MAX_FIR_TAPS 8192      /* m * T */
+
+typedef enum {
+    AROL_OK = 0,
+    AROL_ERR_INVALID = 1,        /* malformed descriptor, null handle/pointer, bad size */
+    AROL_ERR_NOT_PARTITION = 2,  /* an output tiler does not write each element exactly once */
+    AROL_ERR_UNSUPPORTED = 3,    /* well formed, but outside what the kernels implement */
+    AROL_ERR_CUDA = 4,           /* a CUDA runtime call or kernel launch failed */
+    AROL_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    AROL_ERR_OOB = 6             /* a device-side bounds check fired (checked builds only) */
+} arol_status;
+
+typedef enum { AROL_F32 = 0, AROL_BF16 = 1 } arol_dtype;
+
+typedef enum {
+    AROL_ELEM_COPY = 0,    /* y[j] = p[j]: raw bits, NaN payloads kept */
+    AROL_ELEM_FIR = 1,     /* y[j] = sum_k H[j,k] p[k], H is m x T (a bank of m tap rows) */
+    AROL_ELEM_MATMUL = 2   /* y = p_A . p_B, patterns (a x K) and (K x b), bf16 in, f32 out */
+} arol_elem_kind;
+
+/* An array port (Sec. 5 MemoryMap/DataAllocate: dimAllocation = shape,
+ * typeAllocation = dtype).  rank in [1, 4]; shape entries in [0, 2^31).  An
+ * array with no elements is only allowed in a task whose repetition space is
+ * empty (the output must then be empty too: the empty partition). */
+typedef struct {
+    int32_t rank;
+    int32_t dtype;                 /* arol_dtype */
+    int64_t shape[AROL_MAX_RANK];
+} arol_array_desc;
+
+/* A tiler: origin (rank entries), paving [array dim][repetition dim],
+ * fitting [array dim][pattern dim], pattern shape (pattern_rank entries in
+ * [1, 2], each >= 1).  Entries may be negative; they are taken mod shape. */
+typedef struct {
+    int64_t origin[AROL_MAX_RANK];
+    int64_t paving[AROL_MAX_RANK][AROL_MAX_RANK];
+    int64_t fitting[AROL_MAX_RANK][AROL_MAX_PATTERN_RANK];
+    int32_t pattern_rank;
+    int32_t reserved_;
+    int64_t pattern[AROL_MAX_PATTERN_RANK];
+} arol_tiler;
+
+/* One repetitive task.  copy and fir take one input port, matmul two; every
+ * task has one output port.  A repetition-space entry may be 0 (empty task).
+ * fir_taps_host (m x T, row-major, float) is copied at create time; it may be
+ * NULL, in which case arol_task_set_taps must be called before running. */
+typedef struct {
+    int32_t rep_rank;
+    int32_t elem;                  /* arol_elem_kind */
+    int64_t rep[AROL_MAX_RANK];
+    int32_t n_in;
+    int32_t n_out;
+    arol_array_desc in[2];
+    arol_array_desc out[1];
+    arol_tiler in_tiler[2];
+    arol_tiler out_tiler[1];
+    int32_t fir_T;
+    int32_t fir_m;
+    const float* fir_taps_host;
+} arol_task_desc;
+
+typedef struct arol_task_s* arol_task;
+typedef struct arol_batch_s* arol_batch;
+
+/* What the library chose for a task (filled by arol_task_info). */
+typedef struct {
+    int32_t kind;              /* 0 single task, 1 chain */
+    int32_t kernel;            /* 0 generic tiler, 1 fused separable downscaler, 2 tcgen05 matmul, 3 unfused chain */
+    int64_t reps;              /* repetitions of the task (sum over a chain's tasks) */
+    int64_t gathered_elems;    /* pattern elements gathered over all inputs (and tasks) */
+    int64_t scattered_elems;   /* elements scattered (sum over a chain's tasks) */
+    int64_t unique_bytes;      /* algorithmic bytes: every external input element read once,
+                                  every final output element written once */
+    double flops;              /* arithmetic of the elementary tasks (2 per multiply-add) */
+} arol_task_info_t;
+
+/* ---- tasks --------------------------------------------------------------- */
+
+/* Validate `desc` and build a task handle.  Host only: touches no GPU state.
+ * Checks ranks, shapes, the elementary-task/pattern/dtype combination (copy:
+ * same dtype and pattern size in and out; fir: f32 in and out, pattern size T,
+ * output pattern size m; matmul: bf16 inputs with the panel tilers of a tiled
+ * product, f32 output) and that the output tiler partitions its array
+ * (AROL_ERR_NOT_PARTITION otherwise).  On success *out owns a copy of the
+ * descriptor and of the taps. */
+arol_status arol_task_create(const arol_task_desc* desc, arol_task* out);
+
+/* Chain n >= 2 single tasks through shared arrays (Sec. 5, associatedParts:
+ * all elements of the model that use the same allocation): the output array
+ * of tasks[k] is the input array of tasks[k+1] (same shape and dtype,
+ * AROL_ERR_INVALID otherwise).  The chain copies what it needs from the tasks;
+ * they may be destroyed afterwards.  Its run, backward and fwd_bwd take the
+ * first task's inputs and the last task's output.  A chain whose tasks are a
+ * separable block downscaler (horizontal then vertical fir with step == T, no
+ * wrap) runs as one fused kernel that never writes the intermediate to HBM;
+ * other chains run task by task through an intermediate the chain allocates
+ * on first use. */
+arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out);
+
+/* Replace the fir taps.  on_device = 0: `taps` is host memory, copied now.
+ * on_device = 1: `taps` is a device pointer the caller keeps alive and
+ * unchanged while runs that use it are in flight (it is read, never written).
+ * For a chain the taps are the concatenation of each task's m x T block in
+ * task order. */
+arol_status arol_task_set_taps(arol_task t, const float* taps, int on_device);
+
+/* Run the task: in[k] is the device pointer of input port k, out[0] of the
+ * output port.  Inputs are read-only (Sec. 6.3); they must not overlap the
+ * output. */
+arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, void* stream);
+
+/* Same computation from HOST buffers: copies each input from host memory to
+ * device staging buffers owned by the task, runs, copies the output back to
+ * host memory, and synchronizes `stream` before returning.  Host buffers
+ * should be page-locked for full bandwidth. */
+arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* const* host_out, void* stream);
+
+/* Reverse mode of a fir task or chain for a loss L with dL/d(out) = grad_out.
+ * saved_in: the forward inputs (device).  grad_in (nullable, device, input
+ * shape) is OVERWRITTEN with dL/d(in): the transposed-tiler scatter-add, which
+ * sums over every (r, i) whose gather visited an element (overlaps and modulo
+ * wrap included).  grad_taps (nullable, device, m x T floats, a chain's blocks
+ * concatenated) is OVERWRITTEN with dL/dH.  Deterministic: no atomics. */
+arol_status arol_task_backward(arol_task t, const void* grad_out, const void* const* saved_in,
+                               void* grad_in, float* grad_taps, void* stream);
+
+/* Forward and reverse mode in one pass when grad_out is known before the
+ * forward runs (e.g. loss = sum(W * out)): writes out, grad_in and grad_taps
+ * as arol_task_run followed by arol_task_backward would, reading the inputs
+ * once.  Only the fused separable downscaler chain supports it
+ * (AROL_ERR_UNSUPPORTED otherwise). */
+arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* grad_out, void* out,
+                              void* grad_in, float* grad_taps, void* stream);
+
+/* Sizes and work of a task (host only). */
+arol_status arol_task_info(arol_task t, arol_task_info_t* info);
+
+void arol_task_destroy(arol_task t);
+
+/* Host-side partition check (no task needed): *count_max and *count_min
+ * receive the largest and smallest number of (r, j) pairs that the tiler maps
+ * onto one element of the array; a partition has both equal to 1. */
+arol_status arol_tiler_cover(const arol_array_desc* array, const arol_tiler* tiler,
+                             int rep_rank, const int64_t* rep, int64_t* count_min, int64_t* count_max);
+
+/* ---- batches of independent tasks ---------------------------------------- */
+
+/* Build a batch of n independent single-input copy/fir tasks (uneven shapes
+ * allowed).  The batch owns a device work list of (task, repetition range)
+ * tiles, built on first run, and a CUDA graph that launches one persistent
+ * kernel over the whole list. */
+arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out);
+
+/* Run every task of the batch in one graph launch: in[k] / out[k] are task k's
+ * input and output device pointers.  When the pointers differ from the
+ * previous call the device table is refreshed (one copy) before the launch. */
+arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out, void* stream);
+
+/* The same tasks with one kernel launch per task, in order, on `stream`
+ * (the same kernel body; for comparison with arol_batch_run). */
+arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* const* out, void* stream);
+
+/* Autotune the batch's tile size and persistent-grid shape by timing
+ * candidates on the given buffers (outputs are overwritten).  Results are
+ * cached per process by batch signature and device, and persisted as JSON in
+ * the file named by the AROL_TUNE_CACHE environment variable when it is set.
+ * force = 1 re-times even when a cached choice exists.  Synchronizes. */
+arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* out, void* stream, int force);
+
+/* The tile size (repetitions per tile) and CTAs per SM in use. */
+arol_status arol_batch_config(arol_batch b, int64_t* tile_reps, int32_t* ctas_per_sm, int32_t* threads);
+
+void arol_batch_destroy(arol_batch b);
+
+/* ---- errors and version --------------------------------------------------- */
+
+/* Copy the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len).  Returns AROL_OK. */
+arol_status arol_last_error(char* buf, size_t len);
+
+int arol_version(void);
+
+/* sizeof of the ABI structs as this library was compiled (0: arol_array_desc,
+ * 1: arol_tiler, 2: arol_task_desc, 3: arol_task_info_t; -1 otherwise), so a
+ * binding can check its own struct layout against the library's. */
+int64_t arol_abi_struct_size(int which);
+
+/* Synchronize `stream`, then report device-side failures recorded by kernels
+ * of task t since its last run: AROL_ERR_TIMEOUT when a bounded wait inside
+ * the tensor-core matmul gave up, AROL_OK otherwise. */
+arol_status arol_task_sync_status(arol_task t, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AROL_H */

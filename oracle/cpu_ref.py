@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -30,11 +31,16 @@ class OrefPort(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile cpu_ref.c into oracle/_cpu_ref.so (gcc, OpenMP, -O2)."""
+    stamp = _LIB + ".arch"
+    if not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine():
+        force = True   # a library of another host architecture
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
                                "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(platform.machine() + "\n")
     return _LIB
 
 

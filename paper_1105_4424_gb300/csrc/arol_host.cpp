@@ -1,0 +1,1349 @@
+// Host runtime of the Array-OL repetitive-task library: descriptor validation,
+// the output-partition check, kernel selection, tap buffers, chains (shared
+// arrays, Sec. 5 associatedParts), batches (device work list + CUDA graph +
+// autotuner) and the C ABI declared in include/arol.h.
+#include "arol.h"
+#include "arol_internal.h"
+
+#include <algorithm>
+#include <cinttypes>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+using namespace arol;
+
+namespace arol {
+cudaError_t launch_tiler_bwd(const TaskDev& t, const int64_t* inv_start, const int32_t* inv_list,
+                             float* gx, const float* gy, float* grad_taps, float* partials, int nblocks,
+                             int64_t chunk, cudaStream_t s);
+int tiler_bwd_blocks(int64_t nreps, int64_t* chunk);
+}  // namespace arol
+
+namespace {
+
+thread_local std::string g_err;
+
+arol_status fail(arol_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+arol_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(AROL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define AROL_CUDA(call, what)                        \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+int64_t emod(int64_t a, int64_t s) {
+    int64_t r = a % s;
+    return r < 0 ? r + s : r;
+}
+
+int64_t elems_of(const arol_array_desc& a) {
+    int64_t n = 1;
+    for (int k = 0; k < a.rank; ++k) n *= a.shape[k];
+    return n;
+}
+
+int esize_of(int dtype) { return dtype == AROL_BF16 ? 2 : 4; }
+
+int64_t pattern_size(const arol_tiler& t) {
+    int64_t n = 1;
+    for (int p = 0; p < t.pattern_rank; ++p) n *= t.pattern[p];
+    return n;
+}
+
+int64_t reps_of(const arol_task_desc& d) {
+    int64_t n = 1;
+    for (int q = 0; q < d.rep_rank; ++q) n *= d.rep[q];
+    return n;
+}
+
+constexpr int64_t kMaxDim = (int64_t(1) << 31) - 1;
+
+arol_status check_array(const arol_array_desc& a, const char* name) {
+    if (a.rank < 1 || a.rank > AROL_MAX_RANK) return fail(AROL_ERR_INVALID, "%s: rank %d not in [1,4]", name, a.rank);
+    if (a.dtype != AROL_F32 && a.dtype != AROL_BF16) return fail(AROL_ERR_INVALID, "%s: unknown dtype %d", name, a.dtype);
+    double total = 1;
+    for (int k = 0; k < a.rank; ++k) {
+        if (a.shape[k] < 0 || a.shape[k] > kMaxDim)
+            return fail(AROL_ERR_INVALID, "%s: shape[%d] = %" PRId64 " not in [0, 2^31)", name, k, a.shape[k]);
+        total *= (double)a.shape[k];
+    }
+    if (total > 4.0e18) return fail(AROL_ERR_INVALID, "%s: too many elements", name);
+    return AROL_OK;
+}
+
+arol_status check_tiler(const arol_tiler& t, const char* name) {
+    if (t.pattern_rank < 1 || t.pattern_rank > AROL_MAX_PATTERN_RANK)
+        return fail(AROL_ERR_INVALID, "%s: pattern rank %d not in [1,2]", name, t.pattern_rank);
+    double n = 1;
+    for (int p = 0; p < t.pattern_rank; ++p) {
+        if (t.pattern[p] < 1 || t.pattern[p] > kMaxDim)
+            return fail(AROL_ERR_INVALID, "%s: pattern[%d] = %" PRId64 " not in [1, 2^31)", name, p, t.pattern[p]);
+        n *= (double)t.pattern[p];
+    }
+    if (n > (double)kMaxDim) return fail(AROL_ERR_INVALID, "%s: pattern has 2^31 or more elements", name);
+    return AROL_OK;
+}
+
+// ---------------------------------------------------------------- partition
+
+// Sufficient closed-form test: every array dimension is a mixed-radix
+// combination of repetition/pattern dimensions (coefficients 1, n1, n1*n2, ...
+// whose extents multiply to the dimension's size), each repetition/pattern
+// dimension of extent > 1 drives exactly one array dimension.  Such a map is
+// a bijection onto the array (a cyclic shift by the origin keeps it one).
+bool partition_closed_form(const arol_array_desc& a, const arol_tiler& t, int rep_rank, const int64_t* rep) {
+    struct Term { int64_t coef, extent; };
+    const int nd = rep_rank + t.pattern_rank;
+    std::vector<int> used(nd, 0);
+    for (int k = 0; k < a.rank; ++k) {
+        std::vector<Term> terms;
+        for (int q = 0; q < nd; ++q) {
+            const int64_t ext = q < rep_rank ? rep[q] : t.pattern[q - rep_rank];
+            const int64_t c = emod(q < rep_rank ? t.paving[k][q] : t.fitting[k][q - rep_rank], a.shape[k]);
+            if (ext <= 1 || c == 0) continue;
+            terms.push_back({c, ext});
+            ++used[q];
+        }
+        std::sort(terms.begin(), terms.end(), [](const Term& x, const Term& y) { return x.coef < y.coef; });
+        int64_t expect = 1;
+        for (const Term& tm : terms) {
+            if (tm.coef != expect) return false;
+            if (expect > kMaxDim * 4 / tm.extent) return false;
+            expect *= tm.extent;
+        }
+        if (expect != a.shape[k]) return false;
+    }
+    for (int q = 0; q < nd; ++q) {
+        const int64_t ext = q < rep_rank ? rep[q] : t.pattern[q - rep_rank];
+        if (ext > 1 && used[q] != 1) return false;
+    }
+    return true;
+}
+
+// Exact count by enumeration: the largest and smallest number of (r, j) that
+// land on one element.  Address walk with one conditional subtract per step.
+arol_status partition_count(const arol_array_desc& a, const arol_tiler& t, int rep_rank, const int64_t* rep,
+                            int64_t* cmin, int64_t* cmax) {
+    const int64_t n = elems_of(a);
+    int64_t nreps = 1;
+    for (int q = 0; q < rep_rank; ++q) nreps *= rep[q];
+    const int64_t ns = pattern_size(t);
+    std::vector<uint8_t> cnt;
+    try {
+        cnt.assign((size_t)n, 0);
+    } catch (...) {
+        return fail(AROL_ERR_INVALID, "partition check: cannot allocate %" PRId64 " counters", n);
+    }
+    int64_t stride[4] = {0, 0, 0, 0};
+    {
+        int64_t s = 1;
+        for (int k = a.rank - 1; k >= 0; --k) { stride[k] = s; s *= a.shape[k]; }
+    }
+    int64_t pav[4][4] = {}, fit[4][2] = {}, org[4] = {};
+    for (int k = 0; k < a.rank; ++k) {
+        org[k] = emod(t.origin[k], a.shape[k]);
+        for (int q = 0; q < rep_rank; ++q) pav[k][q] = emod(t.paving[k][q], a.shape[k]);
+        for (int p = 0; p < t.pattern_rank; ++p) fit[k][p] = emod(t.fitting[k][p], a.shape[k]);
+    }
+    const int64_t P1 = t.pattern_rank == 2 ? t.pattern[1] : t.pattern[0];
+    const int64_t P0 = t.pattern_rank == 2 ? t.pattern[0] : 1;
+    const int c1 = t.pattern_rank == 2 ? 1 : 0;   // fitting column of the fast pattern dim
+    std::vector<int64_t> r(std::max(rep_rank, 1), 0);
+    int64_t base[4], row[4], cur[4];
+    for (int64_t lr = 0; lr < nreps; ++lr) {
+        for (int k = 0; k < a.rank; ++k) {
+            __int128 v = org[k];
+            for (int q = 0; q < rep_rank; ++q) v += (__int128)pav[k][q] * r[q];
+            base[k] = (int64_t)(v % a.shape[k]);
+            row[k] = base[k];
+        }
+        for (int64_t i0 = 0; i0 < P0; ++i0) {
+            for (int k = 0; k < a.rank; ++k) cur[k] = row[k];
+            for (int64_t i1 = 0; i1 < P1; ++i1) {
+                int64_t off = 0;
+                for (int k = 0; k < a.rank; ++k) off += cur[k] * stride[k];
+                if (cnt[off] < 255) ++cnt[off];
+                for (int k = 0; k < a.rank; ++k) {
+                    cur[k] += fit[k][c1];
+                    if (cur[k] >= a.shape[k]) cur[k] -= a.shape[k];
+                }
+            }
+            if (t.pattern_rank == 2)
+                for (int k = 0; k < a.rank; ++k) {
+                    row[k] += fit[k][0];
+                    if (row[k] >= a.shape[k]) row[k] -= a.shape[k];
+                }
+        }
+        for (int q = rep_rank - 1; q >= 0; --q) {
+            if (++r[q] < rep[q]) break;
+            r[q] = 0;
+        }
+    }
+    (void)ns;
+    uint8_t lo = 255, hi = 0;
+    for (int64_t e = 0; e < n; ++e) {
+        lo = std::min(lo, cnt[e]);
+        hi = std::max(hi, cnt[e]);
+    }
+    *cmin = lo;
+    *cmax = hi;
+    return AROL_OK;
+}
+
+arol_status check_partition(const arol_array_desc& a, const arol_tiler& t, int rep_rank, const int64_t* rep) {
+    int64_t nreps = 1;
+    for (int q = 0; q < rep_rank; ++q) nreps *= rep[q];
+    if (nreps * pattern_size(t) != elems_of(a))
+        return fail(AROL_ERR_NOT_PARTITION, "output tiler writes %" PRId64 " elements into an array of %" PRId64,
+                    nreps * pattern_size(t), elems_of(a));
+    if (nreps == 0) return AROL_OK;   // an empty repetition space partitions an empty array
+    if (partition_closed_form(a, t, rep_rank, rep)) return AROL_OK;
+    int64_t lo = 0, hi = 0;
+    arol_status st = partition_count(a, t, rep_rank, rep, &lo, &hi);
+    if (st != AROL_OK) return st;
+    if (lo != 1 || hi != 1)
+        return fail(AROL_ERR_NOT_PARTITION, "output tiler writes some element %" PRId64 " times and some %" PRId64 " times",
+                    hi, lo);
+    return AROL_OK;
+}
+
+// ------------------------------------------------------------ device params
+
+void make_port(const arol_array_desc& a, const arol_tiler& t, int rep_rank, PortDev& p) {
+    std::memset(&p, 0, sizeof p);
+    int64_t s = 1;
+    for (int k = 3; k >= 0; --k) {
+        if (k < a.rank) {
+            p.shape[k] = (int32_t)a.shape[k];
+            p.stride[k] = s;
+            s *= a.shape[k];
+        } else {
+            p.shape[k] = 1;
+            p.stride[k] = 0;
+        }
+    }
+    for (int k = 0; k < a.rank; ++k) {
+        if (a.shape[k] == 0) continue;   // empty array: never addressed
+        p.origin[k] = (uint32_t)emod(t.origin[k], a.shape[k]);
+        for (int q = 0; q < rep_rank; ++q) p.paving[k][q] = (uint32_t)emod(t.paving[k][q], a.shape[k]);
+        if (t.pattern_rank == 1) {
+            p.fitting[k][0] = 0;
+            p.fitting[k][1] = (uint32_t)emod(t.fitting[k][0], a.shape[k]);
+        } else {
+            p.fitting[k][0] = (uint32_t)emod(t.fitting[k][0], a.shape[k]);
+            p.fitting[k][1] = (uint32_t)emod(t.fitting[k][1], a.shape[k]);
+        }
+    }
+    if (t.pattern_rank == 1) {
+        p.pattern[0] = 1;
+        p.pattern[1] = (int32_t)t.pattern[0];
+    } else {
+        p.pattern[0] = (int32_t)t.pattern[0];
+        p.pattern[1] = (int32_t)t.pattern[1];
+    }
+}
+
+bool port_needs_wide(const PortDev& p, const arol_task_desc& d) {
+    for (int k = 0; k < 4; ++k) {
+        double v = p.origin[k];
+        for (int q = 0; q < d.rep_rank; ++q) v += (double)p.paving[k][q] * (double)(d.rep[q] - 1);
+        if (v >= 4294967295.0) return true;
+    }
+    return false;
+}
+
+TaskDev make_taskdev(const arol_task_desc& d) {
+    TaskDev t;
+    std::memset(&t, 0, sizeof t);
+    for (int q = 0; q < 4; ++q) t.rep[q] = 1;
+    // real repetition dims are right-aligned so that the last one is fastest
+    // in decode_rep; paving columns are re-indexed to match.
+    const int shift = 4 - d.rep_rank;
+    arol_task_desc dd = d;
+    for (int k = 0; k < AROL_MAX_RANK; ++k)
+        for (int q = 0; q < 4; ++q) dd.in_tiler[0].paving[k][q] = dd.out_tiler[0].paving[k][q] = 0;
+    for (int q = 0; q < d.rep_rank; ++q) {
+        t.rep[q + shift] = (int32_t)d.rep[q];
+        for (int k = 0; k < AROL_MAX_RANK; ++k) {
+            dd.in_tiler[0].paving[k][q + shift] = d.in_tiler[0].paving[k][q];
+            dd.out_tiler[0].paving[k][q + shift] = d.out_tiler[0].paving[k][q];
+        }
+    }
+    t.nreps = reps_of(d);
+    make_port(d.in[0], dd.in_tiler[0], 4, t.in);
+    make_port(d.out[0], dd.out_tiler[0], 4, t.out);
+    t.elem = d.elem == AROL_ELEM_FIR ? ELEM_FIR : ELEM_COPY;
+    t.T = (int32_t)pattern_size(d.in_tiler[0]);
+    t.m = (int32_t)pattern_size(d.out_tiler[0]);
+    t.esize = esize_of(d.in[0].dtype);
+    arol_task_desc full = dd;
+    full.rep_rank = 4;
+    for (int q = 0; q < 4; ++q) full.rep[q] = t.rep[q];
+    t.wide = (t.nreps >= 4294967295LL || port_needs_wide(t.in, full) || port_needs_wide(t.out, full)) ? 1 : 0;
+    return t;
+}
+
+// ------------------------------------------------------------------ matchers
+
+bool tiler_is(const arol_tiler& t, int rank, std::initializer_list<int64_t> origin,
+              std::initializer_list<std::initializer_list<int64_t>> paving,
+              std::initializer_list<std::initializer_list<int64_t>> fitting, int rep_rank) {
+    int k = 0;
+    for (int64_t o : origin) if (t.origin[k++] != o) return false;
+    k = 0;
+    for (auto& row : paving) {
+        int q = 0;
+        for (int64_t v : row) if (t.paving[k][q++] != v) return false;
+        if (q != rep_rank) return false;
+        ++k;
+    }
+    if (k != rank) return false;
+    k = 0;
+    for (auto& row : fitting) {
+        int p = 0;
+        for (int64_t v : row) if (t.fitting[k][p++] != v) return false;
+        if (p != t.pattern_rank) return false;
+        ++k;
+    }
+    return k == rank;
+}
+
+// The panel form of a tiled product: A (M,K) row panels, B (K,N) column
+// panels, C (M,N) tiles, all 128 x 128 tiles, origins 0, fittings identity.
+bool is_matmul_panels(const arol_task_desc& d, int* M, int* N, int* K) {
+    if (d.n_in != 2 || d.rep_rank != 2 || d.in[0].rank != 2 || d.in[1].rank != 2 || d.out[0].rank != 2) return false;
+    const int64_t m = d.in[0].shape[0], k = d.in[0].shape[1], n = d.in[1].shape[1];
+    if (d.in[1].shape[0] != k || d.out[0].shape[0] != m || d.out[0].shape[1] != n) return false;
+    const arol_tiler &A = d.in_tiler[0], &B = d.in_tiler[1], &C = d.out_tiler[0];
+    if (A.pattern_rank != 2 || B.pattern_rank != 2 || C.pattern_rank != 2) return false;
+    const int64_t tm = A.pattern[0], tn = B.pattern[1];
+    if (A.pattern[1] != k || B.pattern[0] != k || C.pattern[0] != tm || C.pattern[1] != tn) return false;
+    if (d.rep[0] * tm != m || d.rep[1] * tn != n) return false;
+    if (!tiler_is(A, 2, {0, 0}, {{tm, 0}, {0, 0}}, {{1, 0}, {0, 1}}, 2)) return false;
+    if (!tiler_is(B, 2, {0, 0}, {{0, 0}, {0, tn}}, {{1, 0}, {0, 1}}, 2)) return false;
+    if (!tiler_is(C, 2, {0, 0}, {{tm, 0}, {0, tn}}, {{1, 0}, {0, 1}}, 2)) return false;
+    *M = (int)m;
+    *N = (int)n;
+    *K = (int)k;
+    return tm == 128 && tn == 128;
+}
+
+// A rank-3 (frames, rows, cols) view of a single fir task of the row form
+// (axis = 2: horizontal) or column form (axis = 1: vertical), rank-2 arrays
+// being one frame.  Fills frames/rows/cols/step/T/m; origins must be 0.
+struct Pass { int64_t F, H, W; int64_t S, T, m; };
+
+bool match_pass(const arol_task_desc& d, int axis, Pass* ps) {
+    if (d.elem != AROL_ELEM_FIR || d.n_in != 1 || d.in[0].dtype != AROL_F32) return false;
+    const arol_array_desc &a = d.in[0], &o = d.out[0];
+    const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
+    if (a.rank != o.rank || a.rank != d.rep_rank || (a.rank != 2 && a.rank != 3)) return false;
+    if (ti.pattern_rank != 1 || to.pattern_rank != 1) return false;
+    const int off = a.rank == 3 ? 1 : 0;   // index of the rows dim
+    const int ax = axis - (3 - a.rank);     // axis in this rank
+    const int64_t S = ti.paving[ax][ax], T = ti.pattern[0], m = to.pattern[0];
+    for (int k = 0; k < a.rank; ++k) {
+        if (ti.origin[k] != 0 || to.origin[k] != 0) return false;
+        for (int q = 0; q < a.rank; ++q) {
+            const int64_t want_in = (k == q) ? (k == ax ? S : 1) : 0;
+            const int64_t want_out = (k == q) ? (k == ax ? m : 1) : 0;
+            if (ti.paving[k][q] != want_in || to.paving[k][q] != want_out) return false;
+        }
+        if (ti.fitting[k][0] != (k == ax ? 1 : 0) || to.fitting[k][0] != (k == ax ? 1 : 0)) return false;
+    }
+    for (int k = 0; k < a.rank; ++k) {
+        const int64_t want_rep = k == ax ? a.shape[k] / S : a.shape[k];
+        if (d.rep[k] != want_rep) return false;
+        const int64_t want_out = k == ax ? want_rep * m : a.shape[k];
+        if (o.shape[k] != want_out) return false;
+    }
+    if (a.shape[ax] % S != 0) return false;
+    ps->F = a.rank == 3 ? a.shape[0] : 1;
+    ps->H = a.shape[off];
+    ps->W = a.shape[off + 1];
+    ps->S = S;
+    ps->T = T;
+    ps->m = m;
+    return true;
+}
+
+}  // namespace
+
+// ===================================================================== tasks
+
+struct arol_task_s {
+    int kind = 0;                        // 0 single, 1 chain
+    int kernel = 0;                      // arol_task_info_t.kernel
+    std::vector<arol_task_desc> descs;   // one per task (fir_taps_host cleared)
+    std::vector<int64_t> tap_off;        // offset of each task's taps in taps_host
+    std::vector<float> taps_host;
+    bool taps_ready = true;
+    const float* taps_borrowed = nullptr;
+    float* taps_dev = nullptr;
+    bool taps_dirty = true;
+    int device = -1;
+    // unfused chain intermediates
+    std::vector<void*> mids;
+    // fused downscaler
+    int64_t ds_frames = 0;
+    int ds_H = 0, ds_W = 0;
+    // matmul
+    int mm_M = 0, mm_N = 0, mm_K = 0;
+    unsigned* mm_err = nullptr;
+    // backward scratch and inverse maps
+    float* partials = nullptr;
+    int64_t partials_cap = 0;
+    std::vector<int64_t*> inv_start;
+    std::vector<int32_t*> inv_list;
+    std::vector<float*> grad_mids;
+    // host-buffer staging
+    void* stage_in[2] = {nullptr, nullptr};
+    void* stage_out = nullptr;
+    arol_task_info_t info{};
+};
+
+namespace {
+
+arol_status remember_device(arol_task t) {
+    int dev = 0;
+    AROL_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (t->device < 0) t->device = dev;
+    else if (t->device != dev)
+        return fail(AROL_ERR_INVALID, "task used on device %d but its buffers live on device %d", dev, t->device);
+    return AROL_OK;
+}
+
+arol_status dev_alloc(arol_task t, void** p, size_t bytes, const char* what) {
+    arol_status st = remember_device(t);
+    if (st != AROL_OK) return st;
+    if (*p) return AROL_OK;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, what);
+    }
+    return AROL_OK;
+}
+
+arol_status ensure_taps(arol_task t, cudaStream_t s, const float** out) {
+    *out = nullptr;
+    if (t->taps_host.empty() && !t->taps_borrowed) return AROL_OK;
+    if (t->taps_borrowed) {
+        *out = t->taps_borrowed;
+        return AROL_OK;
+    }
+    if (!t->taps_ready) return fail(AROL_ERR_INVALID, "fir taps were never set");
+    arol_status st = dev_alloc(t, (void**)&t->taps_dev, t->taps_host.size() * sizeof(float), "cudaMalloc(taps)");
+    if (st != AROL_OK) return st;
+    if (t->taps_dirty) {
+        AROL_CUDA(cudaMemcpyAsync(t->taps_dev, t->taps_host.data(), t->taps_host.size() * sizeof(float),
+                                  cudaMemcpyHostToDevice, s),
+                  "upload taps");
+        t->taps_dirty = false;
+    }
+    *out = t->taps_dev;
+    return AROL_OK;
+}
+
+arol_status validate_desc(const arol_task_desc& d) {
+    if (d.rep_rank < 1 || d.rep_rank > AROL_MAX_RANK) return fail(AROL_ERR_INVALID, "rep_rank %d not in [1,4]", d.rep_rank);
+    for (int q = 0; q < d.rep_rank; ++q)
+        if (d.rep[q] < 0 || d.rep[q] > kMaxDim) return fail(AROL_ERR_INVALID, "rep[%d] = %" PRId64 " out of range", q, d.rep[q]);
+    if (d.n_out != 1) return fail(AROL_ERR_INVALID, "n_out must be 1 (got %d)", d.n_out);
+    const int want_in = d.elem == AROL_ELEM_MATMUL ? 2 : 1;
+    if (d.elem < AROL_ELEM_COPY || d.elem > AROL_ELEM_MATMUL) return fail(AROL_ERR_INVALID, "unknown elementary task %d", d.elem);
+    if (d.n_in != want_in) return fail(AROL_ERR_INVALID, "elementary task %d takes %d inputs (got %d)", d.elem, want_in, d.n_in);
+    arol_status st;
+    for (int i = 0; i < d.n_in; ++i) {
+        if ((st = check_array(d.in[i], "input")) != AROL_OK) return st;
+        if ((st = check_tiler(d.in_tiler[i], "input tiler")) != AROL_OK) return st;
+    }
+    if ((st = check_array(d.out[0], "output")) != AROL_OK) return st;
+    if ((st = check_tiler(d.out_tiler[0], "output tiler")) != AROL_OK) return st;
+    if (reps_of(d) > 0) {
+        for (int i = 0; i < d.n_in; ++i)
+            if (elems_of(d.in[i]) == 0) return fail(AROL_ERR_INVALID, "input %d is empty but the repetition space is not", i);
+        if (elems_of(d.out[0]) == 0) return fail(AROL_ERR_INVALID, "output is empty but the repetition space is not");
+    }
+    const int64_t ns_in = pattern_size(d.in_tiler[0]), ns_out = pattern_size(d.out_tiler[0]);
+    switch (d.elem) {
+    case AROL_ELEM_COPY:
+        if (d.in[0].dtype != d.out[0].dtype) return fail(AROL_ERR_INVALID, "copy: input and output dtypes differ");
+        if (ns_in != ns_out) return fail(AROL_ERR_INVALID, "copy: input pattern has %" PRId64 " elements, output %" PRId64, ns_in, ns_out);
+        break;
+    case AROL_ELEM_FIR:
+        if (d.in[0].dtype != AROL_F32 || d.out[0].dtype != AROL_F32)
+            return fail(AROL_ERR_UNSUPPORTED, "fir: float32 input and output only");
+        if (d.fir_T != ns_in || d.fir_m != ns_out)
+            return fail(AROL_ERR_INVALID, "fir: T=%d m=%d but patterns have %" PRId64 " and %" PRId64 " elements",
+                        d.fir_T, d.fir_m, ns_in, ns_out);
+        if (d.fir_m < 1 || d.fir_m > AROL_MAX_FIR_M) return fail(AROL_ERR_UNSUPPORTED, "fir: m=%d not in [1,32]", d.fir_m);
+        if ((int64_t)d.fir_m * d.fir_T > AROL_MAX_FIR_TAPS) return fail(AROL_ERR_UNSUPPORTED, "fir: m*T above 8192");
+        break;
+    case AROL_ELEM_MATMUL: {
+        if (d.in[0].dtype != AROL_BF16 || d.in[1].dtype != AROL_BF16 || d.out[0].dtype != AROL_F32)
+            return fail(AROL_ERR_UNSUPPORTED, "matmul: bf16 inputs and float32 output only");
+        int M, N, K;
+        if (!is_matmul_panels(d, &M, &N, &K))
+            return fail(AROL_ERR_UNSUPPORTED, "matmul: only the 128 x 128 panel/tile tilers of a tiled product are supported");
+        if (K % 64 != 0 || K < 64) return fail(AROL_ERR_UNSUPPORTED, "matmul: K must be a positive multiple of 64");
+        break;
+    }
+    }
+    return check_partition(d.out[0], d.out_tiler[0], d.rep_rank, d.rep);
+}
+
+void fill_info_single(arol_task t) {
+    const arol_task_desc& d = t->descs[0];
+    arol_task_info_t& in = t->info;
+    in.kind = 0;
+    in.kernel = t->kernel;
+    in.reps = reps_of(d);
+    in.gathered_elems = 0;
+    in.unique_bytes = 0;
+    for (int i = 0; i < d.n_in; ++i) {
+        in.gathered_elems += in.reps * pattern_size(d.in_tiler[i]);
+        in.unique_bytes += elems_of(d.in[i]) * esize_of(d.in[i].dtype);
+    }
+    in.scattered_elems = in.reps * pattern_size(d.out_tiler[0]);
+    in.unique_bytes += elems_of(d.out[0]) * esize_of(d.out[0].dtype);
+    if (d.elem == AROL_ELEM_FIR) in.flops = 2.0 * d.fir_m * d.fir_T * (double)in.reps;
+    else if (d.elem == AROL_ELEM_MATMUL)
+        in.flops = 2.0 * (double)d.in_tiler[0].pattern[0] * d.in_tiler[0].pattern[1] * d.in_tiler[1].pattern[1] * (double)in.reps;
+    else in.flops = 0;
+}
+
+void free_dev(void* p) {
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+int arol_version(void) { return AROL_VERSION; }
+
+int64_t arol_abi_struct_size(int which) {
+    switch (which) {
+    case 0: return (int64_t)sizeof(arol_array_desc);
+    case 1: return (int64_t)sizeof(arol_tiler);
+    case 2: return (int64_t)sizeof(arol_task_desc);
+    case 3: return (int64_t)sizeof(arol_task_info_t);
+    default: return -1;
+    }
+}
+
+arol_status arol_last_error(char* buf, size_t len) {
+    if (buf && len) {
+        std::strncpy(buf, g_err.c_str(), len - 1);
+        buf[len - 1] = 0;
+    }
+    return AROL_OK;
+}
+
+arol_status arol_tiler_cover(const arol_array_desc* array, const arol_tiler* tiler, int rep_rank, const int64_t* rep,
+                             int64_t* count_min, int64_t* count_max) {
+    if (!array || !tiler || !rep || !count_min || !count_max) return fail(AROL_ERR_INVALID, "null argument");
+    if (rep_rank < 1 || rep_rank > AROL_MAX_RANK) return fail(AROL_ERR_INVALID, "rep_rank %d not in [1,4]", rep_rank);
+    for (int q = 0; q < rep_rank; ++q)
+        if (rep[q] < 0 || rep[q] > kMaxDim) return fail(AROL_ERR_INVALID, "rep[%d] out of range", q);
+    arol_status st = check_array(*array, "array");
+    if (st != AROL_OK) return st;
+    if ((st = check_tiler(*tiler, "tiler")) != AROL_OK) return st;
+    int64_t nreps = 1;
+    for (int q = 0; q < rep_rank; ++q) nreps *= rep[q];
+    if (elems_of(*array) == 0) {
+        if (nreps > 0) return fail(AROL_ERR_INVALID, "tiler addresses an empty array");
+        *count_min = *count_max = 0;
+        return AROL_OK;
+    }
+    return partition_count(*array, *tiler, rep_rank, rep, count_min, count_max);
+}
+
+arol_status arol_task_create(const arol_task_desc* desc, arol_task* out) {
+    if (!desc || !out) return fail(AROL_ERR_INVALID, "null argument");
+    *out = nullptr;
+    arol_status st = validate_desc(*desc);
+    if (st != AROL_OK) return st;
+    arol_task t = new (std::nothrow) arol_task_s();
+    if (!t) return fail(AROL_ERR_INVALID, "out of host memory");
+    t->descs.push_back(*desc);
+    t->descs[0].fir_taps_host = nullptr;
+    t->tap_off.push_back(0);
+    if (desc->elem == AROL_ELEM_FIR) {
+        t->taps_host.assign((size_t)desc->fir_m * desc->fir_T, 0.f);
+        if (desc->fir_taps_host) std::memcpy(t->taps_host.data(), desc->fir_taps_host, t->taps_host.size() * sizeof(float));
+        else t->taps_ready = false;
+    }
+    int M, N, K;
+    if (desc->elem == AROL_ELEM_MATMUL && is_matmul_panels(*desc, &M, &N, &K)) {
+        t->kernel = 2;
+        t->mm_M = M;
+        t->mm_N = N;
+        t->mm_K = K;
+    }
+    fill_info_single(t);
+    *out = t;
+    return AROL_OK;
+}
+
+arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
+    if (!tasks || !out || n < 2) return fail(AROL_ERR_INVALID, "a chain needs at least 2 tasks");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!tasks[i]) return fail(AROL_ERR_INVALID, "null task %d", i);
+        if (tasks[i]->kind != 0) return fail(AROL_ERR_INVALID, "task %d is itself a chain", i);
+        const arol_task_desc& d = tasks[i]->descs[0];
+        if (d.elem == AROL_ELEM_MATMUL) return fail(AROL_ERR_UNSUPPORTED, "matmul tasks cannot be chained");
+        if (i > 0) {
+            const arol_array_desc &a = tasks[i - 1]->descs[0].out[0], &b = d.in[0];
+            bool same = a.rank == b.rank && a.dtype == b.dtype;
+            for (int k = 0; same && k < a.rank; ++k) same = a.shape[k] == b.shape[k];
+            if (!same) return fail(AROL_ERR_INVALID, "output of task %d is not the input array of task %d", i - 1, i);
+        }
+    }
+    arol_task t = new (std::nothrow) arol_task_s();
+    if (!t) return fail(AROL_ERR_INVALID, "out of host memory");
+    t->kind = 1;
+    for (int i = 0; i < n; ++i) {
+        t->descs.push_back(tasks[i]->descs[0]);
+        t->tap_off.push_back((int64_t)t->taps_host.size());
+        t->taps_host.insert(t->taps_host.end(), tasks[i]->taps_host.begin(), tasks[i]->taps_host.end());
+        t->taps_ready = t->taps_ready && tasks[i]->taps_ready && !tasks[i]->taps_borrowed;
+    }
+    // Fused separable downscaler: horizontal 8->3 then vertical 8->3, step 8.
+    Pass h, v;
+    t->kernel = 3;
+    if (n == 2 && match_pass(t->descs[0], 2, &h) && match_pass(t->descs[1], 1, &v) && h.S == 8 && h.T == 8 &&
+        h.m == 3 && v.S == 8 && v.T == 8 && v.m == 3 && v.F == h.F && v.H == h.H && v.W == h.W / 8 * 3 &&
+        h.W % 8 == 0 && h.H % 8 == 0 && (double)h.F * (h.H / 8) * (h.W / 4) < 2147483647.0) {
+        t->kernel = 1;
+        t->ds_frames = h.F;
+        t->ds_H = (int)h.H;
+        t->ds_W = (int)h.W;
+    }
+    arol_task_info_t& in = t->info;
+    in.kind = 1;
+    in.kernel = t->kernel;
+    for (int i = 0; i < n; ++i) {
+        const arol_task_info_t& s = tasks[i]->info;
+        in.reps += s.reps;
+        in.gathered_elems += s.gathered_elems;
+        in.scattered_elems += s.scattered_elems;
+        in.flops += s.flops;
+    }
+    const arol_task_desc &first = t->descs.front(), &last = t->descs.back();
+    in.unique_bytes = elems_of(first.in[0]) * esize_of(first.in[0].dtype) + elems_of(last.out[0]) * esize_of(last.out[0].dtype);
+    t->mids.assign(n - 1, nullptr);
+    *out = t;
+    return AROL_OK;
+}
+
+arol_status arol_task_set_taps(arol_task t, const float* taps, int on_device) {
+    if (!t || !taps) return fail(AROL_ERR_INVALID, "null argument");
+    if (t->taps_host.empty()) return fail(AROL_ERR_INVALID, "task has no fir taps");
+    if (on_device) {
+        t->taps_borrowed = taps;
+    } else {
+        std::memcpy(t->taps_host.data(), taps, t->taps_host.size() * sizeof(float));
+        t->taps_borrowed = nullptr;
+        t->taps_ready = true;
+        t->taps_dirty = true;
+    }
+    return AROL_OK;
+}
+
+arol_status arol_task_info(arol_task t, arol_task_info_t* info) {
+    if (!t || !info) return fail(AROL_ERR_INVALID, "null argument");
+    *info = t->info;
+    return AROL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+arol_status run_generic(const arol_task_desc& d, const float* taps, const void* x, void* y, cudaStream_t s) {
+    TaskDev td = make_taskdev(d);
+    td.taps = taps;
+    td.x = x;
+    td.y = y;
+    AROL_CUDA(launch_tiler_generic(td, td.elem == ELEM_FIR ? td.m : 1, s), "tiler kernel launch");
+    return AROL_OK;
+}
+
+DownscaleDev ds_params(arol_task t, const float* taps) {
+    DownscaleDev p;
+    std::memset(&p, 0, sizeof p);
+    p.taps = taps;
+    p.frames = t->ds_frames;
+    p.H = t->ds_H;
+    p.W = t->ds_W;
+    return p;
+}
+
+size_t array_bytes(const arol_array_desc& a) { return (size_t)elems_of(a) * esize_of(a.dtype); }
+
+// The fused downscaler moves X and dX with 128-bit accesses: both must be
+// 16-byte aligned (a null pointer counts as aligned).
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, void* stream) {
+    if (!t || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const arol_task_desc& d0 = t->descs[0];
+    for (int i = 0; i < d0.n_in; ++i)
+        if (!in[i] && elems_of(d0.in[i]) > 0) return fail(AROL_ERR_INVALID, "null input pointer %d", i);
+    if (!out[0] && elems_of(t->descs.back().out[0]) > 0) return fail(AROL_ERR_INVALID, "null output pointer");
+    if (t->kind == 0 && reps_of(d0) == 0) return AROL_OK;
+    arol_status st = remember_device(t);
+    if (st != AROL_OK) return st;
+    const float* taps = nullptr;
+    if ((st = ensure_taps(t, s, &taps)) != AROL_OK) return st;
+    if (t->kind == 0) {
+        if (reps_of(d0) == 0) return AROL_OK;
+        if (t->kernel == 2) {
+            if ((st = dev_alloc(t, (void**)&t->mm_err, sizeof(unsigned), "cudaMalloc(matmul flag)")) != AROL_OK) return st;
+            AROL_CUDA(launch_matmul_tc(in[0], in[1], (float*)out[0], t->mm_M, t->mm_N, t->mm_K, t->mm_err, s),
+                      "matmul kernel launch");
+            return AROL_OK;
+        }
+        return run_generic(d0, taps, in[0], out[0], s);
+    }
+    if (t->kernel == 1 && aligned16(in[0])) {
+        DownscaleDev p = ds_params(t, taps);
+        p.x = (const float*)in[0];
+        p.y = (float*)out[0];
+        AROL_CUDA(launch_downscale_fwd(p, s), "downscale kernel launch");
+        return AROL_OK;
+    }
+    // Unfused chain through intermediates owned by the chain.
+    const size_t n = t->descs.size();
+    const void* cur = in[0];
+    for (size_t i = 0; i < n; ++i) {
+        void* dst = out[0];
+        if (i + 1 < n) {
+            if ((st = dev_alloc(t, &t->mids[i], array_bytes(t->descs[i].out[0]), "cudaMalloc(chain intermediate)")) != AROL_OK)
+                return st;
+            dst = t->mids[i];
+        }
+        if (reps_of(t->descs[i]) > 0) {
+            const float* tp = taps ? taps + t->tap_off[i] : nullptr;
+            if ((st = run_generic(t->descs[i], tp, cur, dst, s)) != AROL_OK) return st;
+        }
+        cur = dst;
+    }
+    return AROL_OK;
+}
+
+arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* const* host_out, void* stream) {
+    if (!t || !host_in || !host_out) return fail(AROL_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const arol_task_desc& d0 = t->descs[0];
+    const arol_array_desc& od = t->descs.back().out[0];
+    arol_status st;
+    void* dins[2] = {nullptr, nullptr};
+    for (int i = 0; i < d0.n_in; ++i) {
+        if (!host_in[i]) return fail(AROL_ERR_INVALID, "null input pointer %d", i);
+        if ((st = dev_alloc(t, &t->stage_in[i], array_bytes(d0.in[i]), "cudaMalloc(staging)")) != AROL_OK) return st;
+        AROL_CUDA(cudaMemcpyAsync(t->stage_in[i], host_in[i], array_bytes(d0.in[i]), cudaMemcpyHostToDevice, s),
+                  "copy input to device");
+        dins[i] = t->stage_in[i];
+    }
+    if (!host_out[0]) return fail(AROL_ERR_INVALID, "null output pointer");
+    if ((st = dev_alloc(t, &t->stage_out, array_bytes(od), "cudaMalloc(staging)")) != AROL_OK) return st;
+    void* douts[1] = {t->stage_out};
+    if ((st = arol_task_run(t, dins, douts, stream)) != AROL_OK) return st;
+    AROL_CUDA(cudaMemcpyAsync(host_out[0], t->stage_out, array_bytes(od), cudaMemcpyDeviceToHost, s),
+              "copy output to host");
+    AROL_CUDA(cudaStreamSynchronize(s), "synchronize");
+    return AROL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+arol_status ensure_partials(arol_task t, int64_t n) {
+    if (t->partials && t->partials_cap >= n) return AROL_OK;
+    free_dev(t->partials);
+    t->partials = nullptr;
+    arol_status st = dev_alloc(t, (void**)&t->partials, (size_t)n * sizeof(float), "cudaMalloc(tap-gradient partials)");
+    if (st == AROL_OK) t->partials_cap = n;
+    return st;
+}
+
+// Owner-computes inverse of an input tiler: for every input element e, the
+// list of flat (r * T + k) indices whose gather visits e, in increasing order.
+arol_status ensure_inverse(arol_task t, size_t i) {
+    if (t->inv_start.size() <= i) {
+        t->inv_start.resize(t->descs.size(), nullptr);
+        t->inv_list.resize(t->descs.size(), nullptr);
+    }
+    if (t->inv_start[i]) return AROL_OK;
+    const arol_task_desc& d = t->descs[i];
+    const TaskDev td = make_taskdev(d);
+    const int64_t n = elems_of(d.in[0]);
+    const int64_t total = td.nreps * td.T;
+    if (total >= 2147483647LL) return fail(AROL_ERR_UNSUPPORTED, "backward: more than 2^31 gathered elements");
+    std::vector<int64_t> offs((size_t)total);
+    // host walk of the input tiler (same definition as the device walk)
+    {
+        const PortDev& p = td.in;
+        uint32_t r[4] = {0, 0, 0, 0};
+        for (int64_t lr = 0; lr < td.nreps; ++lr) {
+            int64_t l = lr;
+            for (int q = 3; q >= 0; --q) { r[q] = (uint32_t)(l % td.rep[q]); l /= td.rep[q]; }
+            int64_t row[4], cur[4];
+            for (int k = 0; k < 4; ++k) {
+                __int128 v = p.origin[k];
+                for (int q = 0; q < 4; ++q) v += (__int128)p.paving[k][q] * r[q];
+                row[k] = (int64_t)(v % p.shape[k]);
+            }
+            int64_t kk = 0;
+            for (int i0 = 0; i0 < p.pattern[0]; ++i0) {
+                for (int k = 0; k < 4; ++k) cur[k] = row[k];
+                for (int i1 = 0; i1 < p.pattern[1]; ++i1) {
+                    offs[(size_t)(lr * td.T + kk++)] = cur[0] * p.stride[0] + cur[1] * p.stride[1] + cur[2] * p.stride[2] + cur[3] * p.stride[3];
+                    for (int k = 0; k < 4; ++k) { cur[k] += p.fitting[k][1]; if (cur[k] >= p.shape[k]) cur[k] -= p.shape[k]; }
+                }
+                for (int k = 0; k < 4; ++k) { row[k] += p.fitting[k][0]; if (row[k] >= p.shape[k]) row[k] -= p.shape[k]; }
+            }
+        }
+    }
+    std::vector<int64_t> start((size_t)n + 1, 0);
+    for (int64_t o : offs) ++start[(size_t)o + 1];
+    for (int64_t e = 0; e < n; ++e) start[(size_t)e + 1] += start[(size_t)e];
+    std::vector<int32_t> list((size_t)std::max<int64_t>(total, 1));
+    std::vector<int64_t> fillp(start.begin(), start.end() - 1);
+    for (int64_t idx = 0; idx < total; ++idx) list[(size_t)fillp[(size_t)offs[(size_t)idx]]++] = (int32_t)idx;
+    arol_status st;
+    if ((st = dev_alloc(t, (void**)&t->inv_start[i], start.size() * sizeof(int64_t), "cudaMalloc(inverse map)")) != AROL_OK) return st;
+    if ((st = dev_alloc(t, (void**)&t->inv_list[i], list.size() * sizeof(int32_t), "cudaMalloc(inverse map)")) != AROL_OK) return st;
+    AROL_CUDA(cudaMemcpy(t->inv_start[i], start.data(), start.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "upload inverse map");
+    AROL_CUDA(cudaMemcpy(t->inv_list[i], list.data(), list.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "upload inverse map");
+    return AROL_OK;
+}
+
+arol_status backward_generic_task(arol_task t, size_t i, const float* taps, const void* x, const float* gy, float* gx,
+                                  float* gtaps, cudaStream_t s) {
+    const arol_task_desc& d = t->descs[i];
+    if (d.elem == AROL_ELEM_COPY && d.in[0].dtype != AROL_F32)
+        return fail(AROL_ERR_UNSUPPORTED, "backward: copy tasks on float32 only");
+    arol_status st;
+    if (gx && (st = ensure_inverse(t, i)) != AROL_OK) return st;
+    TaskDev td = make_taskdev(d);
+    td.taps = taps;
+    td.x = x;
+    int64_t chunk = 0;
+    const int nb = tiler_bwd_blocks(td.nreps, &chunk);
+    if (gtaps && d.elem == AROL_ELEM_FIR && (st = ensure_partials(t, (int64_t)nb * td.m * td.T)) != AROL_OK) return st;
+    AROL_CUDA(launch_tiler_bwd(td, gx ? t->inv_start[i] : nullptr, gx ? t->inv_list[i] : nullptr, gx, gy,
+                               d.elem == AROL_ELEM_FIR ? gtaps : nullptr, t->partials, nb, chunk, s),
+              "tiler backward launch");
+    return AROL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+arol_status arol_task_backward(arol_task t, const void* grad_out, const void* const* saved_in, void* grad_in,
+                               float* grad_taps, void* stream) {
+    if (!t || !grad_out || !saved_in || !saved_in[0]) return fail(AROL_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (const arol_task_desc& d : t->descs)
+        if (d.elem == AROL_ELEM_MATMUL) return fail(AROL_ERR_UNSUPPORTED, "backward of matmul tasks is not implemented");
+    arol_status st = remember_device(t);
+    if (st != AROL_OK) return st;
+    const float* taps = nullptr;
+    if ((st = ensure_taps(t, s, &taps)) != AROL_OK) return st;
+    if (t->kind == 1 && t->kernel == 1 && aligned16(saved_in[0]) && aligned16(grad_in)) {
+        const int nparts = downscale_bwd_partials(device_sm_count());
+        if ((st = ensure_partials(t, (int64_t)nparts * 48)) != AROL_OK) return st;
+        DownscaleDev p = ds_params(t, taps);
+        p.x = (const float*)saved_in[0];
+        p.gy = (const float*)grad_out;
+        p.gx = (float*)grad_in;
+        p.partials = t->partials;
+        AROL_CUDA(launch_downscale_bwd(p, grad_taps, nparts, false, s), "downscale backward launch");
+        return AROL_OK;
+    }
+    if (t->kind == 0) {
+        return backward_generic_task(t, 0, taps, saved_in[0], (const float*)grad_out, (float*)grad_in, grad_taps, s);
+    }
+    // Unfused chain: recompute the intermediates, then reverse task by task.
+    const size_t n = t->descs.size();
+    const void* cur = saved_in[0];
+    for (size_t i = 0; i + 1 < n; ++i) {
+        if ((st = dev_alloc(t, &t->mids[i], array_bytes(t->descs[i].out[0]), "cudaMalloc(chain intermediate)")) != AROL_OK)
+            return st;
+        if (reps_of(t->descs[i]) > 0 && (st = run_generic(t->descs[i], taps ? taps + t->tap_off[i] : nullptr, cur, t->mids[i], s)) != AROL_OK)
+            return st;
+        cur = t->mids[i];
+    }
+    if (t->grad_mids.size() < n) t->grad_mids.resize(n, nullptr);
+    const float* g = (const float*)grad_out;
+    for (size_t ii = n; ii-- > 0;) {
+        const void* xin = ii == 0 ? saved_in[0] : t->mids[ii - 1];
+        float* gx = nullptr;
+        if (ii == 0) gx = (float*)grad_in;
+        else {
+            if ((st = dev_alloc(t, (void**)&t->grad_mids[ii], array_bytes(t->descs[ii].in[0]), "cudaMalloc(chain gradient)")) != AROL_OK)
+                return st;
+            gx = t->grad_mids[ii];
+        }
+        const float* tp = taps ? taps + t->tap_off[ii] : nullptr;
+        float* gt = grad_taps ? grad_taps + t->tap_off[ii] : nullptr;
+        if (reps_of(t->descs[ii]) == 0) {
+            if (gx) AROL_CUDA(cudaMemsetAsync(gx, 0, array_bytes(t->descs[ii].in[0]), s), "zero gradient");
+            if (gt) AROL_CUDA(cudaMemsetAsync(gt, 0, sizeof(float) * t->descs[ii].fir_m * t->descs[ii].fir_T, s), "zero gradient");
+        } else if ((st = backward_generic_task(t, ii, tp, xin, g, gx, gt, s)) != AROL_OK) {
+            return st;
+        }
+        g = gx;
+    }
+    return AROL_OK;
+}
+
+arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* grad_out, void* out, void* grad_in,
+                              float* grad_taps, void* stream) {
+    if (!t || !in || !in[0] || !grad_out || !out) return fail(AROL_ERR_INVALID, "null argument");
+    if (!(t->kind == 1 && t->kernel == 1))
+        return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd is implemented for the fused separable downscaler chain only");
+    if (!aligned16(in[0]) || !aligned16(grad_in))
+        return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd needs 16-byte aligned input and input-gradient buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float* taps = nullptr;
+    arol_status st = remember_device(t);
+    if (st != AROL_OK) return st;
+    if ((st = ensure_taps(t, s, &taps)) != AROL_OK) return st;
+    const int nparts = downscale_bwd_partials(device_sm_count());
+    if ((st = ensure_partials(t, (int64_t)nparts * 48)) != AROL_OK) return st;
+    DownscaleDev p = ds_params(t, taps);
+    p.x = (const float*)in[0];
+    p.y = (float*)out;
+    p.gy = (const float*)grad_out;
+    p.gx = (float*)grad_in;
+    p.partials = t->partials;
+    AROL_CUDA(launch_downscale_bwd(p, grad_taps, nparts, true, s), "downscale fwd_bwd launch");
+    return AROL_OK;
+}
+
+arol_status arol_task_sync_status(arol_task t, void* stream) {
+    if (!t) return fail(AROL_ERR_INVALID, "null task");
+    AROL_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
+    if (t->mm_err) {
+        unsigned flag = 0;
+        AROL_CUDA(cudaMemcpy(&flag, t->mm_err, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
+        if (flag) return fail(AROL_ERR_TIMEOUT, "a bounded wait in the matmul kernel gave up (flags 0x%x)", flag);
+    }
+    return AROL_OK;
+}
+
+void arol_task_destroy(arol_task t) {
+    if (!t) return;
+    if (t->device >= 0) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != t->device) cudaSetDevice(t->device);
+        free_dev(t->taps_dev);
+        for (void* p : t->mids) free_dev(p);
+        free_dev(t->mm_err);
+        free_dev(t->partials);
+        for (auto* p : t->inv_start) free_dev(p);
+        for (auto* p : t->inv_list) free_dev(p);
+        for (auto* p : t->grad_mids) free_dev(p);
+        free_dev(t->stage_in[0]);
+        free_dev(t->stage_in[1]);
+        free_dev(t->stage_out);
+        if (cur != t->device) cudaSetDevice(cur);
+    }
+    delete t;
+}
+
+}  // extern "C"
+
+// ==================================================================== batches
+
+struct arol_batch_s {
+    std::vector<arol_task_desc> descs;
+    std::vector<std::vector<float>> taps;
+    std::vector<TaskDev> host_tasks;
+    std::vector<const void*> last_in;
+    std::vector<void*> last_out;
+    int device = -1;
+    int max_m = 1;
+    // device state
+    TaskDev* dev_tasks = nullptr;
+    TaskDev* pinned_tasks = nullptr;
+    cudaEvent_t table_copied = nullptr;
+    TileDev* dev_tiles = nullptr;
+    int64_t tiles_cap = 0;
+    int ntiles = 0;
+    unsigned* counter = nullptr;
+    float* taps_dev = nullptr;
+    bool tables_built = false;
+    // launch configuration
+    int64_t tile_reps = 2048;
+    int threads = 256;
+    int ctas_per_sm = 4;
+    // graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, std::vector<int64_t>> g_tune_cache;   // signature -> {tile, threads, ctas}
+bool g_tune_loaded = false;
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
+    const unsigned char* p = (const unsigned char*)data;
+    for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ULL; }
+    return h;
+}
+
+std::string batch_signature(arol_batch b) {
+    uint64_t h = 1469598103934665603ULL;
+    for (const TaskDev& t : b->host_tasks) {
+        TaskDev c = t;
+        c.x = nullptr; c.y = nullptr; c.taps = nullptr;
+        h = fnv1a(&c, sizeof c, h);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        h = fnv1a(prop.name, std::strlen(prop.name), h);
+        h = fnv1a(&prop.multiProcessorCount, sizeof prop.multiProcessorCount, h);
+    }
+    char buf[32];
+    std::snprintf(buf, sizeof buf, "%016" PRIx64, h);
+    return buf;
+}
+
+// The cache file is a flat JSON object: {"<signature>": [tile, threads, ctas], ...}
+void tune_cache_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("AROL_TUNE_CACHE");
+    if (!path) return;
+    std::ifstream f(path);
+    if (!f) return;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    std::string s = ss.str();
+    size_t pos = 0;
+    while ((pos = s.find('"', pos)) != std::string::npos) {
+        size_t end = s.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        std::string key = s.substr(pos + 1, end - pos - 1);
+        long long a = 0, b2 = 0, c = 0;
+        size_t lb = s.find('[', end);
+        if (lb == std::string::npos) break;
+        if (std::sscanf(s.c_str() + lb, "[%lld , %lld , %lld]", &a, &b2, &c) == 3 ||
+            std::sscanf(s.c_str() + lb, "[%lld, %lld, %lld]", &a, &b2, &c) == 3)
+            g_tune_cache[key] = {a, b2, c};
+        pos = s.find(']', lb);
+        if (pos == std::string::npos) break;
+    }
+}
+
+void tune_cache_save() {
+    const char* path = std::getenv("AROL_TUNE_CACHE");
+    if (!path) return;
+    std::string tmp = std::string(path) + ".tmp";
+    std::ofstream f(tmp);
+    if (!f) return;
+    f << "{";
+    bool first = true;
+    for (auto& kv : g_tune_cache) {
+        f << (first ? "\n" : ",\n") << "  \"" << kv.first << "\": [" << kv.second[0] << ", " << kv.second[1] << ", "
+          << kv.second[2] << "]";
+        first = false;
+    }
+    f << "\n}\n";
+    f.close();
+    std::rename(tmp.c_str(), path);
+}
+
+void invalidate_graph(arol_batch b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Tiles of at most tile_reps repetitions, most expensive tasks first (a
+// longest-processing-time order for the dynamic tile counter).
+arol_status build_tiles(arol_batch b) {
+    std::vector<int> order(b->host_tasks.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    auto cost = [&](int i) {
+        const TaskDev& t = b->host_tasks[i];
+        return (double)t.nreps * (t.T + t.m);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+    std::vector<TileDev> tiles;
+    for (int i : order) {
+        const TaskDev& t = b->host_tasks[i];
+        for (int64_t s = 0; s < t.nreps; s += b->tile_reps) {
+            TileDev td;
+            td.task = i;
+            td.start = s;
+            td.count = (int32_t)std::min<int64_t>(b->tile_reps, t.nreps - s);
+            tiles.push_back(td);
+        }
+    }
+    if ((int64_t)tiles.size() >= 2147483647LL) return fail(AROL_ERR_UNSUPPORTED, "batch: too many tiles");
+    b->ntiles = (int)tiles.size();
+    if ((int64_t)tiles.size() > b->tiles_cap) {
+        free_dev(b->dev_tiles);
+        b->dev_tiles = nullptr;
+        AROL_CUDA(cudaMalloc(&b->dev_tiles, std::max<size_t>(tiles.size(), 1) * sizeof(TileDev)), "cudaMalloc(tiles)");
+        b->tiles_cap = (int64_t)tiles.size();
+    }
+    if (!tiles.empty())
+        AROL_CUDA(cudaMemcpy(b->dev_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice),
+                  "upload tiles");
+    invalidate_graph(b);
+    return AROL_OK;
+}
+
+arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out, cudaStream_t s) {
+    const size_t n = b->descs.size();
+    int dev = 0;
+    AROL_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (b->device < 0) b->device = dev;
+    else if (b->device != dev) return fail(AROL_ERR_INVALID, "batch used on another device than its buffers");
+    for (size_t i = 0; i < n; ++i)
+        if ((!in[i] || !out[i]) && b->host_tasks[i].nreps > 0) return fail(AROL_ERR_INVALID, "null pointer for task %zu", i);
+    if (!b->tables_built) {
+        size_t ntaps = 0;
+        for (auto& v : b->taps) ntaps += v.size();
+        AROL_CUDA(cudaMalloc(&b->dev_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMalloc(task table)");
+        AROL_CUDA(cudaMallocHost(&b->pinned_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMallocHost(task table)");
+        AROL_CUDA(cudaEventCreateWithFlags(&b->table_copied, cudaEventDisableTiming), "cudaEventCreate");
+        AROL_CUDA(cudaMalloc(&b->counter, sizeof(unsigned)), "cudaMalloc(counter)");
+        AROL_CUDA(cudaMalloc(&b->taps_dev, std::max<size_t>(ntaps, 1) * sizeof(float)), "cudaMalloc(taps)");
+        size_t off = 0;
+        for (size_t i = 0; i < n; ++i) {
+            if (!b->taps[i].empty()) {
+                AROL_CUDA(cudaMemcpy(b->taps_dev + off, b->taps[i].data(), b->taps[i].size() * sizeof(float),
+                                     cudaMemcpyHostToDevice),
+                          "upload taps");
+                b->host_tasks[i].taps = b->taps_dev + off;
+                off += b->taps[i].size();
+            }
+        }
+        AROL_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        arol_status st = build_tiles(b);
+        if (st != AROL_OK) return st;
+        b->tables_built = true;
+        b->last_in.assign(n, (const void*)1);   // force the first table upload
+        b->last_out.assign(n, (void*)1);
+    }
+    bool changed = false;
+    for (size_t i = 0; i < n; ++i) changed = changed || in[i] != b->last_in[i] || out[i] != b->last_out[i];
+    if (changed) {
+        AROL_CUDA(cudaEventSynchronize(b->table_copied), "wait for previous table upload");
+        for (size_t i = 0; i < n; ++i) {
+            b->host_tasks[i].x = in[i];
+            b->host_tasks[i].y = out[i];
+            b->last_in[i] = in[i];
+            b->last_out[i] = out[i];
+        }
+        std::memcpy(b->pinned_tasks, b->host_tasks.data(), n * sizeof(TaskDev));
+        AROL_CUDA(cudaMemcpyAsync(b->dev_tasks, b->pinned_tasks, n * sizeof(TaskDev), cudaMemcpyHostToDevice, s),
+                  "upload task table");
+        AROL_CUDA(cudaEventRecord(b->table_copied, s), "cudaEventRecord");
+    }
+    return AROL_OK;
+}
+
+arol_status batch_capture(arol_batch b) {
+    if (b->exec) return AROL_OK;
+    const int grid = device_sm_count() * b->ctas_per_sm;
+    AROL_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t le = launch_batch_persistent(b->dev_tasks, b->dev_tiles, b->ntiles, b->counter, grid, b->threads,
+                                             b->max_m, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(le, "batch kernel capture");
+    }
+    AROL_CUDA(ee, "end capture");
+    b->graph = g;
+    AROL_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+    return AROL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out) {
+    if (!tasks || !out || n < 1) return fail(AROL_ERR_INVALID, "a batch needs at least one task");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!tasks[i]) return fail(AROL_ERR_INVALID, "null task %d", i);
+        if (tasks[i]->kind != 0) return fail(AROL_ERR_UNSUPPORTED, "batch: task %d is a chain", i);
+        const arol_task_desc& d = tasks[i]->descs[0];
+        if (d.elem == AROL_ELEM_MATMUL) return fail(AROL_ERR_UNSUPPORTED, "batch: task %d is a matmul", i);
+        if (tasks[i]->taps_borrowed || !tasks[i]->taps_ready) return fail(AROL_ERR_INVALID, "batch: task %d has no host taps", i);
+    }
+    arol_batch b = new (std::nothrow) arol_batch_s();
+    if (!b) return fail(AROL_ERR_INVALID, "out of host memory");
+    for (int i = 0; i < n; ++i) {
+        const arol_task_desc& d = tasks[i]->descs[0];
+        b->descs.push_back(d);
+        b->taps.push_back(tasks[i]->taps_host);
+        b->host_tasks.push_back(make_taskdev(d));
+        if (d.elem == AROL_ELEM_FIR) b->max_m = std::max(b->max_m, d.fir_m);
+    }
+    *out = b;
+    return AROL_OK;
+}
+
+arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out, void* stream) {
+    if (!b || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    arol_status st = batch_prepare(b, in, out, s);
+    if (st != AROL_OK) return st;
+    if ((st = batch_capture(b)) != AROL_OK) return st;
+    AROL_CUDA(cudaGraphLaunch(b->exec, s), "graph launch");
+    return AROL_OK;
+}
+
+arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* const* out, void* stream) {
+    if (!b || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    arol_status st = batch_prepare(b, in, out, s);
+    if (st != AROL_OK) return st;
+    for (size_t i = 0; i < b->host_tasks.size(); ++i) {
+        const TaskDev& t = b->host_tasks[i];
+        if (t.nreps == 0) continue;
+        AROL_CUDA(launch_tiler_generic(t, t.elem == ELEM_FIR ? t.m : 1, s), "tiler kernel launch");
+    }
+    return AROL_OK;
+}
+
+arol_status arol_batch_config(arol_batch b, int64_t* tile_reps, int32_t* ctas_per_sm, int32_t* threads) {
+    if (!b) return fail(AROL_ERR_INVALID, "null batch");
+    if (tile_reps) *tile_reps = b->tile_reps;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    if (threads) *threads = b->threads;
+    return AROL_OK;
+}
+
+arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* out, void* stream, int force) {
+    if (!b || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    arol_status st = batch_prepare(b, in, out, s);
+    if (st != AROL_OK) return st;
+    const std::string sig = batch_signature(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_load();
+        auto it = g_tune_cache.find(sig);
+        if (!force && it != g_tune_cache.end()) {
+            b->tile_reps = it->second[0];
+            b->threads = (int)it->second[1];
+            b->ctas_per_sm = (int)it->second[2];
+            return build_tiles(b);
+        }
+    }
+    cudaEvent_t e0, e1;
+    AROL_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    AROL_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    float best = 1e30f;
+    int64_t best_tile = b->tile_reps;
+    int best_thr = b->threads, best_ctas = b->ctas_per_sm;
+    const int64_t tiles[] = {512, 1024, 2048, 4096, 8192, 16384};
+    const int thrs[] = {128, 256, 512};
+    const int ctas[] = {2, 4, 8, 16};
+    st = AROL_OK;
+    for (int64_t tile : tiles) {
+        b->tile_reps = tile;
+        if ((st = build_tiles(b)) != AROL_OK) break;
+        for (int thr : thrs)
+            for (int c : ctas) {
+                if ((int64_t)thr * c > 2048) continue;
+                b->threads = thr;
+                b->ctas_per_sm = c;
+                invalidate_graph(b);
+                if ((st = batch_capture(b)) != AROL_OK) break;
+                cudaGraphLaunch(b->exec, s);   // warm-up
+                cudaEventRecord(e0, s);
+                for (int rep = 0; rep < 3; ++rep) cudaGraphLaunch(b->exec, s);
+                cudaEventRecord(e1, s);
+                cudaError_t ce = cudaEventSynchronize(e1);
+                if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune run"); break; }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; best_tile = tile; best_thr = thr; best_ctas = c; }
+            }
+        if (st != AROL_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != AROL_OK) return st;
+    b->tile_reps = best_tile;
+    b->threads = best_thr;
+    b->ctas_per_sm = best_ctas;
+    if ((st = build_tiles(b)) != AROL_OK) return st;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[sig] = {best_tile, best_thr, best_ctas};
+    tune_cache_save();
+    return AROL_OK;
+}
+
+void arol_batch_destroy(arol_batch b) {
+    if (!b) return;
+    if (b->device >= 0) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != b->device) cudaSetDevice(b->device);
+        invalidate_graph(b);
+        if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+        if (b->table_copied) cudaEventDestroy(b->table_copied);
+        if (b->pinned_tasks) cudaFreeHost(b->pinned_tasks);
+        free_dev(b->dev_tasks);
+        free_dev(b->dev_tiles);
+        free_dev(b->counter);
+        free_dev(b->taps_dev);
+        if (cur != b->device) cudaSetDevice(cur);
+    }
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Internal declarations shared by the host runtime (arol_host.cpp) and the
+// CUDA kernels (k_*.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace arol {
+
+// One array port bound to the repetition space, prepared on the host for the
+// generic tiler kernel.  Every entry of origin/paving/fitting is already
+// reduced into [0, shape_k) (Euclidean mod), so the device only ever adds
+// non-negative values and subtracts shape_k once on overflow.  Unused array
+// dimensions have shape 1 and zero coefficients; unused pattern dimensions
+// have extent 1.
+struct PortDev {
+    int32_t shape[4];
+    int64_t stride[4];      // row-major element strides; 0 for unused dims
+    uint32_t origin[4];
+    uint32_t paving[4][4];  // [array dim][repetition dim]
+    uint32_t fitting[4][2]; // [array dim][pattern dim]
+    int32_t pattern[2];
+};
+
+enum ElemCode : int32_t { ELEM_COPY = 0, ELEM_FIR = 1 };
+
+// A copy or fir task for the generic tiler kernel (and one entry of a batch).
+struct TaskDev {
+    int32_t rep[4];         // repetition space, last dimension fastest; unused = 1
+    int64_t nreps;
+    PortDev in, out;
+    int32_t T, m;           // fir: pattern size and outputs; copy: both = pattern size
+    int32_t elem;           // ElemCode
+    int32_t esize;          // copy: element size in bytes (2 or 4)
+    int32_t wide;           // 1 when base addresses need 64-bit arithmetic
+    int32_t pad_;
+    const float* taps;      // m x T (fir)
+    const void* x;
+    void* y;
+};
+
+// One unit of work of a batch: repetitions [start, start + count) of a task.
+struct TileDev {
+    int32_t task;
+    int32_t count;
+    int64_t start;
+};
+
+// Parameters of the fused separable downscaler chain (8-tap -> 3-output on
+// both axes, step 8, no wrap): x (frames, H, W) -> y (frames, 3H/8, 3W/8).
+struct DownscaleDev {
+    const float* x;
+    float* y;
+    const float* taps;      // 3x8 horizontal, then 3x8 vertical
+    const float* gy;        // backward: dL/dy
+    float* gx;              // backward: dL/dx
+    float* partials;        // backward: per-CTA tap-gradient partials (48 floats each)
+    int64_t frames;
+    int32_t H, W;
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s);
+cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, int ntiles,
+                                    unsigned* counter, int grid, int threads, int max_m,
+                                    cudaStream_t s);
+cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s);
+cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int nparts, bool with_fwd,
+                                 cudaStream_t s);
+int downscale_bwd_partials(int sm_count);   // number of per-CTA partial slots the backward uses
+
+// tcgen05 matmul: C (M x N, f32) = A (M x K, bf16 row-major) . B (K x N, bf16 row-major).
+cudaError_t launch_matmul_tc(const void* A, const void* B, float* C, int M, int N, int K,
+                             unsigned* err_flag, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace arol

@@ -1,0 +1,293 @@
+// Fused separable downscaler: two chained repetitive tasks (horizontal then
+// vertical 8-tap -> 3-output FIR bank, step 8, no wrap) sharing one array
+// (Sec. 5, associatedParts).  Each 8x8 input block maps to a 3x3 output block,
+// so the intermediate (the horizontal task's output) lives only in registers:
+// the chain reads X once and writes Y once.
+//
+// Thread mapping.  A work item is 8 rows x 4 columns (one float4 per row) of
+// one frame; the two items of an 8x8 block sit in adjacent lanes (even lane:
+// columns 0-3, odd lane: columns 4-7).  A warp therefore reads 32 contiguous
+// float4 per row: fully coalesced 128-bit loads.  Each lane applies the
+// horizontal taps to its 4 columns and the vertical taps to the partial sums;
+// the two partial 3x3 blocks are added with one shuffle per output.
+//
+// Backward (loss gradient g = dL/dY given):
+//   dmid[kv][jh] = sum_jv Hv[jv,kv] g[jv][jh]          (transposed vertical tiler)
+//   dX[kv][kh]   = sum_jh Hh[jh,kh] dmid[kv][jh]        (transposed horizontal tiler)
+//   dHv[jv,kv]  += sum_jh g[jv][jh] mid[kv][jh]
+//   dHh[jh,kh]  += sum_kv dmid[kv][jh] X[kv][kh]
+// With step == T every input element belongs to exactly one block, so dX is
+// written once per element (owner computes; no atomics).  Tap gradients are
+// reduced per warp (shuffles), per CTA (shared memory, fixed order) into a
+// per-CTA partial, then across CTAs in fixed order by a second kernel:
+// deterministic run to run.
+#include "arol_internal.h"
+
+namespace arol {
+namespace {
+
+constexpr int kThr = 256;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTapGrads = 48;   // 3x8 horizontal + 3x8 vertical
+
+__device__ __forceinline__ float4 ld_stream4(const float* p) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_stream4(float* p, float4 v) {
+    asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+struct Taps {
+    float hh[3][4];   // horizontal taps of this lane's 4 columns: Hh[jh][4*half + t]
+    float hv[3][8];   // vertical taps Hv[jv][kv]
+};
+
+__device__ __forceinline__ void load_taps(const float* taps, int half, Taps& tp) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) tp.hh[j][t] = __ldg(taps + j * 8 + 4 * half + t);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tp.hv[j][k] = __ldg(taps + 24 + j * 8 + k);
+    }
+}
+
+// Horizontal taps on this lane's 4 columns of one row (a partial sum of mid).
+__device__ __forceinline__ void horiz(const Taps& tp, const float4 v, float mh[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        mh[j] = fmaf(tp.hh[j][3], v.w, fmaf(tp.hh[j][2], v.z, fmaf(tp.hh[j][1], v.y, tp.hh[j][0] * v.x)));
+}
+
+struct Item {
+    bool valid;
+    int half;
+    uint32_t f, sy, c4;
+};
+
+__device__ __forceinline__ Item decode(uint32_t item, uint32_t items, uint32_t Q, uint32_t HB) {
+    Item it;
+    it.valid = item < items;
+    it.half = (int)(item & 1u);
+    const uint32_t s = it.valid ? item / Q : 0u;
+    it.c4 = it.valid ? item - s * Q : 0u;
+    it.f = s / HB;
+    it.sy = s - it.f * HB;
+    return it;
+}
+
+// Adds the two lanes' partial 3x3 blocks and stores the block: the even lane
+// writes output rows 0 and 1, the odd lane row 2.
+__device__ __forceinline__ void store_block(const DownscaleDev& p, const Item& it, float y[3][3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) y[j][i] += __shfl_xor_sync(kFull, y[j][i], 1);
+    if (!it.valid) return;
+    const int Wo = (p.W >> 3) * 3;
+    const int Ho = (p.H >> 3) * 3;
+    float* yp = p.y + ((int64_t)it.f * Ho + 3 * it.sy) * (int64_t)Wo + 3 * (it.c4 >> 1);
+    if (it.half == 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) yp[i] = y[0][i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) yp[Wo + i] = y[1][i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) yp[2 * Wo + i] = y[2][i];
+    }
+}
+
+__global__ void __launch_bounds__(kThr) downscale_fwd_kernel(const DownscaleDev p) {
+    const int lane = threadIdx.x & 31;
+    Taps tp;
+    load_taps(p.taps, threadIdx.x & 1, tp);
+    const uint32_t Q = (uint32_t)p.W >> 2, HB = (uint32_t)p.H >> 3;
+    const uint32_t items = (uint32_t)p.frames * HB * Q;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < items; base += stride) {
+        const Item it = decode(base + lane, items, Q, HB);
+        const float* xp = p.x + ((int64_t)it.f * p.H + 8 * it.sy) * (int64_t)p.W + 4 * it.c4;
+        float4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = it.valid ? ld_stream4(xp + (int64_t)k * p.W) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float y[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) y[j][i] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float mh[3];
+            horiz(tp, v[k], mh);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) y[j][i] = fmaf(tp.hv[j][k], mh[i], y[j][i]);
+        }
+        store_block(p, it, y);
+    }
+}
+
+template <bool kFwd>
+__global__ void __launch_bounds__(kThr) downscale_bwd_kernel(const DownscaleDev p) {
+    const int lane = threadIdx.x & 31;
+    const int half = threadIdx.x & 1;
+    Taps tp;
+    load_taps(p.taps, half, tp);
+    float dhh[3][4], dhv[3][8];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) dhh[j][t] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dhv[j][k] = 0.f;
+    }
+    const uint32_t Q = (uint32_t)p.W >> 2, HB = (uint32_t)p.H >> 3;
+    const uint32_t items = (uint32_t)p.frames * HB * Q;
+    const int Wo = (p.W >> 3) * 3, Ho = (p.H >> 3) * 3;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < items; base += stride) {
+        const Item it = decode(base + lane, items, Q, HB);
+        const int64_t xoff = ((int64_t)it.f * p.H + 8 * it.sy) * (int64_t)p.W + 4 * it.c4;
+        float4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            v[k] = it.valid ? ld_stream4(p.x + xoff + (int64_t)k * p.W) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float g[3][3];
+        const float* gp = p.gy + ((int64_t)it.f * Ho + 3 * it.sy) * (int64_t)Wo + 3 * (it.c4 >> 1);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) g[j][i] = it.valid ? __ldg(gp + (int64_t)j * Wo + i) : 0.f;
+        float y[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) y[j][i] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float mh[3];
+            horiz(tp, v[k], mh);
+            float dmid[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                dmid[i] = fmaf(tp.hv[2][k], g[2][i], fmaf(tp.hv[1][k], g[1][i], tp.hv[0][k] * g[0][i]));
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    dhv[j][k] = fmaf(g[j][i], mh[i], dhv[j][k]);
+                    if (kFwd) y[j][i] = fmaf(tp.hv[j][k], mh[i], y[j][i]);
+                }
+            }
+            float dx[4];
+            const float vv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                dx[t] = fmaf(tp.hh[2][t], dmid[2], fmaf(tp.hh[1][t], dmid[1], tp.hh[0][t] * dmid[0]));
+#pragma unroll
+                for (int i = 0; i < 3; ++i) dhh[i][t] = fmaf(dmid[i], vv[t], dhh[i][t]);
+            }
+            if (it.valid && p.gx) st_stream4(p.gx + xoff + (int64_t)k * p.W, make_float4(dx[0], dx[1], dx[2], dx[3]));
+        }
+        if (kFwd) store_block(p, it, y);
+    }
+    // Warp reduction: dHh over lanes of equal parity (same 4 columns), dHv over all lanes.
+#pragma unroll
+    for (int off = 2; off < 32; off <<= 1)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) dhh[j][t] += __shfl_xor_sync(kFull, dhh[j][t], off);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dhv[j][k] += __shfl_xor_sync(kFull, dhv[j][k], off);
+    __shared__ float s_red[kThr / 32][kTapGrads];
+    const int w = threadIdx.x >> 5;
+    if (lane < 2) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) s_red[w][j * 8 + 4 * lane + t] = dhh[j][t];
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s_red[w][24 + j * 8 + k] = dhv[j][k];
+    }
+    __syncthreads();
+    if (threadIdx.x < kTapGrads) {
+        float s = 0.f;
+        for (int ww = 0; ww < kThr / 32; ++ww) s += s_red[ww][threadIdx.x];
+        p.partials[(int64_t)blockIdx.x * kTapGrads + threadIdx.x] = s;
+    }
+}
+
+// Sums the per-CTA partials in a fixed order: 16 lanes per tap gradient, each
+// summing a strided subset, then a fixed shuffle tree over the 16 lanes.
+__global__ void __launch_bounds__(kTapGrads * 16) tapgrad_reduce_kernel(const float* __restrict__ partials,
+                                                                         int nparts, float* __restrict__ out) {
+    const int o = threadIdx.x >> 4, l = threadIdx.x & 15;
+    float s = 0.f;
+    for (int b = l; b < nparts; b += 16) s += partials[(int64_t)b * kTapGrads + o];
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off, 16);
+    if (l == 0) out[o] = s;
+}
+
+int fwd_grid(uint32_t items) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, downscale_fwd_kernel, kThr, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    const int64_t want = ((int64_t)items + kThr - 1) / kThr;
+    const int64_t cap = (int64_t)device_sm_count() * per_sm;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+}  // namespace
+
+int downscale_bwd_partials(int sm_count) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        int a = 0, b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, downscale_bwd_kernel<false>, kThr, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, downscale_bwd_kernel<true>, kThr, 0);
+        per_sm = a < b ? a : b;
+        if (per_sm <= 0) per_sm = 1;
+    }
+    return sm_count * per_sm;
+}
+
+cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s) {
+    const uint32_t items = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * ((uint32_t)p.W >> 2);
+    if (items == 0) return cudaSuccess;
+    downscale_fwd_kernel<<<fwd_grid(items), kThr, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int nparts, bool with_fwd,
+                                 cudaStream_t s) {
+    if (with_fwd) downscale_bwd_kernel<true><<<nparts, kThr, 0, s>>>(p);
+    else downscale_bwd_kernel<false><<<nparts, kThr, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (grad_taps) {
+        tapgrad_reduce_kernel<<<1, kTapGrads * 16, 0, s>>>(p.partials, nparts, grad_taps);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace arol

@@ -1,0 +1,308 @@
+// Matmul elementary task on the 5th-generation tensor cores.
+//
+// The repetitive task has repetition space (M/128, N/128): repetition r reads
+// the 128 x K row panel r0 of A and the K x 128 column panel r1 of B, and its
+// output tiler writes the 128 x 128 tile (r0, r1) of C (a partition of C).
+// One CTA computes BN/128 neighbouring repetitions (a 128 x BN tile):
+//
+//   * TMA (cp.async.bulk.tensor, 128-byte swizzle) streams 128 x 64 slices of
+//     A (K-major) and 64 x BN slices of B (N-major, as B is stored row-major)
+//     into a STAGES-deep shared-memory ring guarded by mbarriers;
+//   * one elected thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32,
+//     M = 128, N = BN, K = 16) with the accumulator in tensor memory; each
+//     stage is released by tcgen05.commit onto its "empty" barrier;
+//   * after the last k-block a final commit releases the epilogue: the four
+//     warps read their 32 TMEM lanes (rows) with tcgen05.ld and store f32 C.
+//
+// Every mbarrier wait is bounded (iteration count and wall time).  A wait that
+// gives up sets a bit in *err and the kernel drains what it issued, frees its
+// tensor memory and returns; the host reports AROL_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "arol_internal.h"
+
+namespace arol {
+namespace {
+
+constexpr int BM = 128, BK = 64, STAGES = 4;
+constexpr uint32_t kSpinIters = 1u << 22;
+constexpr uint64_t kSpinNanos = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < kSpinIters; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 255u) == 255u && global_ns() - t0 > kSpinNanos) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start, leading and stride byte
+// offsets (16-byte units), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;
+    d |= 2ull << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: f32 accumulator, bf16 A and B, A K-major,
+// B N-major, N = bn, M = 128.
+__host__ __device__ constexpr uint32_t instr_desc(int bn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (1u << 16) | ((uint32_t)(bn >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+struct Cfg {
+    static constexpr int kABytes = BM * BK * 2;
+    static constexpr int kBBytes = BK * BN * 2;
+    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kSmem = STAGES * kStageBytes + 1024 + 256;
+    static constexpr uint32_t kTmemCols = BN;   // power of two >= 32
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) matmul_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB, float* __restrict__ C,
+                                                           int M, int N, int K, unsigned* __restrict__ err) {
+    using G = Cfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * G::kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * G::kStageBytes);
+    // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    int* progress = reinterpret_cast<int*>(tmem_slot + 1);   // [0] k-blocks issued, [1] k-blocks consumed
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nkb = K / BK;
+    const uint32_t full0 = smem_addr(bars), empty0 = smem_addr(bars + STAGES), done = smem_addr(bars + 2 * STAGES);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        progress[0] = 0;
+        progress[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(G::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int kb = 0;
+        for (; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ((kb / STAGES) & 1) ^ 1)) {
+                atomicOr(err, 1u);
+                break;
+            }
+            const uint32_t fb = full0 + 8 * s;
+            mbar_expect_tx(fb, G::kStageBytes);
+            tma_load_2d(smem_addr(sA + s * G::kABytes), &tmA, kb * BK, m0, fb);
+#pragma unroll
+            for (int c = 0; c < BN / 64; ++c)
+                tma_load_2d(smem_addr(sB + s * G::kBBytes + c * (BK * 128)), &tmB, n0 + 64 * c, kb * BK, fb);
+        }
+        progress[0] = kb;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = instr_desc(BN);
+        int kb = 0;
+        for (; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1)) {
+                atomicOr(err, 2u);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_addr(sA + s * G::kABytes);
+            const uint32_t b0 = smem_addr(sB + s * G::kBBytes);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                // A: K-major rows of 128 B, 8-row groups 1024 B apart; +32 B per 16 k.
+                const uint64_t ad = smem_desc(a0 + kk * 32, 16, 1024);
+                // B: N-major, 64-column chunks 8 KB apart (LBO), 8-row k groups 1024 B apart
+                // (SBO); +16 rows of 128 B per 16 k.
+                const uint64_t bd = smem_desc(b0 + kk * 16 * 128, BK * 128, 1024);
+                mma_bf16(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(empty0 + 8 * s);
+        }
+        progress[1] = kb;
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.
+    const bool ready = mbar_wait(done, 0);
+    if (!ready && lane == 0) atomicOr(err, 4u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ready) {
+        const int row = m0 + warp * 32 + lane;
+        float* crow = C + (int64_t)row * N + n0;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<float4*>(crow + c + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // On an error path, let every copy that was issued but not consumed land
+    // before the CTA's shared memory goes away.
+    if (threadIdx.x == 0) {
+        for (int kb = progress[1]; kb < progress[0]; ++kb) mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::kTmemCols) : "memory");
+    }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// 2-D bf16 row-major (rows x cols) tensor map with a (box_rows x 64) box and
+// 128-byte swizzle.
+bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {64, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int M, int N, int K, unsigned* err,
+                      cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(matmul_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(N / BN, M / BM);
+    matmul_tc_kernel<BN><<<grid, 128, Cfg<BN>::kSmem, s>>>(ma, mb, C, M, N, K, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_matmul_tc(const void* A, const void* B, float* C, int M, int N, int K, unsigned* err_flag,
+                             cudaStream_t s) {
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) return cudaErrorMisalignedAddress;
+    if ((reinterpret_cast<uintptr_t>(C) & 15u) != 0) return cudaErrorMisalignedAddress;
+    if (M % BM || N % 128 || K % BK || K < BK) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, (uint64_t)M, (uint64_t)K, BM)) return cudaErrorInvalidValue;
+    if (!make_map(&mb, B, (uint64_t)K, (uint64_t)N, BK)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(err_flag, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if (N % 256 == 0) return launch_bn<256>(ma, mb, C, M, N, K, err_flag, s);
+    return launch_bn<128>(ma, mb, C, M, N, K, err_flag, s);
+}
+
+}  // namespace arol

@@ -1,0 +1,145 @@
+"""The C-ABI library on the host (no GPU): it loads, exports every symbol the
+header declares, agrees on struct layout, and its host-only logic (descriptor
+validation, partition check, work accounting) matches the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import tiler as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__._build_module().build()
+    from paper_1105_4424_gb300 import binding
+    return binding
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(arol_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(B):
+    names = declared_symbols()
+    assert "arol_task_create" in names and "arol_batch_run" in names and len(names) >= 20
+    lib = ctypes.CDLL(B.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layout_matches(B):
+    for i, cls in enumerate((B.ArrayDesc, B.Tiler, B.TaskDesc, B.TaskInfo)):
+        assert B.lib.arol_abi_struct_size(i) == ctypes.sizeof(cls)
+    assert B.arol_version() == 100
+
+
+def _err(B, spec):
+    with pytest.raises(B.ArolError) as e:
+        B.arol_task_create(spec)
+    return e.value.status
+
+
+def test_validation_errors(B):
+    tk, _ = W.config0()
+    assert _err(B, W.task(tk["rep"], "fir", tk["inputs"], tk["outputs"], np.zeros((2, 8), np.float32))) == 1
+    bad = W.port((4, 6), (0, 0), ((1, 0), (0, 2)), ((0,), (1,)), (3,))
+    assert _err(B, W.task((4, 3), "copy", [bad], [bad])) == 2            # overlapping output tiler
+    short = W.port((64, 47), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))
+    assert _err(B, W.task(tk["rep"], "fir", tk["inputs"], [short], tk["taps"])) == 2
+    mism = dict(tk["inputs"][0], dtype="bf16")
+    assert _err(B, W.task(tk["rep"], "copy", [mism], [tk["outputs"][0]])) == 1   # dtype differs
+    big = W.task(tk["rep"], "fir", tk["inputs"], tk["outputs"], np.zeros((3, 8), np.float32))
+    d, keep = B.task_desc(big)
+    d.rep_rank = 5
+    with pytest.raises(B.ArolError):
+        B.arol_task_create(d)
+    mm = W.matmul_task(256, 256, 96)                                     # K not a multiple of 64
+    assert _err(B, mm) == 3
+    mm = W.matmul_task(256, 256, 128, 64, 128)                           # tiles other than 128 x 128
+    assert _err(B, mm) == 3
+    assert _err(B, W.task((0,), "copy", [W.port((4,), (0,), ((1,),), ((1,),), (1,))],
+                          [W.port((4,), (0,), ((1,),), ((1,),), (1,))])) == 2   # empty rep, non-empty output
+
+
+def test_empty_task_is_accepted(B):
+    p_in = W.port((4,), (0,), ((1,),), ((1,),), (1,))
+    p_out = W.port((0,), (0,), ((1,),), ((1,),), (1,))
+    h = B.arol_task_create(W.task((0,), "copy", [p_in], [p_out]))
+    info = B.arol_task_info(h)
+    assert info["reps"] == 0 and info["scattered_elems"] == 0
+    B.arol_task_destroy(h)
+
+
+def test_partition_check_matches_oracle(B):
+    g = W.rng(21)
+    for _ in range(200):
+        tk = W.random_tiler_task(g, "copy")
+        R = tk["rep"]
+        for port in (tk["inputs"][0], tk["outputs"][0]):
+            counts = O.cover_count(port, R)
+            lo, hi = B.arol_tiler_cover(port["shape"], port, R)
+            assert (lo, hi) == (int(counts.min()), int(counts.max()))
+            spec = W.task(R, "copy", [tk["inputs"][0]], [port])
+            if port is tk["outputs"][0] or (lo == hi == 1):
+                B.arol_task_destroy(B.arol_task_create(spec))
+            else:
+                with pytest.raises(B.ArolError) as e:
+                    B.arol_task_create(spec)
+                assert e.value.status == 2
+
+
+def test_info_counts_the_downscaler_chain(B):
+    Hh = np.ones((3, 8), np.float32)
+    chain = W.downscale_chain(64, 1080, 1920, Hh, Hh)
+    subs = [B.arol_task_create(s) for s in chain]
+    h = B.arol_chain_create(subs)
+    info = B.arol_task_info(h)
+    assert info["kernel"] == 1                       # fused separable downscaler
+    assert info["unique_bytes"] == 4 * (64 * 1080 * 1920 + 64 * 405 * 720)
+    assert info["gathered_elems"] == 64 * 1080 * 240 * 8 + 64 * 135 * 720 * 8
+    assert info["scattered_elems"] == 64 * 1080 * 720 + 64 * 405 * 720
+    for x in subs + [h]:
+        B.arol_task_destroy(x)
+    # a chain that is not a block downscaler (overlapping step 4) runs unfused
+    tk, _ = W.config0()
+    nxt = W.task((64, 16), "fir", [W.port((64, 48), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))],
+                 [W.port((64, 16), (0, 0), ((1, 0), (0, 1)), ((0,), (1,)), (1,))], np.ones((1, 3), np.float32))
+    subs = [B.arol_task_create(tk), B.arol_task_create(nxt)]
+    h = B.arol_chain_create(subs)
+    assert B.arol_task_info(h)["kernel"] == 3
+    for x in subs + [h]:
+        B.arol_task_destroy(x)
+
+
+def test_chain_rejects_mismatched_arrays(B):
+    tk, _ = W.config0()
+    subs = [B.arol_task_create(tk), B.arol_task_create(tk)]
+    with pytest.raises(B.ArolError) as e:
+        B.arol_chain_create(subs)
+    assert e.value.status == 1
+    for x in subs:
+        B.arol_task_destroy(x)
+
+
+def test_null_arguments_are_rejected(B):
+    with pytest.raises(B.ArolError):
+        B.arol_task_run(None, [0], [0], 0)
+    tk, _ = W.config0()
+    h = B.arol_task_create(tk)
+    with pytest.raises(B.ArolError) as e:
+        B.arol_task_run(h, [None], [None], 0)
+    assert e.value.status == 1
+    B.arol_task_destroy(h)

@@ -1,0 +1,156 @@
+"""Parity of the hand-written adjoint (through the C ABI) with the oracle
+gradient and with FP64 finite differences.
+
+Tolerance: every gradient element within 1e-5 of the sum of absolute terms
+behind it (the FP64 oracle gradient on |H|, |X|, |G|).  The longest FP32
+accumulation chain in a tap gradient is a per-thread sum of a few hundred
+products followed by a log-depth tree, so its error stays below
+~300 * 2^-24 < 2e-5 of that sum in the worst case and far below in practice.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import cpu_ref as C
+from oracle import tiler as O
+from tests.gpu_helpers import assert_fir_close, dev, host
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+def _abs_chain(tasks):
+    return [dict(t, taps=np.abs(np.asarray(t["taps"], np.float64))) for t in tasks]
+
+
+def check_chain_grads(arol, tasks, x, g, vjp=O.chain_vjp):
+    g = np.asarray(g, dtype=np.float32).astype(np.float64)   # the device gets float32
+    c = arol.Chain(tasks) if len(tasks) > 1 else arol.Task(tasks[0])
+    gx = torch.empty(x.shape, device="cuda")
+    ntaps = sum(t["taps"].size for t in tasks)
+    gt = torch.empty(ntaps, device="cuda")
+    c.backward(dev(g.astype(np.float32)), [dev(x)], gx, gt)
+    torch.cuda.synchronize()
+    dX, dHs = vjp(tasks, [x], g) if len(tasks) > 1 else (lambda r: (r[0], [r[1]]))(O.task_vjp(tasks[0], [x], g))
+    sX, sHs = (vjp(_abs_chain(tasks), [np.abs(x)], np.abs(g)) if len(tasks) > 1 else
+               (lambda r: (r[0], [r[1]]))(O.task_vjp(_abs_chain(tasks)[0], [np.abs(x)], np.abs(g))))
+    assert_fir_close(host(gx), dX, sX, RTOL, "dX")
+    got = host(gt)
+    off = 0
+    for dH, sH in zip(dHs, sHs):
+        n = dH.size
+        assert_fir_close(got[off:off + n].reshape(dH.shape), dH, sH, RTOL, "dH")
+        off += n
+    return c, host(gx), got
+
+
+def test_backward_config0_overlap_and_wrap(arol):
+    tk, (x,) = W.config0()
+    g = W.rng(201).standard_normal((64, 48))
+    check_chain_grads(arol, [tk], x, g)
+
+
+def test_backward_random_fir_tilers(arol):
+    g = W.rng(202)
+    for _ in range(25):
+        tk = W.random_tiler_task(g, "fir")
+        x = g.standard_normal(tk["inputs"][0]["shape"]).astype(np.float32)
+        G = g.standard_normal(tk["outputs"][0]["shape"])
+        check_chain_grads(arol, [tk], x, G)
+
+
+@pytest.mark.parametrize("shape", [(1, 8, 8), (2, 16, 32), (3, 24, 40)])
+def test_backward_fused_chain_small(arol, shape):
+    chain, (x,) = W.config1(seed=11, frames=shape[0], height=shape[1], width=shape[2])
+    G = W.rng(203).standard_normal(chain[-1]["outputs"][0]["shape"])
+    c, _, _ = check_chain_grads(arol, chain, x, G)
+    assert c.info["kernel"] == 1
+
+
+def test_backward_unfused_chain(arol):
+    tk, (x,) = W.config0(seed=4)
+    g = W.rng(204)
+    nxt = W.task((64, 16), "fir", [W.port((64, 48), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))],
+                 [W.port((64, 16), (0, 0), ((1, 0), (0, 1)), ((0,), (1,)), (1,))],
+                 g.standard_normal((1, 3)).astype(np.float32))
+    G = g.standard_normal((64, 16))
+    c, _, _ = check_chain_grads(arol, [tk, nxt], x, G)
+    assert c.info["kernel"] == 3
+
+
+def test_backward_config4_full_size(arol):
+    chain, (x,), w = W.config4()
+    check_chain_grads(arol, chain, x, w.astype(np.float64), vjp=C.chain_vjp)
+
+
+def test_fwd_bwd_equals_separate_calls_and_is_deterministic(arol):
+    chain, (x,), w = W.config4(frames=2, height=64, width=128)
+    c = arol.Chain(chain)
+    xd, wd = dev(x), dev(w)
+    y1 = c.run([xd])
+    gx1 = torch.empty_like(xd)
+    gt1 = torch.empty(48, device="cuda")
+    c.backward(wd, [xd], gx1, gt1)
+    y2 = torch.empty_like(y1)
+    gx2 = torch.empty_like(xd)
+    gt2 = torch.empty(48, device="cuda")
+    c.fwd_bwd([xd], wd, y2, gx2, gt2)
+    gx3 = torch.empty_like(xd)
+    gt3 = torch.empty(48, device="cuda")
+    c.backward(wd, [xd], gx3, gt3)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2) and torch.equal(gx1, gx2) and torch.equal(gt1, gt2)
+    assert torch.equal(gx1, gx3) and torch.equal(gt1, gt3)
+
+
+def test_backward_32x32_against_fp64_finite_differences(arol):
+    """GPU gradient of loss = sum(W * out) on one 32x32 frame against FP64
+    central differences of the oracle (exact up to rounding: the loss is
+    linear in X and in every tap)."""
+    g = W.rng(205)
+    x = g.random((1, 32, 32)).astype(np.float32)
+    Hh = (g.standard_normal((3, 8)) / 8).astype(np.float32)
+    Hv = (g.standard_normal((3, 8)) / 8).astype(np.float32)
+    chain = W.downscale_chain(1, 32, 32, Hh, Hv)
+    Wt = g.standard_normal((1, 12, 12))
+    c = arol.Chain(chain)
+    gx = torch.empty((1, 32, 32), device="cuda")
+    gt = torch.empty(48, device="cuda")
+    c.backward(dev(Wt.astype(np.float32)), [dev(x)], gx, gt)
+    torch.cuda.synchronize()
+    gx, gt = host(gx), host(gt)
+    x64 = x.astype(np.float64)
+    c64 = [dict(t, taps=np.asarray(t["taps"], np.float64)) for t in chain]
+    loss = lambda cc, xx: float(np.sum(O.run_chain(cc, [xx])[0] * Wt))
+    h = 1e-3
+    for idx in [(0, 0, 0), (0, 7, 30), (0, 31, 31), (0, 16, 9)]:
+        xp, xm = x64.copy(), x64.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (loss(c64, xp) - loss(c64, xm)) / (2 * h)
+        assert abs(gx[idx] - fd) <= 1e-5 * (1 + abs(fd)), (idx, gx[idx], fd)
+    for n in range(2):
+        for (j, k) in [(0, 0), (2, 7), (1, 4)]:
+            cp = [dict(t, taps=t["taps"].copy()) for t in c64]
+            cm = [dict(t, taps=t["taps"].copy()) for t in c64]
+            cp[n]["taps"][j, k] += h
+            cm[n]["taps"][j, k] -= h
+            fd = (loss(cp, x64) - loss(cm, x64)) / (2 * h)
+            assert abs(gt[24 * n + 8 * j + k] - fd) <= 1e-4 * (1 + abs(fd)), (n, j, k, gt[24 * n + 8 * j + k], fd)
+
+
+def test_autograd_function(arol):
+    chain, (x,), w = W.config4(seed=3, frames=2, height=32, width=64)
+    c = arol.Chain(chain)
+    xd = dev(x).requires_grad_(True)
+    taps = torch.cat([dev(chain[0]["taps"]).reshape(-1), dev(chain[1]["taps"]).reshape(-1)]).requires_grad_(True)
+    out = arol.apply_task(c, xd, taps)
+    loss = (out * dev(w)).sum()
+    loss.backward()
+    dX, (dHh, dHv) = O.chain_vjp(chain, [x], w.astype(np.float64))
+    sX, (sHh, sHv) = O.chain_vjp(_abs_chain(chain), [np.abs(x)], np.abs(w.astype(np.float64)))
+    assert_fir_close(host(xd.grad), dX, sX, RTOL, "autograd dX")
+    gt = host(taps.grad)
+    assert_fir_close(gt[:24].reshape(3, 8), dHh, sHh, RTOL, "autograd dHh")
+    assert_fir_close(gt[24:].reshape(3, 8), dHv, sHv, RTOL, "autograd dHv")

@@ -1,0 +1,257 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact for gather/scatter (copy tasks, NaN payloads included); FP32 FIR
+within 1e-5 of the summed absolute terms per element (see gpu_helpers);
+matmul within 2e-2 of the FP64 result (per element, scaled by (|A||B|)_ij, and
+normwise) with an FP32-accumulation check of 1e-4 normwise on top.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import cpu_ref as C
+from oracle import tiler as O
+from tests.gpu_helpers import assert_fir_close, dev, fir_scale, host
+
+pytestmark = pytest.mark.gpu
+
+
+def run1(A, spec, xs, out=None):
+    t = A.Task(spec)
+    ins = [dev(x) for x in xs]
+    y = t.run(ins, out)
+    torch.cuda.synchronize()
+    return t, host(y)
+
+
+# ------------------------------------------------------------ single tasks
+
+def test_config0_fir(arol):
+    tk, (x,) = W.config0()
+    t, y = run1(arol, tk, [x])
+    assert t.info["kernel"] == 0
+    y64 = O.run_task(tk, [x])[0]
+    assert_fir_close(y, y64, fir_scale(tk, x), what="config0")
+
+
+def test_random_copy_tilers_bit_exact(arol):
+    g = W.rng(101)
+    for n in range(80):
+        tk = W.random_tiler_task(g, "copy")
+        x = g.random(tk["inputs"][0]["shape"], dtype=np.float32)
+        raw = x.reshape(-1).view(np.uint32)
+        raw[:: max(1, raw.size // 3)] = 0x7FA00001 + n     # NaN payloads must survive
+        _, y = run1(arol, tk, [x])
+        ref = O.run_task(tk, [x])[0]
+        np.testing.assert_array_equal(y.view(np.uint32), ref.view(np.uint32))
+
+
+def test_random_bf16_copy_tilers_bit_exact(arol):
+    g = W.rng(102)
+    for _ in range(30):
+        tk = W.random_tiler_task(g, "copy")
+        tk = dict(tk, inputs=[dict(tk["inputs"][0], dtype="bf16")], outputs=[dict(tk["outputs"][0], dtype="bf16")])
+        bits = g.integers(0, 65536, size=tk["inputs"][0]["shape"], dtype=np.uint16)
+        _, y = run1(arol, tk, [bits])
+        np.testing.assert_array_equal(y, O.run_task(tk, [bits])[0])
+
+
+def test_random_fir_tilers(arol):
+    g = W.rng(103)
+    for _ in range(60):
+        tk = W.random_tiler_task(g, "fir")
+        x = g.standard_normal(tk["inputs"][0]["shape"]).astype(np.float32)
+        _, y = run1(arol, tk, [x])
+        assert_fir_close(y, O.run_task(tk, [x])[0], fir_scale(tk, x), what="random fir")
+
+
+def test_fir_bank_sizes(arol):
+    """m from 1 to 32 (every register-bank instantiation), T up to 64."""
+    g = W.rng(104)
+    for (T, m, S) in [(3, 1, 1), (8, 3, 4), (16, 5, 8), (17, 8, 9), (32, 16, 16), (40, 9, 12), (64, 32, 32)]:
+        H = (g.standard_normal((m, T)) / T).astype(np.float32)
+        tk = W.fir_row_task(7, 97, T, m, S, H)
+        x = g.random((7, 97), dtype=np.float32)
+        _, y = run1(arol, tk, [x])
+        assert_fir_close(y, O.run_task(tk, [x])[0], fir_scale(tk, x), what=f"T={T} m={m}")
+
+
+def test_empty_task_is_a_no_op(arol):
+    p_in = W.port((4,), (0,), ((1,),), ((1,),), (1,))
+    p_out = W.port((0,), (0,), ((1,),), ((1,),), (1,))
+    t = arol.Task(W.task((0,), "copy", [p_in], [p_out]))
+    y = t.run([torch.zeros(4, device="cuda")])
+    torch.cuda.synchronize()
+    assert y.numel() == 0
+
+
+def test_identity_round_trip(arol):
+    g = W.rng(105)
+    x = g.random((33, 41), dtype=np.float32)
+    p = W.port((33, 41), (-5, 17), ((1, 0), (0, 1)), ((0,), (0,)), (1,))
+    _, y = run1(arol, W.task((33, 41), "copy", [p], [p]), [x])
+    np.testing.assert_array_equal(y.view(np.uint32), x.view(np.uint32))
+
+
+# ------------------------------------------------------------------ chains
+
+@pytest.mark.parametrize("shape", [(1, 8, 8), (2, 16, 32), (3, 24, 40), (1, 64, 136), (2, 8, 1928)])
+def test_fused_chain_small(arol, shape):
+    chain, (x,) = W.config1(seed=7, frames=shape[0], height=shape[1], width=shape[2])
+    c = arol.Chain(chain)
+    assert c.info["kernel"] == 1
+    y = host(c.run([dev(x)]))
+    ref = (C.run_chain if x.size > 50000 else O.run_chain)(chain, [x])[0]
+    assert_fir_close(y, ref, fir_scale(chain, x, C.run_chain), what=f"chain {shape}")
+
+
+def test_fused_chain_rank2_frame(arol):
+    g = W.rng(106)
+    x = g.random((24, 48), dtype=np.float32)
+    Hh = (g.standard_normal((3, 8)) / 8).astype(np.float32)
+    Hv = (g.standard_normal((3, 8)) / 8).astype(np.float32)
+    h = W.task((24, 6), "fir", [W.port((24, 48), (0, 0), ((1, 0), (0, 8)), ((0,), (1,)), (8,))],
+               [W.port((24, 18), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))], Hh)
+    v = W.task((3, 18), "fir", [W.port((24, 18), (0, 0), ((8, 0), (0, 1)), ((1,), (0,)), (8,))],
+               [W.port((9, 18), (0, 0), ((3, 0), (0, 1)), ((1,), (0,)), (3,))], Hv)
+    c = arol.Chain([h, v])
+    assert c.info["kernel"] == 1
+    y = host(c.run([dev(x)]))
+    assert_fir_close(y, O.run_chain([h, v], [x])[0], fir_scale([h, v], x), what="rank-2 chain")
+
+
+def test_config1_full_size(arol):
+    """64 frames of 1080x1920, the full workload, against the C oracle."""
+    chain, (x,) = W.config1()
+    c = arol.Chain(chain)
+    y = host(c.run([dev(x)]))
+    ref = C.run_chain(chain, [x])[0]
+    assert_fir_close(y, ref, fir_scale(chain, x, C.run_chain), what="config1 full")
+
+
+def test_unfused_chain_with_overlap_and_wrap(arol):
+    tk, (x,) = W.config0(seed=3)
+    g = W.rng(107)
+    nxt = W.task((64, 16), "fir", [W.port((64, 48), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))],
+                 [W.port((64, 16), (0, 0), ((1, 0), (0, 1)), ((0,), (1,)), (1,))],
+                 g.standard_normal((1, 3)).astype(np.float32))
+    c = arol.Chain([tk, nxt])
+    assert c.info["kernel"] == 3
+    y = host(c.run([dev(x)]))
+    assert_fir_close(y, O.run_chain([tk, nxt], [x])[0], fir_scale([tk, nxt], x), what="unfused chain")
+
+
+def test_misaligned_input_takes_the_unfused_path(arol):
+    chain, (x,) = W.config1(seed=8, frames=2, height=16, width=32)
+    c = arol.Chain(chain)
+    buf = torch.zeros(x.size + 1, device="cuda")
+    buf[1:] = dev(x).reshape(-1)
+    y = host(c.run([buf[1:].view(x.shape)]))
+    assert_fir_close(y, O.run_chain(chain, [x])[0], fir_scale(chain, x), what="misaligned")
+
+
+def test_run_host_matches_run(arol):
+    chain, (x,) = W.config1(seed=9, frames=3, height=32, width=64)
+    c = arol.Chain(chain)
+    y_dev = host(c.run([dev(x)]))
+    out = np.empty(chain[-1]["outputs"][0]["shape"], dtype=np.float32)
+    c.run_host([x], out)
+    np.testing.assert_array_equal(out, y_dev)
+    tk, (x0,) = W.config0()
+    t = arol.Task(tk)
+    out0 = np.empty((64, 48), np.float32)
+    t.run_host([x0], out0)
+    np.testing.assert_array_equal(out0, host(t.run([dev(x0)])))
+
+
+# ------------------------------------------------------------------ matmul
+
+def _check_matmul(A_bits, B_bits, Cg, rows=None, cols=None, tk=None):
+    if rows is None:
+        Af = W.bf16_bits_to_f32(A_bits).astype(np.float64)
+        Bf = W.bf16_bits_to_f32(B_bits).astype(np.float64)
+        ref = Af @ Bf
+        scale = np.abs(Af) @ np.abs(Bf)
+        got = Cg.astype(np.float64)
+    else:
+        ref, scale = C.matmul_sample(tk, A_bits, B_bits, rows, cols)
+        got = Cg[rows, cols].astype(np.float64)
+    err = np.abs(got - ref)
+    assert np.all(err <= 2e-2 * scale + 1e-30), float(np.max(err / scale))
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel <= 2e-2
+    assert rel <= 1e-4, rel      # FP32 accumulation of exact bf16 products
+    return rel
+
+
+@pytest.mark.parametrize("mnk", [(128, 128, 64), (256, 384, 192), (512, 512, 512), (384, 768, 1024)])
+def test_matmul_full(arol, mnk):
+    M, N, K = mnk
+    g = W.rng(108)
+    a = W.bf16_round(g.standard_normal((M, K), dtype=np.float32))
+    b = W.bf16_round(g.standard_normal((K, N), dtype=np.float32))
+    tk = W.matmul_task(M, N, K)
+    t = arol.Task(tk)
+    assert t.info["kernel"] == 2
+    c = t.run([dev(a), dev(b)])
+    t.sync_status()
+    _check_matmul(a, b, host(c))
+
+
+def test_matmul_4096_sampled(arol):
+    tk, (a, b) = W.config2()
+    t = arol.Task(tk)
+    c = t.run([dev(a), dev(b)])
+    t.sync_status()
+    Cg = host(c)
+    g = W.rng(109)
+    rows = g.integers(0, 4096, 1024)
+    cols = g.integers(0, 4096, 1024)
+    # four whole 128x128 tiles: corners and one interior tile
+    for (r0, c0) in [(0, 0), (31, 31), (0, 31), (17, 9)]:
+        rr, cc = np.meshgrid(np.arange(128) + 128 * r0, np.arange(128) + 128 * c0, indexing="ij")
+        rows = np.concatenate([rows, rr.reshape(-1)])
+        cols = np.concatenate([cols, cc.reshape(-1)])
+    _check_matmul(a, b, Cg, rows, cols, tk)
+
+
+# ------------------------------------------------------------------ batches
+
+def test_batch_config3_matches_per_task_and_oracle(arol):
+    tasks, xs = W.config3()
+    b = arol.Batch(tasks)
+    ins = [dev(x) for x in xs]
+    outs = b.empty_outputs()
+    b.run(ins, outs)
+    outs2 = b.empty_outputs()
+    b.run_per_task(ins, outs2)
+    torch.cuda.synchronize()
+    for i, (tk, x) in enumerate(zip(tasks, xs)):
+        y = host(outs[i])
+        np.testing.assert_array_equal(y, host(outs2[i]))
+        if i % 8 == 0:
+            assert_fir_close(y, C.run_task(tk, [x])[0], fir_scale(tk, x, C.run_chain), what=f"instance {i}")
+    # the autotuner changes the tiling, not the results; new buffers refresh the table
+    b.tune(ins, outs, force=True)
+    outs3 = b.empty_outputs()
+    b.run(ins, outs3)
+    torch.cuda.synchronize()
+    for i in range(len(tasks)):
+        np.testing.assert_array_equal(host(outs3[i]), host(outs2[i]))
+
+
+def test_batch_of_random_tilers(arol):
+    g = W.rng(110)
+    tasks = [W.random_tiler_task(g, "fir" if i % 2 else "copy") for i in range(40)]
+    xs = [g.random(t["inputs"][0]["shape"], dtype=np.float32) for t in tasks]
+    b = arol.Batch(tasks)
+    outs = b.empty_outputs()
+    b.run([dev(x) for x in xs], outs)
+    torch.cuda.synchronize()
+    for tk, x, y in zip(tasks, xs, outs):
+        ref = O.run_task(tk, [x])[0]
+        if tk["elem"] == "copy":
+            np.testing.assert_array_equal(host(y).view(np.uint32), ref.view(np.uint32))
+        else:
+            assert_fir_close(host(y), ref, fir_scale(tk, x), what="batch fir")
