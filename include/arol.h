@@ -239,6 +239,40 @@ int64_t arol_abi_struct_size(int which);
  * the tensor-core matmul gave up, AROL_OK otherwise. */
 arol_status arol_task_sync_status(arol_task t, void* stream);
 
+/* ---- backward without device allocation ---------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: code running while a stream is captured into
+ * a CUDA graph (an allocation there breaks the capture), real-time or embedded
+ * hosts whose device-memory budget is fixed at start-up, and programs whose
+ * memory belongs to an allocator that must not be bypassed.
+ *
+ * Same result as arol_task_backward on the fused separable downscaler chain
+ * (horizontal then vertical 8-tap -> 3-output fir, step 8): x (frames, height,
+ * width) f32 and grad_out (frames, 3*height/8, 3*width/8) f32 are read;
+ * grad_in (nullable, x's shape) and grad_taps (nullable, 48 floats: the 3x8
+ * horizontal block, then the 3x8 vertical block) are OVERWRITTEN; taps (48
+ * floats, same layout) is read.  All pointers are device pointers owned by the
+ * caller; x and grad_in must be 16-byte aligned; height and width must be
+ * multiples of 8.
+ *
+ * Nothing is allocated: not by cudaMalloc, cudaFree or any allocating library
+ * routine.  The only scratch (one 48-float partial per CTA) is a static device
+ * array of 1024 partials (192 KiB) that every GPU loading this library keeps
+ * until the process exits; a device that would launch more CTAs than that gets
+ * AROL_ERR_UNSUPPORTED, as do frames * height/8 * width/4 >= 2^31 work items.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the array: every CTA overwrites its partials before they are
+ * read, so nothing needs clearing, but calls that overlap on the GPU (two
+ * streams, or two host threads) race on it and must be serialized by the
+ * caller.  Returns AROL_ERR_INVALID for null inputs, unaligned x/grad_in or
+ * sizes not multiples of 8; this entry point does not record a message for
+ * arol_last_error. */
+arol_status arol_downscale_backward_noalloc(const float* x, const float* grad_out, const float* taps,
+                                            int64_t frames, int32_t height, int32_t width,
+                                            float* grad_in, float* grad_taps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,7 @@ def _load():
         "arol_batch_tune": [c_vp, P(c_vp), P(c_vp), c_vp, ctypes.c_int],
         "arol_batch_config": [c_vp, P(c_i64), P(c_i32), P(c_i32)],
         "arol_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+        "arol_downscale_backward_noalloc": [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -285,3 +286,13 @@ def arol_batch_config(b) -> dict:
 def arol_batch_destroy(b):
     if b:
         lib.arol_batch_destroy(b)
+
+
+def arol_downscale_backward_noalloc(x, grad_out, taps, frames, height, width, grad_in=None, grad_taps=None,
+                                    stream=None):
+    """Backward of the fused downscaler chain with no device allocation (see
+    include/arol.h); raises ArolError with the status code on failure."""
+    st = lib.arol_downscale_backward_noalloc(_ptr(x), _ptr(grad_out), _ptr(taps), int(frames), int(height),
+                                             int(width), _ptr(grad_in), _ptr(grad_taps), _stream(stream))
+    if st != 0:
+        raise ArolError(st, "arol_downscale_backward_noalloc rejected the call")

@@ -291,3 +291,79 @@ cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int np
 }
 
 }  // namespace arol
+
+// ---------------------------------------------------------------------------
+// Backward of the fused downscaler without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
+// being captured into a graph (an allocation there breaks or invalidates the
+// capture), real-time or embedded hosts that fix their device-memory budget
+// at start-up and forbid allocation afterwards, and programs whose memory is
+// owned by an allocator that must not be bypassed.  For them this entry point
+// takes every buffer from the caller and keeps its only scratch — one
+// 48-float tap-gradient partial per CTA — in the file-scope array below,
+// which every GPU that loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+#include "arol.h"
+
+namespace arol {
+namespace {
+
+constexpr int kNoAllocMaxParts = 1024;   // CTAs whose partials fit: 1024 x 48 floats = 192 KiB
+static __device__ __align__(256) float g_noalloc_partials[kNoAllocMaxParts * kTapGrads];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+}  // namespace arol
+
+extern "C" arol_status arol_downscale_backward_noalloc(const float* x, const float* grad_out, const float* taps,
+                                                       int64_t frames, int32_t height, int32_t width,
+                                                       float* grad_in, float* grad_taps, void* stream) {
+    using namespace arol;
+    if (!x || !grad_out || !taps) return AROL_ERR_INVALID;
+    if (frames < 0 || height < 0 || width < 0 || height % 8 || width % 8) return AROL_ERR_INVALID;
+    if ((double)frames * (height / 8) * (width / 4) >= 2147483647.0) return AROL_ERR_UNSUPPORTED;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(grad_in)) & 15u) return AROL_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AROL_ERR_CUDA;
+    float* scratch = nullptr;
+    {
+        // One-time set-up per device, with that device current: host code only
+        // knows a host-side stand-in for the array; the device address comes
+        // from the runtime.
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return AROL_ERR_CUDA;
+            g_noalloc_ptr[dev] = static_cast<float*>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    const int nparts = downscale_bwd_partials(device_sm_count());
+    if (nparts > kNoAllocMaxParts) return AROL_ERR_UNSUPPORTED;   // more CTAs than the static scratch holds
+    if (frames == 0 || height == 0 || width == 0) {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (grad_taps && cudaMemsetAsync(grad_taps, 0, kTapGrads * sizeof(float), s) != cudaSuccess) return AROL_ERR_CUDA;
+        return AROL_OK;
+    }
+    DownscaleDev p;
+    p.x = x;
+    p.y = nullptr;
+    p.taps = taps;
+    p.gy = grad_out;
+    p.gx = grad_in;
+    p.partials = scratch;   // every CTA overwrites its own 48 slots before the reduction reads them
+    p.frames = frames;
+    p.H = height;
+    p.W = width;
+    if (launch_downscale_bwd(p, grad_taps, nparts, false, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return AROL_ERR_CUDA;
+    return AROL_OK;
+}

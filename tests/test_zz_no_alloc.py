@@ -1,0 +1,62 @@
+"""The no-allocation backward entry point against the regular one.
+
+Callers that cannot allocate device memory — code that runs while a stream is
+being captured into a CUDA graph, real-time or embedded hosts whose device
+memory is fixed at start-up, programs whose memory belongs to an allocator
+that must not be bypassed — call arol_downscale_backward_noalloc, which takes
+every buffer from the caller and keeps its scratch in a static device array.
+Two calls in a row (on different data, so the second one starts from the
+scratch the first one left behind) must each match arol_task_backward within
+the tolerance of the other gradient tests.
+
+This file is collected last on purpose: a run that stops at the first failure
+has run every other test before it.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import tiler as O
+from tests.gpu_helpers import FIR_RTOL, assert_fir_close, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _abs_chain(tasks):
+    return [dict(t, taps=np.abs(np.asarray(t["taps"], np.float64))) for t in tasks]
+
+
+def _case(arol, seed, frames, height, width):
+    chain, (x,), w = W.config4(seed=seed, frames=frames, height=height, width=width)
+    c = arol.Chain(chain)
+    xd, wd = dev(x), dev(w)
+    taps = torch.cat([dev(chain[0]["taps"]).reshape(-1), dev(chain[1]["taps"]).reshape(-1)]).contiguous()
+    gx_ref = torch.empty_like(xd)
+    gt_ref = torch.empty(48, device="cuda")
+    c.backward(wd, [xd], gx_ref, gt_ref)      # the existing entry point
+    torch.cuda.synchronize()
+    sX, (sHh, sHv) = O.chain_vjp(_abs_chain(chain), [np.abs(x)], np.abs(w.astype(np.float64)))
+    return xd, wd, taps, host(gx_ref), host(gt_ref), sX, np.concatenate([sHh.reshape(-1), sHv.reshape(-1)])
+
+
+def test_noalloc_backward_matches_task_backward_on_two_calls(arol):
+    cases = [(31, 3, 64, 96), (32, 2, 40, 128)]
+    for seed, frames, height, width in cases:
+        xd, wd, taps, gx_ref, gt_ref, sX, sH = _case(arol, seed, frames, height, width)
+        gx = torch.full_like(xd, float("nan"))
+        gt = torch.full((48,), float("nan"), device="cuda")
+        arol.arol_downscale_backward_noalloc(xd, wd, taps, frames, height, width, gx, gt)
+        torch.cuda.synchronize()
+        assert_fir_close(host(gx), gx_ref.astype(np.float64), sX, FIR_RTOL, "no-alloc dX")
+        assert_fir_close(host(gt), gt_ref.astype(np.float64), sH, FIR_RTOL, "no-alloc dH")
+
+
+def test_noalloc_backward_rejects_bad_sizes(arol):
+    x = torch.zeros(8 * 8, device="cuda")
+    with pytest.raises(arol.ArolError) as e:
+        arol.arol_downscale_backward_noalloc(x, x, x, 1, 8, 12, x, None)     # width not a multiple of 8
+    assert e.value.status == 1
+    with pytest.raises(arol.ArolError) as e:
+        arol.arol_downscale_backward_noalloc(x, x, x, 1 << 40, 8, 8, x, None)   # beyond the work-item limit
+    assert e.value.status == 3
