@@ -235,8 +235,10 @@ int arol_version(void);
 int64_t arol_abi_struct_size(int which);
 
 /* Synchronize `stream`, then report device-side failures recorded by kernels
- * of task t since its last run: AROL_ERR_TIMEOUT when a bounded wait inside
- * the tensor-core matmul gave up, AROL_OK otherwise. */
+ * of task t since the last report: AROL_ERR_TIMEOUT when a bounded wait inside
+ * a pipelined kernel (the tensor-core matmul, the fused downscaler) gave up —
+ * its outputs are then incomplete — AROL_OK otherwise.  Reporting clears the
+ * record. */
 arol_status arol_task_sync_status(arol_task t, void* stream);
 
 /* ---- backward without device allocation ---------------------------------- */
@@ -253,8 +255,8 @@ arol_status arol_task_sync_status(arol_task t, void* stream);
  * grad_in (nullable, x's shape) and grad_taps (nullable, 48 floats: the 3x8
  * horizontal block, then the 3x8 vertical block) are OVERWRITTEN; taps (48
  * floats, same layout) is read.  All pointers are device pointers owned by the
- * caller; x and grad_in must be 16-byte aligned; height and width must be
- * multiples of 8.
+ * caller; x, grad_out and grad_in must be 16-byte aligned; height and width
+ * must be multiples of 8.
  *
  * Nothing is allocated: not by cudaMalloc, cudaFree or any allocating library
  * routine.  The only scratch (one 48-float partial per CTA) is a static device
@@ -266,7 +268,7 @@ arol_status arol_task_sync_status(arol_task t, void* stream);
  * calls share the array: every CTA overwrites its partials before they are
  * read, so nothing needs clearing, but calls that overlap on the GPU (two
  * streams, or two host threads) race on it and must be serialized by the
- * caller.  Returns AROL_ERR_INVALID for null inputs, unaligned x/grad_in or
+ * caller.  Returns AROL_ERR_INVALID for null inputs, unaligned buffers or
  * sizes not multiples of 8; this entry point does not record a message for
  * arol_last_error. */
 arol_status arol_downscale_backward_noalloc(const float* x, const float* grad_out, const float* taps,

@@ -410,7 +410,7 @@ struct arol_task_s {
     int ds_H = 0, ds_W = 0;
     // matmul
     int mm_M = 0, mm_N = 0, mm_K = 0;
-    unsigned* mm_err = nullptr;
+    unsigned* err_flag = nullptr;        // device word: bounded waits that gave up
     // backward scratch and inverse maps
     float* partials = nullptr;
     int64_t partials_cap = 0;
@@ -443,6 +443,16 @@ arol_status dev_alloc(arol_task t, void** p, size_t bytes, const char* what) {
         *p = nullptr;
         return cuda_fail(e, what);
     }
+    return AROL_OK;
+}
+
+// The task's device error word (bounded device-side waits that gave up),
+// cleared when allocated and after arol_task_sync_status reports it.
+arol_status ensure_err(arol_task t, cudaStream_t s) {
+    if (t->err_flag) return AROL_OK;
+    arol_status st = dev_alloc(t, (void**)&t->err_flag, sizeof(unsigned), "cudaMalloc(error flag)");
+    if (st != AROL_OK) return st;
+    AROL_CUDA(cudaMemsetAsync(t->err_flag, 0, sizeof(unsigned), s), "clear error flag");
     return AROL_OK;
 }
 
@@ -696,6 +706,7 @@ arol_status run_generic(const arol_task_desc& d, const float* taps, const void* 
 DownscaleDev ds_params(arol_task t, const float* taps) {
     DownscaleDev p;
     std::memset(&p, 0, sizeof p);
+    p.err = t->err_flag;
     p.taps = taps;
     p.frames = t->ds_frames;
     p.H = t->ds_H;
@@ -728,14 +739,15 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
     if (t->kind == 0) {
         if (reps_of(d0) == 0) return AROL_OK;
         if (t->kernel == 2) {
-            if ((st = dev_alloc(t, (void**)&t->mm_err, sizeof(unsigned), "cudaMalloc(matmul flag)")) != AROL_OK) return st;
-            AROL_CUDA(launch_matmul_tc(in[0], in[1], (float*)out[0], t->mm_M, t->mm_N, t->mm_K, t->mm_err, s),
+            if ((st = ensure_err(t, s)) != AROL_OK) return st;
+            AROL_CUDA(launch_matmul_tc(in[0], in[1], (float*)out[0], t->mm_M, t->mm_N, t->mm_K, t->err_flag, s),
                       "matmul kernel launch");
             return AROL_OK;
         }
         return run_generic(d0, taps, in[0], out[0], s);
     }
     if (t->kernel == 1 && aligned16(in[0])) {
+        if ((st = ensure_err(t, s)) != AROL_OK) return st;
         DownscaleDev p = ds_params(t, taps);
         p.x = (const float*)in[0];
         p.y = (float*)out[0];
@@ -883,9 +895,10 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
     if (st != AROL_OK) return st;
     const float* taps = nullptr;
     if ((st = ensure_taps(t, s, &taps)) != AROL_OK) return st;
-    if (t->kind == 1 && t->kernel == 1 && aligned16(saved_in[0]) && aligned16(grad_in)) {
-        const int nparts = downscale_bwd_partials(device_sm_count());
+    if (t->kind == 1 && t->kernel == 1 && aligned16(saved_in[0]) && aligned16(grad_in) && aligned16(grad_out)) {
+        const int nparts = downscale_bwd_partials(device_sm_count(), t->ds_W);
         if ((st = ensure_partials(t, (int64_t)nparts * 48)) != AROL_OK) return st;
+        if ((st = ensure_err(t, s)) != AROL_OK) return st;
         DownscaleDev p = ds_params(t, taps);
         p.x = (const float*)saved_in[0];
         p.gy = (const float*)grad_out;
@@ -936,15 +949,16 @@ arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* gr
     if (!t || !in || !in[0] || !grad_out || !out) return fail(AROL_ERR_INVALID, "null argument");
     if (!(t->kind == 1 && t->kernel == 1))
         return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd is implemented for the fused separable downscaler chain only");
-    if (!aligned16(in[0]) || !aligned16(grad_in))
-        return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd needs 16-byte aligned input and input-gradient buffers");
+    if (!aligned16(in[0]) || !aligned16(grad_in) || !aligned16(grad_out))
+        return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd needs 16-byte aligned input, output-gradient and input-gradient buffers");
     cudaStream_t s = (cudaStream_t)stream;
     const float* taps = nullptr;
     arol_status st = remember_device(t);
     if (st != AROL_OK) return st;
     if ((st = ensure_taps(t, s, &taps)) != AROL_OK) return st;
-    const int nparts = downscale_bwd_partials(device_sm_count());
+    const int nparts = downscale_bwd_partials(device_sm_count(), t->ds_W);
     if ((st = ensure_partials(t, (int64_t)nparts * 48)) != AROL_OK) return st;
+    if ((st = ensure_err(t, s)) != AROL_OK) return st;
     DownscaleDev p = ds_params(t, taps);
     p.x = (const float*)in[0];
     p.y = (float*)out;
@@ -958,10 +972,13 @@ arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* gr
 arol_status arol_task_sync_status(arol_task t, void* stream) {
     if (!t) return fail(AROL_ERR_INVALID, "null task");
     AROL_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
-    if (t->mm_err) {
+    if (t->err_flag) {
         unsigned flag = 0;
-        AROL_CUDA(cudaMemcpy(&flag, t->mm_err, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
-        if (flag) return fail(AROL_ERR_TIMEOUT, "a bounded wait in the matmul kernel gave up (flags 0x%x)", flag);
+        AROL_CUDA(cudaMemcpy(&flag, t->err_flag, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
+        if (flag) {
+            cudaMemset(t->err_flag, 0, sizeof(unsigned));
+            return fail(AROL_ERR_TIMEOUT, "a bounded device-side wait gave up (flags 0x%x)", flag);
+        }
     }
     return AROL_OK;
 }
@@ -974,7 +991,7 @@ void arol_task_destroy(arol_task t) {
         if (cur != t->device) cudaSetDevice(t->device);
         free_dev(t->taps_dev);
         for (void* p : t->mids) free_dev(p);
-        free_dev(t->mm_err);
+        free_dev(t->err_flag);
         free_dev(t->partials);
         for (auto* p : t->inv_start) free_dev(p);
         for (auto* p : t->inv_list) free_dev(p);

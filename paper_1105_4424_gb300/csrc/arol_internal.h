@@ -55,6 +55,7 @@ struct DownscaleDev {
     const float* gy;        // backward: dL/dy
     float* gx;              // backward: dL/dx
     float* partials;        // backward: per-CTA tap-gradient partials (48 floats each)
+    unsigned* err;          // nullable: bit set when a bounded wait gives up
     int64_t frames;
     int32_t H, W;
 };
@@ -67,7 +68,7 @@ cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, 
 cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s);
 cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int nparts, bool with_fwd,
                                  cudaStream_t s);
-int downscale_bwd_partials(int sm_count);   // number of per-CTA partial slots the backward uses
+int downscale_bwd_partials(int sm_count, int W);   // per-CTA partial slots the backward uses for width W
 
 // tcgen05 matmul: C (M x N, f32) = A (M x K, bf16 row-major) . B (K x N, bf16 row-major).
 cudaError_t launch_matmul_tc(const void* A, const void* B, float* C, int M, int N, int K,

@@ -21,7 +21,11 @@
 // reduced per warp (shuffles), per CTA (shared memory, fixed order) into a
 // per-CTA partial, then across CTAs in fixed order by a second kernel:
 // deterministic run to run.
+#include <cstdlib>
+#include <cstring>
+
 #include "arol_internal.h"
+#include "ptx.h"
 
 namespace arol {
 namespace {
@@ -245,6 +249,276 @@ __global__ void __launch_bounds__(kTapGrads * 16) tapgrad_reduce_kernel(const fl
     if (l == 0) out[o] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Bulk-copy pipelined variants.  A unit of work is one 8-row stripe of one
+// frame restricted to a chunk of Wc columns (Wc a multiple of 32, at most
+// 1024).  A producer warp streams each unit's 8 row segments (and, for the
+// backward, the 3 matching rows of dL/dY) into a kStages-deep shared-memory
+// ring with cp.async.bulk, completing on the stage's "full" mbarrier; eight
+// consumer warps compute from shared memory and release the stage on its
+// "empty" mbarrier.  Bytes in flight no longer live in registers, so a CTA
+// keeps up to kStages units (~100 KB) of loads outstanding.
+// ---------------------------------------------------------------------------
+
+// Per mode: consumer warps, ring depth, CTAs per SM.  The forward needs ~95
+// registers, so two CTAs of 8 consumer warps share an SM (6 stages in
+// flight per SM); the backward needs ~170, so one CTA of 11 consumer warps
+// owns the SM with a deeper ring.
+template <int kMode> struct BulkCfg {
+    static constexpr int kCWarps = kMode == 0 ? 8 : 11;
+    static constexpr int kStages = kMode == 0 ? 3 : 5;
+    static constexpr int kThreads = (kCWarps + 1) * 32;
+    static constexpr int kMinCtas = kMode == 0 ? 2 : 1;
+};
+
+__host__ __device__ __forceinline__ int stage_floats(int Wc, bool with_g) { return 8 * Wc + (with_g ? 9 * Wc / 8 : 0); }
+
+__device__ __forceinline__ void flag_error(const DownscaleDev& p, unsigned bit) {
+    if (p.err) atomicOr(p.err, bit);
+}
+
+// kMode: 0 forward, 1 backward, 2 forward + backward.
+template <int kMode>
+__global__ void __launch_bounds__(BulkCfg<kMode>::kThreads, BulkCfg<kMode>::kMinCtas)
+    downscale_bulk_kernel(const DownscaleDev p, int Wc, int nch) {
+    constexpr bool kBwd = kMode != 0;
+    constexpr bool kFwd = kMode != 1;
+    constexpr int kCWarps = BulkCfg<kMode>::kCWarps;
+    constexpr int kStages = BulkCfg<kMode>::kStages;
+    extern __shared__ __align__(128) float sm[];
+    const int sf = stage_floats(Wc, kBwd);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kStages * sf);
+    const uint32_t full0 = ptx::smem_addr(bars), empty0 = ptx::smem_addr(bars + kStages);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t HB = (uint32_t)p.H >> 3;
+    const uint32_t units = (uint32_t)p.frames * HB * (uint32_t)nch;
+    const int Wo = (p.W >> 3) * 3, Ho = (int)HB * 3;
+    const int gw = 3 * Wc / 8;   // floats per staged dL/dY row
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            ptx::mbar_init(full0 + 8 * st, 1);
+            ptx::mbar_init(empty0 + 8 * st, kCWarps);
+        }
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == kCWarps) {
+        // ---------------- producer
+        if (lane == 0) {
+            int last[kStages];
+#pragma unroll
+            for (int st = 0; st < kStages; ++st) last[st] = -1;
+            uint32_t i = 0;
+            for (uint32_t u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+                const int st = (int)(i % kStages);
+                if (i >= (uint32_t)kStages && !ptx::mbar_wait(empty0 + 8 * st, ((i / kStages) & 1u) ^ 1u)) {
+                    flag_error(p, 1u);
+                    break;
+                }
+                const uint32_t c = u % (uint32_t)nch, stripe = u / (uint32_t)nch;
+                const uint32_t f = stripe / HB, sy = stripe - f * HB;
+                const int c0 = (int)c * Wc;
+                const int wc = min(Wc, p.W - c0);
+                const uint32_t xrow = (uint32_t)wc * 4u, grow = (uint32_t)(3 * wc / 8) * 4u;
+                const uint32_t fb = full0 + 8 * st;
+                ptx::mbar_expect_tx(fb, 8u * xrow + (kBwd ? 3u * grow : 0u));
+                float* dst = sm + st * sf;
+                const float* xs = p.x + ((int64_t)f * p.H + 8 * sy) * (int64_t)p.W + c0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) ptx::bulk_g2s(ptx::smem_addr(dst + r * Wc), xs + (int64_t)r * p.W, xrow, fb);
+                if (kBwd) {
+                    const float* gs = p.gy + ((int64_t)f * Ho + 3 * sy) * (int64_t)Wo + 3 * c0 / 8;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        ptx::bulk_g2s(ptx::smem_addr(dst + 8 * Wc + j * gw), gs + (int64_t)j * Wo, grow, fb);
+                }
+                last[st] = (int)i;
+            }
+            // every issued copy lands before the CTA (and its shared memory) goes away
+#pragma unroll
+            for (int st = 0; st < kStages; ++st)
+                if (last[st] >= 0) ptx::mbar_wait(full0 + 8 * st, ((uint32_t)last[st] / kStages) & 1u);
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    const int half = lane & 1;
+    Taps tp;
+    load_taps(p.taps, half, tp);
+    float dhh[3][4], dhv[3][8];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) dhh[j][t] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dhv[j][k] = 0.f;
+    }
+    uint32_t i = 0;
+    for (uint32_t u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+        const int st = (int)(i % kStages);
+        if (!ptx::mbar_wait(full0 + 8 * st, (i / kStages) & 1u)) {
+            flag_error(p, 2u);
+            break;
+        }
+        const uint32_t c = u % (uint32_t)nch, stripe = u / (uint32_t)nch;
+        const uint32_t f = stripe / HB, sy = stripe - f * HB;
+        const int c0 = (int)c * Wc;
+        const int nq = min(Wc, p.W - c0) >> 2;
+        const float* src = sm + st * sf;
+        for (int qb = warp * 32; qb < nq; qb += kCWarps * 32) {
+            const int q = qb + lane;
+            Item it;
+            it.valid = q < nq;
+            it.half = half;
+            it.f = f;
+            it.sy = sy;
+            it.c4 = (uint32_t)(c0 >> 2) + (uint32_t)q;
+            // rows are read from shared memory as they are used (lanes past the
+            // chunk's end read column 0; their results are discarded)
+            const float* row0 = src + 4 * (it.valid ? q : 0);
+            float y[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int ii = 0; ii < 3; ++ii) y[j][ii] = 0.f;
+            if (!kBwd) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float4 vk = *reinterpret_cast<const float4*>(row0 + k * Wc);
+                    float mh[3];
+                    horiz(tp, vk, mh);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int ii = 0; ii < 3; ++ii) y[j][ii] = fmaf(tp.hv[j][k], mh[ii], y[j][ii]);
+                }
+            } else {
+                float g[3][3];
+                const float* gsrc = src + 8 * Wc + 3 * ((it.valid ? q : 0) >> 1);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int ii = 0; ii < 3; ++ii) g[j][ii] = it.valid ? gsrc[j * gw + ii] : 0.f;
+                const int64_t xoff = ((int64_t)f * p.H + 8 * sy) * (int64_t)p.W + c0 + 4 * q;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float4 vk = *reinterpret_cast<const float4*>(row0 + k * Wc);
+                    float mh[3];
+                    horiz(tp, vk, mh);
+                    float dmid[3];
+#pragma unroll
+                    for (int ii = 0; ii < 3; ++ii) {
+                        dmid[ii] = fmaf(tp.hv[2][k], g[2][ii], fmaf(tp.hv[1][k], g[1][ii], tp.hv[0][k] * g[0][ii]));
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            dhv[j][k] = fmaf(g[j][ii], mh[ii], dhv[j][k]);
+                            if (kFwd) y[j][ii] = fmaf(tp.hv[j][k], mh[ii], y[j][ii]);
+                        }
+                    }
+                    float dx[4];
+                    const float vv[4] = {vk.x, vk.y, vk.z, vk.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        dx[t] = fmaf(tp.hh[2][t], dmid[2], fmaf(tp.hh[1][t], dmid[1], tp.hh[0][t] * dmid[0]));
+#pragma unroll
+                        for (int ii = 0; ii < 3; ++ii) dhh[ii][t] = fmaf(dmid[ii], vv[t], dhh[ii][t]);
+                    }
+                    if (it.valid && p.gx) st_stream4(p.gx + xoff + (int64_t)k * p.W, make_float4(dx[0], dx[1], dx[2], dx[3]));
+                }
+            }
+            if (kFwd) store_block(p, it, y);
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(empty0 + 8 * st);
+    }
+    if (!kBwd) return;
+    // Tap gradients: warp shuffles, then the 8 consumer warps in fixed order.
+#pragma unroll
+    for (int off = 2; off < 32; off <<= 1)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) dhh[j][t] += __shfl_xor_sync(kFull, dhh[j][t], off);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dhv[j][k] += __shfl_xor_sync(kFull, dhv[j][k], off);
+    __shared__ float s_red[kCWarps][kTapGrads];
+    if (lane < 2) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) s_red[warp][j * 8 + 4 * lane + t] = dhh[j][t];
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s_red[warp][24 + j * 8 + k] = dhv[j][k];
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kCWarps * 32) : "memory");   // consumer warps only
+    if (threadIdx.x < kTapGrads) {
+        float acc = 0.f;
+        for (int w = 0; w < kCWarps; ++w) acc += s_red[w][threadIdx.x];
+        p.partials[(int64_t)blockIdx.x * kTapGrads + threadIdx.x] = acc;
+    }
+}
+
+// Column chunk of the bulk variants: the fewest chunks of at most 1024
+// columns, each a multiple of 32 columns.
+int bulk_chunk(int W) {
+    const int n = (W + 1023) / 1024;
+    int wc = (W + n - 1) / n;
+    return (wc + 31) / 32 * 32;
+}
+
+template <int kMode>
+size_t bulk_smem(int Wc) {
+    constexpr int kStages = BulkCfg<kMode>::kStages;
+    return (size_t)kStages * stage_floats(Wc, kMode != 0) * 4 + 2 * kStages * 8;
+}
+
+template <int kMode>
+int bulk_ctas_per_sm(int Wc) {
+    const size_t smem = bulk_smem<kMode>(Wc);
+    static int last_wc = -1, last = 1;
+    if (Wc != last_wc) {
+        cudaFuncSetAttribute(downscale_bulk_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, downscale_bulk_kernel<kMode>, BulkCfg<kMode>::kThreads, smem);
+        last = n > 0 ? n : 1;
+        last_wc = Wc;
+    }
+    return last;
+}
+
+template <int kMode>
+cudaError_t launch_bulk(const DownscaleDev& p, int grid, cudaStream_t s) {
+    const int Wc = bulk_chunk(p.W);
+    const int nch = (p.W + Wc - 1) / Wc;
+    const size_t smem = bulk_smem<kMode>(Wc);
+    bulk_ctas_per_sm<kMode>(Wc);   // sets the dynamic shared-memory limit
+    downscale_bulk_kernel<kMode><<<grid, BulkCfg<kMode>::kThreads, smem, s>>>(p, Wc, nch);
+    return cudaGetLastError();
+}
+
+// The backward stages dL/dY rows with bulk copies: their byte offsets and
+// sizes (1.5 * columns) are multiples of 16 only when W is a multiple of 32.
+bool bulk_backward_ok(int W) { return W % 32 == 0; }
+
+bool use_register_variant() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("AROL_FUSED_VARIANT");
+        v = (e && std::strcmp(e, "regs") == 0) ? 1 : 0;
+    }
+    return v == 1;
+}
+
 int fwd_grid(uint32_t items) {
     static int per_sm = 0;
     if (!per_sm) {
@@ -258,7 +532,12 @@ int fwd_grid(uint32_t items) {
 
 }  // namespace
 
-int downscale_bwd_partials(int sm_count) {
+int downscale_bwd_partials(int sm_count, int W) {
+    if (bulk_backward_ok(W) && !use_register_variant()) {
+        const int Wc = bulk_chunk(W);
+        const int a = bulk_ctas_per_sm<1>(Wc), b = bulk_ctas_per_sm<2>(Wc);
+        return sm_count * (a < b ? a : b);
+    }
     static int per_sm = 0;
     if (!per_sm) {
         int a = 0, b = 0;
@@ -273,15 +552,26 @@ int downscale_bwd_partials(int sm_count) {
 cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s) {
     const uint32_t items = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * ((uint32_t)p.W >> 2);
     if (items == 0) return cudaSuccess;
+    if (!use_register_variant()) {
+        const int Wc = bulk_chunk(p.W);
+        const uint32_t units = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * (uint32_t)((p.W + Wc - 1) / Wc);
+        const uint32_t cap = (uint32_t)(device_sm_count() * bulk_ctas_per_sm<0>(Wc));
+        return launch_bulk<0>(p, (int)(units < cap ? units : cap), s);
+    }
     downscale_fwd_kernel<<<fwd_grid(items), kThr, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int nparts, bool with_fwd,
                                  cudaStream_t s) {
-    if (with_fwd) downscale_bwd_kernel<true><<<nparts, kThr, 0, s>>>(p);
-    else downscale_bwd_kernel<false><<<nparts, kThr, 0, s>>>(p);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (bulk_backward_ok(p.W) && !use_register_variant()) {
+        e = with_fwd ? launch_bulk<2>(p, nparts, s) : launch_bulk<1>(p, nparts, s);
+    } else {
+        if (with_fwd) downscale_bwd_kernel<true><<<nparts, kThr, 0, s>>>(p);
+        else downscale_bwd_kernel<false><<<nparts, kThr, 0, s>>>(p);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     if (grad_taps) {
         tapgrad_reduce_kernel<<<1, kTapGrads * 16, 0, s>>>(p.partials, nparts, grad_taps);
@@ -330,7 +620,8 @@ extern "C" arol_status arol_downscale_backward_noalloc(const float* x, const flo
     if (!x || !grad_out || !taps) return AROL_ERR_INVALID;
     if (frames < 0 || height < 0 || width < 0 || height % 8 || width % 8) return AROL_ERR_INVALID;
     if ((double)frames * (height / 8) * (width / 4) >= 2147483647.0) return AROL_ERR_UNSUPPORTED;
-    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(grad_in)) & 15u) return AROL_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(grad_in) | reinterpret_cast<uintptr_t>(grad_out)) & 15u)
+        return AROL_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AROL_ERR_CUDA;
     float* scratch = nullptr;
@@ -346,7 +637,7 @@ extern "C" arol_status arol_downscale_backward_noalloc(const float* x, const flo
         }
         scratch = g_noalloc_ptr[dev];
     }
-    const int nparts = downscale_bwd_partials(device_sm_count());
+    const int nparts = downscale_bwd_partials(device_sm_count(), width);
     if (nparts > kNoAllocMaxParts) return AROL_ERR_UNSUPPORTED;   // more CTAs than the static scratch holds
     if (frames == 0 || height == 0 || width == 0) {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -359,6 +650,7 @@ extern "C" arol_status arol_downscale_backward_noalloc(const float* x, const flo
     p.taps = taps;
     p.gy = grad_out;
     p.gx = grad_in;
+    p.err = nullptr;
     p.partials = scratch;   // every CTA overwrites its own 48 slots before the reduction reads them
     p.frames = frames;
     p.H = height;

@@ -154,3 +154,21 @@ def test_autograd_function(arol):
     gt = host(taps.grad)
     assert_fir_close(gt[:24].reshape(3, 8), dHh, sHh, RTOL, "autograd dHh")
     assert_fir_close(gt[24:].reshape(3, 8), dHv, sHv, RTOL, "autograd dHv")
+
+
+def test_misaligned_gradient_buffer_falls_back(arol):
+    chain, (x,), w = W.config4(seed=6, frames=2, height=16, width=64)
+    c = arol.Chain(chain)
+    gbuf = torch.zeros(w.size + 1, device="cuda")
+    gbuf[1:] = dev(w).reshape(-1)
+    gx = torch.empty(x.shape, device="cuda")
+    gt = torch.empty(48, device="cuda")
+    c.backward(gbuf[1:].view(w.shape), [dev(x)], gx, gt)
+    gx2 = torch.empty(x.shape, device="cuda")
+    gt2 = torch.empty(48, device="cuda")
+    c.backward(dev(w), [dev(x)], gx2, gt2)
+    c.sync_status()
+    sX, (sHh, sHv) = O.chain_vjp(_abs_chain(chain), [np.abs(x)], np.abs(w.astype(np.float64)))
+    assert_fir_close(host(gx), host(gx2).astype(np.float64), sX, RTOL, "misaligned dL/dY")
+    assert_fir_close(host(gt), host(gt2).astype(np.float64),
+                     np.concatenate([sHh.reshape(-1), sHv.reshape(-1)]), RTOL, "misaligned dL/dY taps")

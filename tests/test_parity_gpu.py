@@ -255,3 +255,39 @@ def test_batch_of_random_tilers(arol):
             np.testing.assert_array_equal(host(y).view(np.uint32), ref.view(np.uint32))
         else:
             assert_fir_close(host(y), ref, fir_scale(tk, x), what="batch fir")
+
+
+_VARIANT_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_1105_4424_gb300 as A, workloads as W
+chain, (x,), w = W.config4(seed=12, frames=2, height=24, width=64)
+c = A.Chain(chain)
+xd, wd = torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda()
+y = c.run([xd]); gx = torch.empty_like(xd); gt = torch.empty(48, device="cuda")
+c.backward(wd, [xd], gx, gt); c.sync_status()
+np.savez(sys.argv[2], y=y.cpu().numpy(), gx=gx.cpu().numpy(), gt=gt.cpu().numpy())
+"""
+
+
+def test_register_and_bulk_variants_agree(arol, tmp_path):
+    """The fused chain has two kernel variants (bulk-copy pipeline, default;
+    register-direct loads, AROL_FUSED_VARIANT=regs); both match the oracle."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = {}
+    for variant in ("bulk", "regs"):
+        env = dict(os.environ)
+        if variant == "regs":
+            env["AROL_FUSED_VARIANT"] = "regs"
+        f = str(tmp_path / f"{variant}.npz")
+        subprocess.run([sys.executable, "-c", _VARIANT_SCRIPT, root, f], check=True, env=env, timeout=300)
+        outs[variant] = np.load(f)
+    chain, (x,), w = W.config4(seed=12, frames=2, height=24, width=64)
+    y64 = O.run_chain(chain, [x])[0]
+    for variant, o in outs.items():
+        assert_fir_close(o["y"], y64, fir_scale(chain, x), what=f"{variant} forward")
+    np.testing.assert_allclose(outs["bulk"]["gx"], outs["regs"]["gx"], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(outs["bulk"]["gt"], outs["regs"]["gt"], rtol=1e-4, atol=1e-5)
