@@ -116,6 +116,77 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (read-only queries)
+    every ~0.5 ms by a background thread while the timed region runs, so even
+    a few-millisecond region gets samples."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_index):
+        import ctypes
+        import threading
+        import torch
+        self.ok = False
+        self.samples = []
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            L = ctypes.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() != 0:
+                return
+            pr = torch.cuda.get_device_properties(torch_index)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+            h = ctypes.c_void_p()
+            if L.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) != 0:
+                return
+            self._reasons_fn = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                L.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            L.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+            self.max_mhz = mx.value
+            self.L, self.h, self.ctypes = L, h, ctypes
+            self.ok = True
+        except (OSError, AttributeError, RuntimeError):
+            self.ok = False
+
+    def _run(self):
+        c = self.ctypes
+        mhz, rs = c.c_uint(), c.c_ulonglong()
+        while not self._stop.is_set():
+            if self.L.nvmlDeviceGetClockInfo(self.h, 1, c.byref(mhz)) == 0 and \
+                    self._reasons_fn(self.h, c.byref(rs)) == 0:
+                self.samples.append((mhz.value, rs.value))
+            time.sleep(0.0005)
+
+    def __enter__(self):
+        import threading
+        if self.ok:
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+            t0 = time.perf_counter()
+            while not self.samples and self._thread.is_alive() and time.perf_counter() - t0 < 0.5:
+                time.sleep(0.0002)
+        return self
+
+    def __exit__(self, *exc):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join()
+
+    def summary(self):
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml"}
+
+
 # -------------------------------------------------------- rank aggregation
 
 def aggregate(elapsed_ms_per_rank, units_per_rank, steps):
@@ -185,12 +256,12 @@ def time_each_flushed(fn, reps, stream, flush):
     return ts
 
 
-def bench_batched(A, torch, stream, flush, reps):
+def bench_batched(A, torch, stream, flush, reps, tune=True):
     tasks, xs = W.config3()
     b = A.Batch(tasks)
     ins = [torch.from_numpy(x).cuda() for x in xs]
     outs = b.empty_outputs()
-    cfg = b.tune(ins, outs)
+    cfg = b.tune(ins, outs) if tune else b.config
     for _ in range(3):
         b.run(ins, outs)
         b.run_per_task(ins, outs)
@@ -324,13 +395,15 @@ def run_gpu(args):
     units = chain_units(FRAMES)
     nbytes = chain_bytes(FRAMES)
 
+    nvml = NvmlSampler(local)
     with ClockSampler(local) as clk:
         for _ in range(args.warmup):
             c.run([xd], y)
         torch.cuda.synchronize()
         barrier(world)
         torch.cuda.synchronize()
-        ms = time_loop(lambda: c.run([xd], y), args.steps, stream)
+        with nvml:
+            ms = time_loop(lambda: c.run([xd], y), args.steps, stream)
         torch.cuda.synchronize()
         barrier(world)
     all_ms = dist_max(ms, world)
@@ -363,7 +436,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(yh.numel() * 4), "ms_per_step": e2e_s * 1e3},
             "gpu_launches": args.steps,
-            "clocks": clk.summary()}
+            "clocks": nvml.summary() or dict(clk.summary(), source="nvidia-smi")}
     if rank == 0 and world == 1 and not args.no_extras:
         flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
         reps = max(5, min(args.steps, 20))
@@ -382,6 +455,26 @@ def run_gpu(args):
     return 0
 
 
+def run_case(args):
+    """One measurement alone (for profiling): prints its JSON object."""
+    import torch
+    import paper_1105_4424_gb300 as A
+    hbm, bf16, _, _ = measured_peaks()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    reps = max(1, args.steps)
+    if args.case == "batched":
+        out = bench_batched(A, torch, stream, flush, reps, tune=not args.no_tune)
+    elif args.case == "backward":
+        out = bench_backward(A, torch, stream, flush, reps)
+    elif args.case == "matmul":
+        out = bench_matmul(A, torch, stream, flush, reps, bf16)
+    else:
+        out = bench_config0(A, torch, stream, reps)
+    print(json.dumps({"case": args.case, **out}))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,11 +483,16 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["batched", "backward", "matmul", "config0"],
+                    help="run one extra measurement alone (profiling)")
+    ap.add_argument("--no-tune", action="store_true", help="batched case: keep the default launch shape")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     return run_gpu(args)
 
 

@@ -205,8 +205,9 @@ arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out);
  * previous call the device table is refreshed (one copy) before the launch. */
 arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out, void* stream);
 
-/* The same tasks with one kernel launch per task, in order, on `stream`
- * (the same kernel body; for comparison with arol_batch_run). */
+/* The same tasks with one kernel launch per task, in order, on `stream`:
+ * the same kernel over each task's own tiles, without the graph or the shared
+ * tile counter (for comparison with arol_batch_run). */
 arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* const* out, void* stream);
 
 /* Autotune the batch's tile size and persistent-grid shape by timing

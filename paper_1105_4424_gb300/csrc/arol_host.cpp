@@ -230,6 +230,17 @@ arol_status check_partition(const arol_array_desc& a, const arol_tiler& t, int r
 
 // ------------------------------------------------------------ device params
 
+FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f{};
+    f.d = d ? d : 1;
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < f.d) ++l;          // l = ceil(log2 d)
+    f.s = 31 + l;
+    const uint64_t two_s = uint64_t(1) << f.s;
+    f.m = (uint32_t)((two_s + f.d - 1) / f.d);       // < 2^32 for every d >= 1
+    return f;
+}
+
 void make_port(const arol_array_desc& a, const arol_tiler& t, int rep_rank, PortDev& p) {
     std::memset(&p, 0, sizeof p);
     int64_t s = 1;
@@ -262,13 +273,27 @@ void make_port(const arol_array_desc& a, const arol_tiler& t, int rep_rank, Port
         p.pattern[0] = (int32_t)t.pattern[0];
         p.pattern[1] = (int32_t)t.pattern[1];
     }
+    for (int k = 0; k < 4; ++k) p.shape_div[k] = make_fastdiv((uint32_t)p.shape[k]);
+    // Contiguous-row pattern: the whole pattern advances along the last array
+    // dimension (stride 1) by one element per step, so the walk is an
+    // increment with one wrap test.
+    p.fdim = a.rank - 1;
+    bool fast = p.pattern[0] == 1;                 // one pattern row
+    if (p.pattern[1] > 1) {
+        for (int k = 0; k < 4; ++k) {
+            // reduced fittings: 1 along the last dimension (0 if its extent is 1), 0 elsewhere
+            const uint32_t want = (k == p.fdim && a.shape[k] > 1) ? 1u : 0u;
+            if (p.fitting[k][1] != want) fast = false;
+        }
+    }
+    p.fast = (fast && p.stride[p.fdim] == 1) ? 1 : 0;
 }
 
 bool port_needs_wide(const PortDev& p, const arol_task_desc& d) {
     for (int k = 0; k < 4; ++k) {
         double v = p.origin[k];
         for (int q = 0; q < d.rep_rank; ++q) v += (double)p.paving[k][q] * (double)(d.rep[q] - 1);
-        if (v >= 4294967295.0) return true;
+        if (v >= 2147483647.0) return true;
     }
     return false;
 }
@@ -291,6 +316,7 @@ TaskDev make_taskdev(const arol_task_desc& d) {
         }
     }
     t.nreps = reps_of(d);
+    for (int q = 0; q < 4; ++q) t.rep_div[q] = make_fastdiv((uint32_t)t.rep[q]);
     make_port(d.in[0], dd.in_tiler[0], 4, t.in);
     make_port(d.out[0], dd.out_tiler[0], 4, t.out);
     t.elem = d.elem == AROL_ELEM_FIR ? ELEM_FIR : ELEM_COPY;
@@ -300,7 +326,22 @@ TaskDev make_taskdev(const arol_task_desc& d) {
     arol_task_desc full = dd;
     full.rep_rank = 4;
     for (int q = 0; q < 4; ++q) full.rep[q] = t.rep[q];
-    t.wide = (t.nreps >= 4294967295LL || port_needs_wide(t.in, full) || port_needs_wide(t.out, full)) ? 1 : 0;
+    t.wide = (t.nreps >= 2147483647LL || port_needs_wide(t.in, full) || port_needs_wide(t.out, full)) ? 1 : 0;
+    // Row FIR: one row per r0, step along the row per r1, one contiguous
+    // pattern of T taps, m contiguous outputs per repetition.
+    const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
+    if (d.elem == AROL_ELEM_FIR && !t.wide && d.rep_rank == 2 && d.in[0].rank == 2 && d.out[0].rank == 2 &&
+        ti.pattern_rank == 1 && to.pattern_rank == 1 && ti.paving[0][0] == 1 && ti.paving[0][1] == 0 &&
+        ti.paving[1][0] == 0 && ti.fitting[0][0] == 0 && ti.fitting[1][0] == 1 && to.paving[0][0] == 1 &&
+        to.paving[0][1] == 0 && to.paving[1][0] == 0 && to.paving[1][1] == d.fir_m && to.fitting[0][0] == 0 &&
+        to.fitting[1][0] == 1 && ti.paving[1][1] >= 1 && ti.paving[1][1] <= 32 && d.fir_T <= 32 && d.fir_m <= 16 &&
+        d.in[0].shape[1] > 1 && d.out[0].shape[1] > 1) {
+        t.rowfir = 1;
+        t.step = (int32_t)emod(ti.paving[1][1], d.in[0].shape[1]);
+        if (t.step < 1) t.rowfir = 0;
+        t.wfull = t.step * (int32_t)(d.rep[1] > 0 ? d.rep[1] - 1 : 0) + d.fir_T;
+        t.wfull_div = make_fastdiv((uint32_t)std::max(t.wfull, 1));
+    }
     return t;
 }
 
@@ -1023,6 +1064,8 @@ struct arol_batch_s {
     TileDev* dev_tiles = nullptr;
     int64_t tiles_cap = 0;
     int ntiles = 0;
+    TileDev* dev_tiles_pt = nullptr;      // the same tiles grouped by task, for one launch per task
+    std::vector<int> pt_off, pt_cnt;
     unsigned* counter = nullptr;
     float* taps_dev = nullptr;
     bool tables_built = false;
@@ -1132,6 +1175,39 @@ arol_status build_tiles(arol_batch b) {
     std::vector<TileDev> tiles;
     for (int i : order) {
         const TaskDev& t = b->host_tasks[i];
+        if (t.rowfir) {
+            // Row tiles: pieces of kRowTile repetitions of a long row, or as
+            // many whole short rows as fit kRowTile repetitions and a staged
+            // window of kWinFloats floats.
+            const int64_t R1 = t.rep[3];
+            if (R1 > kRowTile) {
+                for (int64_t r0 = 0; r0 < t.rep[2]; ++r0)
+                    for (int64_t a = 0; a < R1; a += kRowTile) {
+                        TileDev td;
+                        td.task = i;
+                        td.start = r0 * R1 + a;
+                        td.count = (int32_t)std::min<int64_t>(kRowTile, R1 - a);
+                        tiles.push_back(td);
+                    }
+            } else if (R1 > 0) {
+                // Whole rows per tile: at most kRowTile repetitions, the rows
+                // themselves (W words each) within the staged window, no row
+                // twice (rows <= H), and extents below 2^30 so that column
+                // sums stay inside the 31-bit division.
+                const int64_t W = t.in.shape[1], H = t.in.shape[0];
+                int64_t per = std::min<int64_t>(kRowTile / R1, kWinFloats / W);
+                per = std::min<int64_t>(per, H);
+                if (H >= (1 << 30) || W >= (1 << 30) || per < 2) per = 1;
+                for (int64_t r0 = 0; r0 < t.rep[2]; r0 += per) {
+                    TileDev td;
+                    td.task = i;
+                    td.start = r0 * R1;
+                    td.count = (int32_t)(std::min<int64_t>(per, t.rep[2] - r0) * R1);
+                    tiles.push_back(td);
+                }
+            }
+            continue;
+        }
         for (int64_t s = 0; s < t.nreps; s += b->tile_reps) {
             TileDev td;
             td.task = i;
@@ -1142,15 +1218,27 @@ arol_status build_tiles(arol_batch b) {
     }
     if ((int64_t)tiles.size() >= 2147483647LL) return fail(AROL_ERR_UNSUPPORTED, "batch: too many tiles");
     b->ntiles = (int)tiles.size();
+    std::vector<TileDev> by_task(tiles);
+    std::stable_sort(by_task.begin(), by_task.end(), [](const TileDev& x, const TileDev& y) { return x.task < y.task; });
+    b->pt_off.assign(b->host_tasks.size(), 0);
+    b->pt_cnt.assign(b->host_tasks.size(), 0);
+    for (size_t k = 0; k < by_task.size(); ++k) {
+        if (b->pt_cnt[by_task[k].task]++ == 0) b->pt_off[by_task[k].task] = (int)k;
+    }
     if ((int64_t)tiles.size() > b->tiles_cap) {
         free_dev(b->dev_tiles);
-        b->dev_tiles = nullptr;
+        free_dev(b->dev_tiles_pt);
+        b->dev_tiles = b->dev_tiles_pt = nullptr;
         AROL_CUDA(cudaMalloc(&b->dev_tiles, std::max<size_t>(tiles.size(), 1) * sizeof(TileDev)), "cudaMalloc(tiles)");
+        AROL_CUDA(cudaMalloc(&b->dev_tiles_pt, std::max<size_t>(tiles.size(), 1) * sizeof(TileDev)), "cudaMalloc(tiles)");
         b->tiles_cap = (int64_t)tiles.size();
     }
-    if (!tiles.empty())
+    if (!tiles.empty()) {
         AROL_CUDA(cudaMemcpy(b->dev_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice),
                   "upload tiles");
+        AROL_CUDA(cudaMemcpy(b->dev_tiles_pt, by_task.data(), by_task.size() * sizeof(TileDev), cudaMemcpyHostToDevice),
+                  "upload tiles");
+    }
     invalidate_graph(b);
     return AROL_OK;
 }
@@ -1266,10 +1354,14 @@ arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* c
     cudaStream_t s = (cudaStream_t)stream;
     arol_status st = batch_prepare(b, in, out, s);
     if (st != AROL_OK) return st;
+    // one launch of the batch kernel per task, over that task's tiles only
+    const int cap = device_sm_count() * b->ctas_per_sm;
     for (size_t i = 0; i < b->host_tasks.size(); ++i) {
-        const TaskDev& t = b->host_tasks[i];
-        if (t.nreps == 0) continue;
-        AROL_CUDA(launch_tiler_generic(t, t.elem == ELEM_FIR ? t.m : 1, s), "tiler kernel launch");
+        const int cnt = b->pt_cnt[i];
+        if (cnt == 0) continue;
+        AROL_CUDA(launch_batch_persistent(b->dev_tasks, b->dev_tiles_pt + b->pt_off[i], cnt, nullptr,
+                                          std::min(cnt, cap), b->threads, b->max_m, s),
+                  "tiler kernel launch");
     }
     return AROL_OK;
 }
@@ -1306,7 +1398,7 @@ arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* ou
     int64_t best_tile = b->tile_reps;
     int best_thr = b->threads, best_ctas = b->ctas_per_sm;
     const int64_t tiles[] = {512, 1024, 2048, 4096, 8192, 16384};
-    const int thrs[] = {128, 256, 512};
+    const int thrs[] = {128, 256};
     const int ctas[] = {2, 4, 8, 16};
     st = AROL_OK;
     for (int64_t tile : tiles) {
@@ -1356,6 +1448,7 @@ void arol_batch_destroy(arol_batch b) {
         if (b->pinned_tasks) cudaFreeHost(b->pinned_tasks);
         free_dev(b->dev_tasks);
         free_dev(b->dev_tiles);
+        free_dev(b->dev_tiles_pt);
         free_dev(b->counter);
         free_dev(b->taps_dev);
         if (cur != b->device) cudaSetDevice(cur);

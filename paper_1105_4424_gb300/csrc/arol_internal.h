@@ -13,8 +13,17 @@ namespace arol {
 // non-negative values and subtracts shape_k once on overflow.  Unused array
 // dimensions have shape 1 and zero coefficients; unused pattern dimensions
 // have extent 1.
+// n / d for every n < 2^31 as (n * m) >> s (multiply-shift division with a
+// rounded-up reciprocal; m < 2^32).  Prepared on the host by make_fastdiv.
+struct FastDiv {
+    uint32_t d, m, s, pad_;
+};
+
 struct PortDev {
     int32_t shape[4];
+    FastDiv shape_div[4];   // division by shape[k]
+    int32_t fast;           // 1: the pattern walks one contiguous dimension with step 1
+    int32_t fdim;           // that dimension
     int64_t stride[4];      // row-major element strides; 0 for unused dims
     uint32_t origin[4];
     uint32_t paving[4][4];  // [array dim][repetition dim]
@@ -27,13 +36,18 @@ enum ElemCode : int32_t { ELEM_COPY = 0, ELEM_FIR = 1 };
 // A copy or fir task for the generic tiler kernel (and one entry of a batch).
 struct TaskDev {
     int32_t rep[4];         // repetition space, last dimension fastest; unused = 1
+    FastDiv rep_div[4];
     int64_t nreps;
     PortDev in, out;
     int32_t T, m;           // fir: pattern size and outputs; copy: both = pattern size
     int32_t elem;           // ElemCode
     int32_t esize;          // copy: element size in bytes (2 or 4)
-    int32_t wide;           // 1 when base addresses need 64-bit arithmetic
-    int32_t pad_;
+    int32_t wide;           // 1 when repetition indices or base sums reach 2^31 (64-bit path)
+    int32_t rowfir;         // 1: rank-2 row FIR (paving [[1,0],[0,step]], fitting [[0],[1]], output
+                            //    paving [[1,0],[0,m]]) with step, T <= 32 and m <= 16: row-tile path
+    int32_t step;           // input paving along the row (reduced), row-FIR tasks
+    int32_t wfull;          // staged window of one whole row: step * (rep[3] - 1) + T
+    FastDiv wfull_div;      // division by wfull
     const float* taps;      // m x T (fir)
     const void* x;
     void* y;
@@ -62,9 +76,13 @@ struct DownscaleDev {
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s);
+// counter != nullptr: CTAs take tiles from the shared counter (reset by the
+// launcher); nullptr: CTA b takes tiles b, b + grid, ... (no counter).
 cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, int ntiles,
                                     unsigned* counter, int grid, int threads, int max_m,
                                     cudaStream_t s);
+constexpr int kRowTile = 256;                      // at most this many repetitions per row tile
+constexpr int kWinFloats = 32 * (kRowTile - 1) + 32;   // staged input window of a row tile (step, T <= 32)
 cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s);
 cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int nparts, bool with_fwd,
                                  cudaStream_t s);

@@ -8,11 +8,17 @@
 // walks the pattern by adding fitting columns with one conditional subtract
 // per dimension (strength-reduced modulo), all in 32-bit registers.
 #include "arol_internal.h"
+#include "ptx.h"
 
 namespace arol {
 namespace {
 
 constexpr int kThreads = 256;
+
+// n / d for n < 2^31 by multiply-shift (host-prepared reciprocal).
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
+    return (uint32_t)(((uint64_t)n * f.m) >> f.s);
+}
 
 __device__ __forceinline__ void base_index(const PortDev& p, const uint32_t r[4], bool wide, uint32_t e[4]) {
 #pragma unroll
@@ -23,12 +29,17 @@ __device__ __forceinline__ void base_index(const PortDev& p, const uint32_t r[4]
             for (int q = 0; q < 4; ++q) v += (uint64_t)p.paving[k][q] * r[q];
             e[k] = (uint32_t)(v % (uint64_t)(uint32_t)p.shape[k]);
         } else {
+            // the host guarantees v < 2^31 on this path
             uint32_t v = p.origin[k];
 #pragma unroll
             for (int q = 0; q < 4; ++q) v += p.paving[k][q] * r[q];
-            e[k] = v % (uint32_t)p.shape[k];
+            e[k] = v - fast_div(v, p.shape_div[k]) * (uint32_t)p.shape[k];
         }
     }
+}
+
+__device__ __forceinline__ uint32_t pick(const uint32_t c[4], int k) {
+    return k == 0 ? c[0] : k == 1 ? c[1] : k == 2 ? c[2] : c[3];
 }
 
 // c += fitting column `col`, modulo the shape (every term already in [0, s)).
@@ -76,28 +87,94 @@ __device__ __forceinline__ void decode_rep(const TaskDev& t, int64_t lr, bool wi
             lr = qq;
         }
     } else {
-        uint32_t l = (uint32_t)lr;
+        uint32_t l = (uint32_t)lr;   // < 2^31 on this path
 #pragma unroll
         for (int q = 3; q >= 0; --q) {
-            uint32_t d = (uint32_t)t.rep[q];
-            uint32_t qq = l / d;
-            r[q] = l - qq * d;
+            const uint32_t qq = fast_div(l, t.rep_div[q]);
+            r[q] = l - qq * (uint32_t)t.rep[q];
             l = qq;
         }
     }
 }
 
 // One repetition of a copy or fir task: gather, elementary task, scatter.
+// Contiguous-row pattern walk: offset of the row start plus a coordinate
+// along the last dimension that wraps to 0 at its extent.
+struct RowWalk {
+    int64_t base;
+    uint32_t c, extent;
+    __device__ __forceinline__ void start(const PortDev& p, const uint32_t b[4]) {
+        c = pick(b, p.fdim);
+        extent = (uint32_t)p.shape[p.fdim];
+        base = offset_of(p, b) - (int64_t)c;
+    }
+    __device__ __forceinline__ int64_t off() const { return base + (int64_t)c; }
+    __device__ __forceinline__ void next() { c = (c + 1u == extent) ? 0u : c + 1u; }
+};
+
+template <int MAXM>
+__device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_t bi[4], const uint32_t bo[4]) {
+    RowWalk wi, wo;
+    wi.start(t.in, bi);
+    wo.start(t.out, bo);
+    const int n = t.T;
+    if (t.elem == ELEM_COPY) {
+        if (t.esize == 4) {
+            const uint32_t* x = static_cast<const uint32_t*>(t.x);
+            uint32_t* y = static_cast<uint32_t*>(t.y);
+            for (int k = 0; k < n; ++k) {
+                y[wo.off()] = __ldg(x + wi.off());
+                wi.next();
+                wo.next();
+            }
+        } else {
+            const uint16_t* x = static_cast<const uint16_t*>(t.x);
+            uint16_t* y = static_cast<uint16_t*>(t.y);
+            for (int k = 0; k < n; ++k) {
+                y[wo.off()] = __ldg(x + wi.off());
+                wi.next();
+                wo.next();
+            }
+        }
+        return;
+    }
+    const float* x = static_cast<const float*>(t.x);
+    float* y = static_cast<float*>(t.y);
+    const int m = t.m;
+    float acc[MAXM];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) acc[j] = 0.f;
+    for (int k = 0; k < n; ++k) {
+        const float p = __ldg(x + wi.off());
+        wi.next();
+        const float* h = t.taps + k;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+            if (j < m) acc[j] = fmaf(__ldg(h + j * n), p, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+        if (j < m) {
+            y[wo.off()] = acc[j];
+            wo.next();
+        }
+    }
+}
+
 template <int MAXM>
 __device__ __forceinline__ void process_rep(const TaskDev& t, int64_t lr) {
     const bool wide = t.wide != 0;
-    uint32_t r[4], b[4];
+    uint32_t r[4], b[4], bo[4];
     decode_rep(t, lr, wide, r);
-    PatternWalk wi, wo;
     base_index(t.in, r, wide, b);
+    base_index(t.out, r, wide, bo);
+    if (t.in.fast && t.out.fast) {
+        process_rep_rows<MAXM>(t, b, bo);
+        return;
+    }
+    PatternWalk wi, wo;
     wi.start(b);
-    base_index(t.out, r, wide, b);
-    wo.start(b);
+    wo.start(bo);
     const int n = t.T;
     if (t.elem == ELEM_COPY) {
         if (t.esize == 4) {
@@ -150,21 +227,207 @@ __global__ void __launch_bounds__(kThreads) tiler_generic_kernel(const TaskDev t
         process_rep<MAXM>(t, lr);
 }
 
-// Persistent batched kernel: CTAs take tiles (task, repetition range) from a
-// shared counter until the list is exhausted.  No CTA waits on another.
+// ---------------------------------------------------------------------------
+// Row tile of a row-FIR task: repetitions (r0, a .. a+count-1) read the input
+// window of row r0 covering columns o1 + step*a .. o1 + step*(a+count-1) + T-1
+// (mod the row length).  The window is staged once into shared memory with
+// coalesced loads (one extra word every 32 so that lanes reading at stride
+// `step` spread over the banks); the taps are staged transposed so that one
+// 128-bit shared load feeds four outputs; each thread computes two
+// repetitions per tap fetch.
+// ---------------------------------------------------------------------------
+constexpr int kWinPad = kWinFloats + kWinFloats / 32;
+
+__device__ __forceinline__ int padw(int w) { return w + (w >> 5); }
+
+// Row tiles come in two layouts (chosen by the host when it builds tiles):
+//  * window: part of one long row (count <= kRowTile repetitions from column
+//    step a0); shared memory holds the window o1 + step*a0 + w, w <
+//    step*(count-1) + T, already wrapped, and repetition i reads words
+//    step*i .. step*i + T - 1;
+//  * rows: whole short rows (a0 == 0, rows * W <= kWinFloats); shared memory
+//    holds the rows themselves, W words each (a contiguous copy), and
+//    repetition (k, r1) walks columns (o1 + step*r1 + kk) mod W with one
+//    compare per step.
+// One thread per repetition; the m outputs of a repetition are computed in
+// NG groups of four so one 128-bit load of the transposed taps feeds four
+// FMAs.
+template <int NG, bool kRowsLayout>
+__device__ __forceinline__ void row_fir_compute(const TaskDev& t, const float* win, const float* ht, int count,
+                                                uint32_t r0, uint32_t a0, uint32_t cb) {
+    constexpr int kHt = 16;   // ht row stride (floats)
+    const int T = t.T, S = t.step, m = t.m;
+    const uint32_t R1 = (uint32_t)t.rep[3];
+    const uint32_t wi = (uint32_t)t.in.shape[1];
+    const uint32_t hout = (uint32_t)t.out.shape[0], wout = (uint32_t)t.out.shape[1];
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        float acc[4 * NG];
+#pragma unroll
+        for (int j = 0; j < 4 * NG; ++j) acc[j] = 0.f;
+        uint32_t k, r1;
+        if (kRowsLayout) {
+            k = fast_div((uint32_t)i, t.rep_div[3]);
+            r1 = (uint32_t)i - k * R1;
+            uint32_t c = cb + (uint32_t)S * r1;                 // < 2^31: extents below 2^30
+            c -= fast_div(c, t.in.shape_div[1]) * wi;
+            const int rowoff = (int)(k * wi);
+            for (int kk = 0; kk < T; ++kk) {
+                const float p = win[padw(rowoff + (int)c)];
+                c = (c + 1u == wi) ? 0u : c + 1u;
+                const float4* h4 = reinterpret_cast<const float4*>(ht + kk * kHt);
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    const float4 h = h4[g];
+                    acc[4 * g + 0] = fmaf(h.x, p, acc[4 * g + 0]);
+                    acc[4 * g + 1] = fmaf(h.y, p, acc[4 * g + 1]);
+                    acc[4 * g + 2] = fmaf(h.z, p, acc[4 * g + 2]);
+                    acc[4 * g + 3] = fmaf(h.w, p, acc[4 * g + 3]);
+                }
+            }
+        } else {
+            k = 0;
+            r1 = a0 + (uint32_t)i;
+            const int base = S * i;
+            for (int kk = 0; kk < T; ++kk) {
+                const float p = win[padw(base + kk)];
+                const float4* h4 = reinterpret_cast<const float4*>(ht + kk * kHt);
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    const float4 h = h4[g];
+                    acc[4 * g + 0] = fmaf(h.x, p, acc[4 * g + 0]);
+                    acc[4 * g + 1] = fmaf(h.y, p, acc[4 * g + 1]);
+                    acc[4 * g + 2] = fmaf(h.z, p, acc[4 * g + 2]);
+                    acc[4 * g + 3] = fmaf(h.w, p, acc[4 * g + 3]);
+                }
+            }
+        }
+        // output row (o0 + r0 + k) mod H_out and first column (o1 + m*r1) mod W_out
+        const uint32_t ov = t.out.origin[0] + r0 + k;            // < 2^31: checked on the host
+        const uint32_t orow = ov - fast_div(ov, t.out.shape_div[0]) * hout;
+        const uint64_t v = (uint64_t)t.out.origin[1] + (uint64_t)m * r1;
+        uint32_t c = v < 0x7fffffffull ? (uint32_t)v - fast_div((uint32_t)v, t.out.shape_div[1]) * wout
+                                       : (uint32_t)(v % wout);
+        float* yrow = static_cast<float*>(t.y) + (int64_t)orow * wout;
+#pragma unroll
+        for (int j = 0; j < 4 * NG; ++j) {
+            if (j < m) {
+                yrow[c] = acc[j];
+                c = (c + 1u == wout) ? 0u : c + 1u;
+            }
+        }
+    }
+}
+
+// Stages the window layout: words (o1 + step*a + w) mod W of input row r, w < len.
+__device__ __forceinline__ void stage_window(const TaskDev& t, uint32_t row, uint32_t a, int len, float* win) {
+    const uint32_t wi = (uint32_t)t.in.shape[1];
+    uint32_t v = t.in.origin[1] + (uint32_t)t.step * a;       // < 2^31: checked on the host
+    const uint32_t cb = v - fast_div(v, t.in.shape_div[1]) * wi;
+    const float* xr = static_cast<const float*>(t.x) + (int64_t)row * wi;
+    if ((int)wi >= len) {
+        for (int w = threadIdx.x; w < len; w += blockDim.x) {
+            uint32_t c = cb + (uint32_t)w;
+            c = c >= wi ? c - wi : c;
+            ptx::cp_async4(win + padw(w), xr + c);
+        }
+    } else {
+        for (int w = threadIdx.x; w < len; w += blockDim.x) ptx::cp_async4(win + padw(w), xr + (cb + (uint32_t)w) % wi);
+    }
+}
+
+template <bool kRowsLayout>
+__device__ __forceinline__ void row_fir_dispatch(const TaskDev& t, const float* win, const float* ht, int count,
+                                                 uint32_t r0, uint32_t a0, uint32_t cb) {
+    switch ((t.m + 3) >> 2) {
+    case 1: row_fir_compute<1, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
+    case 2: row_fir_compute<2, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
+    case 3: row_fir_compute<3, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
+    default: row_fir_compute<4, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
+    }
+}
+
+__device__ __forceinline__ void row_fir_tile(const TaskDev& t, int task, int64_t start, int count, float* win,
+                                             float* ht, int* s_task) {
+    constexpr int kHt = 16;
+    const uint32_t R1 = (uint32_t)t.rep[3];
+    const int T = t.T, m = t.m;
+    // taps, transposed and zero padded (ht[k * 16 + j] = H[j, k]); kept across
+    // consecutive tiles of the same task.  Every thread reads the same
+    // *s_task: it is written only between two barriers.
+    if (*s_task != task) {
+        for (int i = threadIdx.x; i < T * kHt; i += blockDim.x) {
+            const int k = i >> 4, j = i & 15;
+            if (j < m) ptx::cp_async4(ht + i, t.taps + j * T + k);
+            else ht[i] = 0.f;
+        }
+    }
+    const uint32_t r0 = fast_div((uint32_t)start, t.rep_div[3]);
+    const uint32_t a0 = (uint32_t)start - r0 * R1;
+    const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
+    uint32_t v = t.in.origin[0] + r0;                          // < 2^31: checked on the host
+    const uint32_t row0 = v - fast_div(v, t.in.shape_div[0]) * hin;
+    // The host builds multi-row tiles only as whole rows (count = rows * R1,
+    // rows >= 2, rows <= H, rows * W <= kWinFloats); every other row tile lies
+    // within one row (count <= R1).
+    const bool rows_layout = a0 == 0u && (uint32_t)count > R1;
+    if (rows_layout) {
+        // whole rows, copied as they lie in memory (rows may wrap past H)
+        const int rows = (int)((uint32_t)count / R1);
+        const float* x = static_cast<const float*>(t.x);
+        const int64_t plane = (int64_t)hin * wi;
+        const int64_t g0 = (int64_t)row0 * wi;
+        const int total = rows * (int)wi;
+        for (int w = threadIdx.x; w < total; w += blockDim.x) {
+            int64_t gofs = g0 + w;
+            if (gofs >= plane) gofs -= plane;
+            ptx::cp_async4(win + padw(w), x + gofs);
+        }
+    } else {
+        stage_window(t, row0, a0, t.step * (count - 1) + T, win);
+    }
+    ptx::cp_async_wait_all();   // this thread's copies (window and taps) have landed
+    __syncthreads();            // ... and everyone else's
+    if (rows_layout) row_fir_dispatch<true>(t, win, ht, count, r0, 0u, t.in.origin[1]);
+    else row_fir_dispatch<false>(t, win, ht, count, r0, a0, 0u);
+    // Every thread read *s_task before the barrier above; the next read comes
+    // after the barrier below, so this write is seen consistently.
+    if (threadIdx.x == 0) *s_task = task;
+    __syncthreads();   // the next tile overwrites win (and possibly ht)
+}
+
+// Persistent batched kernel.  With a counter, CTAs take tiles (task,
+// repetition range) from it until the list is exhausted; without one, CTA b
+// takes tiles b, b + gridDim.x, ...  No CTA ever waits on another.
 template <int MAXM>
-__global__ void __launch_bounds__(512) batch_persistent_kernel(const TaskDev* __restrict__ tasks,
+__global__ void __launch_bounds__(256, 1) batch_persistent_kernel(const TaskDev* __restrict__ tasks,
                                                                const TileDev* __restrict__ tiles,
                                                                int ntiles, unsigned* counter) {
     __shared__ int s_tile;
+    __shared__ int s_task;   // task whose taps s_ht holds
+    constexpr bool kRows = MAXM <= 16;
+    __shared__ __align__(16) float s_win[kRows ? kWinPad : 1];
+    __shared__ __align__(16) float s_ht[kRows ? 32 * 16 : 4];
+    if (threadIdx.x == 0) s_task = -1;
+    __syncthreads();
+    int next = blockIdx.x;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int ti = s_tile;
-        __syncthreads();
+        int ti;
+        if (counter) {
+            if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
+            __syncthreads();
+            ti = s_tile;
+            __syncthreads();
+        } else {
+            ti = next;
+            next += gridDim.x;
+        }
         if (ti >= ntiles) break;
         const TileDev tile = tiles[ti];
         const TaskDev& t = tasks[tile.task];
+        if (kRows && t.rowfir) {
+            row_fir_tile(t, tile.task, tile.start, tile.count, s_win, s_ht, &s_task);
+            continue;
+        }
         const int64_t end = tile.start + tile.count;
         for (int64_t lr = tile.start + threadIdx.x; lr < end; lr += blockDim.x) process_rep<MAXM>(t, lr);
     }
@@ -277,8 +540,10 @@ cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s) {
 
 cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, int ntiles, unsigned* counter,
                                     int grid, int threads, int max_m, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
+    if (counter) {
+        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
     if (ntiles == 0) return cudaSuccess;
     if (max_m <= 4) batch_persistent_kernel<4><<<grid, threads, 0, s>>>(tasks, tiles, ntiles, counter);
     else if (max_m <= 8) batch_persistent_kernel<8><<<grid, threads, 0, s>>>(tasks, tiles, ntiles, counter);

@@ -291,3 +291,42 @@ def test_register_and_bulk_variants_agree(arol, tmp_path):
         assert_fir_close(o["y"], y64, fir_scale(chain, x), what=f"{variant} forward")
     np.testing.assert_allclose(outs["bulk"]["gx"], outs["regs"]["gx"], rtol=1e-5, atol=1e-6)
     np.testing.assert_allclose(outs["bulk"]["gt"], outs["regs"]["gt"], rtol=1e-4, atol=1e-5)
+
+
+def test_large_indices_near_the_32bit_limit(arol):
+    """Repetition indices up to 7e5 and base sums just under 2^31 (the 32-bit
+    multiply-shift division path) with awkward extents, and a variant just
+    over it (64-bit path), both bit-exact against the C oracle."""
+    g = W.rng(111)
+    x = g.random((7, 999983), dtype=np.float32)
+    for pav in (3000, 3100):            # 3000 * 700000 < 2^31 <= 3100 * 700000
+        inp = W.port((7, 999983), (5, 999980), ((3, 0), (0, pav)), ((0,), (1,)), (3,))
+        out = W.port((3, 700001 * 3), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))
+        tk = W.task((3, 700001), "copy", [inp], [out])
+        _, y = run1(arol, tk, [x])
+        np.testing.assert_array_equal(y.view(np.uint32), C.run_task(tk, [x])[0].view(np.uint32))
+
+
+def test_batch_row_fir_tasks_with_shifted_origins(arol):
+    """Row-FIR tasks (the row-tile path) whose input and output origins are
+    shifted, negative or past the array (so reads and writes wrap), long rows
+    split across tiles and short rows packed into one tile."""
+    g = W.rng(112)
+    tasks, xs = [], []
+    for (h, w, T, m, S) in [(5, 3000, 7, 2, 3), (9, 40, 32, 16, 32), (3, 17, 5, 1, 1), (40, 64, 12, 5, 6),
+                            (2, 999, 31, 4, 17), (1, 8, 3, 3, 3)]:
+        base = W.fir_row_task(h, w, T, m, S, (g.standard_normal((m, T)) / T).astype(np.float32))
+        inp = dict(base["inputs"][0], origin=(int(g.integers(-50, 50)), int(g.integers(-5000, 5000))))
+        out = dict(base["outputs"][0], origin=(int(g.integers(-50, 50)), int(g.integers(-5000, 5000))))
+        tasks.append(W.task(base["rep"], "fir", [inp], [out], base["taps"]))
+        xs.append(g.random((h, w), dtype=np.float32))
+    b = arol.Batch(tasks)
+    outs = b.empty_outputs()
+    b.run([dev(x) for x in xs], outs)
+    outs2 = b.empty_outputs()
+    b.run_per_task([dev(x) for x in xs], outs2)
+    torch.cuda.synchronize()
+    for tk, x, y, y2 in zip(tasks, xs, outs, outs2):
+        ref = C.run_task(tk, [x])[0]
+        assert_fir_close(host(y), ref, fir_scale(tk, x, C.run_chain), what="row fir batch")
+        np.testing.assert_array_equal(host(y), host(y2))
