@@ -53,6 +53,24 @@ def chain_bytes(frames, height=HEIGHT, width=WIDTH):
     return 4 * frames * height * width + 4 * frames * (height // 8 * 3) * (width // 8 * 3)
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the headline kernel from an ncu capture, with the source version it was
+# taken on; reported as null once the kernel source differs.
+HEADLINE_TRAFFIC = {"source": "paper_1105_4424_gb300/csrc/k_downscale.cu", "sha256_prefix": "d34bf2bb6411f4eb",
+                    "bytes": 530879744 + 64140032}
+
+
+def headline_traffic():
+    import hashlib
+    path = os.path.join(ROOT, HEADLINE_TRAFFIC["source"])
+    try:
+        with open(path, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return HEADLINE_TRAFFIC["bytes"] if digest.startswith(HEADLINE_TRAFFIC["sha256_prefix"]) else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -209,11 +227,13 @@ def dist_setup(n_gpus):
 
 
 def dist_max(value, world):
+    """Every rank's value (all-gather), on the device the backend needs."""
     if world == 1:
         return [value]
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     out = [torch.zeros_like(t) for _ in range(world)]
     dist.all_gather(out, t)
     return [float(o.item()) for o in out]
@@ -431,8 +451,9 @@ def run_gpu(args):
                        "unique_bytes_per_step_per_gpu": nbytes,
                        "l2": "inputs (531 MB per step) exceed L2 (126 MB): no flush; extras flush L2 with a 256 MB write",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "downscale_fwd_kernel", "achieved": achieved, "peak": hbm,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None},
+            "roofline": {"bound": "hbm", "kernel": "downscale_bulk_kernel<0>", "achieved": achieved, "peak": hbm,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": headline_traffic(), "algorithmic_bytes": nbytes},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(yh.numel() * 4), "ms_per_step": e2e_s * 1e3},
             "gpu_launches": args.steps,
