@@ -3,7 +3,8 @@
 // The repetitive task has repetition space (M/128, N/128): repetition r reads
 // the 128 x K row panel r0 of A and the K x 128 column panel r1 of B, and its
 // output tiler writes the 128 x 128 tile (r0, r1) of C (a partition of C).
-// One CTA computes BN/128 neighbouring repetitions (a 128 x BN tile):
+// A tile is BN/128 neighbouring repetitions (128 x BN outputs); one
+// persistent CTA per SM walks the tiles:
 //
 //   * TMA (cp.async.bulk.tensor, 128-byte swizzle) streams 128 x 64 slices of
 //     A (K-major) and 64 x BN slices of B (N-major, as B is stored row-major)
@@ -11,8 +12,9 @@
 //   * one elected thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32,
 //     M = 128, N = BN, K = 16) with the accumulator in tensor memory; each
 //     stage is released by tcgen05.commit onto its "empty" barrier;
-//   * after the last k-block a final commit releases the epilogue: the four
-//     warps read their 32 TMEM lanes (rows) with tcgen05.ld and store f32 C.
+//   * after a tile's last k-block a commit hands its TMEM accumulator (one of
+//     two) to four epilogue warps, which read their 32 lanes (rows) with
+//     tcgen05.ld and store f32 C while the next tile accumulates in the other.
 //
 // Every mbarrier wait is bounded (iteration count and wall time).  A wait that
 // gives up sets a bit in *err and the kernel drains what it issued, frees its
@@ -45,6 +47,10 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // Bounded wait for the completion of the phase with the given parity.
@@ -126,11 +132,15 @@ struct Cfg {
     static constexpr int kBBytes = BK * BN * 2;
     static constexpr int kStageBytes = kABytes + kBBytes;
     static constexpr int kSmem = STAGES * kStageBytes + 1024 + 256;
-    static constexpr uint32_t kTmemCols = BN;   // power of two >= 32
+    static constexpr uint32_t kTmemCols = 2 * BN;   // two accumulators, a power of two <= 512
+    static constexpr int kThreads = 192;            // TMA warp, MMA warp, 4 epilogue warps
 };
 
+// Persistent CTAs (one per SM) walk the output tiles t = blockIdx.x + i * gridDim.x
+// (N-fastest order).  Tile i accumulates into TMEM buffer i & 1, so the four
+// epilogue warps drain tile i while the MMA warp already fills tile i + 1.
 template <int BN>
-__global__ void __launch_bounds__(128, 1) matmul_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(192, 1) matmul_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB, float* __restrict__ C,
                                                            int M, int N, int K, unsigned* __restrict__ err) {
     using G = Cfg<BN>;
@@ -139,21 +149,26 @@ __global__ void __launch_bounds__(128, 1) matmul_tc_kernel(const __grid_constant
     uint8_t* sA = smem;
     uint8_t* sB = smem + STAGES * G::kABytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * G::kStageBytes);
-    // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
-    int* progress = reinterpret_cast<int*>(tmem_slot + 1);   // [0] k-blocks issued, [1] k-blocks consumed
+    // bars: [0,S) full, [S,2S) empty, 2S + a: accumulator a ready, 2S + 2 + a: accumulator a free
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+    int* progress = reinterpret_cast<int*>(tmem_slot + 1);   // [0] k-blocks issued by TMA, [1] consumed by MMA
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nkb = K / BK;
-    const uint32_t full0 = smem_addr(bars), empty0 = smem_addr(bars + STAGES), done = smem_addr(bars + 2 * STAGES);
+    const int tiles_n = N / BN;
+    const int ntiles = (M / BM) * tiles_n;
+    const uint32_t full0 = smem_addr(bars), empty0 = smem_addr(bars + STAGES);
+    const uint32_t accf0 = smem_addr(bars + 2 * STAGES), acce0 = smem_addr(bars + 2 * STAGES + 2);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(full0 + 8 * st, 1);
+            mbar_init(empty0 + 8 * st, 1);
         }
-        mbar_init(done, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf0 + 8 * a, 1);
+            mbar_init(acce0 + 8 * a, 4);
+        }
         progress[0] = 0;
         progress[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -170,74 +185,105 @@ __global__ void __launch_bounds__(128, 1) matmul_tc_kernel(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        int kb = 0;
-        for (; kb < nkb; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ((kb / STAGES) & 1) ^ 1)) {
-                atomicOr(err, 1u);
-                break;
-            }
-            const uint32_t fb = full0 + 8 * s;
-            mbar_expect_tx(fb, G::kStageBytes);
-            tma_load_2d(smem_addr(sA + s * G::kABytes), &tmA, kb * BK, m0, fb);
+    if (warp == 0) {
+        // ---------------- TMA producer (one lane)
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int st = (int)(g % STAGES);
+                    if (g >= (uint32_t)STAGES && !mbar_wait(empty0 + 8 * st, ((g / STAGES) & 1u) ^ 1u)) {
+                        atomicOr(err, 1u);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = full0 + 8 * st;
+                    mbar_expect_tx(fb, G::kStageBytes);
+                    tma_load_2d(smem_addr(sA + st * G::kABytes), &tmA, kb * BK, m0, fb);
 #pragma unroll
-            for (int c = 0; c < BN / 64; ++c)
-                tma_load_2d(smem_addr(sB + s * G::kBBytes + c * (BK * 128)), &tmB, n0 + 64 * c, kb * BK, fb);
+                    for (int c = 0; c < BN / 64; ++c)
+                        tma_load_2d(smem_addr(sB + st * G::kBBytes + c * (BK * 128)), &tmB, n0 + 64 * c, kb * BK, fb);
+                }
+            }
+            progress[0] = (int)g;
         }
-        progress[0] = kb;
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = instr_desc(BN);
-        int kb = 0;
-        for (; kb < nkb; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1)) {
-                atomicOr(err, 2u);
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (one lane)
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc(BN);
+            uint32_t g = 0;
+            int i = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+                const int acc = i & 1;
+                if (i >= 2 && !mbar_wait(acce0 + 8 * acc, (((uint32_t)i >> 1) & 1u) ^ 1u)) {
+                    atomicOr(err, 8u);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int st = (int)(g % STAGES);
+                    if (!mbar_wait(full0 + 8 * st, (g / STAGES) & 1u)) {
+                        atomicOr(err, 2u);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_addr(sA + st * G::kABytes);
+                    const uint32_t b0 = smem_addr(sB + st * G::kBBytes);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        // A: K-major rows of 128 B, 8-row groups 1024 B apart; +32 B per 16 k.
+                        const uint64_t ad = smem_desc(a0 + kk * 32, 16, 1024);
+                        // B: N-major, 64-column chunks 8 KB apart (LBO), 8-row k groups
+                        // 1024 B apart (SBO); +16 rows of 128 B per 16 k.
+                        const uint64_t bd = smem_desc(b0 + kk * 16 * 128, BK * 128, 1024);
+                        mma_bf16(d, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(empty0 + 8 * st);
+                }
+                mma_commit(accf0 + 8 * acc);   // accumulator ready once these MMAs complete
+            }
+            progress[1] = (int)g;
+        }
+    } else {
+        // ---------------- epilogue: warp w reads TMEM lanes 32 * (w % 4) .. + 31
+        const int quad = warp & 3;
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int acc = i & 1;
+            if (!mbar_wait(accf0 + 8 * acc, ((uint32_t)i >> 1) & 1u)) {
+                if (lane == 0) atomicOr(err, 4u);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_addr(sA + s * G::kABytes);
-            const uint32_t b0 = smem_addr(sB + s * G::kBBytes);
+            const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+            const int row = m0 + quad * 32 + lane;
+            float* crow = C + (int64_t)row * N + n0;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN + c), v);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                // A: K-major rows of 128 B, 8-row groups 1024 B apart; +32 B per 16 k.
-                const uint64_t ad = smem_desc(a0 + kk * 32, 16, 1024);
-                // B: N-major, 64-column chunks 8 KB apart (LBO), 8-row k groups 1024 B apart
-                // (SBO); +16 rows of 128 B per 16 k.
-                const uint64_t bd = smem_desc(b0 + kk * 16 * 128, BK * 128, 1024);
-                mma_bf16(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                for (int q = 0; q < 8; ++q)
+                    *reinterpret_cast<float4*>(crow + c + 4 * q) =
+                        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
-            mma_commit(empty0 + 8 * s);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * acc);   // this warp is done with accumulator acc
         }
-        progress[1] = kb;
-        mma_commit(done);
     }
     __syncwarp();
-
-    // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.
-    const bool ready = mbar_wait(done, 0);
-    if (!ready && lane == 0) atomicOr(err, 4u);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ready) {
-        const int row = m0 + warp * 32 + lane;
-        float* crow = C + (int64_t)row * N + n0;
-#pragma unroll 1
-        for (int c = 0; c < BN; c += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                *reinterpret_cast<float4*>(crow + c + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     // On an error path, let every copy that was issued but not consumed land
     // before the CTA's shared memory goes away.
     if (threadIdx.x == 0) {
-        for (int kb = progress[1]; kb < progress[0]; ++kb) mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
+        for (int g = progress[1]; g < progress[0]; ++g) mbar_wait(full0 + 8 * (g % STAGES), (g / STAGES) & 1);
     }
     if (warp == 2) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -284,8 +330,9 @@ cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, float* C, in
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid(N / BN, M / BM);
-    matmul_tc_kernel<BN><<<grid, 128, Cfg<BN>::kSmem, s>>>(ma, mb, C, M, N, K, err);
+    const int ntiles = (M / BM) * (N / BN);
+    const int grid = ntiles < device_sm_count() ? ntiles : device_sm_count();
+    matmul_tc_kernel<BN><<<grid, Cfg<BN>::kThreads, Cfg<BN>::kSmem, s>>>(ma, mb, C, M, N, K, err);
     return cudaGetLastError();
 }
 
