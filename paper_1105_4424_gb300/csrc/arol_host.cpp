@@ -433,6 +433,8 @@ bool match_pass(const arol_task_desc& d, int axis, Pass* ps) {
 
 // ===================================================================== tasks
 
+constexpr int kPipeChunks = 8;   // frame chunks of the host-buffer pipeline
+
 struct arol_task_s {
     int kind = 0;                        // 0 single, 1 chain
     int kernel = 0;                      // arol_task_info_t.kernel
@@ -461,6 +463,10 @@ struct arol_task_s {
     // host-buffer staging
     void* stage_in[2] = {nullptr, nullptr};
     void* stage_out = nullptr;
+    bool pipe_ready = false;             // chunked host-buffer pipeline (fused downscaler)
+    cudaStream_t pipe_stream[2] = {nullptr, nullptr};
+    cudaEvent_t pipe_in[8] = {}, pipe_done[8] = {};
+    cudaEvent_t pipe_last = nullptr;
     arol_task_info_t info{};
 };
 
@@ -814,23 +820,88 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
     return AROL_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Host buffers through the fused downscaler, pipelined over frame chunks on
+// three streams: the copy of chunk c+1 to the device overlaps the kernel on
+// chunk c and the copy of chunk c-1 back to the host.  `s` (the caller's
+// stream) carries the input copies; the caller's prior work on it is ordered
+// before everything, and the call returns after the last output copy.
+arol_status run_host_pipelined(arol_task t, const void* hin, void* hout, cudaStream_t s) {
+    if (!t->pipe_ready) {
+        AROL_CUDA(cudaStreamCreateWithFlags(&t->pipe_stream[0], cudaStreamNonBlocking), "cudaStreamCreate");
+        AROL_CUDA(cudaStreamCreateWithFlags(&t->pipe_stream[1], cudaStreamNonBlocking), "cudaStreamCreate");
+        for (int c = 0; c < kPipeChunks; ++c) {
+            AROL_CUDA(cudaEventCreateWithFlags(&t->pipe_in[c], cudaEventDisableTiming), "cudaEventCreate");
+            AROL_CUDA(cudaEventCreateWithFlags(&t->pipe_done[c], cudaEventDisableTiming), "cudaEventCreate");
+        }
+        AROL_CUDA(cudaEventCreateWithFlags(&t->pipe_last, cudaEventDisableTiming), "cudaEventCreate");
+        t->pipe_ready = true;
+    }
+    const float* taps = nullptr;
+    arol_status st = ensure_taps(t, s, &taps);
+    if (st != AROL_OK) return st;
+    if ((st = ensure_err(t, s)) != AROL_OK) return st;
+    const int64_t F = t->ds_frames;
+    const int nch = (int)std::min<int64_t>(kPipeChunks, F);
+    const int64_t in_frame = (int64_t)t->ds_H * t->ds_W, out_frame = (int64_t)(t->ds_H / 8 * 3) * (t->ds_W / 8 * 3);
+    cudaStream_t ks = t->pipe_stream[0], os = t->pipe_stream[1];
+    // the compute and output streams start after everything already queued on s
+    AROL_CUDA(cudaEventRecord(t->pipe_last, s), "cudaEventRecord");
+    AROL_CUDA(cudaStreamWaitEvent(ks, t->pipe_last, 0), "cudaStreamWaitEvent");
+    AROL_CUDA(cudaStreamWaitEvent(os, t->pipe_last, 0), "cudaStreamWaitEvent");
+    for (int c = 0; c < nch; ++c) {
+        const int64_t f0 = F * c / nch, f1 = F * (c + 1) / nch;
+        const float* hx = static_cast<const float*>(hin) + f0 * in_frame;
+        float* dx = static_cast<float*>(t->stage_in[0]) + f0 * in_frame;
+        float* dy = static_cast<float*>(t->stage_out) + f0 * out_frame;
+        AROL_CUDA(cudaMemcpyAsync(dx, hx, (size_t)((f1 - f0) * in_frame) * 4, cudaMemcpyHostToDevice, s),
+                  "copy input chunk to device");
+        AROL_CUDA(cudaEventRecord(t->pipe_in[c], s), "cudaEventRecord");
+        AROL_CUDA(cudaStreamWaitEvent(ks, t->pipe_in[c], 0), "cudaStreamWaitEvent");
+        DownscaleDev p = ds_params(t, taps);
+        p.x = dx;
+        p.y = dy;
+        p.frames = f1 - f0;
+        AROL_CUDA(launch_downscale_fwd(p, ks), "downscale kernel launch");
+        AROL_CUDA(cudaEventRecord(t->pipe_done[c], ks), "cudaEventRecord");
+        AROL_CUDA(cudaStreamWaitEvent(os, t->pipe_done[c], 0), "cudaStreamWaitEvent");
+        AROL_CUDA(cudaMemcpyAsync(static_cast<float*>(hout) + f0 * out_frame, dy, (size_t)((f1 - f0) * out_frame) * 4,
+                                  cudaMemcpyDeviceToHost, os),
+                  "copy output chunk to host");
+    }
+    AROL_CUDA(cudaStreamSynchronize(os), "synchronize");
+    AROL_CUDA(cudaStreamSynchronize(s), "synchronize");
+    return AROL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* const* host_out, void* stream) {
     if (!t || !host_in || !host_out) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const arol_task_desc& d0 = t->descs[0];
     const arol_array_desc& od = t->descs.back().out[0];
     arol_status st;
+    const bool pipelined = t->kind == 1 && t->kernel == 1 && t->ds_frames >= 2;
     void* dins[2] = {nullptr, nullptr};
     for (int i = 0; i < d0.n_in; ++i) {
         if (!host_in[i]) return fail(AROL_ERR_INVALID, "null input pointer %d", i);
         if ((st = dev_alloc(t, &t->stage_in[i], array_bytes(d0.in[i]), "cudaMalloc(staging)")) != AROL_OK) return st;
-        AROL_CUDA(cudaMemcpyAsync(t->stage_in[i], host_in[i], array_bytes(d0.in[i]), cudaMemcpyHostToDevice, s),
-                  "copy input to device");
+        if (!pipelined)
+            AROL_CUDA(cudaMemcpyAsync(t->stage_in[i], host_in[i], array_bytes(d0.in[i]), cudaMemcpyHostToDevice, s),
+                      "copy input to device");
         dins[i] = t->stage_in[i];
     }
     if (!host_out[0]) return fail(AROL_ERR_INVALID, "null output pointer");
     if ((st = dev_alloc(t, &t->stage_out, array_bytes(od), "cudaMalloc(staging)")) != AROL_OK) return st;
     void* douts[1] = {t->stage_out};
+    if (t->kind == 1 && t->kernel == 1 && t->ds_frames >= 2)
+        return run_host_pipelined(t, host_in[0], host_out[0], s);
     if ((st = arol_task_run(t, dins, douts, stream)) != AROL_OK) return st;
     AROL_CUDA(cudaMemcpyAsync(host_out[0], t->stage_out, array_bytes(od), cudaMemcpyDeviceToHost, s),
               "copy output to host");
@@ -1040,6 +1111,15 @@ void arol_task_destroy(arol_task t) {
         free_dev(t->stage_in[0]);
         free_dev(t->stage_in[1]);
         free_dev(t->stage_out);
+        if (t->pipe_ready) {
+            cudaStreamDestroy(t->pipe_stream[0]);
+            cudaStreamDestroy(t->pipe_stream[1]);
+            for (int c = 0; c < 8; ++c) {
+                cudaEventDestroy(t->pipe_in[c]);
+                cudaEventDestroy(t->pipe_done[c]);
+            }
+            cudaEventDestroy(t->pipe_last);
+        }
         if (cur != t->device) cudaSetDevice(cur);
     }
     delete t;
