@@ -913,14 +913,21 @@ arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* co
 
 namespace {
 
-arol_status ensure_partials(arol_task t, int64_t n) {
+// Per-CTA tap-gradient partials (n floats) followed by one word, the ticket
+// of the last-CTA reduction; zeroed once here, left at zero by every launch.
+arol_status ensure_partials(arol_task t, int64_t n, cudaStream_t s) {
     if (t->partials && t->partials_cap >= n) return AROL_OK;
+    if (t->partials) AROL_CUDA(cudaStreamSynchronize(s), "synchronize");   // earlier launches may still use it
     free_dev(t->partials);
     t->partials = nullptr;
-    arol_status st = dev_alloc(t, (void**)&t->partials, (size_t)n * sizeof(float), "cudaMalloc(tap-gradient partials)");
-    if (st == AROL_OK) t->partials_cap = n;
-    return st;
+    arol_status st = dev_alloc(t, (void**)&t->partials, (size_t)(n + 4) * sizeof(float), "cudaMalloc(tap-gradient partials)");
+    if (st != AROL_OK) return st;
+    AROL_CUDA(cudaMemsetAsync(t->partials, 0, (size_t)(n + 4) * sizeof(float), s), "clear tap-gradient partials");
+    t->partials_cap = n;
+    return AROL_OK;
 }
+
+unsigned* partials_ticket(arol_task t) { return reinterpret_cast<unsigned*>(t->partials + t->partials_cap); }
 
 // Owner-computes inverse of an input tiler: for every input element e, the
 // list of flat (r * T + k) indices whose gather visits e, in increasing order.
@@ -986,7 +993,7 @@ arol_status backward_generic_task(arol_task t, size_t i, const float* taps, cons
     td.x = x;
     int64_t chunk = 0;
     const int nb = tiler_bwd_blocks(td.nreps, &chunk);
-    if (gtaps && d.elem == AROL_ELEM_FIR && (st = ensure_partials(t, (int64_t)nb * td.m * td.T)) != AROL_OK) return st;
+    if (gtaps && d.elem == AROL_ELEM_FIR && (st = ensure_partials(t, (int64_t)nb * td.m * td.T, s)) != AROL_OK) return st;
     AROL_CUDA(launch_tiler_bwd(td, gx ? t->inv_start[i] : nullptr, gx ? t->inv_list[i] : nullptr, gx, gy,
                                d.elem == AROL_ELEM_FIR ? gtaps : nullptr, t->partials, nb, chunk, s),
               "tiler backward launch");
@@ -1009,13 +1016,14 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
     if ((st = ensure_taps(t, s, &taps)) != AROL_OK) return st;
     if (t->kind == 1 && t->kernel == 1 && aligned16(saved_in[0]) && aligned16(grad_in) && aligned16(grad_out)) {
         const int nparts = downscale_bwd_partials(device_sm_count(), t->ds_W);
-        if ((st = ensure_partials(t, (int64_t)nparts * 48)) != AROL_OK) return st;
+        if ((st = ensure_partials(t, (int64_t)nparts * 48, s)) != AROL_OK) return st;
         if ((st = ensure_err(t, s)) != AROL_OK) return st;
         DownscaleDev p = ds_params(t, taps);
         p.x = (const float*)saved_in[0];
         p.gy = (const float*)grad_out;
         p.gx = (float*)grad_in;
         p.partials = t->partials;
+        p.ticket = partials_ticket(t);
         AROL_CUDA(launch_downscale_bwd(p, grad_taps, nparts, false, s), "downscale backward launch");
         return AROL_OK;
     }
@@ -1069,7 +1077,7 @@ arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* gr
     if (st != AROL_OK) return st;
     if ((st = ensure_taps(t, s, &taps)) != AROL_OK) return st;
     const int nparts = downscale_bwd_partials(device_sm_count(), t->ds_W);
-    if ((st = ensure_partials(t, (int64_t)nparts * 48)) != AROL_OK) return st;
+    if ((st = ensure_partials(t, (int64_t)nparts * 48, s)) != AROL_OK) return st;
     if ((st = ensure_err(t, s)) != AROL_OK) return st;
     DownscaleDev p = ds_params(t, taps);
     p.x = (const float*)in[0];
@@ -1077,6 +1085,7 @@ arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* gr
     p.gy = (const float*)grad_out;
     p.gx = (float*)grad_in;
     p.partials = t->partials;
+    p.ticket = partials_ticket(t);
     AROL_CUDA(launch_downscale_bwd(p, grad_taps, nparts, true, s), "downscale fwd_bwd launch");
     return AROL_OK;
 }

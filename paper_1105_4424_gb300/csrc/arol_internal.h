@@ -70,6 +70,8 @@ struct DownscaleDev {
     float* gx;              // backward: dL/dx
     float* partials;        // backward: per-CTA tap-gradient partials (48 floats each)
     unsigned* err;          // nullable: bit set when a bounded wait gives up
+    float* grad_taps;       // backward: 48 tap gradients, written by the last CTA (nullable)
+    unsigned* ticket;       // backward: CTAs done (zero before the launch; the last CTA resets it)
     int64_t frames;
     int32_t H, W;
 };

@@ -33,6 +33,7 @@ namespace {
 constexpr int kThr = 256;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTapGrads = 48;   // 3x8 horizontal + 3x8 vertical
+constexpr int kTapGroups = 8;   // thread groups of the last-CTA tap-gradient reduction
 
 __device__ __forceinline__ float4 ld_stream4(const float* p) {
     float4 v;
@@ -265,16 +266,176 @@ __global__ void __launch_bounds__(kTapGrads * 16) tapgrad_reduce_kernel(const fl
 // flight per SM); the backward needs ~170, so one CTA of 11 consumer warps
 // owns the SM with a deeper ring.
 template <int kMode> struct BulkCfg {
-    static constexpr int kCWarps = kMode == 0 ? 8 : 11;
-    static constexpr int kStages = kMode == 0 ? 3 : 5;
+    static constexpr int kCWarps = kMode == 2 ? 11 : 8;      // the backward (mode 1): one warp per stripe row
+    static constexpr int kStages = kMode == 2 ? 5 : 3;
     static constexpr int kThreads = (kCWarps + 1) * 32;
-    static constexpr int kMinCtas = kMode == 0 ? 2 : 1;
+    static constexpr int kMinCtas = kMode == 2 ? 1 : 2;
 };
 
 __host__ __device__ __forceinline__ int stage_floats(int Wc, bool with_g) { return 8 * Wc + (with_g ? 9 * Wc / 8 : 0); }
 
 __device__ __forceinline__ void flag_error(const DownscaleDev& p, unsigned bit) {
     if (p.err) atomicOr(p.err, bit);
+}
+
+// After each CTA's 48 partials are stored: the last CTA to finish (a ticket
+// counter) adds all CTAs' partials in block order into grad_taps and resets
+// the ticket, so the tap gradients are deterministic and need no second
+// launch.  Called by the `nthreads` consumer threads of every CTA.
+__device__ __forceinline__ void finish_tap_gradients(const DownscaleDev& p, int nthreads) {
+    if (!p.grad_taps) return;
+    __shared__ int s_last;
+    __threadfence();                                            // partials visible device-wide
+    asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory");
+    if (threadIdx.x == 0) s_last = atomicAdd(p.ticket, 1u) == gridDim.x - 1 ? 1 : 0;
+    asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory");
+    if (!s_last) return;
+    __threadfence();
+    // G groups of 48 threads: group g sums the partials of CTAs g, g + G, ...
+    // (four interleaved accumulators), then thread o adds the G group sums in
+    // order.  Fixed thread count and grid give a fixed summation order.
+    __shared__ float s_grp[kTapGroups][kTapGrads];
+    const int G = nthreads / kTapGrads < kTapGroups ? nthreads / kTapGrads : kTapGroups;
+    const int grp = threadIdx.x / kTapGrads, o = threadIdx.x - grp * kTapGrads;
+    if (grp < G) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const float* q = p.partials + o;
+        const int n = (int)gridDim.x;
+        int b = grp;
+        for (; b + 3 * G < n; b += 4 * G) {
+            a0 += __ldcg(q + (int64_t)b * kTapGrads);
+            a1 += __ldcg(q + (int64_t)(b + G) * kTapGrads);
+            a2 += __ldcg(q + (int64_t)(b + 2 * G) * kTapGrads);
+            a3 += __ldcg(q + (int64_t)(b + 3 * G) * kTapGrads);
+        }
+        for (; b < n; b += G) a0 += __ldcg(q + (int64_t)b * kTapGrads);
+        s_grp[grp][o] = (a0 + a1) + (a2 + a3);
+    }
+    asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory");
+    if (threadIdx.x < kTapGrads) {
+        float acc = 0.f;
+        for (int g = 0; g < G; ++g) acc += s_grp[g][threadIdx.x];
+        p.grad_taps[threadIdx.x] = acc;
+    }
+    if (threadIdx.x == 0) *p.ticket = 0u;
+}
+
+// Backward consumers, one warp per stripe row k (8 warps) and one lane per
+// 8-column block: the thread holds the 24 horizontal taps but only column k
+// of the vertical taps, and accumulates dHh (3 x 8) and column k of dHv.
+//   mid[j]  = sum_c Hh[j,c] x[k,c]           dmid[j] = sum_i Hv[i,k] g[i,j]
+//   dx[c]   = sum_j Hh[j,c] dmid[j]           dHh[j,c] += dmid[j] x[k,c]
+//   dHv[i,k] += sum_j g[i,j] mid[j]
+__device__ __forceinline__ void backward_rows(const DownscaleDev& p, const float* sm, int sf, uint32_t full0,
+                                              uint32_t empty0, int Wc, int nch, uint32_t units, uint32_t HB,
+                                              int Wo, int Ho, int gw) {
+    constexpr int kStages = BulkCfg<1>::kStages;
+    static_assert(BulkCfg<1>::kCWarps == 8, "one consumer warp per stripe row");
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float hh[3][8], hvk[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) hh[j][c] = __ldg(p.taps + j * 8 + c);
+        hvk[j] = __ldg(p.taps + 24 + j * 8 + k);
+    }
+    float dhh[3][8], dhv[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        dhv[j] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) dhh[j][c] = 0.f;
+    }
+    (void)Ho;
+    uint32_t i = 0;
+    for (uint32_t u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+        const int st = (int)(i % kStages);
+        if (!ptx::mbar_wait(full0 + 8 * st, (i / kStages) & 1u)) {
+            flag_error(p, 2u);
+            break;
+        }
+        const uint32_t c = u % (uint32_t)nch, stripe = u / (uint32_t)nch;
+        const uint32_t f = stripe / HB, sy = stripe - f * HB;
+        const int c0 = (int)c * Wc;
+        const int nb = min(Wc, p.W - c0) >> 3;
+        const float* src = sm + st * sf;
+        float* gxrow = p.gx ? p.gx + ((int64_t)f * p.H + 8 * sy + k) * (int64_t)p.W + c0 : nullptr;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            const bool valid = b < nb;
+            const int bb = valid ? b : 0;
+            const float4 xa = *reinterpret_cast<const float4*>(src + k * Wc + 8 * bb);
+            const float4 xb = *reinterpret_cast<const float4*>(src + k * Wc + 8 * bb + 4);
+            float x[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+            float g[3][3];
+            const float* gs = src + 8 * Wc + 3 * bb;
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) g[ii][j] = gs[ii * gw + j];
+            if (!valid) {
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) x[cc] = 0.f;
+#pragma unroll
+                for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) g[ii][j] = 0.f;
+            }
+            float mid[3], dmid[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float a = hh[j][0] * x[0];
+#pragma unroll
+                for (int cc = 1; cc < 8; ++cc) a = fmaf(hh[j][cc], x[cc], a);
+                mid[j] = a;
+                dmid[j] = fmaf(hvk[2], g[2][j], fmaf(hvk[1], g[1][j], hvk[0] * g[0][j]));
+            }
+            float dx[8];
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                dx[cc] = fmaf(hh[2][cc], dmid[2], fmaf(hh[1][cc], dmid[1], hh[0][cc] * dmid[0]));
+#pragma unroll
+                for (int j = 0; j < 3; ++j) dhh[j][cc] = fmaf(dmid[j], x[cc], dhh[j][cc]);
+            }
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+                dhv[ii] = fmaf(g[ii][2], mid[2], fmaf(g[ii][1], mid[1], fmaf(g[ii][0], mid[0], dhv[ii])));
+            if (valid && gxrow) {
+                st_stream4(gxrow + 8 * b, make_float4(dx[0], dx[1], dx[2], dx[3]));
+                st_stream4(gxrow + 8 * b + 4, make_float4(dx[4], dx[5], dx[6], dx[7]));
+            }
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(empty0 + 8 * st);
+    }
+    // Tap gradients: warp shuffles, then the 8 row warps in fixed order.
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dhv[j] += __shfl_xor_sync(kFull, dhv[j], off);
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) dhh[j][cc] += __shfl_xor_sync(kFull, dhh[j][cc], off);
+        }
+    }
+    __shared__ float s_red[8][kTapGrads];
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                s_red[k][j * 8 + cc] = dhh[j][cc];
+                s_red[k][24 + j * 8 + cc] = cc == k ? dhv[j] : 0.f;
+            }
+        }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(8 * 32) : "memory");   // the 8 consumer warps
+    if (threadIdx.x < kTapGrads) {
+        float acc = 0.f;
+        for (int w = 0; w < 8; ++w) acc += s_red[w][threadIdx.x];
+        p.partials[(int64_t)blockIdx.x * kTapGrads + threadIdx.x] = acc;
+    }
+    finish_tap_gradients(p, 8 * 32);
 }
 
 // kMode: 0 forward, 1 backward, 2 forward + backward.
@@ -344,6 +505,10 @@ __global__ void __launch_bounds__(BulkCfg<kMode>::kThreads, BulkCfg<kMode>::kMin
     }
 
     // ---------------- consumers
+    if (kMode == 1) {
+        backward_rows(p, sm, sf, full0, empty0, Wc, nch, units, HB, Wo, Ho, gw);
+        return;
+    }
     const int half = lane & 1;
     Taps tp;
     load_taps(p.taps, half, tp);
@@ -466,6 +631,7 @@ __global__ void __launch_bounds__(BulkCfg<kMode>::kThreads, BulkCfg<kMode>::kMin
         for (int w = 0; w < kCWarps; ++w) acc += s_red[w][threadIdx.x];
         p.partials[(int64_t)blockIdx.x * kTapGrads + threadIdx.x] = acc;
     }
+    finish_tap_gradients(p, kCWarps * 32);
 }
 
 // Column chunk of the bulk variants: the fewest chunks of at most 1024
@@ -532,12 +698,8 @@ int fwd_grid(uint32_t items) {
 
 }  // namespace
 
-int downscale_bwd_partials(int sm_count, int W) {
-    if (bulk_backward_ok(W) && !use_register_variant()) {
-        const int Wc = bulk_chunk(W);
-        const int a = bulk_ctas_per_sm<1>(Wc), b = bulk_ctas_per_sm<2>(Wc);
-        return sm_count * (a < b ? a : b);
-    }
+// Register-direct backward: CTAs per SM (both modes).
+int regs_bwd_per_sm() {
     static int per_sm = 0;
     if (!per_sm) {
         int a = 0, b = 0;
@@ -546,7 +708,22 @@ int downscale_bwd_partials(int sm_count, int W) {
         per_sm = a < b ? a : b;
         if (per_sm <= 0) per_sm = 1;
     }
-    return sm_count * per_sm;
+    return per_sm;
+}
+
+// Grid (= tap-gradient partial slots) of one backward launch.
+int bwd_grid(int sm_count, int W, bool with_fwd) {
+    if (bulk_backward_ok(W) && !use_register_variant()) {
+        const int Wc = bulk_chunk(W);
+        return sm_count * (with_fwd ? bulk_ctas_per_sm<2>(Wc) : bulk_ctas_per_sm<1>(Wc));
+    }
+    return sm_count * regs_bwd_per_sm();
+}
+
+// Partial slots a caller must provide: enough for either backward mode.
+int downscale_bwd_partials(int sm_count, int W) {
+    const int a = bwd_grid(sm_count, W, false), b = bwd_grid(sm_count, W, true);
+    return a > b ? a : b;
 }
 
 cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s) {
@@ -562,16 +739,20 @@ cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int nparts, bool with_fwd,
+cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int capacity, bool with_fwd,
                                  cudaStream_t s) {
     cudaError_t e;
+    int nparts = bwd_grid(device_sm_count(), p.W, with_fwd);
+    if (nparts > capacity) nparts = capacity;   // grid-stride kernels: fewer CTAs still cover the work
     if (bulk_backward_ok(p.W) && !use_register_variant()) {
-        e = with_fwd ? launch_bulk<2>(p, nparts, s) : launch_bulk<1>(p, nparts, s);
-    } else {
-        if (with_fwd) downscale_bwd_kernel<true><<<nparts, kThr, 0, s>>>(p);
-        else downscale_bwd_kernel<false><<<nparts, kThr, 0, s>>>(p);
-        e = cudaGetLastError();
+        // the last CTA reduces the tap gradients itself
+        DownscaleDev q = p;
+        q.grad_taps = grad_taps;
+        return with_fwd ? launch_bulk<2>(q, nparts, s) : launch_bulk<1>(q, nparts, s);
     }
+    if (with_fwd) downscale_bwd_kernel<true><<<nparts, kThr, 0, s>>>(p);
+    else downscale_bwd_kernel<false><<<nparts, kThr, 0, s>>>(p);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (grad_taps) {
         tapgrad_reduce_kernel<<<1, kTapGrads * 16, 0, s>>>(p.partials, nparts, grad_taps);
@@ -603,7 +784,9 @@ namespace arol {
 namespace {
 
 constexpr int kNoAllocMaxParts = 1024;   // CTAs whose partials fit: 1024 x 48 floats = 192 KiB
-static __device__ __align__(256) float g_noalloc_partials[kNoAllocMaxParts * kTapGrads];
+// the 48-float partial of each CTA, then one word: the CTAs-done ticket of the
+// last-CTA reduction (zero at load; every launch leaves it at zero)
+static __device__ __align__(256) float g_noalloc_partials[kNoAllocMaxParts * kTapGrads + 4];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
@@ -651,7 +834,9 @@ extern "C" arol_status arol_downscale_backward_noalloc(const float* x, const flo
     p.gy = grad_out;
     p.gx = grad_in;
     p.err = nullptr;
+    p.grad_taps = nullptr;
     p.partials = scratch;   // every CTA overwrites its own 48 slots before the reduction reads them
+    p.ticket = reinterpret_cast<unsigned*>(scratch + kNoAllocMaxParts * kTapGrads);
     p.frames = frames;
     p.H = height;
     p.W = width;

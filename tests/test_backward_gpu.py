@@ -100,7 +100,14 @@ def test_fwd_bwd_equals_separate_calls_and_is_deterministic(arol):
     gt3 = torch.empty(48, device="cuda")
     c.backward(wd, [xd], gx3, gt3)
     torch.cuda.synchronize()
-    assert torch.equal(y1, y2) and torch.equal(gx1, gx2) and torch.equal(gt1, gt2)
+    # the fused kernel computes the forward exactly as the forward kernel does;
+    # its gradients sum in another order (another thread layout): tolerance
+    assert torch.equal(y1, y2)
+    sX, (sHh, sHv) = O.chain_vjp(_abs_chain(chain), [np.abs(x)], np.abs(w.astype(np.float64)))
+    assert_fir_close(host(gx2), host(gx1).astype(np.float64), sX, RTOL, "fwd_bwd dX")
+    assert_fir_close(host(gt2), host(gt1).astype(np.float64),
+                     np.concatenate([sHh.reshape(-1), sHv.reshape(-1)]), RTOL, "fwd_bwd dH")
+    # the same call twice gives the same bits (no atomics in any sum)
     assert torch.equal(gx1, gx3) and torch.equal(gt1, gt3)
 
 
