@@ -136,6 +136,22 @@ class Batch:
         B.arol_batch_run(self.handle, list(ins), list(outs), stream)
         return outs
 
+    def prepare(self, ins, outs):
+        """Marshal the pointer arrays once; returns (run, run_per_task)
+        callables that reuse them (for timing loops)."""
+        pin, pout = B._ptrs(list(ins)), B._ptrs(list(outs))
+        keep = (list(ins), list(outs))
+
+        def run(stream=None):
+            B._check(B.lib.arol_batch_run(self.handle, pin, pout, B._stream(stream)))
+            return keep[1]
+
+        def run_per_task(stream=None):
+            B._check(B.lib.arol_batch_run_per_task(self.handle, pin, pout, B._stream(stream)))
+            return keep[1]
+
+        return run, run_per_task
+
     def run_per_task(self, ins, outs, stream=None):
         B.arol_batch_run_per_task(self.handle, list(ins), list(outs), stream)
         return outs

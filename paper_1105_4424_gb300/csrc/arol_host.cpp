@@ -1341,8 +1341,13 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
     for (size_t i = 0; i < n; ++i)
         if ((!in[i] || !out[i]) && b->host_tasks[i].nreps > 0) return fail(AROL_ERR_INVALID, "null pointer for task %zu", i);
     if (!b->tables_built) {
+        // each task's taps, then (row-FIR tasks) the same taps transposed and
+        // zero padded to T x 16 for the row-tile path
         size_t ntaps = 0;
-        for (auto& v : b->taps) ntaps += v.size();
+        for (size_t i = 0; i < n; ++i) {
+            ntaps += b->taps[i].size();
+            if (b->host_tasks[i].rowfir) ntaps += (size_t)b->host_tasks[i].T * 16;
+        }
         AROL_CUDA(cudaMalloc(&b->dev_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMalloc(task table)");
         AROL_CUDA(cudaMallocHost(&b->pinned_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMallocHost(task table)");
         AROL_CUDA(cudaEventCreateWithFlags(&b->table_copied, cudaEventDisableTiming), "cudaEventCreate");
@@ -1356,6 +1361,16 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
                           "upload taps");
                 b->host_tasks[i].taps = b->taps_dev + off;
                 off += b->taps[i].size();
+            }
+            TaskDev& td = b->host_tasks[i];
+            if (td.rowfir) {
+                std::vector<float> ht((size_t)td.T * 16, 0.f);
+                for (int k = 0; k < td.T; ++k)
+                    for (int j = 0; j < td.m; ++j) ht[(size_t)k * 16 + j] = b->taps[i][(size_t)j * td.T + k];
+                AROL_CUDA(cudaMemcpy(b->taps_dev + off, ht.data(), ht.size() * sizeof(float), cudaMemcpyHostToDevice),
+                          "upload taps");
+                td.taps_t = b->taps_dev + off;
+                off += ht.size();
             }
         }
         AROL_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");

@@ -49,6 +49,7 @@ struct TaskDev {
     int32_t wfull;          // staged window of one whole row: step * (rep[3] - 1) + T
     FastDiv wfull_div;      // division by wfull
     const float* taps;      // m x T (fir)
+    const float* taps_t;    // row-FIR tasks in a batch: taps transposed, T x 16, zero padded
     const void* x;
     void* y;
 };
@@ -78,8 +79,7 @@ struct DownscaleDev {
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s);
-// counter != nullptr: CTAs take tiles from the shared counter (reset by the
-// launcher); nullptr: CTA b takes tiles b, b + grid, ... (no counter).
+// CTA b takes tiles b, b + grid, ... (a static schedule; `counter` is unused).
 cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, int ntiles,
                                     unsigned* counter, int grid, int threads, int max_m,
                                     cudaStream_t s);

@@ -346,91 +346,119 @@ __device__ __forceinline__ void row_fir_dispatch(const TaskDev& t, const float* 
     }
 }
 
-__device__ __forceinline__ void row_fir_tile(const TaskDev& t, int task, int64_t start, int count, float* win,
-                                             float* ht, int* s_task) {
-    constexpr int kHt = 16;
+// One ring slot of the batch kernel: a copy of the tile's TaskDev (so that
+// the compute reads its fields from shared memory), the staged window, then
+// the taps of the tile's task transposed and zero padded
+// (ht[k * 16 + j] = H[j, k], k < 32).
+constexpr int kTaskFloats = (int)((sizeof(TaskDev) + 15) / 16 * 4);
+constexpr int kSlotFloats = kTaskFloats + kWinPad + 32 * 16;
+static_assert(sizeof(TaskDev) % 4 == 0, "TaskDev is copied in 4-byte words");
+
+struct RowGeom {
+    uint32_t r0, a0, row0;
+    bool rows_layout;
+};
+
+__device__ __forceinline__ RowGeom row_geom(const TaskDev& t, int64_t start, int count) {
+    RowGeom g;
     const uint32_t R1 = (uint32_t)t.rep[3];
-    const int T = t.T, m = t.m;
-    // taps, transposed and zero padded (ht[k * 16 + j] = H[j, k]); kept across
-    // consecutive tiles of the same task.  Every thread reads the same
-    // *s_task: it is written only between two barriers.
-    if (*s_task != task) {
-        for (int i = threadIdx.x; i < T * kHt; i += blockDim.x) {
-            const int k = i >> 4, j = i & 15;
-            if (j < m) ptx::cp_async4(ht + i, t.taps + j * T + k);
-            else ht[i] = 0.f;
-        }
-    }
-    const uint32_t r0 = fast_div((uint32_t)start, t.rep_div[3]);
-    const uint32_t a0 = (uint32_t)start - r0 * R1;
-    const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
-    uint32_t v = t.in.origin[0] + r0;                          // < 2^31: checked on the host
-    const uint32_t row0 = v - fast_div(v, t.in.shape_div[0]) * hin;
+    g.r0 = fast_div((uint32_t)start, t.rep_div[3]);
+    g.a0 = (uint32_t)start - g.r0 * R1;
+    const uint32_t v = t.in.origin[0] + g.r0;               // < 2^31: checked on the host
+    g.row0 = v - fast_div(v, t.in.shape_div[0]) * (uint32_t)t.in.shape[0];
     // The host builds multi-row tiles only as whole rows (count = rows * R1,
     // rows >= 2, rows <= H, rows * W <= kWinFloats); every other row tile lies
     // within one row (count <= R1).
-    const bool rows_layout = a0 == 0u && (uint32_t)count > R1;
-    if (rows_layout) {
-        // whole rows, copied as they lie in memory (rows may wrap past H)
-        const int rows = (int)((uint32_t)count / R1);
+    g.rows_layout = g.a0 == 0u && (uint32_t)count > R1;
+    return g;
+}
+
+// Issues (cp.async, no wait) the copies of a row tile's window and, unless
+// the slot already holds them, its task's transposed taps.
+__device__ __forceinline__ void stage_row_tile(const TaskDev& t, int64_t start, int count, float* slot,
+                                               bool need_taps) {
+    const RowGeom g = row_geom(t, start, count);
+    if (g.rows_layout) {
+        const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
+        const int rows = (int)((uint32_t)count / (uint32_t)t.rep[3]);
         const float* x = static_cast<const float*>(t.x);
         const int64_t plane = (int64_t)hin * wi;
-        const int64_t g0 = (int64_t)row0 * wi;
+        const int64_t g0 = (int64_t)g.row0 * wi;
         const int total = rows * (int)wi;
         for (int w = threadIdx.x; w < total; w += blockDim.x) {
             int64_t gofs = g0 + w;
             if (gofs >= plane) gofs -= plane;
-            ptx::cp_async4(win + padw(w), x + gofs);
+            ptx::cp_async4(slot + padw(w), x + gofs);
         }
     } else {
-        stage_window(t, row0, a0, t.step * (count - 1) + T, win);
+        stage_window(t, g.row0, g.a0, t.step * (count - 1) + t.T, slot);
     }
-    ptx::cp_async_wait_all();   // this thread's copies (window and taps) have landed
-    __syncthreads();            // ... and everyone else's
-    if (rows_layout) row_fir_dispatch<true>(t, win, ht, count, r0, 0u, t.in.origin[1]);
-    else row_fir_dispatch<false>(t, win, ht, count, r0, a0, 0u);
-    // Every thread read *s_task before the barrier above; the next read comes
-    // after the barrier below, so this write is seen consistently.
-    if (threadIdx.x == 0) *s_task = task;
-    __syncthreads();   // the next tile overwrites win (and possibly ht)
+    if (need_taps) {
+        float* ht = slot + kWinPad;
+        for (int i = threadIdx.x; i < t.T * 16; i += blockDim.x) ptx::cp_async4(ht + i, t.taps_t + i);
+    }
 }
 
-// Persistent batched kernel.  With a counter, CTAs take tiles (task,
-// repetition range) from it until the list is exhausted; without one, CTA b
-// takes tiles b, b + gridDim.x, ...  No CTA ever waits on another.
+__device__ __forceinline__ void compute_row_tile(const TaskDev& t, int64_t start, int count, const float* slot) {
+    const RowGeom g = row_geom(t, start, count);
+    const float* ht = slot + kWinPad;
+    if (g.rows_layout) row_fir_dispatch<true>(t, slot, ht, count, g.r0, 0u, t.in.origin[1]);
+    else row_fir_dispatch<false>(t, slot, ht, count, g.r0, g.a0, 0u);
+}
+
+// Persistent batched kernel.  CTA b takes tiles b, b + gridDim.x, ... (the
+// host orders tiles by cost).  Row tiles of row-FIR tasks go through a
+// two-slot shared-memory ring: while the CTA computes tile i from one slot,
+// the copies of tile i + 1 fill the other.  Other tiles run the generic
+// per-repetition path.  No CTA ever waits on another.
 template <int MAXM>
 __global__ void __launch_bounds__(256, 1) batch_persistent_kernel(const TaskDev* __restrict__ tasks,
-                                                               const TileDev* __restrict__ tiles,
-                                                               int ntiles, unsigned* counter) {
-    __shared__ int s_tile;
-    __shared__ int s_task;   // task whose taps s_ht holds
+                                                                  const TileDev* __restrict__ tiles, int ntiles) {
     constexpr bool kRows = MAXM <= 16;
-    __shared__ __align__(16) float s_win[kRows ? kWinPad : 1];
-    __shared__ __align__(16) float s_ht[kRows ? 32 * 16 : 4];
-    if (threadIdx.x == 0) s_task = -1;
-    __syncthreads();
-    int next = blockIdx.x;
-    for (;;) {
-        int ti;
-        if (counter) {
-            if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
-            __syncthreads();
-            ti = s_tile;
-            __syncthreads();
-        } else {
-            ti = next;
-            next += gridDim.x;
-        }
-        if (ti >= ntiles) break;
+    extern __shared__ __align__(16) float dsm[];
+    int slot_task[2] = {-1, -1};   // task whose taps each slot holds (the same in every thread)
+    int ti = blockIdx.x;
+    if (kRows && ti < ntiles) {
         const TileDev tile = tiles[ti];
         const TaskDev& t = tasks[tile.task];
-        if (kRows && t.rowfir) {
-            row_fir_tile(t, tile.task, tile.start, tile.count, s_win, s_ht, &s_task);
+        if (t.rowfir) {
+            const float* src = reinterpret_cast<const float*>(&t);
+            for (int w = threadIdx.x; w < (int)(sizeof(TaskDev) / 4); w += blockDim.x) ptx::cp_async4(dsm + w, src + w);
+            stage_row_tile(t, tile.start, tile.count, dsm + kTaskFloats, true);
+            slot_task[0] = tile.task;
+        }
+    }
+    ptx::cp_async_commit();
+    for (int i = 0; ti < ntiles; ++i, ti += gridDim.x) {
+        const int cur = i & 1, nxt = cur ^ 1;
+        const int nti = ti + gridDim.x;
+        __syncthreads();   // every thread is done with the next slot (tile i - 1)
+        if (kRows && nti < ntiles) {
+            const TileDev tile = tiles[nti];
+            const TaskDev& t = tasks[tile.task];
+            if (t.rowfir) {
+                float* slot = dsm + nxt * kSlotFloats;
+                const float* src = reinterpret_cast<const float*>(&t);
+                for (int w = threadIdx.x; w < (int)(sizeof(TaskDev) / 4); w += blockDim.x)
+                    ptx::cp_async4(slot + w, src + w);
+                stage_row_tile(t, tile.start, tile.count, slot + kTaskFloats, slot_task[nxt] != tile.task);
+                slot_task[nxt] = tile.task;
+            }
+        }
+        ptx::cp_async_commit();
+        ptx::cp_async_wait_group<1>();   // this thread's copies for tile i have landed
+        __syncthreads();                 // ... and everyone else's
+        const TileDev tile = tiles[ti];
+        if (kRows && tasks[tile.task].rowfir) {
+            const float* slot = dsm + cur * kSlotFloats;
+            compute_row_tile(*reinterpret_cast<const TaskDev*>(slot), tile.start, tile.count, slot + kTaskFloats);
             continue;
         }
+        const TaskDev& t = tasks[tile.task];
         const int64_t end = tile.start + tile.count;
         for (int64_t lr = tile.start + threadIdx.x; lr < end; lr += blockDim.x) process_rep<MAXM>(t, lr);
     }
+    ptx::cp_async_wait_all();
 }
 
 // Element of port p at flat pattern index j of the repetition whose base is b
@@ -538,18 +566,42 @@ cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+size_t batch_smem(int max_m) { return max_m <= 16 ? 2 * (size_t)kSlotFloats * sizeof(float) : 0; }
+
+template <int MAXM>
+cudaError_t launch_batch_m(const TaskDev* tasks, const TileDev* tiles, int ntiles, int grid, int threads,
+                           cudaStream_t s) {
+    static bool attr = false;
+    static int occ_threads = 0, occ = 1;
+    const size_t smem = batch_smem(MAXM);
+    if (!attr && smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(batch_persistent_kernel<MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (occ_threads != threads) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_persistent_kernel<MAXM>, threads, smem);
+        occ = n > 0 ? n : 1;
+        occ_threads = threads;
+    }
+    // static schedule: every CTA must be resident, or late CTAs stretch the tail
+    const int cap = device_sm_count() * occ;
+    if (grid > cap) grid = cap;
+    batch_persistent_kernel<MAXM><<<grid, threads, smem, s>>>(tasks, tiles, ntiles);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, int ntiles, unsigned* counter,
                                     int grid, int threads, int max_m, cudaStream_t s) {
-    if (counter) {
-        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
-        if (e != cudaSuccess) return e;
-    }
+    (void)counter;   // the schedule is static: CTA b takes tiles b, b + grid, ...
     if (ntiles == 0) return cudaSuccess;
-    if (max_m <= 4) batch_persistent_kernel<4><<<grid, threads, 0, s>>>(tasks, tiles, ntiles, counter);
-    else if (max_m <= 8) batch_persistent_kernel<8><<<grid, threads, 0, s>>>(tasks, tiles, ntiles, counter);
-    else if (max_m <= 16) batch_persistent_kernel<16><<<grid, threads, 0, s>>>(tasks, tiles, ntiles, counter);
-    else batch_persistent_kernel<32><<<grid, threads, 0, s>>>(tasks, tiles, ntiles, counter);
-    return cudaGetLastError();
+    if (grid > ntiles) grid = ntiles;
+    if (max_m <= 4) return launch_batch_m<4>(tasks, tiles, ntiles, grid, threads, s);
+    if (max_m <= 8) return launch_batch_m<8>(tasks, tiles, ntiles, grid, threads, s);
+    if (max_m <= 16) return launch_batch_m<16>(tasks, tiles, ntiles, grid, threads, s);
+    return launch_batch_m<32>(tasks, tiles, ntiles, grid, threads, s);
 }
 
 int tiler_bwd_blocks(int64_t nreps, int64_t* chunk) {
