@@ -422,3 +422,16 @@ def test_planted_address_mistake_is_caught(monkeypatch, attr, bad):
 def test_planted_fir_mistake_is_caught(monkeypatch, bad):
     monkeypatch.setattr(O, "elem_fir", bad)
     assert _some_pin_fails(_FIR_PINS)
+
+
+def test_2d_fir_patterns_c_oracle_and_adjoint():
+    from oracle import cpu_ref as C
+    g = W.rng(16)
+    for _ in range(20):
+        tk = W.random_tiler_task(g, "fir", fir_pattern_rank=2)
+        x = g.standard_normal(tk["inputs"][0]["shape"])
+        y = O.run_task(tk, [x])[0]
+        np.testing.assert_allclose(C.run_task(tk, [x])[0], y, rtol=1e-13, atol=1e-14)
+        G = g.standard_normal(tk["outputs"][0]["shape"])
+        dX, dH = O.task_vjp(tk, [x], G)
+        assert abs(_inner(y, G) - _inner(x, dX)) <= 1e-10 * (1 + abs(_inner(y, G)))

@@ -330,3 +330,68 @@ def test_batch_row_fir_tasks_with_shifted_origins(arol):
         ref = C.run_task(tk, [x])[0]
         assert_fir_close(host(y), ref, fir_scale(tk, x, C.run_chain), what="row fir batch")
         np.testing.assert_array_equal(host(y), host(y2))
+
+
+def test_random_2d_fir_patterns(arol):
+    """FIR banks on 2-D patterns (2-D fittings: stencils, oriented windows) and
+    2-D output patterns, with wrap and overlap."""
+    g = W.rng(113)
+    for _ in range(40):
+        tk = W.random_tiler_task(g, "fir", fir_pattern_rank=2)
+        x = g.standard_normal(tk["inputs"][0]["shape"]).astype(np.float32)
+        _, y = run1(arol, tk, [x])
+        assert_fir_close(y, O.run_task(tk, [x])[0], fir_scale(tk, x), what="2-D fir")
+
+
+def test_3x3_stencil_as_a_repetitive_task(arol):
+    """A 3x3 stencil (pattern (3, 3), fitting identity) over a wrapped image:
+    numpy.roll sums are the closed form."""
+    g = W.rng(114)
+    x = g.standard_normal((37, 53)).astype(np.float32)
+    H = g.standard_normal((1, 9)).astype(np.float32)
+    inp = W.port((37, 53), (-1, -1), ((1, 0), (0, 1)), ((1, 0), (0, 1)), (3, 3))
+    out = W.port((37, 53), (0, 0), ((1, 0), (0, 1)), ((0,), (0,)), (1,))
+    tk = W.task((37, 53), "fir", [inp], [out], H)
+    _, y = run1(arol, tk, [x])
+    ref = np.zeros((37, 53))
+    for a in range(3):
+        for b in range(3):
+            ref += H[0, 3 * a + b] * np.roll(x.astype(np.float64), (1 - a, 1 - b), axis=(0, 1))
+    assert_fir_close(y, ref, fir_scale(tk, x), what="3x3 stencil")
+
+
+def _three_task_chain(g):
+    """Horizontal 2:1, vertical 2:1, horizontal 4-tap/2-output: an unfused chain."""
+    H1 = (g.standard_normal((1, 2)) / 2).astype(np.float32)
+    H2 = (g.standard_normal((1, 2)) / 2).astype(np.float32)
+    H3 = (g.standard_normal((2, 4)) / 4).astype(np.float32)
+    t1 = W.task((24, 16), "fir", [W.port((24, 32), (0, 0), ((1, 0), (0, 2)), ((0,), (1,)), (2,))],
+                [W.port((24, 16), (0, 0), ((1, 0), (0, 1)), ((0,), (1,)), (1,))], H1)
+    t2 = W.task((12, 16), "fir", [W.port((24, 16), (0, 0), ((2, 0), (0, 1)), ((1,), (0,)), (2,))],
+                [W.port((12, 16), (0, 0), ((1, 0), (0, 1)), ((1,), (0,)), (1,))], H2)
+    t3 = W.task((12, 4), "fir", [W.port((12, 16), (0, 3), ((1, 0), (0, 4)), ((0,), (1,)), (4,))],
+                [W.port((12, 8), (0, 0), ((1, 0), (0, 2)), ((0,), (1,)), (2,))], H3)
+    return [t1, t2, t3]
+
+
+def test_three_task_chain_forward_and_backward(arol):
+    g = W.rng(115)
+    chain = _three_task_chain(g)
+    x = g.standard_normal((24, 32)).astype(np.float32)
+    c = arol.Chain(chain)
+    assert c.info["kernel"] == 3
+    y = host(c.run([dev(x)]))
+    assert_fir_close(y, O.run_chain(chain, [x])[0], fir_scale(chain, x), what="3-task chain")
+    G = g.standard_normal((12, 8)).astype(np.float32)
+    gx = torch.empty((24, 32), device="cuda")
+    gt = torch.empty(2 + 2 + 8, device="cuda")
+    c.backward(dev(G), [dev(x)], gx, gt)
+    torch.cuda.synchronize()
+    dX, dHs = O.chain_vjp(chain, [x], G.astype(np.float64))
+    abs_chain = [dict(t, taps=np.abs(t["taps"].astype(np.float64))) for t in chain]
+    sX, sHs = O.chain_vjp(abs_chain, [np.abs(x)], np.abs(G.astype(np.float64)))
+    assert_fir_close(host(gx), dX, sX, what="3-task chain dX")
+    got, off = host(gt), 0
+    for dH, sH in zip(dHs, sHs):
+        assert_fir_close(got[off:off + dH.size].reshape(dH.shape), dH, sH, what="3-task chain dH")
+        off += dH.size

@@ -220,7 +220,7 @@ def config4(seed=0, frames=16, height=1080, width=1920):
 
 
 def random_tiler_task(g: np.random.Generator, elem="copy", max_side=12,
-                      max_rank=3, max_abs=6):
+                      max_rank=3, max_abs=6, fir_pattern_rank=1):
     """A random small task: random input tiler (negative origin, paving and
     fitting entries allowed, overlaps and wrap-around allowed) and an output
     tiler that partitions its array by construction.
@@ -234,7 +234,7 @@ def random_tiler_task(g: np.random.Generator, elem="copy", max_side=12,
     R = tuple(int(v) for v in g.integers(1, 6, size=q))
     d = int(g.integers(1, max_rank + 1))
     shape = tuple(int(v) for v in g.integers(1, max_side + 1, size=d))
-    p = 1 if elem == "fir" else int(g.integers(1, 3))
+    p = fir_pattern_rank if elem == "fir" else int(g.integers(1, 3))
     S = tuple(int(v) for v in g.integers(1, 5, size=p))
     origin = tuple(int(v) for v in g.integers(-3 * max_abs, 3 * max_abs + 1, size=d))
     paving = tuple(tuple(int(v) for v in g.integers(-max_abs, max_abs + 1, size=q)) for _ in range(d))
@@ -243,7 +243,10 @@ def random_tiler_task(g: np.random.Generator, elem="copy", max_side=12,
     T = int(np.prod(S))
     if elem == "fir":
         m = int(g.integers(1, T + 1))
-        S_out = (m,)
+        if fir_pattern_rank == 2 and m > 1 and m % 2 == 0:
+            S_out = (2, m // 2)          # a 2-D output pattern (m flattened row-major)
+        else:
+            S_out = (m,)
         taps = _taps(g, m, T)
     else:
         S_out = S
