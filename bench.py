@@ -208,7 +208,8 @@ class NvmlSampler:
 # -------------------------------------------------------- rank aggregation
 
 def aggregate(elapsed_ms_per_rank, units_per_rank, steps):
-    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    """Whole-job throughput: the units all ranks processed over the whole timed
+    region (all steps), divided by the slowest rank's time for it."""
     t = max(elapsed_ms_per_rank)
     total = sum(units_per_rank)
     return total / (t / 1e3), t / steps
@@ -341,6 +342,22 @@ def bench_matmul(A, torch, stream, flush, reps, peak_tf):
             "torch_matmul_bf16_out_ms": ref, "torch_tflops": flops / (ref * 1e-3) / 1e12}
 
 
+def bench_bf16(A, torch, stream, flush, reps, hbm):
+    """The same 64x1080x1920 chain with bfloat16 frames and output (f32
+    arithmetic and intermediate): half the bytes per tiler element."""
+    chain, (x,) = W.config1_bf16(seed=2)
+    c = A.Chain(chain)
+    xd = torch.from_numpy(x.view(np.int16)).cuda().view(torch.bfloat16)
+    y = c.run([xd])
+    for _ in range(3):
+        c.run([xd], y)
+    ms = statistics.median(time_each_flushed(lambda: c.run([xd], y), reps, stream, flush))
+    nbytes = 2 * FRAMES * HEIGHT * WIDTH + 2 * FRAMES * (HEIGHT // 8 * 3) * (WIDTH // 8 * 3)
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": "64x1080x1920 bf16 -> 64x405x720 bf16", "ms": ms, "elems_per_s": chain_units(FRAMES) / (ms * 1e-3),
+            "unique_bytes": nbytes, "gbs": gbs, "frac_of_hbm": gbs / hbm}
+
+
 def bench_config0(A, torch, stream, reps):
     tk, (x,) = W.config0()
     t = A.Task(tk)
@@ -428,7 +445,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
         barrier(world)
     all_ms = dist_max(ms, world)
-    value, ms_per_step = aggregate(all_ms, [units] * world, args.steps)
+    value, ms_per_step = aggregate(all_ms, [units * args.steps] * world, args.steps)
+    # one step moves `units` tiler elements per rank: value * time per step must give them back
+    assert abs(value * ms_per_step * 1e-3 - units * world) <= 1e-6 * units * world
     kernel_ms = ms / args.steps                      # one kernel launch per step
     achieved = nbytes / (kernel_ms * 1e-3) / 1e9
 
@@ -479,6 +498,7 @@ def run_gpu(args):
         line["batched"] = bench_batched(A, torch, stream, flush, reps)
         line["fwd_bwd"] = bench_backward(A, torch, stream, flush, reps)
         line["matmul"] = bench_matmul(A, torch, stream, flush, reps, bf16)
+        line["bf16_storage"] = bench_bf16(A, torch, stream, flush, reps, hbm)
         del flush
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_chain()

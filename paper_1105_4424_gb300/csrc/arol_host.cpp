@@ -323,6 +323,8 @@ TaskDev make_taskdev(const arol_task_desc& d) {
     t.T = (int32_t)pattern_size(d.in_tiler[0]);
     t.m = (int32_t)pattern_size(d.out_tiler[0]);
     t.esize = esize_of(d.in[0].dtype);
+    t.in_bf16 = d.elem == AROL_ELEM_FIR && d.in[0].dtype == AROL_BF16 ? 1 : 0;
+    t.out_bf16 = d.elem == AROL_ELEM_FIR && d.out[0].dtype == AROL_BF16 ? 1 : 0;
     arol_task_desc full = dd;
     full.rep_rank = 4;
     for (int q = 0; q < 4; ++q) full.rep[q] = t.rep[q];
@@ -330,7 +332,8 @@ TaskDev make_taskdev(const arol_task_desc& d) {
     // Row FIR: one row per r0, step along the row per r1, one contiguous
     // pattern of T taps, m contiguous outputs per repetition.
     const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
-    if (d.elem == AROL_ELEM_FIR && !t.wide && d.rep_rank == 2 && d.in[0].rank == 2 && d.out[0].rank == 2 &&
+    if (d.elem == AROL_ELEM_FIR && !t.wide && !t.in_bf16 && !t.out_bf16 && d.rep_rank == 2 && d.in[0].rank == 2 &&
+        d.out[0].rank == 2 &&
         ti.pattern_rank == 1 && to.pattern_rank == 1 && ti.paving[0][0] == 1 && ti.paving[0][1] == 0 &&
         ti.paving[1][0] == 0 && ti.fitting[0][0] == 0 && ti.fitting[1][0] == 1 && to.paving[0][0] == 1 &&
         to.paving[0][1] == 0 && to.paving[1][0] == 0 && to.paving[1][1] == d.fir_m && to.fitting[0][0] == 0 &&
@@ -396,7 +399,7 @@ bool is_matmul_panels(const arol_task_desc& d, int* M, int* N, int* K) {
 struct Pass { int64_t F, H, W; int64_t S, T, m; };
 
 bool match_pass(const arol_task_desc& d, int axis, Pass* ps) {
-    if (d.elem != AROL_ELEM_FIR || d.n_in != 1 || d.in[0].dtype != AROL_F32) return false;
+    if (d.elem != AROL_ELEM_FIR || d.n_in != 1) return false;
     const arol_array_desc &a = d.in[0], &o = d.out[0];
     const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
     if (a.rank != o.rank || a.rank != d.rep_rank || (a.rank != 2 && a.rank != 3)) return false;
@@ -451,6 +454,7 @@ struct arol_task_s {
     // fused downscaler
     int64_t ds_frames = 0;
     int ds_H = 0, ds_W = 0;
+    bool ds_in_bf16 = false, ds_mid_bf16 = false, ds_out_bf16 = false;
     // matmul
     int mm_M = 0, mm_N = 0, mm_K = 0;
     unsigned* err_flag = nullptr;        // device word: bounded waits that gave up
@@ -550,8 +554,7 @@ arol_status validate_desc(const arol_task_desc& d) {
         if (ns_in != ns_out) return fail(AROL_ERR_INVALID, "copy: input pattern has %" PRId64 " elements, output %" PRId64, ns_in, ns_out);
         break;
     case AROL_ELEM_FIR:
-        if (d.in[0].dtype != AROL_F32 || d.out[0].dtype != AROL_F32)
-            return fail(AROL_ERR_UNSUPPORTED, "fir: float32 input and output only");
+        // f32 or bf16 storage on either side (Sec. 5 typeAllocation); arithmetic in f32
         if (d.fir_T != ns_in || d.fir_m != ns_out)
             return fail(AROL_ERR_INVALID, "fir: T=%d m=%d but patterns have %" PRId64 " and %" PRId64 " elements",
                         d.fir_T, d.fir_m, ns_in, ns_out);
@@ -695,10 +698,20 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     if (n == 2 && match_pass(t->descs[0], 2, &h) && match_pass(t->descs[1], 1, &v) && h.S == 8 && h.T == 8 &&
         h.m == 3 && v.S == 8 && v.T == 8 && v.m == 3 && v.F == h.F && v.H == h.H && v.W == h.W / 8 * 3 &&
         h.W % 8 == 0 && h.H % 8 == 0 && (double)h.F * (h.H / 8) * (h.W / 4) < 2147483647.0) {
-        t->kernel = 1;
-        t->ds_frames = h.F;
-        t->ds_H = (int)h.H;
-        t->ds_W = (int)h.W;
+        // fused storage combinations: all f32, or bf16 frames with an f32 or
+        // bf16 intermediate and output; others run task by task
+        const bool in_bf16 = t->descs[0].in[0].dtype == AROL_BF16;
+        const bool mid_bf16 = t->descs[0].out[0].dtype == AROL_BF16;
+        const bool out_bf16 = t->descs[1].out[0].dtype == AROL_BF16;
+        if (in_bf16 || (!mid_bf16 && !out_bf16)) {
+            t->kernel = 1;
+            t->ds_frames = h.F;
+            t->ds_H = (int)h.H;
+            t->ds_W = (int)h.W;
+            t->ds_in_bf16 = in_bf16;
+            t->ds_mid_bf16 = mid_bf16;
+            t->ds_out_bf16 = out_bf16;
+        }
     }
     arol_task_info_t& in = t->info;
     in.kind = 1;
@@ -754,6 +767,9 @@ DownscaleDev ds_params(arol_task t, const float* taps) {
     DownscaleDev p;
     std::memset(&p, 0, sizeof p);
     p.err = t->err_flag;
+    p.in_bf16 = t->ds_in_bf16;
+    p.mid_bf16 = t->ds_mid_bf16;
+    p.out_bf16 = t->ds_out_bf16;
     p.taps = taps;
     p.frames = t->ds_frames;
     p.H = t->ds_H;
@@ -887,7 +903,7 @@ arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* co
     const arol_task_desc& d0 = t->descs[0];
     const arol_array_desc& od = t->descs.back().out[0];
     arol_status st;
-    const bool pipelined = t->kind == 1 && t->kernel == 1 && t->ds_frames >= 2;
+    const bool pipelined = t->kind == 1 && t->kernel == 1 && t->ds_frames >= 2 && !t->ds_in_bf16 && !t->ds_out_bf16;
     void* dins[2] = {nullptr, nullptr};
     for (int i = 0; i < d0.n_in; ++i) {
         if (!host_in[i]) return fail(AROL_ERR_INVALID, "null input pointer %d", i);
@@ -900,8 +916,7 @@ arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* co
     if (!host_out[0]) return fail(AROL_ERR_INVALID, "null output pointer");
     if ((st = dev_alloc(t, &t->stage_out, array_bytes(od), "cudaMalloc(staging)")) != AROL_OK) return st;
     void* douts[1] = {t->stage_out};
-    if (t->kind == 1 && t->kernel == 1 && t->ds_frames >= 2)
-        return run_host_pipelined(t, host_in[0], host_out[0], s);
+    if (pipelined) return run_host_pipelined(t, host_in[0], host_out[0], s);
     if ((st = arol_task_run(t, dins, douts, stream)) != AROL_OK) return st;
     AROL_CUDA(cudaMemcpyAsync(host_out[0], t->stage_out, array_bytes(od), cudaMemcpyDeviceToHost, s),
               "copy output to host");
@@ -1008,8 +1023,11 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
                                float* grad_taps, void* stream) {
     if (!t || !grad_out || !saved_in || !saved_in[0]) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
-    for (const arol_task_desc& d : t->descs)
+    for (const arol_task_desc& d : t->descs) {
         if (d.elem == AROL_ELEM_MATMUL) return fail(AROL_ERR_UNSUPPORTED, "backward of matmul tasks is not implemented");
+        if (d.in[0].dtype != AROL_F32 || d.out[0].dtype != AROL_F32)
+            return fail(AROL_ERR_UNSUPPORTED, "backward: float32 storage only");
+    }
     arol_status st = remember_device(t);
     if (st != AROL_OK) return st;
     const float* taps = nullptr;
@@ -1067,8 +1085,8 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
 arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* grad_out, void* out, void* grad_in,
                               float* grad_taps, void* stream) {
     if (!t || !in || !in[0] || !grad_out || !out) return fail(AROL_ERR_INVALID, "null argument");
-    if (!(t->kind == 1 && t->kernel == 1))
-        return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd is implemented for the fused separable downscaler chain only");
+    if (!(t->kind == 1 && t->kernel == 1) || t->ds_in_bf16 || t->ds_mid_bf16 || t->ds_out_bf16)
+        return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd is implemented for the float32 fused separable downscaler chain only");
     if (!aligned16(in[0]) || !aligned16(grad_in) || !aligned16(grad_out))
         return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd needs 16-byte aligned input, output-gradient and input-gradient buffers");
     cudaStream_t s = (cudaStream_t)stream;

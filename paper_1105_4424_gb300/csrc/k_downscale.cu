@@ -24,6 +24,8 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "arol_internal.h"
 #include "ptx.h"
 
@@ -685,6 +687,155 @@ bool use_register_variant() {
     return v == 1;
 }
 
+// ---------------------------------------------------------------------------
+// bfloat16 frames (Sec. 5 typeAllocation): the same bulk-copy ring, now with
+// one consumer thread per 8x8 block (one 16-byte shared load holds 8 pixels
+// of a row, so no lane pairs and no shuffles).  The arithmetic is f32; an
+// intermediate declared bfloat16 is rounded to nearest even exactly where the
+// unfused chain would store it; the output is stored as f32 or bfloat16.
+// ---------------------------------------------------------------------------
+constexpr int kB16Stages = 4;
+constexpr int kB16CWarps = 4;
+constexpr int kB16Threads = (kB16CWarps + 1) * 32;
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+template <bool kRoundMid, bool kOutBf16>
+__global__ void __launch_bounds__(kB16Threads, 3) downscale_bf16_kernel(const DownscaleDev p, int Wc, int nch) {
+    extern __shared__ __align__(128) unsigned short smb[];
+    const int sf = 8 * Wc;                                   // bf16 elements per stage
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smb + kB16Stages * sf);
+    const uint32_t full0 = ptx::smem_addr(bars), empty0 = ptx::smem_addr(bars + kB16Stages);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t HB = (uint32_t)p.H >> 3;
+    const uint32_t units = (uint32_t)p.frames * HB * (uint32_t)nch;
+    const int Wo = (p.W >> 3) * 3, Ho = (int)HB * 3;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kB16Stages; ++st) {
+            ptx::mbar_init(full0 + 8 * st, 1);
+            ptx::mbar_init(empty0 + 8 * st, kB16CWarps);
+        }
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    const unsigned short* x = static_cast<const unsigned short*>(static_cast<const void*>(p.x));
+    if (warp == kB16CWarps) {
+        if (lane == 0) {
+            int last[kB16Stages];
+#pragma unroll
+            for (int st = 0; st < kB16Stages; ++st) last[st] = -1;
+            uint32_t i = 0;
+            for (uint32_t u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+                const int st = (int)(i % kB16Stages);
+                if (i >= (uint32_t)kB16Stages && !ptx::mbar_wait(empty0 + 8 * st, ((i / kB16Stages) & 1u) ^ 1u)) {
+                    flag_error(p, 1u);
+                    break;
+                }
+                const uint32_t c = u % (uint32_t)nch, stripe = u / (uint32_t)nch;
+                const uint32_t f = stripe / HB, sy = stripe - f * HB;
+                const int c0 = (int)c * Wc;
+                const uint32_t row_bytes = (uint32_t)min(Wc, p.W - c0) * 2u;
+                const uint32_t fb = full0 + 8 * st;
+                ptx::mbar_expect_tx(fb, 8u * row_bytes);
+                const unsigned short* xs = x + ((int64_t)f * p.H + 8 * sy) * (int64_t)p.W + c0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    ptx::bulk_g2s(ptx::smem_addr(smb + st * sf + r * Wc), xs + (int64_t)r * p.W, row_bytes, fb);
+                last[st] = (int)i;
+            }
+#pragma unroll
+            for (int st = 0; st < kB16Stages; ++st)
+                if (last[st] >= 0) ptx::mbar_wait(full0 + 8 * st, ((uint32_t)last[st] / kB16Stages) & 1u);
+        }
+        return;
+    }
+    float hh[3][8], hv[3][8];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            hh[j][k] = __ldg(p.taps + j * 8 + k);
+            hv[j][k] = __ldg(p.taps + 24 + j * 8 + k);
+        }
+    uint32_t i = 0;
+    for (uint32_t u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+        const int st = (int)(i % kB16Stages);
+        if (!ptx::mbar_wait(full0 + 8 * st, (i / kB16Stages) & 1u)) {
+            flag_error(p, 2u);
+            break;
+        }
+        const uint32_t c = u % (uint32_t)nch, stripe = u / (uint32_t)nch;
+        const uint32_t f = stripe / HB, sy = stripe - f * HB;
+        const int c0 = (int)c * Wc;
+        const int nb = min(Wc, p.W - c0) >> 3;
+        const unsigned short* src = smb + st * sf;
+        for (int bb = warp * 32; bb < nb; bb += kB16CWarps * 32) {
+            const int b = bb + lane;
+            if (b >= nb) continue;
+            float y[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) y[j][jj] = 0.f;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const uint4 q = *reinterpret_cast<const uint4*>(src + r * Wc + 8 * b);
+                const float xr[8] = {bf16_lo(q.x), bf16_hi(q.x), bf16_lo(q.y), bf16_hi(q.y),
+                                     bf16_lo(q.z), bf16_hi(q.z), bf16_lo(q.w), bf16_hi(q.w)};
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    float mid = hh[j][0] * xr[0];
+#pragma unroll
+                    for (int k = 1; k < 8; ++k) mid = fmaf(hh[j][k], xr[k], mid);
+                    if (kRoundMid) mid = __bfloat162float(__float2bfloat16_rn(mid));
+#pragma unroll
+                    for (int jv = 0; jv < 3; ++jv) y[jv][j] = fmaf(hv[jv][r], mid, y[jv][j]);
+                }
+            }
+            const int64_t ob = ((int64_t)f * Ho + 3 * sy) * (int64_t)Wo + 3 * ((c0 >> 3) + b);
+#pragma unroll
+            for (int jv = 0; jv < 3; ++jv)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (kOutBf16) static_cast<__nv_bfloat16*>(static_cast<void*>(p.y))[ob + (int64_t)jv * Wo + j] =
+                        __float2bfloat16_rn(y[jv][j]);
+                    else p.y[ob + (int64_t)jv * Wo + j] = y[jv][j];
+                }
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(empty0 + 8 * st);
+    }
+}
+
+// Column chunk of the bf16 variant: at most 1024 columns, a multiple of 64.
+int bf16_chunk(int W) {
+    const int n = (W + 1023) / 1024;
+    const int wc = (W + n - 1) / n;
+    return (wc + 63) / 64 * 64;
+}
+
+template <bool kRoundMid, bool kOutBf16>
+cudaError_t launch_bf16_variant(const DownscaleDev& p, cudaStream_t s) {
+    const int Wc = bf16_chunk(p.W);
+    const int nch = (p.W + Wc - 1) / Wc;
+    const size_t smem = (size_t)kB16Stages * 8 * Wc * 2 + 2 * kB16Stages * 8;
+    static int last_wc = -1, per_sm = 1;
+    if (Wc != last_wc) {
+        cudaError_t e = cudaFuncSetAttribute(downscale_bf16_kernel<kRoundMid, kOutBf16>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, downscale_bf16_kernel<kRoundMid, kOutBf16>, kB16Threads, smem);
+        per_sm = n > 0 ? n : 1;
+        last_wc = Wc;
+    }
+    const uint32_t units = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * (uint32_t)nch;
+    const uint32_t cap = (uint32_t)(device_sm_count() * per_sm);
+    downscale_bf16_kernel<kRoundMid, kOutBf16><<<(int)(units < cap ? units : cap), kB16Threads, smem, s>>>(p, Wc, nch);
+    return cudaGetLastError();
+}
+
 int fwd_grid(uint32_t items) {
     static int per_sm = 0;
     if (!per_sm) {
@@ -729,6 +880,10 @@ int downscale_bwd_partials(int sm_count, int W) {
 cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s) {
     const uint32_t items = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * ((uint32_t)p.W >> 2);
     if (items == 0) return cudaSuccess;
+    if (p.in_bf16) {
+        if (p.mid_bf16) return p.out_bf16 ? launch_bf16_variant<true, true>(p, s) : launch_bf16_variant<true, false>(p, s);
+        return p.out_bf16 ? launch_bf16_variant<false, true>(p, s) : launch_bf16_variant<false, false>(p, s);
+    }
     if (!use_register_variant()) {
         const int Wc = bulk_chunk(p.W);
         const uint32_t units = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * (uint32_t)((p.W + Wc - 1) / Wc);

@@ -7,6 +7,8 @@
 // so the device computes the base (o + P r) mod s once per repetition and then
 // walks the pattern by adding fitting columns with one conditional subtract
 // per dimension (strength-reduced modulo), all in 32-bit registers.
+#include <cuda_bf16.h>
+
 #include "arol_internal.h"
 #include "ptx.h"
 
@@ -98,6 +100,18 @@ __device__ __forceinline__ void decode_rep(const TaskDev& t, int64_t lr, bool wi
 }
 
 // One repetition of a copy or fir task: gather, elementary task, scatter.
+// FIR storage: f32, or bfloat16 widened exactly on load and rounded to
+// nearest even on store; the arithmetic is f32 either way.
+__device__ __forceinline__ float load_value(const TaskDev& t, int64_t off) {
+    if (t.in_bf16) return __uint_as_float((uint32_t)__ldg(static_cast<const unsigned short*>(t.x) + off) << 16);
+    return __ldg(static_cast<const float*>(t.x) + off);
+}
+
+__device__ __forceinline__ void store_value(const TaskDev& t, int64_t off, float v) {
+    if (t.out_bf16) static_cast<__nv_bfloat16*>(t.y)[off] = __float2bfloat16_rn(v);
+    else static_cast<float*>(t.y)[off] = v;
+}
+
 // Contiguous-row pattern walk: offset of the row start plus a coordinate
 // along the last dimension that wraps to 0 at its extent.
 struct RowWalk {
@@ -138,14 +152,12 @@ __device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_
         }
         return;
     }
-    const float* x = static_cast<const float*>(t.x);
-    float* y = static_cast<float*>(t.y);
     const int m = t.m;
     float acc[MAXM];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) acc[j] = 0.f;
     for (int k = 0; k < n; ++k) {
-        const float p = __ldg(x + wi.off());
+        const float p = load_value(t, wi.off());
         wi.next();
         const float* h = t.taps + k;
 #pragma unroll
@@ -155,7 +167,7 @@ __device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
         if (j < m) {
-            y[wo.off()] = acc[j];
+            store_value(t, wo.off(), acc[j]);
             wo.next();
         }
     }
@@ -197,14 +209,12 @@ __device__ __forceinline__ void process_rep(const TaskDev& t, int64_t lr) {
         return;
     }
     // FIR bank: y[j] = sum_k H[j,k] p[k], accumulated in k order with fma.
-    const float* x = static_cast<const float*>(t.x);
-    float* y = static_cast<float*>(t.y);
     const int m = t.m;
     float acc[MAXM];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) acc[j] = 0.f;
     for (int k = 0; k < n; ++k) {
-        const float p = __ldg(x + offset_of(t.in, wi.cur));
+        const float p = load_value(t, offset_of(t.in, wi.cur));
         wi.next(t.in);
         const float* h = t.taps + k;
 #pragma unroll
@@ -214,7 +224,7 @@ __device__ __forceinline__ void process_rep(const TaskDev& t, int64_t lr) {
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
         if (j < m) {
-            y[offset_of(t.out, wo.cur)] = acc[j];
+            store_value(t, offset_of(t.out, wo.cur), acc[j]);
             wo.next(t.out);
         }
     }

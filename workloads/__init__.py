@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "rng", "port", "task", "fir_row_task", "downscale_chain",
-    "config0", "config1", "config2", "config3", "config4",
+    "config0", "config1", "config1_bf16", "config2", "config3", "config4",
     "bf16_round", "bf16_bits_to_f32", "random_tiler_task",
 ]
 
@@ -69,7 +69,7 @@ def fir_row_task(height, width, T, m, step, taps):
     return task((height, reps), "fir", [inp], [out], taps)
 
 
-def downscale_chain(frames, height, width, taps_h, taps_v, step_h=8, step_v=8):
+def downscale_chain(frames, height, width, taps_h, taps_v, step_h=8, step_v=8, dtypes=("f32", "f32", "f32")):
     """Horizontal then vertical FIR downscaler on rank-3 (frames, height, width).
 
     The frame dimension enters every tiler as an extra array dimension and an
@@ -85,21 +85,32 @@ def downscale_chain(frames, height, width, taps_h, taps_v, step_h=8, step_v=8):
     mid_w = wr * mh
     hr = height // step_v
     out_h = hr * mv
+    d_in, d_mid, d_out = dtypes
     t_h = task(
         (frames, height, wr), "fir",
         [port((frames, height, width), (0, 0, 0),
-              ((1, 0, 0), (0, 1, 0), (0, 0, step_h)), ((0,), (0,), (1,)), (th,))],
+              ((1, 0, 0), (0, 1, 0), (0, 0, step_h)), ((0,), (0,), (1,)), (th,), d_in)],
         [port((frames, height, mid_w), (0, 0, 0),
-              ((1, 0, 0), (0, 1, 0), (0, 0, mh)), ((0,), (0,), (1,)), (mh,))],
+              ((1, 0, 0), (0, 1, 0), (0, 0, mh)), ((0,), (0,), (1,)), (mh,), d_mid)],
         taps_h)
     t_v = task(
         (frames, hr, mid_w), "fir",
         [port((frames, height, mid_w), (0, 0, 0),
-              ((1, 0, 0), (0, step_v, 0), (0, 0, 1)), ((0,), (1,), (0,)), (tv,))],
+              ((1, 0, 0), (0, step_v, 0), (0, 0, 1)), ((0,), (1,), (0,)), (tv,), d_mid)],
         [port((frames, out_h, mid_w), (0, 0, 0),
-              ((1, 0, 0), (0, mv, 0), (0, 0, 1)), ((0,), (1,), (0,)), (mv,))],
+              ((1, 0, 0), (0, mv, 0), (0, 0, 1)), ((0,), (1,), (0,)), (mv,), d_out)],
         taps_v)
     return [t_h, t_v]
+
+
+def config1_bf16(seed=0, frames=64, height=1080, width=1920, mid="f32", out="bf16"):
+    """The chained downscaler with bfloat16 frames: X drawn as in config1
+    (U[0,1) float32), then rounded to bfloat16 (RNE); returns bit patterns."""
+    g = rng(seed)
+    x = bf16_round(g.random((frames, height, width), dtype=np.float32))
+    Hh = _taps(g, 3, 8)
+    Hv = _taps(g, 3, 8)
+    return downscale_chain(frames, height, width, Hh, Hv, dtypes=("bf16", mid, out)), [x]
 
 
 def _taps(g, m, T):
