@@ -358,6 +358,40 @@ def bench_bf16(A, torch, stream, flush, reps, hbm):
             "unique_bytes": nbytes, "gbs": gbs, "frac_of_hbm": gbs / hbm}
 
 
+def bench_cg(A, torch, stream, flush, reps, hbm):
+    """Conjugate gradient of the case study on a synthetic SPD matrix with the
+    paper's N and NNZ (27-point stencil on 51^3), tol 1e-10, float64."""
+    from oracle import cg as CG
+    row_ptr, col, vals, b = W.stencil27_csr(51)
+    rp, cd, vd = (torch.from_numpy(a).cuda() for a in (row_ptr, col, vals))
+    solver = A.ConjugateGradient(rp, cd, vd)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    solver.solve(bd, x, 1e-10, 1000)
+    ts = []
+    for _ in range(max(3, min(reps, 10))):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters, rel = solver.solve(bd, x, 1e-10, 1000)[1:]
+        ts.append(time.perf_counter() - t0)
+    solve_s = statistics.median(ts)
+    y = torch.empty_like(bd)
+    spmv_hbm = statistics.median(time_each_flushed(lambda: solver.spmv(bd, y), reps, stream, flush))
+    spmv_l2 = time_loop(lambda: solver.spmv(bd, y), 20, stream) / 20
+    n, nnz = len(b), int(row_ptr[-1])
+    nbytes = 12 * nnz + 8 * (n + 1) + 16 * n
+    t0 = time.perf_counter()
+    _, k_cpu, _ = CG.cg(row_ptr, col, vals, b, tol=1e-10)
+    cpu_s = time.perf_counter() - t0
+    return {"n": n, "nnz": nnz, "tol": 1e-10, "iterations": iters, "rel_residual": rel, "solve_ms": solve_s * 1e3,
+            "ms_per_iteration": solve_s * 1e3 / max(iters, 1), "spmv_us_after_l2_flush": spmv_hbm * 1e3,
+            "spmv_gbs_after_l2_flush": nbytes / (spmv_hbm * 1e-3) / 1e9, "spmv_frac_of_hbm": nbytes / (spmv_hbm * 1e-3) / 1e9 / hbm,
+            "spmv_us_l2_resident": spmv_l2 * 1e3, "oracle_cpu_s": cpu_s, "oracle_iterations": k_cpu,
+            "paper_table1_context": {"hardware": "Tesla T10 (OpenCL, 1 GPU) / Core 2 Duo (Matlab pcg), FP64",
+                                     "opencl_1gpu_s": 0.659, "matlab_pcg_s": 3.17, "iterations": 116}}
+
+
 def bench_config0(A, torch, stream, reps):
     tk, (x,) = W.config0()
     t = A.Task(tk)
@@ -499,6 +533,7 @@ def run_gpu(args):
         line["fwd_bwd"] = bench_backward(A, torch, stream, flush, reps)
         line["matmul"] = bench_matmul(A, torch, stream, flush, reps, bf16)
         line["bf16_storage"] = bench_bf16(A, torch, stream, flush, reps, hbm)
+        line["cg"] = bench_cg(A, torch, stream, flush, reps, hbm)
         del flush
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_chain()
@@ -534,6 +569,10 @@ def run_case(args):
         out = bench_backward(A, torch, stream, flush, reps)
     elif args.case == "matmul":
         out = bench_matmul(A, torch, stream, flush, reps, bf16)
+    elif args.case == "cg":
+        out = bench_cg(A, torch, stream, flush, reps, hbm)
+    elif args.case == "bf16":
+        out = bench_bf16(A, torch, stream, flush, reps, hbm)
     else:
         out = bench_config0(A, torch, stream, reps)
     print(json.dumps({"case": args.case, **out}))
@@ -548,7 +587,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["batched", "backward", "matmul", "config0"],
+    ap.add_argument("--case", choices=["batched", "backward", "matmul", "config0", "cg", "bf16"],
                     help="run one extra measurement alone (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="batched case: keep the default launch shape")
     args = ap.parse_args(argv)

@@ -242,6 +242,46 @@ int64_t arol_abi_struct_size(int which);
  * record. */
 arol_status arol_task_sync_status(arol_task t, void* stream);
 
+/* ---- sparse rows and conjugate gradient (Sec. 7 case study) -------------- */
+
+/* The case study of Sec. 7 solves a symmetric positive definite system stored
+ * in Compressed Sparse Row format with conjugate gradient; its DGEMV(sparse)
+ * step is a repetitive task over the rows, where row i gathers the columns of
+ * its nonzeros, and a continue-condition ends the loop (Table 1: N = 132651,
+ * NNZ = 3442951, tol = 1e-10, double precision).  All matrix and vector
+ * pointers are DEVICE pointers owned by the caller: row_ptr (n_rows + 1
+ * int64, row_ptr[0] = 0, non-decreasing, row_ptr[n_rows] = nnz), col_idx
+ * (nnz int32 in [0, n_rows)), vals (nnz float64).  Column indices are not
+ * checked on the device: out-of-range entries are the caller's error. */
+typedef struct arol_cg_s* arol_cg;
+
+/* y = A x (float64) with a fixed summation order: 1, 2, 4 or 8 lanes per row
+ * chosen from the mean row length (or by the AROL_SPMV_LPR environment
+ * variable).  x and y have n_rows entries and must not overlap. */
+arol_status arol_csr_spmv(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                          const double* vals, const double* x, double* y, void* stream);
+
+/* Prepare conjugate gradient on A: allocates five float64 work vectors, the
+ * reduction scratch and the device-side state, and captures a CUDA graph of
+ * eight iterations.  The matrix buffers must stay alive and unchanged while
+ * the handle is used.  A must be symmetric positive definite (not checked). */
+arol_status arol_cg_create(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                           const double* vals, arol_cg* out);
+
+/* Solve A x = b: x holds the initial guess on entry and the solution on
+ * return.  Iterates r = b - A x, p = r; alpha = r.r / p.Ap; x += alpha p;
+ * r -= alpha Ap; beta = r.r(new) / r.r(old); p = r + beta p, until
+ * ||r|| <= tol ||b|| or max_iter iterations.  The whole loop runs on the
+ * device (reductions in a fixed order: the same bits every run); the call
+ * synchronizes `stream` and reports the iteration count and ||r|| / ||b||. */
+arol_status arol_cg_solve(arol_cg h, const double* b, double* x, double tol, int max_iter, int* iterations,
+                          double* rel_residual, void* stream);
+
+void arol_cg_destroy(arol_cg h);
+
+/* The calling thread's last error message of the sparse/CG entry points. */
+arol_status arol_cg_last_error(char* buf, size_t len);
+
 /* ---- backward without device allocation ---------------------------------- */
 
 /* The paper has no counterpart to this entry point; it serves callers that

@@ -10,7 +10,7 @@ built.
 """
 from .binding import *  # noqa: F401,F403
 from .binding import ArolError, lib  # noqa: F401
-from .api import Batch, Chain, Task, TaskFunction, apply_task  # noqa: F401
+from .api import Batch, Chain, ConjugateGradient, Task, TaskFunction, apply_task  # noqa: F401
 
 __all__ = [n for n in dir() if n.startswith("arol_")] + [
-    "ArolError", "Task", "Chain", "Batch", "TaskFunction", "apply_task"]
+    "ArolError", "Task", "Chain", "Batch", "TaskFunction", "apply_task", "ConjugateGradient"]

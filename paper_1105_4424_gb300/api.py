@@ -205,3 +205,39 @@ class TaskFunction(torch.autograd.Function):
 
 def apply_task(task, x, taps):
     return TaskFunction.apply(task, x, taps)
+
+
+class ConjugateGradient:
+    """CG on a CSR matrix held in device tensors (row_ptr int64, col_idx
+    int32, vals float64); the loop runs on the device."""
+
+    def __init__(self, row_ptr, col_idx, vals):
+        for t, dt in ((row_ptr, torch.int64), (col_idx, torch.int32), (vals, torch.float64)):
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise TypeError(f"expected a contiguous CUDA {dt} tensor")
+        self.n = row_ptr.numel() - 1
+        self.nnz = vals.numel()
+        self._keep = (row_ptr, col_idx, vals)
+        self.handle = B.arol_cg_create(self.n, self.nnz, row_ptr, col_idx, vals)
+
+    def spmv(self, x, y=None, stream=None):
+        y = torch.empty_like(x) if y is None else y
+        row_ptr, col_idx, vals = self._keep
+        B.arol_csr_spmv(self.n, self.nnz, row_ptr, col_idx, vals, x, y, stream)
+        return y
+
+    def solve(self, b, x=None, tol=1e-10, max_iter=1000, stream=None):
+        x = torch.zeros_like(b) if x is None else x
+        iters, rel = B.arol_cg_solve(self.handle, b, x, tol, max_iter, stream)
+        return x, iters, rel
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.arol_cg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

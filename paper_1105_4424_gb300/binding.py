@@ -74,6 +74,10 @@ def _load():
         "arol_batch_config": [c_vp, P(c_i64), P(c_i32), P(c_i32)],
         "arol_last_error": [ctypes.c_char_p, ctypes.c_size_t],
         "arol_downscale_backward_noalloc": [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp],
+        "arol_csr_spmv": [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
+        "arol_cg_create": [c_i64, c_i64, c_vp, c_vp, c_vp, P(c_vp)],
+        "arol_cg_solve": [c_vp, c_vp, c_vp, ctypes.c_double, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double), c_vp],
+        "arol_cg_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -83,6 +87,8 @@ def _load():
     L.arol_task_destroy.restype = None
     L.arol_batch_destroy.argtypes = [c_vp]
     L.arol_batch_destroy.restype = None
+    L.arol_cg_destroy.argtypes = [c_vp]
+    L.arol_cg_destroy.restype = None
     L.arol_version.restype = ctypes.c_int
     L.arol_abi_struct_size.argtypes = [ctypes.c_int]
     L.arol_abi_struct_size.restype = c_i64
@@ -296,3 +302,33 @@ def arol_downscale_backward_noalloc(x, grad_out, taps, frames, height, width, gr
                                              int(width), _ptr(grad_in), _ptr(grad_taps), _stream(stream))
     if st != 0:
         raise ArolError(st, "arol_downscale_backward_noalloc rejected the call")
+
+
+def _check_cg(st):
+    if st != 0:
+        buf = ctypes.create_string_buffer(1024)
+        lib.arol_cg_last_error(buf, len(buf))
+        raise ArolError(st, buf.value.decode(errors="replace"))
+
+
+def arol_csr_spmv(n_rows, nnz, row_ptr, col_idx, vals, x, y, stream=None):
+    _check_cg(lib.arol_csr_spmv(int(n_rows), int(nnz), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(x), _ptr(y),
+                                _stream(stream)))
+
+
+def arol_cg_create(n_rows, nnz, row_ptr, col_idx, vals) -> int:
+    h = c_vp()
+    _check_cg(lib.arol_cg_create(int(n_rows), int(nnz), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), ctypes.byref(h)))
+    return h.value
+
+
+def arol_cg_solve(h, b, x, tol, max_iter, stream=None):
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    _check_cg(lib.arol_cg_solve(h, _ptr(b), _ptr(x), float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(rel),
+                                _stream(stream)))
+    return it.value, rel.value
+
+
+def arol_cg_destroy(h):
+    if h:
+        lib.arol_cg_destroy(h)

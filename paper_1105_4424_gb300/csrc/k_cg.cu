@@ -1,0 +1,413 @@
+// Sparse matrix-vector product over CSR rows and the conjugate-gradient loop
+// (Sec. 7 of the paper: the DGEMV(sparse) step of CG is a repetitive task over
+// the rows of a Compressed Sparse Row matrix, scalar steps run between the
+// repetitive ones, and a continue-condition ends the loop; Table 1 solves
+// N = 132651, NNZ = 3442951 to tol = 1e-10 in double precision).
+//
+// Row i gathers its nonzeros k in [row_ptr[i], row_ptr[i+1]): LPR lanes
+// share a row (chosen from the mean row length), each summing every LPR-th
+// product, then a fixed shuffle tree adds their partial sums.  Dot products are reduced per warp, per CTA
+// (fixed order) and across CTAs by the last CTA to take a ticket (fixed
+// order): results are identical run to run.  One CG iteration is three
+// kernels (A p with p.Ap; x, r update with r.r; the new direction), all on the
+// device; the scalars live in device memory, a "done" word turns later
+// iterations into no-ops, and the host captures iterations into a CUDA graph
+// and polls a page-locked copy of the state between graph launches.
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "arol.h"
+#include "arol_internal.h"
+
+namespace arol {
+namespace {
+
+constexpr int kCgThreads = 256;
+constexpr unsigned kFullMask = 0xffffffffu;
+
+struct CgState {
+    double rr, bb, alpha, beta, pap, tol2;
+    int32_t done, iters, max_iter, pad_;
+    unsigned ticket, pad2_;
+};
+
+struct Csr {
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const double* val;
+    int64_t n;
+};
+
+// (A v)_row with LPR lanes per row (a power of two <= 8); every lane of the
+// group returns the sum.  Lane `sub` adds products k = a + sub, + LPR, ... in
+// order, four per step with all loads issued first; then a fixed shuffle
+// tree adds the LPR partial sums.  Fewer lanes per row means fewer
+// predicated FMAs and adds on the float64 pipe, more means wider loads.
+template <int LPR>
+__device__ __forceinline__ double row_dot(const Csr& A, const double* __restrict__ v, int64_t row, int sub) {
+    double s = 0.0;
+    if (row < A.n) {
+        const int64_t a = __ldg(A.row_ptr + row), z = __ldg(A.row_ptr + row + 1);
+        for (int64_t k0 = a + sub; k0 < z; k0 += 4 * LPR) {
+            double w[4];
+            int32_t c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = k0 + u * LPR;
+                w[u] = k < z ? __ldg(A.val + k) : 0.0;
+                c[u] = k < z ? __ldg(A.col + k) : -1;
+            }
+            double xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? __ldg(v + c[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c[u] >= 0) s = fma(w[u], xv[u], s);
+        }
+    }
+#pragma unroll
+    for (int off = LPR / 2; off > 0; off >>= 1) s += __shfl_xor_sync(kFullMask, s, off, LPR);
+    return s;
+}
+
+// Block sum of one value per thread in a fixed order (warp tree, then warps in order).
+__device__ __forceinline__ double block_sum(double v, double* s_warp) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFullMask, v, off);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s_warp[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kCgThreads / 32; ++i) t += s_warp[i];
+    __syncthreads();
+    return t;   // valid in thread 0
+}
+
+// Stores this CTA's partial(s); returns true in every thread of the last CTA
+// to finish, after which partials of all CTAs are visible.
+__device__ __forceinline__ bool last_cta(CgState* st) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1 ? 1 : 0;
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// Sum of n partials in a fixed order by the whole CTA (valid in thread 0).
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int n, double* s_warp) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += kCgThreads) a += __ldcg(part + i);
+    return block_sum(a, s_warp);
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(kCgThreads) spmv_kernel(const Csr A, const double* __restrict__ x, double* __restrict__ y) {
+    constexpr int kRowsPerBlock = kCgThreads / LPR;
+    const int sub = threadIdx.x & (LPR - 1);
+    const int64_t stride = (int64_t)gridDim.x * kRowsPerBlock;
+    for (int64_t base = (int64_t)blockIdx.x * kRowsPerBlock; base < A.n; base += stride) {
+        const int64_t row = base + threadIdx.x / LPR;
+        const double s = row_dot<LPR>(A, x, row, sub);
+        if (sub == 0 && row < A.n) y[row] = s;
+    }
+}
+
+// r = b - A x, p = r; rr = r.r, bb = b.b; done if ||r|| <= tol ||b||.
+template <int LPR>
+__global__ void __launch_bounds__(kCgThreads) cg_init_kernel(const Csr A, const double* __restrict__ b,
+                                                             const double* __restrict__ x, double* __restrict__ r,
+                                                             double* __restrict__ p, double* __restrict__ part,
+                                                             CgState* st) {
+    __shared__ double s_warp[kCgThreads / 32];
+    constexpr int kRowsPerBlock = kCgThreads / LPR;
+    const int sub = threadIdx.x & (LPR - 1);
+    double rr = 0.0, bb = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kRowsPerBlock;
+    for (int64_t base = (int64_t)blockIdx.x * kRowsPerBlock; base < A.n; base += stride) {
+        const int64_t row = base + threadIdx.x / LPR;
+        const double ax = row_dot<LPR>(A, x, row, sub);
+        if (sub == 0 && row < A.n) {
+            const double bi = b[row], ri = bi - ax;
+            r[row] = ri;
+            p[row] = ri;
+            rr = fma(ri, ri, rr);
+            bb = fma(bi, bi, bb);
+        }
+    }
+    const double trr = block_sum(rr, s_warp), tbb = block_sum(bb, s_warp);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = trr;
+        part[gridDim.x + blockIdx.x] = tbb;
+    }
+    if (!last_cta(st)) return;
+    const double srr = sum_partials(part, gridDim.x, s_warp), sbb = sum_partials(part + gridDim.x, gridDim.x, s_warp);
+    if (threadIdx.x == 0) {
+        st->rr = srr;
+        st->bb = sbb;
+        st->iters = 0;
+        st->done = (srr <= st->tol2 * sbb || st->max_iter <= 0) ? 1 : 0;
+        st->ticket = 0u;
+    }
+}
+
+// Ap = A p and alpha = rr / p.Ap.
+template <int LPR>
+__global__ void __launch_bounds__(kCgThreads) cg_ap_kernel(const Csr A, const double* __restrict__ p,
+                                                           double* __restrict__ ap, double* __restrict__ part,
+                                                           CgState* st) {
+    __shared__ double s_warp[kCgThreads / 32];
+    if (st->done) return;
+    constexpr int kRowsPerBlock = kCgThreads / LPR;
+    const int sub = threadIdx.x & (LPR - 1);
+    double pap = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kRowsPerBlock;
+    for (int64_t base = (int64_t)blockIdx.x * kRowsPerBlock; base < A.n; base += stride) {
+        const int64_t row = base + threadIdx.x / LPR;
+        const double s = row_dot<LPR>(A, p, row, sub);
+        if (sub == 0 && row < A.n) {
+            ap[row] = s;
+            pap = fma(p[row], s, pap);
+        }
+    }
+    const double t = block_sum(pap, s_warp);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (!last_cta(st)) return;
+    const double s = sum_partials(part, gridDim.x, s_warp);
+    if (threadIdx.x == 0) {
+        st->pap = s;
+        st->alpha = st->rr / s;
+        st->ticket = 0u;
+    }
+}
+
+// x += alpha p, r -= alpha Ap; rr_new = r.r, beta = rr_new / rr; stop test.
+__global__ void __launch_bounds__(kCgThreads) cg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                               const double* __restrict__ p, const double* __restrict__ ap,
+                                                               double* __restrict__ part, CgState* st) {
+    __shared__ double s_warp[kCgThreads / 32];
+    if (st->done) return;
+    const double alpha = st->alpha;
+    double rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kCgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCgThreads) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, ap[i], r[i]);
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+    }
+    const double t = block_sum(rr, s_warp);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (!last_cta(st)) return;
+    const double s = sum_partials(part, gridDim.x, s_warp);
+    if (threadIdx.x == 0) {
+        st->beta = s / st->rr;
+        st->rr = s;
+        st->iters += 1;
+        if (s <= st->tol2 * st->bb || st->iters >= st->max_iter) st->done = 1;
+        st->ticket = 0u;
+    }
+}
+
+// p = r + beta p.
+__global__ void __launch_bounds__(kCgThreads) cg_direction_kernel(int64_t n, const double* __restrict__ r,
+                                                                  double* __restrict__ p, const CgState* st) {
+    if (st->done) return;
+    const double beta = st->beta;
+    for (int64_t i = (int64_t)blockIdx.x * kCgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCgThreads)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+// Lanes per row: AROL_SPMV_LPR (1, 2, 4 or 8) when set, else about 8 to 16
+// products per lane from the mean row length (on the 27-point system, mean 26,
+// two lanes per row beat one, four and eight).  Fixed per matrix, so results
+// are reproducible.
+int choose_lpr(int64_t n, int64_t nnz) {
+    const char* e = std::getenv("AROL_SPMV_LPR");
+    const int v = e ? std::atoi(e) : 0;
+    if (v == 1 || v == 2 || v == 4 || v == 8) return v;
+    const double mean = n > 0 ? (double)nnz / (double)n : 0.0;
+    return mean < 16 ? 1 : mean < 32 ? 2 : mean < 64 ? 4 : 8;
+}
+
+int row_grid(int64_t n, int lpr) {
+    const int rows_per_block = kCgThreads / lpr;
+    const int64_t want = (n + rows_per_block - 1) / rows_per_block;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+int vec_grid(int64_t n) {
+    const int64_t want = (n + kCgThreads - 1) / kCgThreads;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+thread_local std::string t_cg_err;
+
+}  // namespace
+}  // namespace arol
+
+using namespace arol;
+
+struct arol_cg_s {
+    Csr A{};
+    int device = -1;
+    int lpr = 8;
+    double *r = nullptr, *p = nullptr, *ap = nullptr, *xw = nullptr, *bw = nullptr, *part = nullptr;
+    CgState* st = nullptr;
+    CgState* host_st = nullptr;   // page-locked copy for polling
+    int grid_rows = 1, grid_vec = 1, chunk = 8;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+namespace {
+
+arol_status cg_fail(arol_status st, const std::string& msg) {
+    t_cg_err = msg;
+    return st;
+}
+
+#define CG_CUDA(call, what)                                                                 \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return cg_fail(AROL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+arol_status arol_cg_last_error(char* buf, size_t len) {
+    if (buf && len) {
+        std::strncpy(buf, t_cg_err.c_str(), len - 1);
+        buf[len - 1] = 0;
+    }
+    return AROL_OK;
+}
+
+arol_status arol_csr_spmv(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                          const double* vals, const double* x, double* y, void* stream) {
+    if (n_rows < 0 || nnz < 0) return cg_fail(AROL_ERR_INVALID, "negative size");
+    if (n_rows == 0) return AROL_OK;
+    if (!row_ptr || !x || !y || (nnz > 0 && (!col_idx || !vals))) return cg_fail(AROL_ERR_INVALID, "null pointer");
+    Csr A{row_ptr, col_idx, vals, n_rows};
+    const int lpr = choose_lpr(n_rows, nnz);
+    const int grid = row_grid(n_rows, lpr);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (lpr) {
+    case 1: spmv_kernel<1><<<grid, kCgThreads, 0, s>>>(A, x, y); break;
+    case 2: spmv_kernel<2><<<grid, kCgThreads, 0, s>>>(A, x, y); break;
+    case 4: spmv_kernel<4><<<grid, kCgThreads, 0, s>>>(A, x, y); break;
+    default: spmv_kernel<8><<<grid, kCgThreads, 0, s>>>(A, x, y); break;
+    }
+    CG_CUDA(cudaGetLastError(), "spmv launch");
+    return AROL_OK;
+}
+
+arol_status arol_cg_create(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                           const double* vals, arol_cg* out) {
+    if (!out) return cg_fail(AROL_ERR_INVALID, "null handle pointer");
+    *out = nullptr;
+    if (n_rows < 1 || nnz < 0 || !row_ptr || (nnz > 0 && (!col_idx || !vals)))
+        return cg_fail(AROL_ERR_INVALID, "bad matrix");
+    arol_cg h = new (std::nothrow) arol_cg_s();
+    if (!h) return cg_fail(AROL_ERR_INVALID, "out of host memory");
+    h->A = Csr{row_ptr, col_idx, vals, n_rows};
+    cudaGetDevice(&h->device);
+    h->lpr = choose_lpr(n_rows, nnz);
+    h->grid_rows = row_grid(n_rows, h->lpr);
+    h->grid_vec = vec_grid(n_rows);
+    const size_t vb = (size_t)n_rows * sizeof(double);
+    const int nparts = 2 * (h->grid_rows > h->grid_vec ? h->grid_rows : h->grid_vec);
+    cudaError_t e = cudaSuccess;
+    double** vecs[] = {&h->r, &h->p, &h->ap, &h->xw, &h->bw};
+    for (double** v : vecs)
+        if (e == cudaSuccess) e = cudaMalloc(v, vb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->part, (size_t)nparts * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->st, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaMemset(h->st, 0, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->host_st, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // one graph of `chunk` iterations (three kernels each)
+        e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        for (int it = 0; it < h->chunk && e == cudaSuccess; ++it) {
+            switch (h->lpr) {
+            case 1: cg_ap_kernel<1><<<h->grid_rows, kCgThreads, 0, h->cap_stream>>>(h->A, h->p, h->ap, h->part, h->st); break;
+            case 2: cg_ap_kernel<2><<<h->grid_rows, kCgThreads, 0, h->cap_stream>>>(h->A, h->p, h->ap, h->part, h->st); break;
+            case 4: cg_ap_kernel<4><<<h->grid_rows, kCgThreads, 0, h->cap_stream>>>(h->A, h->p, h->ap, h->part, h->st); break;
+            default: cg_ap_kernel<8><<<h->grid_rows, kCgThreads, 0, h->cap_stream>>>(h->A, h->p, h->ap, h->part, h->st); break;
+            }
+            cg_update_kernel<<<h->grid_vec, kCgThreads, 0, h->cap_stream>>>(n_rows, h->xw, h->r, h->p, h->ap, h->part, h->st);
+            cg_direction_kernel<<<h->grid_vec, kCgThreads, 0, h->cap_stream>>>(n_rows, h->r, h->p, h->st);
+            e = cudaGetLastError();
+        }
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &h->graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+    }
+    if (e != cudaSuccess) {
+        arol_cg_destroy(h);
+        return cg_fail(AROL_ERR_CUDA, std::string("cg setup: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    return AROL_OK;
+}
+
+arol_status arol_cg_solve(arol_cg h, const double* b, double* x, double tol, int max_iter, int* iterations,
+                          double* rel_residual, void* stream) {
+    if (!h || !b || !x) return cg_fail(AROL_ERR_INVALID, "null argument");
+    if (!(tol >= 0.0) || max_iter < 0) return cg_fail(AROL_ERR_INVALID, "bad tolerance or iteration limit");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = (size_t)h->A.n * sizeof(double);
+    CgState init{};
+    init.tol2 = tol * tol;
+    init.max_iter = max_iter;
+    std::memcpy(h->host_st, &init, sizeof init);
+    CG_CUDA(cudaMemcpyAsync(h->st, h->host_st, sizeof(CgState), cudaMemcpyHostToDevice, s), "upload state");
+    CG_CUDA(cudaMemcpyAsync(h->bw, b, vb, cudaMemcpyDeviceToDevice, s), "copy b");
+    CG_CUDA(cudaMemcpyAsync(h->xw, x, vb, cudaMemcpyDeviceToDevice, s), "copy x0");
+    switch (h->lpr) {
+    case 1: cg_init_kernel<1><<<h->grid_rows, kCgThreads, 0, s>>>(h->A, h->bw, h->xw, h->r, h->p, h->part, h->st); break;
+    case 2: cg_init_kernel<2><<<h->grid_rows, kCgThreads, 0, s>>>(h->A, h->bw, h->xw, h->r, h->p, h->part, h->st); break;
+    case 4: cg_init_kernel<4><<<h->grid_rows, kCgThreads, 0, s>>>(h->A, h->bw, h->xw, h->r, h->p, h->part, h->st); break;
+    default: cg_init_kernel<8><<<h->grid_rows, kCgThreads, 0, s>>>(h->A, h->bw, h->xw, h->r, h->p, h->part, h->st); break;
+    }
+    CG_CUDA(cudaGetLastError(), "cg init launch");
+    for (int launched = 0;; launched += h->chunk) {
+        CG_CUDA(cudaMemcpyAsync(h->host_st, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s), "read state");
+        CG_CUDA(cudaStreamSynchronize(s), "synchronize");
+        if (h->host_st->done || launched >= max_iter) break;
+        CG_CUDA(cudaGraphLaunch(h->exec, s), "graph launch");
+    }
+    CG_CUDA(cudaMemcpyAsync(x, h->xw, vb, cudaMemcpyDeviceToDevice, s), "copy solution");
+    CG_CUDA(cudaStreamSynchronize(s), "synchronize");
+    if (iterations) *iterations = h->host_st->iters;
+    if (rel_residual) *rel_residual = h->host_st->bb > 0 ? __builtin_sqrt(h->host_st->rr / h->host_st->bb) : 0.0;
+    return AROL_OK;
+}
+
+void arol_cg_destroy(arol_cg h) {
+    if (!h) return;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaFree(h->r);
+    cudaFree(h->p);
+    cudaFree(h->ap);
+    cudaFree(h->xw);
+    cudaFree(h->bw);
+    cudaFree(h->part);
+    cudaFree(h->st);
+    if (h->host_st) cudaFreeHost(h->host_st);
+    delete h;
+}
+
+}  // extern "C"

@@ -30,7 +30,7 @@ import numpy as np
 __all__ = [
     "rng", "port", "task", "fir_row_task", "downscale_chain",
     "config0", "config1", "config1_bf16", "config2", "config3", "config4",
-    "bf16_round", "bf16_bits_to_f32", "random_tiler_task",
+    "bf16_round", "bf16_bits_to_f32", "random_tiler_task", "stencil27_csr",
 ]
 
 
@@ -283,3 +283,65 @@ def random_tiler_task(g: np.random.Generator, elem="copy", max_side=12,
     oorigin = tuple(int(v) for v in g.integers(-max_abs, max_abs + 1, size=len(oshape)))
     out = port(tuple(oshape), oorigin, tuple(opav), tuple(ofit), S_out)
     return task(R, elem, [inp], [out], taps)
+
+
+def stencil27_csr(side=51, seed=0, shift=0.012):
+    """A symmetric positive definite CSR matrix with the sparsity of a 27-point
+    stencil on a side^3 grid (side = 51 gives N = 132651 rows and
+    NNZ = 151^3 = 3442951 nonzeros) and a right-hand side.
+
+    Off-diagonal weights w_ij = w_ji ~ U(0.5, 1.5) are drawn once per
+    neighbour pair (i < j), in row-major order of i, then neighbour offset
+    order; a_ij = -w_ij and a_ii = (1 + shift) * sum_j w_ij (strictly
+    diagonally dominant, hence SPD).  Then b ~ N(0, 1).
+    Returns (row_ptr int64, col_idx int32, vals float64, b float64).
+    """
+    g = rng(seed)
+    n = side ** 3
+    idx = np.arange(n, dtype=np.int64)
+    iz, iy, ix = idx // (side * side), (idx // side) % side, idx % side
+    offs = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    upper = [o for o in offs if (o[0], o[1], o[2]) > (0, 0, 0)]     # j > i in row-major order
+    rows, cols, ws = [], [], []
+    for (dz, dy, dx) in upper:
+        ok = (iz + dz >= 0) & (iz + dz < side) & (iy + dy >= 0) & (iy + dy < side) & (ix + dx >= 0) & (ix + dx < side)
+        i = idx[ok]
+        j = i + dz * side * side + dy * side + dx
+        rows.append(i)
+        cols.append(j)
+        ws.append(g.uniform(0.5, 1.5, size=i.size))
+    i = np.concatenate(rows)
+    j = np.concatenate(cols)
+    w = np.concatenate(ws)
+    diag = np.zeros(n)
+    np.add.at(diag, i, w)
+    np.add.at(diag, j, w)
+    r = np.concatenate([i, j, idx])
+    c = np.concatenate([j, i, idx])
+    v = np.concatenate([-w, -w, (1.0 + shift) * diag])
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, r + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    b = g.standard_normal(n)
+    return row_ptr, c.astype(np.int32), v, b
+
+
+def ragged_csr(n=3000, seed=0, max_row=70):
+    """A general (unsymmetric) CSR matrix with ragged rows for SpMV edge cases:
+    row lengths uniform in [0, max_row] with every tenth row empty and every
+    seventh row a single entry; columns distinct, sorted, uniform in [0, n);
+    values ~ N(0, 1).  Returns (row_ptr int64, col_idx int32, vals float64).
+    """
+    g = rng(seed)
+    lens = g.integers(0, max_row + 1, size=n)
+    lens[::10] = 0
+    lens[3::7] = 1
+    lens = np.minimum(lens, n)
+    cols = [np.sort(g.choice(n, size=int(k), replace=False)) for k in lens]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(lens)
+    col = np.concatenate(cols).astype(np.int32) if n else np.zeros(0, np.int32)
+    vals = g.standard_normal(int(row_ptr[-1]))
+    return row_ptr, col, vals
