@@ -317,6 +317,40 @@ def bench_batched(A, torch, stream, flush, reps, tune=True):
             "launches_batched": 1, "launches_per_task": len(tasks), "autotuned": cfg}
 
 
+def bench_batched_chains(A, torch, stream, flush, reps):
+    """128 two-stage downscaler chains of uneven frame sizes in one batch
+    (one graph, one persistent launch per stage) against one launch per
+    stage task and against one fused chain launch per member."""
+    chains, xs = W.chain_batch()
+    b = A.Batch(chains)
+    ins = [torch.from_numpy(x).cuda() for x in xs]
+    outs = b.empty_outputs()
+    run, run_per_task = b.prepare(ins, outs)
+    fused = [A.Chain(c) for c in chains]
+    fouts = [torch.empty_like(o) for o in outs]
+    fused_calls = [f.prepare([x], y) for f, x, y in zip(fused, ins, fouts)]
+
+    def run_fused():
+        for call in fused_calls:
+            call()
+
+    for _ in range(3):
+        run()
+        run_per_task()
+        run_fused()
+    tb = statistics.median(time_each_flushed(run, reps, stream, flush))
+    tp = statistics.median(time_each_flushed(run_per_task, reps, stream, flush))
+    tf = statistics.median(time_each_flushed(run_fused, reps, stream, flush))
+    mid = sum(4 * int(np.prod(c[0]["outputs"][0]["shape"])) for c in chains)
+    nbytes = sum(4 * x.size for x in xs) + sum(4 * int(np.prod(c[-1]["outputs"][0]["shape"])) for c in chains)
+    return {"chains": len(chains), "unique_bytes": nbytes, "intermediate_bytes": mid,
+            "batched_ms": tb, "per_task_ms": tp, "fused_per_chain_ms": tf,
+            "speedup_vs_per_task": tp / tb, "speedup_vs_fused_per_chain": tf / tb,
+            "batched_gbs_unique": nbytes / (tb * 1e-3) / 1e9,
+            "batched_gbs_with_intermediate": (nbytes + 2 * mid) / (tb * 1e-3) / 1e9,
+            "launches": {"batched": 2, "per_task": 2 * len(chains), "fused_per_chain": len(chains)}}
+
+
 def bench_backward(A, torch, stream, flush, reps):
     chain, (x,), w = W.config4()
     c = A.Chain(chain)
@@ -548,6 +582,7 @@ def run_gpu(args):
         reps = max(5, min(args.steps, 20))
         line["config0"] = bench_config0(A, torch, stream, 200)
         line["batched"] = bench_batched(A, torch, stream, flush, reps)
+        line["batched_chains"] = bench_batched_chains(A, torch, stream, flush, reps)
         line["fwd_bwd"] = bench_backward(A, torch, stream, flush, reps)
         line["matmul"] = bench_matmul(A, torch, stream, flush, reps, bf16)
         line["bf16_storage"] = bench_bf16(A, torch, stream, flush, reps, hbm)
@@ -583,6 +618,8 @@ def run_case(args):
     warm_clocks(torch, flush.w)
     if args.case == "batched":
         out = bench_batched(A, torch, stream, flush, reps, tune=not args.no_tune)
+    elif args.case == "chains":
+        out = bench_batched_chains(A, torch, stream, flush, reps)
     elif args.case == "backward":
         out = bench_backward(A, torch, stream, flush, reps)
     elif args.case == "matmul":
@@ -605,7 +642,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["batched", "backward", "matmul", "config0", "cg", "bf16"],
+    ap.add_argument("--case", choices=["batched", "chains", "backward", "matmul", "config0", "cg", "bf16"],
                     help="run one extra measurement alone (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="batched case: keep the default launch shape")
     args = ap.parse_args(argv)

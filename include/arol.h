@@ -194,18 +194,27 @@ arol_status arol_tiler_cover(const arol_array_desc* array, const arol_tiler* til
 
 /* ---- batches of independent tasks ---------------------------------------- */
 
-/* Build a batch of n independent single-input copy/fir tasks (uneven shapes
- * allowed).  The batch owns a device work list of (task, repetition range)
- * tiles, built on first run, and a CUDA graph that launches one persistent
- * kernel over the whole list. */
+/* Build a batch of n independent members (uneven shapes allowed).  A member
+ * is a single-input copy/fir task or a chain of them from arol_chain_create
+ * (Sec. 5: tasks linked through shared arrays), which enters as its tasks,
+ * one per stage, without the fused chain kernels.  The batch copies the
+ * descriptors and host taps (the handles may be destroyed afterwards), owns
+ * one device arena for every chain intermediate, a device work list of
+ * (task, repetition range) tiles grouped by stage, built on first run, and a
+ * CUDA graph that launches one persistent kernel per stage: stage k of every
+ * chain runs after stage k - 1 of every chain.  Matmul tasks and tasks whose
+ * taps live on the device are rejected (AROL_ERR_UNSUPPORTED /
+ * AROL_ERR_INVALID). */
 arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out);
 
-/* Run every task of the batch in one graph launch: in[k] / out[k] are task k's
- * input and output device pointers.  When the pointers differ from the
+/* Run every member of the batch in one graph launch: in[k] / out[k] are
+ * member k's input and output device pointers (for a chain, the first task's
+ * input and the last task's output).  When the pointers differ from the
  * previous call the device table is refreshed (one copy) before the launch. */
 arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out, void* stream);
 
-/* The same tasks with one kernel launch per task, in order, on `stream`:
+/* The same tasks with one kernel launch per task (each stage of a chain is a
+ * task), in order, on `stream`:
  * the same kernel over each task's own tiles, without the graph or the shared
  * tile counter (for comparison with arol_batch_run). */
 arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* const* out, void* stream);

@@ -69,6 +69,21 @@ class Task:
         B.arol_task_run(self.handle, list(ins), [out], stream)
         return out
 
+    def prepare(self, ins, out, stream=None):
+        """Check and marshal the buffers once; returns a callable that runs
+        the task on them (for timing loops)."""
+        for t, p in zip(ins, self.in_ports):
+            _check_tensor(t, p, "input")
+        _check_tensor(out, self.out_port, "output")
+        pin, pout, s = B._ptrs(list(ins)), B._ptrs([out]), B._stream(stream)
+        keep = (list(ins), out)
+
+        def run():
+            B._check(B.lib.arol_task_run(self.handle, pin, pout, s))
+            return keep[1]
+
+        return run
+
     def run_host(self, ins, out, stream=None):
         B.arol_task_run_host(self.handle, list(ins), [out], stream)
         return out
@@ -117,20 +132,35 @@ class Chain(Task):
 
 
 class Batch:
-    """Independent copy/fir tasks run by one persistent, graph-captured launch."""
+    """Independent copy/fir tasks and chains of them, run by one graph
+    launch: one persistent launch per chain stage over every member's tiles
+    of that stage.  A member is a task spec or a list of specs (a chain,
+    whose intermediates the batch allocates); its input is the first task's
+    input, its output the last task's output."""
 
     def __init__(self, specs):
         self.specs = specs
-        subs = [B.arol_task_create(s) for s in specs]
+        subs = []
         try:
+            for s in specs:
+                if isinstance(s, (list, tuple)):
+                    parts = [B.arol_task_create(x) for x in s]
+                    try:
+                        subs.append(B.arol_chain_create(parts))
+                    finally:
+                        for h in parts:
+                            B.arol_task_destroy(h)
+                else:
+                    subs.append(B.arol_task_create(s))
             self.handle = B.arol_batch_create(subs)
         finally:
             for h in subs:
                 B.arol_task_destroy(h)
 
     def empty_outputs(self, device="cuda"):
+        lasts = [s[-1] if isinstance(s, (list, tuple)) else s for s in self.specs]
         return [torch.empty(_out_port(s)["shape"], dtype=_TORCH_DTYPE[_out_port(s)["dtype"]], device=device)
-                for s in self.specs]
+                for s in lasts]
 
     def run(self, ins, outs, stream=None):
         B.arol_batch_run(self.handle, list(ins), list(outs), stream)

@@ -1157,10 +1157,18 @@ void arol_task_destroy(arol_task t) {
 // ==================================================================== batches
 
 struct arol_batch_s {
+    // Internal tasks, member-major: member i (a task or a chain of len_of[i]
+    // tasks) owns internal tasks first_of[i] .. first_of[i] + len_of[i] - 1.
     std::vector<arol_task_desc> descs;
     std::vector<std::vector<float>> taps;
     std::vector<TaskDev> host_tasks;
-    std::vector<const void*> last_in;
+    std::vector<int> member_of, stage_of;
+    std::vector<int> first_of, len_of;
+    int nstages = 1;
+    std::vector<int> stage_off, stage_cnt;   // tile range of each stage in dev_tiles
+    std::vector<size_t> mid_off;             // arena offset of a non-final task's output
+    unsigned char* arena = nullptr;          // chain intermediates, owned
+    std::vector<const void*> last_in;        // per member
     std::vector<void*> last_out;
     int device = -1;
     int max_m = 1;
@@ -1178,7 +1186,7 @@ struct arol_batch_s {
     bool tables_built = false;
     // launch configuration
     int64_t tile_reps = 2048;
-    int threads = 256;
+    int threads = 128;
     int ctas_per_sm = 4;
     // graph
     cudaStream_t cap_stream = nullptr;
@@ -1200,10 +1208,11 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
 
 std::string batch_signature(arol_batch b) {
     uint64_t h = 1469598103934665603ULL;
-    for (const TaskDev& t : b->host_tasks) {
-        TaskDev c = t;
-        c.x = nullptr; c.y = nullptr; c.taps = nullptr;
+    for (size_t j = 0; j < b->host_tasks.size(); ++j) {
+        TaskDev c = b->host_tasks[j];
+        c.x = nullptr; c.y = nullptr; c.taps = nullptr; c.taps_t = nullptr;
         h = fnv1a(&c, sizeof c, h);
+        h = fnv1a(&b->stage_of[j], sizeof(int), h);
     }
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1269,59 +1278,70 @@ void invalidate_graph(arol_batch b) {
     b->graph = nullptr;
 }
 
-// Tiles of at most tile_reps repetitions, most expensive tasks first (a
-// longest-processing-time order for the dynamic tile counter).
+// Tiles of at most tile_reps repetitions, grouped by chain stage (stage k of
+// every chain runs in the k-th launch, after stage k-1 has finished), most
+// expensive tasks first within a stage (a longest-processing-time order for
+// the static round-robin schedule).
 arol_status build_tiles(arol_batch b) {
-    std::vector<int> order(b->host_tasks.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     auto cost = [&](int i) {
         const TaskDev& t = b->host_tasks[i];
         return (double)t.nreps * (t.T + t.m);
     };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
     std::vector<TileDev> tiles;
-    for (int i : order) {
-        const TaskDev& t = b->host_tasks[i];
-        if (t.rowfir) {
-            // Row tiles: pieces of kRowTile repetitions of a long row, or as
-            // many whole short rows as fit kRowTile repetitions and a staged
-            // window of kWinFloats floats.
-            const int64_t R1 = t.rep[3];
-            if (R1 > kRowTile) {
-                for (int64_t r0 = 0; r0 < t.rep[2]; ++r0)
-                    for (int64_t a = 0; a < R1; a += kRowTile) {
+    b->stage_off.assign(b->nstages, 0);
+    b->stage_cnt.assign(b->nstages, 0);
+    for (int stage = 0; stage < b->nstages; ++stage) {
+        b->stage_off[stage] = (int)std::min<size_t>(tiles.size(), 2147483647);
+        std::vector<int> order;
+        for (size_t i = 0; i < b->host_tasks.size(); ++i)
+            if (b->stage_of[i] == stage) order.push_back((int)i);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+        for (int i : order) {
+            const TaskDev& t = b->host_tasks[i];
+            if (t.rowfir) {
+                // Row tiles: pieces of at most cmax repetitions of a long row
+                // (their window, step * (count - 1) + T words, fits kWinFloats),
+                // or as many whole short rows as fit kRowTile repetitions and a
+                // staged window of kWinFloats floats.
+                const int64_t R1 = t.rep[3];
+                const int64_t cmax = std::min<int64_t>(kRowTile, (kWinFloats - t.T) / t.step + 1);
+                if (R1 > cmax) {
+                    for (int64_t r0 = 0; r0 < t.rep[2]; ++r0)
+                        for (int64_t a = 0; a < R1; a += cmax) {
+                            TileDev td;
+                            td.task = i;
+                            td.start = r0 * R1 + a;
+                            td.count = (int32_t)std::min<int64_t>(cmax, R1 - a);
+                            tiles.push_back(td);
+                        }
+                } else if (R1 > 0) {
+                    // Whole rows per tile: at most kRowTile repetitions, the rows
+                    // themselves (W words each) within the staged window, no row
+                    // twice (rows <= H), and extents below 2^30 so that column
+                    // sums stay inside the 31-bit division.
+                    const int64_t W = t.in.shape[1], H = t.in.shape[0];
+                    int64_t per = std::min<int64_t>(kRowTile / R1, kWinFloats / W);
+                    per = std::min<int64_t>(per, H);
+                    if (H >= (1 << 30) || W >= (1 << 30) || per < 2) per = 1;
+                    for (int64_t r0 = 0; r0 < t.rep[2]; r0 += per) {
                         TileDev td;
                         td.task = i;
-                        td.start = r0 * R1 + a;
-                        td.count = (int32_t)std::min<int64_t>(kRowTile, R1 - a);
+                        td.start = r0 * R1;
+                        td.count = (int32_t)(std::min<int64_t>(per, t.rep[2] - r0) * R1);
                         tiles.push_back(td);
                     }
-            } else if (R1 > 0) {
-                // Whole rows per tile: at most kRowTile repetitions, the rows
-                // themselves (W words each) within the staged window, no row
-                // twice (rows <= H), and extents below 2^30 so that column
-                // sums stay inside the 31-bit division.
-                const int64_t W = t.in.shape[1], H = t.in.shape[0];
-                int64_t per = std::min<int64_t>(kRowTile / R1, kWinFloats / W);
-                per = std::min<int64_t>(per, H);
-                if (H >= (1 << 30) || W >= (1 << 30) || per < 2) per = 1;
-                for (int64_t r0 = 0; r0 < t.rep[2]; r0 += per) {
-                    TileDev td;
-                    td.task = i;
-                    td.start = r0 * R1;
-                    td.count = (int32_t)(std::min<int64_t>(per, t.rep[2] - r0) * R1);
-                    tiles.push_back(td);
                 }
+                continue;
             }
-            continue;
+            for (int64_t s = 0; s < t.nreps; s += b->tile_reps) {
+                TileDev td;
+                td.task = i;
+                td.start = s;
+                td.count = (int32_t)std::min<int64_t>(b->tile_reps, t.nreps - s);
+                tiles.push_back(td);
+            }
         }
-        for (int64_t s = 0; s < t.nreps; s += b->tile_reps) {
-            TileDev td;
-            td.task = i;
-            td.start = s;
-            td.count = (int32_t)std::min<int64_t>(b->tile_reps, t.nreps - s);
-            tiles.push_back(td);
-        }
+        b->stage_cnt[stage] = (int)std::min<size_t>(tiles.size() - b->stage_off[stage], 2147483647);
     }
     if ((int64_t)tiles.size() >= 2147483647LL) return fail(AROL_ERR_UNSUPPORTED, "batch: too many tiles");
     b->ntiles = (int)tiles.size();
@@ -1351,13 +1371,16 @@ arol_status build_tiles(arol_batch b) {
 }
 
 arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out, cudaStream_t s) {
-    const size_t n = b->descs.size();
+    const size_t n = b->descs.size(), nm = b->first_of.size();
     int dev = 0;
     AROL_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     if (b->device < 0) b->device = dev;
     else if (b->device != dev) return fail(AROL_ERR_INVALID, "batch used on another device than its buffers");
-    for (size_t i = 0; i < n; ++i)
-        if ((!in[i] || !out[i]) && b->host_tasks[i].nreps > 0) return fail(AROL_ERR_INVALID, "null pointer for task %zu", i);
+    for (size_t i = 0; i < nm; ++i) {
+        const int f = b->first_of[i], l = f + b->len_of[i] - 1;
+        if (!in[i] && b->host_tasks[f].nreps > 0) return fail(AROL_ERR_INVALID, "null input pointer for task %zu", i);
+        if (!out[i] && b->host_tasks[l].nreps > 0) return fail(AROL_ERR_INVALID, "null output pointer for task %zu", i);
+    }
     if (!b->tables_built) {
         // each task's taps, then (row-FIR tasks) the same taps transposed and
         // zero padded to T x 16 for the row-tile path
@@ -1391,20 +1414,34 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
                 off += ht.size();
             }
         }
+        // one arena for every chain intermediate, 256-byte aligned slices
+        size_t arena = 0;
+        b->mid_off.assign(n, 0);
+        for (size_t j = 0; j < n; ++j) {
+            const int m = b->member_of[j];
+            if (b->stage_of[j] == b->len_of[m] - 1) continue;
+            b->mid_off[j] = arena;
+            const arol_array_desc& o = b->descs[j].out[0];
+            arena += ((size_t)elems_of(o) * esize_of(o.dtype) + 255) / 256 * 256;
+        }
+        if (arena) AROL_CUDA(cudaMalloc(&b->arena, arena), "cudaMalloc(chain intermediates)");
         AROL_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         arol_status st = build_tiles(b);
         if (st != AROL_OK) return st;
         b->tables_built = true;
-        b->last_in.assign(n, (const void*)1);   // force the first table upload
-        b->last_out.assign(n, (void*)1);
+        b->last_in.assign(nm, (const void*)1);   // force the first table upload
+        b->last_out.assign(nm, (void*)1);
     }
     bool changed = false;
-    for (size_t i = 0; i < n; ++i) changed = changed || in[i] != b->last_in[i] || out[i] != b->last_out[i];
+    for (size_t i = 0; i < nm; ++i) changed = changed || in[i] != b->last_in[i] || out[i] != b->last_out[i];
     if (changed) {
         AROL_CUDA(cudaEventSynchronize(b->table_copied), "wait for previous table upload");
-        for (size_t i = 0; i < n; ++i) {
-            b->host_tasks[i].x = in[i];
-            b->host_tasks[i].y = out[i];
+        for (size_t j = 0; j < n; ++j) {
+            const int m = b->member_of[j], k = b->stage_of[j];
+            b->host_tasks[j].x = k == 0 ? in[m] : (const void*)(b->arena + b->mid_off[j - 1]);
+            b->host_tasks[j].y = k == b->len_of[m] - 1 ? out[m] : (void*)(b->arena + b->mid_off[j]);
+        }
+        for (size_t i = 0; i < nm; ++i) {
             b->last_in[i] = in[i];
             b->last_out[i] = out[i];
         }
@@ -1420,8 +1457,14 @@ arol_status batch_capture(arol_batch b) {
     if (b->exec) return AROL_OK;
     const int grid = device_sm_count() * b->ctas_per_sm;
     AROL_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    cudaError_t le = launch_batch_persistent(b->dev_tasks, b->dev_tiles, b->ntiles, b->counter, grid, b->threads,
-                                             b->max_m, b->cap_stream);
+    // one launch per chain stage; stage k reads what stage k - 1 wrote
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < b->nstages && le == cudaSuccess; ++k) {
+        const int cnt = b->stage_cnt[k];
+        if (cnt == 0) continue;
+        le = launch_batch_persistent(b->dev_tasks, b->dev_tiles + b->stage_off[k], cnt, b->counter,
+                                     std::min(grid, cnt), b->threads, b->max_m, b->cap_stream);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -1443,19 +1486,31 @@ arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out) {
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         if (!tasks[i]) return fail(AROL_ERR_INVALID, "null task %d", i);
-        if (tasks[i]->kind != 0) return fail(AROL_ERR_UNSUPPORTED, "batch: task %d is a chain", i);
-        const arol_task_desc& d = tasks[i]->descs[0];
-        if (d.elem == AROL_ELEM_MATMUL) return fail(AROL_ERR_UNSUPPORTED, "batch: task %d is a matmul", i);
+        for (const arol_task_desc& d : tasks[i]->descs)
+            if (d.elem == AROL_ELEM_MATMUL) return fail(AROL_ERR_UNSUPPORTED, "batch: task %d is a matmul", i);
         if (tasks[i]->taps_borrowed || !tasks[i]->taps_ready) return fail(AROL_ERR_INVALID, "batch: task %d has no host taps", i);
     }
     arol_batch b = new (std::nothrow) arol_batch_s();
     if (!b) return fail(AROL_ERR_INVALID, "out of host memory");
+    // a chain enters as its tasks, one per stage, in chain order
     for (int i = 0; i < n; ++i) {
-        const arol_task_desc& d = tasks[i]->descs[0];
-        b->descs.push_back(d);
-        b->taps.push_back(tasks[i]->taps_host);
-        b->host_tasks.push_back(make_taskdev(d));
-        if (d.elem == AROL_ELEM_FIR) b->max_m = std::max(b->max_m, d.fir_m);
+        const arol_task t = tasks[i];
+        const int len = (int)t->descs.size();
+        b->first_of.push_back((int)b->descs.size());
+        b->len_of.push_back(len);
+        b->nstages = std::max(b->nstages, len);
+        for (int k = 0; k < len; ++k) {
+            const arol_task_desc& d = t->descs[k];
+            // a chain's taps are its tasks' m x T blocks back to back
+            const size_t a = t->kind == 0 ? 0 : (size_t)t->tap_off[k];
+            const size_t z = t->kind == 0 || k + 1 == len ? t->taps_host.size() : (size_t)t->tap_off[k + 1];
+            b->descs.push_back(d);
+            b->taps.emplace_back(t->taps_host.begin() + a, t->taps_host.begin() + z);
+            b->host_tasks.push_back(make_taskdev(d));
+            b->member_of.push_back(i);
+            b->stage_of.push_back(k);
+            if (d.elem == AROL_ELEM_FIR) b->max_m = std::max(b->max_m, d.fir_m);
+        }
     }
     *out = b;
     return AROL_OK;
@@ -1573,6 +1628,7 @@ void arol_batch_destroy(arol_batch b) {
         free_dev(b->dev_tiles_pt);
         free_dev(b->counter);
         free_dev(b->taps_dev);
+        free_dev(b->arena);
         if (cur != b->device) cudaSetDevice(cur);
     }
     delete b;

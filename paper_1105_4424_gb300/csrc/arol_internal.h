@@ -89,7 +89,10 @@ cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, 
                                     unsigned* counter, int grid, int threads, int max_m,
                                     cudaStream_t s);
 constexpr int kRowTile = 256;                      // at most this many repetitions per row tile
-constexpr int kWinFloats = 32 * (kRowTile - 1) + 32;   // staged input window of a row tile (step, T <= 32)
+// Staged input window of a row tile.  A tile that is a piece of one row holds
+// at most min(kRowTile, (kWinFloats - T) / step + 1) repetitions, so its
+// window (step * (count - 1) + T words) always fits.
+constexpr int kWinFloats = 4096;
 cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s);
 cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int nparts, bool with_fwd,
                                  cudaStream_t s);

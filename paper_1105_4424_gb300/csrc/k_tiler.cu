@@ -243,8 +243,7 @@ __global__ void __launch_bounds__(kThreads) tiler_generic_kernel(const TaskDev t
 // (mod the row length).  The window is staged once into shared memory with
 // coalesced loads (one extra word every 32 so that lanes reading at stride
 // `step` spread over the banks); the taps are staged transposed so that one
-// 128-bit shared load feeds four outputs; each thread computes two
-// repetitions per tap fetch.
+// 128-bit shared load feeds four outputs.
 // ---------------------------------------------------------------------------
 constexpr int kWinPad = kWinFloats + kWinFloats / 32;
 
@@ -428,10 +427,15 @@ __global__ void __launch_bounds__(256, 1) batch_persistent_kernel(const TaskDev*
     extern __shared__ __align__(16) float dsm[];
     int slot_task[2] = {-1, -1};   // task whose taps each slot holds (the same in every thread)
     int ti = blockIdx.x;
-    if (kRows && ti < ntiles) {
-        const TileDev tile = tiles[ti];
+    // The record of the tile to compute next is read while its copies are
+    // issued, one iteration ahead, so no global load waits behind a barrier.
+    TileDev tile{};
+    bool row = false;
+    if (ti < ntiles) {
+        tile = tiles[ti];
         const TaskDev& t = tasks[tile.task];
-        if (t.rowfir) {
+        row = kRows && t.rowfir;
+        if (row) {
             const float* src = reinterpret_cast<const float*>(&t);
             for (int w = threadIdx.x; w < (int)(sizeof(TaskDev) / 4); w += blockDim.x) ptx::cp_async4(dsm + w, src + w);
             stage_row_tile(t, tile.start, tile.count, dsm + kTaskFloats, true);
@@ -442,31 +446,35 @@ __global__ void __launch_bounds__(256, 1) batch_persistent_kernel(const TaskDev*
     for (int i = 0; ti < ntiles; ++i, ti += gridDim.x) {
         const int cur = i & 1, nxt = cur ^ 1;
         const int nti = ti + gridDim.x;
+        TileDev next{};
+        bool next_row = false;
         __syncthreads();   // every thread is done with the next slot (tile i - 1)
-        if (kRows && nti < ntiles) {
-            const TileDev tile = tiles[nti];
-            const TaskDev& t = tasks[tile.task];
-            if (t.rowfir) {
+        if (nti < ntiles) {
+            next = tiles[nti];
+            const TaskDev& t = tasks[next.task];
+            next_row = kRows && t.rowfir;
+            if (next_row) {
                 float* slot = dsm + nxt * kSlotFloats;
                 const float* src = reinterpret_cast<const float*>(&t);
                 for (int w = threadIdx.x; w < (int)(sizeof(TaskDev) / 4); w += blockDim.x)
                     ptx::cp_async4(slot + w, src + w);
-                stage_row_tile(t, tile.start, tile.count, slot + kTaskFloats, slot_task[nxt] != tile.task);
-                slot_task[nxt] = tile.task;
+                stage_row_tile(t, next.start, next.count, slot + kTaskFloats, slot_task[nxt] != next.task);
+                slot_task[nxt] = next.task;
             }
         }
         ptx::cp_async_commit();
         ptx::cp_async_wait_group<1>();   // this thread's copies for tile i have landed
         __syncthreads();                 // ... and everyone else's
-        const TileDev tile = tiles[ti];
-        if (kRows && tasks[tile.task].rowfir) {
+        if (row) {
             const float* slot = dsm + cur * kSlotFloats;
             compute_row_tile(*reinterpret_cast<const TaskDev*>(slot), tile.start, tile.count, slot + kTaskFloats);
-            continue;
+        } else {
+            const TaskDev& t = tasks[tile.task];
+            const int64_t end = tile.start + tile.count;
+            for (int64_t lr = tile.start + threadIdx.x; lr < end; lr += blockDim.x) process_rep<MAXM>(t, lr);
         }
-        const TaskDev& t = tasks[tile.task];
-        const int64_t end = tile.start + tile.count;
-        for (int64_t lr = tile.start + threadIdx.x; lr < end; lr += blockDim.x) process_rep<MAXM>(t, lr);
+        tile = next;
+        row = next_row;
     }
     ptx::cp_async_wait_all();
 }

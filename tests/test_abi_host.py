@@ -143,3 +143,21 @@ def test_null_arguments_are_rejected(B):
         B.arol_task_run(h, [None], [None], 0)
     assert e.value.status == 1
     B.arol_task_destroy(h)
+
+
+def test_batch_accepts_chain_members_and_rejects_matmul(B):
+    """Batch creation is host-only: chains enter as their stages, matmul
+    tasks are refused with AROL_ERR_UNSUPPORTED."""
+    chain, _ = W.config1(seed=1, frames=1, height=16, width=64)
+    single, _ = W.config0()
+    parts = [B.arol_task_create(t) for t in chain]
+    ch = B.arol_chain_create(parts)
+    one = B.arol_task_create(single)
+    b = B.arol_batch_create([ch, one, ch])
+    B.arol_batch_destroy(b)
+    mm = B.arol_task_create(W.matmul_task(128, 128, 128))
+    with pytest.raises(B.ArolError) as e:
+        B.arol_batch_create([one, mm])
+    assert e.value.status == 3
+    for h in parts + [ch, one, mm]:
+        B.arol_task_destroy(h)

@@ -1,0 +1,87 @@
+"""Batches whose members are chains (Sec. 5: tasks linked through shared
+arrays) mixed with single tasks: one graph launch, one persistent launch per
+chain stage.  Every member against the oracle's chain; the graph path equals
+the one-launch-per-task path and a second run bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import tiler as O
+from tests.gpu_helpers import FIR_RTOL, assert_fir_close, dev, fir_scale, host
+from tests.test_parity_gpu import _three_task_chain
+
+pytestmark = pytest.mark.gpu
+
+
+def _members(g):
+    """(member spec, input) pairs: single tasks, 2- and 3-stage chains."""
+    out = []
+    tk, (x,) = W.config0(seed=21)
+    out.append((tk, x))
+    chain, (x,) = W.config1(seed=22, frames=2, height=16, width=64)
+    out.append((chain, x))
+    out.append((_three_task_chain(g), g.standard_normal((24, 32)).astype(np.float32)))
+    for i in range(6):
+        tk = W.random_tiler_task(g, "fir" if i % 2 else "copy")
+        out.append((tk, g.random(tk["inputs"][0]["shape"], dtype=np.float32)))
+    chain, (x,) = W.config1(seed=23, frames=3, height=24, width=1928)
+    out.append((chain, x))
+    out.append((_three_task_chain(g), g.standard_normal((24, 32)).astype(np.float32)))
+    return out
+
+
+def _check(spec, x, y):
+    chain = spec if isinstance(spec, list) else [spec]
+    ref = O.run_chain(chain, [x])[0]
+    if len(chain) == 1 and chain[0]["elem"] == "copy":
+        np.testing.assert_array_equal(y.view(np.uint32), ref.view(np.uint32))
+    else:
+        assert_fir_close(y, ref, fir_scale(chain, x), what=f"batch member of {len(chain)} stage(s)")
+
+
+def test_batch_of_chains_and_tasks(arol):
+    g = W.rng(120)
+    members = _members(g)
+    b = arol.Batch([m for m, _ in members])
+    ins = [dev(x) for _, x in members]
+    outs = b.empty_outputs()
+    b.run(ins, outs)
+    outs2 = b.empty_outputs()
+    b.run_per_task(ins, outs2)
+    outs3 = b.empty_outputs()
+    b.run(ins, outs3)
+    torch.cuda.synchronize()
+    for (spec, x), y, y2, y3 in zip(members, outs, outs2, outs3):
+        y = host(y)
+        _check(spec, x, y)
+        np.testing.assert_array_equal(y, host(y2))
+        np.testing.assert_array_equal(y, host(y3))
+
+
+def test_batch_chain_with_bf16_intermediate(arol):
+    """bfloat16 frames and intermediate inside a batch: the intermediate is
+    rounded to nearest even by the first stage, as in a standalone chain."""
+    chain, (x,) = W.config1_bf16(seed=24, frames=2, height=16, width=64, mid="bf16", out="f32")
+    g = W.rng(121)
+    tk = W.random_tiler_task(g, "fir")
+    xt = g.random(tk["inputs"][0]["shape"], dtype=np.float32)
+    b = arol.Batch([chain, tk])
+    outs = b.empty_outputs()
+    b.run([dev(x), dev(xt)], outs)
+    torch.cuda.synchronize()
+    xv = W.bf16_bits_to_f32(x).astype(np.float64)
+    f32_chain = [dict(chain[0], inputs=[dict(chain[0]["inputs"][0], dtype="f32")],
+                      outputs=[dict(chain[0]["outputs"][0], dtype="f32")]),
+                 dict(chain[1], inputs=[dict(chain[1]["inputs"][0], dtype="f32")])]
+    ref = O.run_chain(f32_chain, [xv])[0]
+    scale = fir_scale(f32_chain, xv)
+    err = np.abs(host(outs[0]).astype(np.float64) - ref)
+    assert np.all(err <= (FIR_RTOL + 2.0 ** -8) * scale + 1e-38)
+    assert_fir_close(host(outs[1]), O.run_task(tk, [xt])[0], fir_scale(tk, xt), what="batch fir next to a chain")
+
+
+def test_batch_rejects_matmul_members(arol):
+    spec = W.matmul_task(128, 128, 128)
+    with pytest.raises(arol.ArolError):
+        arol.Batch([spec])

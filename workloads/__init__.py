@@ -345,3 +345,19 @@ def ragged_csr(n=3000, seed=0, max_row=70):
     col = np.concatenate(cols).astype(np.int32) if n else np.zeros(0, np.int32)
     vals = g.standard_normal(int(row_ptr[-1]))
     return row_ptr, col, vals
+
+
+def chain_batch(seed=0, n=128):
+    """n independent two-task 8->3 downscaler chains on single float32 frames
+    of uneven sizes: per chain, in a fixed draw order, height = 8 * U{8..128},
+    width = 8 * U{8..256}, X ~ U[0,1), taps_h and taps_v ~ N(0,1)/8 (3 x 8).
+    Returns (list of chains, list of inputs)."""
+    g = rng(seed)
+    chains, xs = [], []
+    for _ in range(n):
+        h = 8 * int(g.integers(8, 129))
+        w = 8 * int(g.integers(8, 257))
+        x = g.random((1, h, w), dtype=np.float32)
+        chains.append(downscale_chain(1, h, w, _taps(g, 3, 8), _taps(g, 3, 8)))
+        xs.append(x)
+    return chains, xs
