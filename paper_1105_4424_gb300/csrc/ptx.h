@@ -40,9 +40,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Bounded wait for the completion of the phase with the given parity.
+// Bounded wait for the completion of the phase with the given parity.  The
+// wall clock is read only once a wait has polled 256 times, so a barrier
+// that is already complete costs one try_wait.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const uint64_t t0 = global_ns();
+    uint64_t t0 = 0;
     for (uint32_t i = 0; i < kSpinIters; ++i) {
         uint32_t ok;
         asm volatile(
@@ -53,7 +55,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if ((i & 255u) == 255u && global_ns() - t0 > kSpinNanos) return false;
+        if ((i & 255u) == 255u) {
+            const uint64_t now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kSpinNanos) return false;
+        }
     }
     return false;
 }

@@ -185,7 +185,8 @@ def _check_matmul(A_bits, B_bits, Cg, rows=None, cols=None, tk=None):
     return rel
 
 
-@pytest.mark.parametrize("mnk", [(128, 128, 64), (256, 384, 192), (512, 512, 512), (384, 768, 1024)])
+@pytest.mark.parametrize("mnk", [(128, 128, 64), (256, 256, 64), (256, 384, 192), (512, 512, 512), (384, 768, 1024),
+                                 (768, 2048, 320)])
 def test_matmul_full(arol, mnk):
     M, N, K = mnk
     g = W.rng(108)
@@ -214,6 +215,38 @@ def test_matmul_4096_sampled(arol):
         rows = np.concatenate([rows, rr.reshape(-1)])
         cols = np.concatenate([cols, cc.reshape(-1)])
     _check_matmul(a, b, Cg, rows, cols, tk)
+
+
+_MATMUL_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_1105_4424_gb300 as A, workloads as W
+M, N, K = 768, 2048, 320
+g = W.rng(111)
+a = W.bf16_round(g.standard_normal((M, K), dtype=np.float32))
+b = W.bf16_round(g.standard_normal((K, N), dtype=np.float32))
+t = A.Task(W.matmul_task(M, N, K))
+bf = lambda u: torch.from_numpy(u.view(np.int16)).cuda().view(torch.bfloat16)
+c = t.run([bf(a), bf(b)])
+t.sync_status()
+np.savez(sys.argv[2], a=a, b=b, c=c.cpu().numpy())
+"""
+
+
+@pytest.mark.parametrize("env", [{"AROL_MATMUL_MAX_CLUSTERS": "7"}, {"AROL_MATMUL_MAX_CLUSTERS": "5"},
+                                 {"AROL_MATMUL_PAIR": "0"}])
+def test_matmul_schedules(arol, tmp_path, env):
+    """24 tiles of 256 x 256 on 7 clusters: three rounds of whole tiles and a
+    fourth of half-width tiles; on 5 clusters: five rounds, no split; and the
+    one-SM kernel.  All against the FP64 product."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    f = str(tmp_path / "mm.npz")
+    subprocess.run([sys.executable, "-c", _MATMUL_SCRIPT, root, f], check=True, env=dict(os.environ, **env), timeout=300)
+    o = np.load(f)
+    _check_matmul(o["a"], o["b"], o["c"])
 
 
 # ------------------------------------------------------------------ batches
