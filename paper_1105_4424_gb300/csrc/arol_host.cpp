@@ -1186,7 +1186,7 @@ struct arol_batch_s {
     bool tables_built = false;
     // launch configuration
     int64_t tile_reps = 2048;
-    int threads = 128;
+    int threads = kBatchThreads;
     int ctas_per_sm = 4;
     // graph
     cudaStream_t cap_stream = nullptr;
@@ -1575,8 +1575,8 @@ arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* ou
     int64_t best_tile = b->tile_reps;
     int best_thr = b->threads, best_ctas = b->ctas_per_sm;
     const int64_t tiles[] = {512, 1024, 2048, 4096, 8192, 16384};
-    const int thrs[] = {128, 256};
-    const int ctas[] = {2, 4, 8, 16};
+    const int thrs[] = {kBatchThreads};
+    const int ctas[] = {2, 4, 6, 8};
     st = AROL_OK;
     for (int64_t tile : tiles) {
         b->tile_reps = tile;

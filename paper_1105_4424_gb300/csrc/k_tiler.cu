@@ -258,72 +258,102 @@ __device__ __forceinline__ int padw(int w) { return w + (w >> 5); }
 //    holds the rows themselves, W words each (a contiguous copy), and
 //    repetition (k, r1) walks columns (o1 + step*r1 + kk) mod W with one
 //    compare per step.
-// One thread per repetition; the m outputs of a repetition are computed in
-// NG groups of four so one 128-bit load of the transposed taps feeds four
-// FMAs.
-template <int NG, bool kRowsLayout>
+// Each thread computes two repetitions, i and i + blockDim.x, so every tap
+// fetch feeds both; the exact output count M is a template parameter (taps
+// are read from the transposed block as float4 / float2 / float pieces, no
+// padded FMAs), and a repetition's M outputs go to consecutive columns with
+// one wrap test each.
+template <int M>
+__device__ __forceinline__ void load_taps(const float* hrow, float (&h)[M]) {
+#pragma unroll
+    for (int j = 0; j + 4 <= M; j += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(hrow + j);
+        h[j] = v.x;
+        h[j + 1] = v.y;
+        h[j + 2] = v.z;
+        h[j + 3] = v.w;
+    }
+    constexpr int j0 = M / 4 * 4;
+    if (M - j0 >= 2) {
+        const float2 v = *reinterpret_cast<const float2*>(hrow + j0);
+        h[j0] = v.x;
+        h[j0 + 1] = v.y;
+    }
+    if ((M - j0) & 1) h[M - 1] = hrow[M - 1];
+}
+
+template <int M>
+__device__ __forceinline__ void store_outputs(const TaskDev& t, uint32_t r0, uint32_t k, uint32_t r1, const float (&acc)[M]) {
+    const uint32_t hout = (uint32_t)t.out.shape[0], wout = (uint32_t)t.out.shape[1];
+    // output row (o0 + r0 + k) mod H_out and first column (o1 + m*r1) mod W_out
+    const uint32_t ov = t.out.origin[0] + r0 + k;            // < 2^31: checked on the host
+    const uint32_t orow = ov - fast_div(ov, t.out.shape_div[0]) * hout;
+    const uint64_t v = (uint64_t)t.out.origin[1] + (uint64_t)M * r1;
+    uint32_t c = v < 0x7fffffffull ? (uint32_t)v - fast_div((uint32_t)v, t.out.shape_div[1]) * wout
+                                   : (uint32_t)(v % wout);
+    float* yrow = static_cast<float*>(t.y) + (int64_t)orow * wout;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        yrow[c] = acc[j];
+        c = (c + 1u == wout) ? 0u : c + 1u;
+    }
+}
+
+template <int M, bool kRowsLayout>
 __device__ __forceinline__ void row_fir_compute(const TaskDev& t, const float* win, const float* ht, int count,
                                                 uint32_t r0, uint32_t a0, uint32_t cb) {
     constexpr int kHt = 16;   // ht row stride (floats)
-    const int T = t.T, S = t.step, m = t.m;
+    const int T = t.T, S = t.step;
     const uint32_t R1 = (uint32_t)t.rep[3];
     const uint32_t wi = (uint32_t)t.in.shape[1];
-    const uint32_t hout = (uint32_t)t.out.shape[0], wout = (uint32_t)t.out.shape[1];
-    for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        float acc[4 * NG];
+    const int B = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < count; i0 += 2 * B) {
+        const int i1 = i0 + B < count ? i0 + B : i0;   // a missing second repetition recomputes the first
+        float acc0[M], acc1[M];
 #pragma unroll
-        for (int j = 0; j < 4 * NG; ++j) acc[j] = 0.f;
-        uint32_t k, r1;
+        for (int j = 0; j < M; ++j) acc0[j] = acc1[j] = 0.f;
+        uint32_t k0, k1, r10, r11;
         if (kRowsLayout) {
-            k = fast_div((uint32_t)i, t.rep_div[3]);
-            r1 = (uint32_t)i - k * R1;
-            uint32_t c = cb + (uint32_t)S * r1;                 // < 2^31: extents below 2^30
-            c -= fast_div(c, t.in.shape_div[1]) * wi;
-            const int rowoff = (int)(k * wi);
+            k0 = fast_div((uint32_t)i0, t.rep_div[3]);
+            k1 = fast_div((uint32_t)i1, t.rep_div[3]);
+            r10 = (uint32_t)i0 - k0 * R1;
+            r11 = (uint32_t)i1 - k1 * R1;
+            uint32_t c0 = cb + (uint32_t)S * r10, c1 = cb + (uint32_t)S * r11;   // < 2^31: extents below 2^30
+            c0 -= fast_div(c0, t.in.shape_div[1]) * wi;
+            c1 -= fast_div(c1, t.in.shape_div[1]) * wi;
+            const int ro0 = (int)(k0 * wi), ro1 = (int)(k1 * wi);
+#pragma unroll 2
             for (int kk = 0; kk < T; ++kk) {
-                const float p = win[padw(rowoff + (int)c)];
-                c = (c + 1u == wi) ? 0u : c + 1u;
-                const float4* h4 = reinterpret_cast<const float4*>(ht + kk * kHt);
+                const float p0 = win[padw(ro0 + (int)c0)], p1 = win[padw(ro1 + (int)c1)];
+                c0 = (c0 + 1u == wi) ? 0u : c0 + 1u;
+                c1 = (c1 + 1u == wi) ? 0u : c1 + 1u;
+                float h[M];
+                load_taps<M>(ht + kk * kHt, h);
 #pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    const float4 h = h4[g];
-                    acc[4 * g + 0] = fmaf(h.x, p, acc[4 * g + 0]);
-                    acc[4 * g + 1] = fmaf(h.y, p, acc[4 * g + 1]);
-                    acc[4 * g + 2] = fmaf(h.z, p, acc[4 * g + 2]);
-                    acc[4 * g + 3] = fmaf(h.w, p, acc[4 * g + 3]);
+                for (int j = 0; j < M; ++j) {
+                    acc0[j] = fmaf(h[j], p0, acc0[j]);
+                    acc1[j] = fmaf(h[j], p1, acc1[j]);
                 }
             }
         } else {
-            k = 0;
-            r1 = a0 + (uint32_t)i;
-            const int base = S * i;
+            k0 = k1 = 0;
+            r10 = a0 + (uint32_t)i0;
+            r11 = a0 + (uint32_t)i1;
+            const int b0 = S * i0, b1 = S * i1;
+#pragma unroll 2
             for (int kk = 0; kk < T; ++kk) {
-                const float p = win[padw(base + kk)];
-                const float4* h4 = reinterpret_cast<const float4*>(ht + kk * kHt);
+                const float p0 = win[padw(b0 + kk)], p1 = win[padw(b1 + kk)];
+                float h[M];
+                load_taps<M>(ht + kk * kHt, h);
 #pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    const float4 h = h4[g];
-                    acc[4 * g + 0] = fmaf(h.x, p, acc[4 * g + 0]);
-                    acc[4 * g + 1] = fmaf(h.y, p, acc[4 * g + 1]);
-                    acc[4 * g + 2] = fmaf(h.z, p, acc[4 * g + 2]);
-                    acc[4 * g + 3] = fmaf(h.w, p, acc[4 * g + 3]);
+                for (int j = 0; j < M; ++j) {
+                    acc0[j] = fmaf(h[j], p0, acc0[j]);
+                    acc1[j] = fmaf(h[j], p1, acc1[j]);
                 }
             }
         }
-        // output row (o0 + r0 + k) mod H_out and first column (o1 + m*r1) mod W_out
-        const uint32_t ov = t.out.origin[0] + r0 + k;            // < 2^31: checked on the host
-        const uint32_t orow = ov - fast_div(ov, t.out.shape_div[0]) * hout;
-        const uint64_t v = (uint64_t)t.out.origin[1] + (uint64_t)m * r1;
-        uint32_t c = v < 0x7fffffffull ? (uint32_t)v - fast_div((uint32_t)v, t.out.shape_div[1]) * wout
-                                       : (uint32_t)(v % wout);
-        float* yrow = static_cast<float*>(t.y) + (int64_t)orow * wout;
-#pragma unroll
-        for (int j = 0; j < 4 * NG; ++j) {
-            if (j < m) {
-                yrow[c] = acc[j];
-                c = (c + 1u == wout) ? 0u : c + 1u;
-            }
-        }
+        store_outputs<M>(t, r0, k0, r10, acc0);
+        if (i1 != i0) store_outputs<M>(t, r0, k1, r11, acc1);
     }
 }
 
@@ -347,20 +377,26 @@ __device__ __forceinline__ void stage_window(const TaskDev& t, uint32_t row, uin
 template <bool kRowsLayout>
 __device__ __forceinline__ void row_fir_dispatch(const TaskDev& t, const float* win, const float* ht, int count,
                                                  uint32_t r0, uint32_t a0, uint32_t cb) {
-    switch ((t.m + 3) >> 2) {
-    case 1: row_fir_compute<1, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
-    case 2: row_fir_compute<2, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
-    case 3: row_fir_compute<3, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
-    default: row_fir_compute<4, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
+#define AROL_ROW_FIR_CASE(M) \
+    case M: row_fir_compute<M, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
+    switch (t.m) {
+        AROL_ROW_FIR_CASE(1) AROL_ROW_FIR_CASE(2) AROL_ROW_FIR_CASE(3) AROL_ROW_FIR_CASE(4)
+        AROL_ROW_FIR_CASE(5) AROL_ROW_FIR_CASE(6) AROL_ROW_FIR_CASE(7) AROL_ROW_FIR_CASE(8)
+        AROL_ROW_FIR_CASE(9) AROL_ROW_FIR_CASE(10) AROL_ROW_FIR_CASE(11) AROL_ROW_FIR_CASE(12)
+        AROL_ROW_FIR_CASE(13) AROL_ROW_FIR_CASE(14) AROL_ROW_FIR_CASE(15)
+        default: row_fir_compute<16, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
     }
+#undef AROL_ROW_FIR_CASE
 }
 
-// One ring slot of the batch kernel: a copy of the tile's TaskDev (so that
-// the compute reads its fields from shared memory), the staged window, then
-// the taps of the tile's task transposed and zero padded
-// (ht[k * 16 + j] = H[j, k], k < 32).
+// Shared memory of the batch kernel: a ring of three task records (the
+// TaskDev of the tile being computed, of the next tile, whose copies are in
+// flight, and of the one after, being copied), then two data slots, each the
+// staged window followed by the taps of the tile's task transposed and zero
+// padded (ht[k * 16 + j] = H[j, k], k < 32).
 constexpr int kTaskFloats = (int)((sizeof(TaskDev) + 15) / 16 * 4);
-constexpr int kSlotFloats = kTaskFloats + kWinPad + 32 * 16;
+constexpr int kMetaSlots = 3;
+constexpr int kSlotFloats = kWinPad + 32 * 16;
 static_assert(sizeof(TaskDev) % 4 == 0, "TaskDev is copied in 4-byte words");
 
 struct RowGeom {
@@ -415,66 +451,79 @@ __device__ __forceinline__ void compute_row_tile(const TaskDev& t, int64_t start
     else row_fir_dispatch<false>(t, slot, ht, count, g.r0, g.a0, 0u);
 }
 
+// Copies (cp.async, no wait) task record `t` into a meta slot.
+__device__ __forceinline__ void stage_meta(const TaskDev& t, float* meta) {
+    const float* src = reinterpret_cast<const float*>(&t);
+    for (int w = threadIdx.x; w < (int)(sizeof(TaskDev) / 4); w += blockDim.x) ptx::cp_async4(meta + w, src + w);
+}
+
 // Persistent batched kernel.  CTA b takes tiles b, b + gridDim.x, ... (the
-// host orders tiles by cost).  Row tiles of row-FIR tasks go through a
-// two-slot shared-memory ring: while the CTA computes tile i from one slot,
-// the copies of tile i + 1 fill the other.  Other tiles run the generic
-// per-repetition path.  No CTA ever waits on another.
+// host orders tiles by cost).  Two pipelines run ahead of the compute: the
+// task record of tile i + 2 is copied into shared memory while tile i is
+// computed, and the window and taps of tile i + 1, whose addresses come from
+// its record already in shared memory, fill the other data slot.  So no
+// global load stands between a barrier and the compute.  Row tiles of row-FIR
+// tasks use the staged data; other tiles run the generic per-repetition path.
+// No CTA ever waits on another.
 template <int MAXM>
-__global__ void __launch_bounds__(256, 1) batch_persistent_kernel(const TaskDev* __restrict__ tasks,
+__global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(const TaskDev* __restrict__ tasks,
                                                                   const TileDev* __restrict__ tiles, int ntiles) {
     constexpr bool kRows = MAXM <= 16;
     extern __shared__ __align__(16) float dsm[];
-    int slot_task[2] = {-1, -1};   // task whose taps each slot holds (the same in every thread)
-    int ti = blockIdx.x;
-    // The record of the tile to compute next is read while its copies are
-    // issued, one iteration ahead, so no global load waits behind a barrier.
-    TileDev tile{};
-    bool row = false;
-    if (ti < ntiles) {
-        tile = tiles[ti];
-        const TaskDev& t = tasks[tile.task];
-        row = kRows && t.rowfir;
-        if (row) {
-            const float* src = reinterpret_cast<const float*>(&t);
-            for (int w = threadIdx.x; w < (int)(sizeof(TaskDev) / 4); w += blockDim.x) ptx::cp_async4(dsm + w, src + w);
-            stage_row_tile(t, tile.start, tile.count, dsm + kTaskFloats, true);
-            slot_task[0] = tile.task;
-        }
-    }
-    ptx::cp_async_commit();
-    for (int i = 0; ti < ntiles; ++i, ti += gridDim.x) {
-        const int cur = i & 1, nxt = cur ^ 1;
-        const int nti = ti + gridDim.x;
-        TileDev next{};
-        bool next_row = false;
-        __syncthreads();   // every thread is done with the next slot (tile i - 1)
-        if (nti < ntiles) {
-            next = tiles[nti];
-            const TaskDev& t = tasks[next.task];
-            next_row = kRows && t.rowfir;
-            if (next_row) {
-                float* slot = dsm + nxt * kSlotFloats;
-                const float* src = reinterpret_cast<const float*>(&t);
-                for (int w = threadIdx.x; w < (int)(sizeof(TaskDev) / 4); w += blockDim.x)
-                    ptx::cp_async4(slot + w, src + w);
-                stage_row_tile(t, next.start, next.count, slot + kTaskFloats, slot_task[nxt] != next.task);
-                slot_task[nxt] = next.task;
+    float* meta = dsm;                                  // kMetaSlots task records
+    float* data = dsm + kMetaSlots * kTaskFloats;       // two data slots
+    const int G = gridDim.x;
+    int slot_task[2] = {-1, -1};   // task whose taps each data slot holds (the same in every thread)
+    // records of tiles i, i + 1, i + 2 (registers), valid when the index < ntiles
+    const int t0 = blockIdx.x;
+    TileDev tl0{}, tl1{}, tl2{};
+    if (t0 < ntiles) tl0 = tiles[t0];
+    if (t0 + G < ntiles) tl1 = tiles[t0 + G];
+    if (t0 + 2 * G < ntiles) tl2 = tiles[t0 + 2 * G];
+    if (kRows) {
+        if (t0 < ntiles) stage_meta(tasks[tl0.task], meta);
+        if (t0 + G < ntiles) stage_meta(tasks[tl1.task], meta + kTaskFloats);
+        ptx::cp_async_commit();
+        ptx::cp_async_wait_group<0>();
+        __syncthreads();
+        if (t0 < ntiles) {
+            const TaskDev& m0 = *reinterpret_cast<const TaskDev*>(meta);
+            if (m0.rowfir) {
+                stage_row_tile(m0, tl0.start, tl0.count, data, true);
+                slot_task[0] = tl0.task;
             }
         }
         ptx::cp_async_commit();
-        ptx::cp_async_wait_group<1>();   // this thread's copies for tile i have landed
-        __syncthreads();                 // ... and everyone else's
-        if (row) {
-            const float* slot = dsm + cur * kSlotFloats;
-            compute_row_tile(*reinterpret_cast<const TaskDev*>(slot), tile.start, tile.count, slot + kTaskFloats);
-        } else {
-            const TaskDev& t = tasks[tile.task];
-            const int64_t end = tile.start + tile.count;
-            for (int64_t lr = tile.start + threadIdx.x; lr < end; lr += blockDim.x) process_rep<MAXM>(t, lr);
+    }
+    for (int i = 0, ti = t0; ti < ntiles; ++i, ti += G) {
+        const int cur = i & 1, nxt = cur ^ 1;
+        if (kRows) {
+            // data of tile i and the record of tile i + 1 have landed; every
+            // thread is done with tile i - 1 (its data slot and its record)
+            ptx::cp_async_wait_group<0>();
+            __syncthreads();
+            if (ti + G < ntiles) {
+                const TaskDev& m1 = *reinterpret_cast<const TaskDev*>(meta + ((i + 1) % kMetaSlots) * kTaskFloats);
+                if (m1.rowfir) {
+                    stage_row_tile(m1, tl1.start, tl1.count, data + nxt * kSlotFloats, slot_task[nxt] != tl1.task);
+                    slot_task[nxt] = tl1.task;
+                }
+            }
+            if (ti + 2 * G < ntiles) stage_meta(tasks[tl2.task], meta + ((i + 2) % kMetaSlots) * kTaskFloats);
+            ptx::cp_async_commit();
         }
-        tile = next;
-        row = next_row;
+        const TileDev tile = tl0;
+        tl0 = tl1;
+        tl1 = tl2;
+        if (ti + 3 * G < ntiles) tl2 = tiles[ti + 3 * G];   // used at the next iteration
+        const TaskDev* mcur = reinterpret_cast<const TaskDev*>(meta + (i % kMetaSlots) * kTaskFloats);
+        if (kRows && mcur->rowfir) {
+            compute_row_tile(*mcur, tile.start, tile.count, data + cur * kSlotFloats);
+            continue;
+        }
+        const TaskDev& t = tasks[tile.task];
+        const int64_t end = tile.start + tile.count;
+        for (int64_t lr = tile.start + threadIdx.x; lr < end; lr += blockDim.x) process_rep<MAXM>(t, lr);
     }
     ptx::cp_async_wait_all();
 }
@@ -584,7 +633,9 @@ cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-size_t batch_smem(int max_m) { return max_m <= 16 ? 2 * (size_t)kSlotFloats * sizeof(float) : 0; }
+size_t batch_smem(int max_m) {
+    return max_m <= 16 ? ((size_t)kMetaSlots * kTaskFloats + 2 * (size_t)kSlotFloats) * sizeof(float) : 0;
+}
 
 template <int MAXM>
 cudaError_t launch_batch_m(const TaskDev* tasks, const TileDev* tiles, int ntiles, int grid, int threads,
@@ -616,6 +667,7 @@ cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, 
     (void)counter;   // the schedule is static: CTA b takes tiles b, b + grid, ...
     if (ntiles == 0) return cudaSuccess;
     if (grid > ntiles) grid = ntiles;
+    threads = kBatchThreads;   // the kernel's launch bound
     if (max_m <= 4) return launch_batch_m<4>(tasks, tiles, ntiles, grid, threads, s);
     if (max_m <= 8) return launch_batch_m<8>(tasks, tiles, ntiles, grid, threads, s);
     if (max_m <= 16) return launch_batch_m<16>(tasks, tiles, ntiles, grid, threads, s);
