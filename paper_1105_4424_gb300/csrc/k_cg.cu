@@ -29,7 +29,7 @@ constexpr int kCgThreads = 256;
 constexpr unsigned kFullMask = 0xffffffffu;
 
 struct CgState {
-    double rr, bb, alpha, beta, pap, tol2;
+    double rr, bb, alpha, beta, pap, tol2, rr_old;
     int32_t done, iters, max_iter, pad_;
     unsigned ticket, pad2_;
 };
@@ -156,11 +156,17 @@ __global__ void __launch_bounds__(kCgThreads) cg_init_kernel(const Csr A, const 
     }
 }
 
-// Ap = A p and alpha = rr / p.Ap.
+// One CG iteration is three kernels.  Each posts one partial sum per CTA;
+// the next kernel sums all of them in every CTA, in the same fixed order,
+// so every CTA sees the same scalar (no fence, ticket or last-CTA pass), and
+// CTA 0 records it in the state.  part[0, grid_rows) holds the p.Ap
+// partials, part[grid_rows, grid_rows + grid_vec) the r.r partials.
+
+// Ap = A p; p.Ap partial per CTA.
 template <int LPR>
 __global__ void __launch_bounds__(kCgThreads) cg_ap_kernel(const Csr A, const double* __restrict__ p,
                                                            double* __restrict__ ap, double* __restrict__ part,
-                                                           CgState* st) {
+                                                           const CgState* st) {
     __shared__ double s_warp[kCgThreads / 32];
     if (st->done) return;
     constexpr int kRowsPerBlock = kCgThreads / LPR;
@@ -177,22 +183,28 @@ __global__ void __launch_bounds__(kCgThreads) cg_ap_kernel(const Csr A, const do
     }
     const double t = block_sum(pap, s_warp);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
-    if (!last_cta(st)) return;
-    const double s = sum_partials(part, gridDim.x, s_warp);
-    if (threadIdx.x == 0) {
-        st->pap = s;
-        st->alpha = st->rr / s;
-        st->ticket = 0u;
-    }
 }
 
-// x += alpha p, r -= alpha Ap; rr_new = r.r, beta = rr_new / rr; stop test.
+// alpha = rr / p.Ap; x += alpha p, r -= alpha Ap; r.r partial per CTA.
 __global__ void __launch_bounds__(kCgThreads) cg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                                const double* __restrict__ p, const double* __restrict__ ap,
-                                                               double* __restrict__ part, CgState* st) {
+                                                               const double* __restrict__ pap_part, int n_pap,
+                                                               double* __restrict__ rr_part, CgState* st) {
     __shared__ double s_warp[kCgThreads / 32];
+    __shared__ double s_alpha;
     if (st->done) return;
-    const double alpha = st->alpha;
+    const double pap = sum_partials(pap_part, n_pap, s_warp);
+    if (threadIdx.x == 0) {
+        const double rr = st->rr;
+        s_alpha = rr / pap;
+        if (blockIdx.x == 0) {
+            st->pap = pap;
+            st->alpha = s_alpha;
+            st->rr_old = rr;   // the direction kernel reads this while CTA 0 there overwrites rr
+        }
+    }
+    __syncthreads();
+    const double alpha = s_alpha;
     double rr = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * kCgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCgThreads) {
         x[i] = fma(alpha, p[i], x[i]);
@@ -201,25 +213,29 @@ __global__ void __launch_bounds__(kCgThreads) cg_update_kernel(int64_t n, double
         rr = fma(ri, ri, rr);
     }
     const double t = block_sum(rr, s_warp);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
-    if (!last_cta(st)) return;
-    const double s = sum_partials(part, gridDim.x, s_warp);
-    if (threadIdx.x == 0) {
-        st->beta = s / st->rr;
-        st->rr = s;
-        st->iters += 1;
-        if (s <= st->tol2 * st->bb || st->iters >= st->max_iter) st->done = 1;
-        st->ticket = 0u;
-    }
+    if (threadIdx.x == 0) rr_part[blockIdx.x] = t;
 }
 
-// p = r + beta p.
+// rr_new = r.r, beta = rr_new / rr_old; p = r + beta p; stop test.
 __global__ void __launch_bounds__(kCgThreads) cg_direction_kernel(int64_t n, const double* __restrict__ r,
-                                                                  double* __restrict__ p, const CgState* st) {
-    if (st->done) return;
-    const double beta = st->beta;
+                                                                  double* __restrict__ p,
+                                                                  const double* __restrict__ rr_part, int n_rr,
+                                                                  CgState* st) {
+    __shared__ double s_warp[kCgThreads / 32];
+    __shared__ double s_beta;
+    if (st->done) return;   // only CTA 0 below sets it, after this iteration's work
+    const double rr_new = sum_partials(rr_part, n_rr, s_warp);
+    if (threadIdx.x == 0) s_beta = rr_new / st->rr_old;
+    __syncthreads();
+    const double beta = s_beta;
     for (int64_t i = (int64_t)blockIdx.x * kCgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCgThreads)
         p[i] = fma(beta, p[i], r[i]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->beta = beta;
+        st->rr = rr_new;
+        st->iters += 1;
+        if (rr_new <= st->tol2 * st->bb || st->iters >= st->max_iter) st->done = 1;
+    }
 }
 
 // Lanes per row: AROL_SPMV_LPR (1, 2, 4 or 8) when set, else about 8 to 16
@@ -345,8 +361,11 @@ arol_status arol_cg_create(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, 
             case 4: cg_ap_kernel<4><<<h->grid_rows, kCgThreads, 0, h->cap_stream>>>(h->A, h->p, h->ap, h->part, h->st); break;
             default: cg_ap_kernel<8><<<h->grid_rows, kCgThreads, 0, h->cap_stream>>>(h->A, h->p, h->ap, h->part, h->st); break;
             }
-            cg_update_kernel<<<h->grid_vec, kCgThreads, 0, h->cap_stream>>>(n_rows, h->xw, h->r, h->p, h->ap, h->part, h->st);
-            cg_direction_kernel<<<h->grid_vec, kCgThreads, 0, h->cap_stream>>>(n_rows, h->r, h->p, h->st);
+            double* rr_part = h->part + h->grid_rows;
+            cg_update_kernel<<<h->grid_vec, kCgThreads, 0, h->cap_stream>>>(n_rows, h->xw, h->r, h->p, h->ap, h->part,
+                                                                            h->grid_rows, rr_part, h->st);
+            cg_direction_kernel<<<h->grid_vec, kCgThreads, 0, h->cap_stream>>>(n_rows, h->r, h->p, rr_part, h->grid_vec,
+                                                                               h->st);
             e = cudaGetLastError();
         }
         cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &h->graph);
