@@ -356,7 +356,10 @@ __device__ __forceinline__ void backward_rows(const DownscaleDev& p, const float
             flag_error(p, 2u);
             break;
         }
-        const uint32_t c = u % (uint32_t)nch, stripe = u / (uint32_t)nch;
+        // units in reverse: a backward that follows the forward finds the last
+        // frames that pass read still in L2
+        const uint32_t v = units - 1u - u;
+        const uint32_t c = v % (uint32_t)nch, stripe = v / (uint32_t)nch;
         const uint32_t f = stripe / HB, sy = stripe - f * HB;
         const int c0 = (int)c * Wc;
         const int nb = min(Wc, p.W - c0) >> 3;
@@ -479,7 +482,8 @@ __global__ void __launch_bounds__(BulkCfg<kMode>::kThreads, BulkCfg<kMode>::kMin
                     flag_error(p, 1u);
                     break;
                 }
-                const uint32_t c = u % (uint32_t)nch, stripe = u / (uint32_t)nch;
+                const uint32_t v = kMode == 1 ? units - 1u - u : u;   // the backward walks units in reverse
+                const uint32_t c = v % (uint32_t)nch, stripe = v / (uint32_t)nch;
                 const uint32_t f = stripe / HB, sy = stripe - f * HB;
                 const int c0 = (int)c * Wc;
                 const int wc = min(Wc, p.W - c0);
