@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import workloads as W
+from oracle import cpu_ref as C
 from oracle import tiler as O
 from tests.gpu_helpers import FIR_RTOL, assert_fir_close, dev, fir_scale, host
 from tests.test_parity_gpu import _three_task_chain
@@ -85,3 +86,71 @@ def test_batch_rejects_matmul_members(arol):
     spec = W.matmul_task(128, 128, 128)
     with pytest.raises(arol.ArolError):
         arol.Batch([spec])
+
+
+def _row_cases():
+    """Row-FIR tasks that reach every exact-m template and both tile layouts
+    at their capacity edges (4096-float windows; whole rows up to 2048
+    words), with origins that wrap."""
+    g = W.rng(122)
+    cases = []
+    for m in range(1, 17):                          # every output count, T up to 32
+        T = max(m, int(g.integers(m, 33)))
+        S = int(g.integers(1, T + 1))
+        cases.append((int(g.integers(1, 6)), int(g.integers(40, 700)), T, m, S))
+    # a long row: step 32, T 32 -> at most (4096 - 32) / 32 + 1 = 128 repetitions per tile
+    for w in (32 * 127, 32 * 128, 32 * 128 + 5, 32 * 129):
+        cases.append((2, w, 32, 3, 32))
+    for w in (2047, 2048, 2049):                    # whole rows: two per tile, then one
+        cases.append((5, w, 9, 2, 5))
+    cases.append((3, 2, 7, 1, 1))                   # a row shorter than its pattern
+    tasks, xs = [], []
+    for (h, w, T, m, S) in cases:
+        taps = (g.standard_normal((m, T)) / T).astype(np.float32)
+        tk = W.fir_row_task(h, w, T, m, S, taps)
+        tasks.append(tk)
+        xs.append(g.standard_normal((h, w)).astype(np.float32))
+    return tasks, xs
+
+
+def test_batch_row_fir_edges(arol):
+    tasks, xs = _row_cases()
+    b = arol.Batch(tasks)
+    ins = [dev(x) for x in xs]
+    outs, outs2 = b.empty_outputs(), b.empty_outputs()
+    b.run(ins, outs)
+    b.run_per_task(ins, outs2)
+    torch.cuda.synchronize()
+    for tk, x, y, y2 in zip(tasks, xs, outs, outs2):
+        y = host(y)
+        assert_fir_close(y, C.run_task(tk, [x])[0], fir_scale(tk, x, C.run_chain),
+                         what=f"row fir {x.shape} m={tk['outputs'][0]['pattern'][0]}")
+        np.testing.assert_array_equal(y, host(y2))
+    # other launch shapes give the same bits
+    b.tune(ins, outs, force=True)
+    outs3 = b.empty_outputs()
+    b.run(ins, outs3)
+    torch.cuda.synchronize()
+    for y2, y3 in zip(outs2, outs3):
+        np.testing.assert_array_equal(host(y2), host(y3))
+
+
+def test_batch_mixes_bf16_and_row_tasks(arol):
+    """A bf16 task (generic path) among row-FIR tasks (staged path)."""
+    g = W.rng(123)
+    tasks, xs = _row_cases()
+    tasks, xs = tasks[:4], xs[:4]
+    tk = W.random_tiler_task(g, "fir")
+    tk = dict(tk, inputs=[dict(tk["inputs"][0], dtype="bf16")], outputs=[dict(tk["outputs"][0], dtype="bf16")])
+    xb = W.bf16_round(g.standard_normal(tk["inputs"][0]["shape"]).astype(np.float32))
+    b = arol.Batch(tasks + [tk])
+    outs = b.empty_outputs()
+    b.run([dev(x) for x in xs] + [dev(xb)], outs)
+    torch.cuda.synchronize()
+    for t, x, y in zip(tasks, xs, outs[:4]):
+        assert_fir_close(host(y), C.run_task(t, [x])[0], fir_scale(t, x, C.run_chain), what="row fir next to bf16")
+    xv = W.bf16_bits_to_f32(xb).astype(np.float64)
+    tk_v = dict(tk, inputs=[dict(tk["inputs"][0], dtype="f32")], outputs=[dict(tk["outputs"][0], dtype="f32")])
+    ref = O.run_task(tk_v, [xv])[0]
+    got = W.bf16_bits_to_f32(host(outs[4])).astype(np.float64)
+    assert np.all(np.abs(got - ref) <= FIR_RTOL * fir_scale(tk_v, xv) + 2.0 ** -8 * np.abs(ref) + 1e-38)
