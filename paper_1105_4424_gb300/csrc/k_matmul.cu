@@ -511,12 +511,13 @@ __global__ void __launch_bounds__(192, 1) matmul_tc2_kernel(const __grid_constan
                 const uint32_t d = tmem + (uint32_t)(acc * 256);
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int st = (int)(g % STAGES2);
+                    // the stage's bytes were written by the copy engine and
+                    // completed on this barrier: no tcgen05 fence is needed here
                     if (!mbar_wait(full0 + 8 * st, (g / STAGES2) & 1u)) {
                         atomicOr(err, 2u);
                         ok = false;
                         break;
                     }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = smem_addr(sA + st * G::kABytes);
                     const uint32_t b0 = smem_addr(sB + st * G::kBBytes);
 #pragma unroll
