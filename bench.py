@@ -470,9 +470,19 @@ def cpu_baseline_chain(max_seconds=12.0):
             break
         frames = min(FRAMES, max(frames * 2, int(frames * max_seconds / max(dt, 1e-3) / 2)))
     del g
-    return {"value": chain_units(frames) / dt, "unit": UNIT, "cores": C.threads(), "kind": "oracle",
+    # the same oracle on one core, one frame
+    cores = C.threads()
+    chain1, (x1,) = W.config1(seed=1, frames=1)
+    C.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        C.run_chain(chain1, [x1])
+        dt1 = time.perf_counter() - t0
+    finally:
+        C.set_threads(cores)
+    return {"value": chain_units(frames) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{frames} of 64 frames (1080x1920), full chain, float64 accumulation",
-            "seconds": dt}
+            "seconds": dt, "single_core": {"value": chain_units(1) / dt1, "sample": "1 frame", "seconds": dt1}}
 
 
 # -------------------------------------------------------------- main arms
