@@ -298,7 +298,67 @@ bool port_needs_wide(const PortDev& p, const arol_task_desc& d) {
     return false;
 }
 
+// A FIR task whose leading array dimensions are frames (origin 0, paving 1
+// on their own repetition dimension, fitting 0, iterated completely, the
+// same extents in and out) is the same task on (frames x rows, W): the rows
+// of every frame follow each other in memory, so every linear offset is
+// unchanged.  This lets such tasks (and frames = 1) take the row-FIR path.
+bool flatten_frames(const arol_task_desc& d, arol_task_desc* o) {
+    const int R = d.in[0].rank;
+    if (d.elem != AROL_ELEM_FIR || R < 3 || d.out[0].rank != R || d.rep_rank != R) return false;
+    const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
+    if (ti.pattern_rank != 1 || to.pattern_rank != 1) return false;
+    int64_t rows = 1;
+    for (int k = 0; k < R - 1; ++k) {
+        if (d.in[0].shape[k] != d.rep[k] || d.out[0].shape[k] != d.rep[k]) return false;
+        if (ti.origin[k] != 0 || to.origin[k] != 0 || ti.fitting[k][0] != 0 || to.fitting[k][0] != 0) return false;
+        for (int q = 0; q < R; ++q)
+            if (ti.paving[k][q] != (q == k ? 1 : 0) || to.paving[k][q] != (q == k ? 1 : 0)) return false;
+        rows *= d.rep[k];
+    }
+    for (int q = 0; q < R - 1; ++q)
+        if (ti.paving[R - 1][q] != 0 || to.paving[R - 1][q] != 0) return false;
+    if (rows >= 2147483647LL) return false;
+    *o = d;
+    o->rep_rank = 2;
+    o->rep[0] = rows;
+    o->rep[1] = d.rep[R - 1];
+    arol_array_desc* arrs[2] = {&o->in[0], &o->out[0]};
+    const arol_array_desc* src[2] = {&d.in[0], &d.out[0]};
+    for (int a = 0; a < 2; ++a) {
+        arrs[a]->rank = 2;
+        arrs[a]->shape[0] = rows;
+        arrs[a]->shape[1] = src[a]->shape[R - 1];
+        arrs[a]->shape[2] = arrs[a]->shape[3] = 1;
+    }
+    arol_tiler* tls[2] = {&o->in_tiler[0], &o->out_tiler[0]};
+    const arol_tiler* tsrc[2] = {&ti, &to};
+    for (int a = 0; a < 2; ++a) {
+        arol_tiler& t = *tls[a];
+        const arol_tiler& u = *tsrc[a];
+        std::memset(&t, 0, sizeof t);
+        t.origin[1] = u.origin[R - 1];
+        t.paving[0][0] = 1;
+        t.paving[1][1] = u.paving[R - 1][R - 1];
+        t.fitting[1][0] = u.fitting[R - 1][0];
+        t.pattern_rank = 1;
+        t.pattern[0] = u.pattern[0];
+    }
+    return true;
+}
+
+TaskDev make_taskdev_exact(const arol_task_desc& d);
+
 TaskDev make_taskdev(const arol_task_desc& d) {
+    arol_task_desc flat;
+    if (flatten_frames(d, &flat)) {
+        const TaskDev t = make_taskdev_exact(flat);
+        if (t.rowfir) return t;
+    }
+    return make_taskdev_exact(d);
+}
+
+TaskDev make_taskdev_exact(const arol_task_desc& d) {
     TaskDev t;
     std::memset(&t, 0, sizeof t);
     for (int q = 0; q < 4; ++q) t.rep[q] = 1;
