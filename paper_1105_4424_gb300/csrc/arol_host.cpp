@@ -347,6 +347,68 @@ bool flatten_frames(const arol_task_desc& d, arol_task_desc* o) {
     return true;
 }
 
+// The column form: leading frames as above, then rows (step S down the
+// rows per repetition, the pattern running down them) and columns (one per
+// repetition).  Frames merge into rows only when every frame's rows are
+// covered exactly without wrap (origin 0, rows = S * repetitions, T <= S, and
+// the output likewise), or when there is a single frame.
+bool flatten_frames_col(const arol_task_desc& d, arol_task_desc* o) {
+    const int R = d.in[0].rank;
+    if (d.elem != AROL_ELEM_FIR || R < 3 || d.out[0].rank != R || d.rep_rank != R) return false;
+    const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
+    if (ti.pattern_rank != 1 || to.pattern_rank != 1) return false;
+    int64_t frames = 1;
+    for (int k = 0; k < R - 2; ++k) {
+        if (d.in[0].shape[k] != d.rep[k] || d.out[0].shape[k] != d.rep[k]) return false;
+        if (ti.origin[k] != 0 || to.origin[k] != 0 || ti.fitting[k][0] != 0 || to.fitting[k][0] != 0) return false;
+        for (int q = 0; q < R; ++q)
+            if (ti.paving[k][q] != (q == k ? 1 : 0) || to.paving[k][q] != (q == k ? 1 : 0)) return false;
+        frames *= d.rep[k];
+    }
+    const int rr = R - 2, cc = R - 1;
+    for (int q = 0; q < R; ++q) {
+        if (q != rr && (ti.paving[rr][q] != 0 || to.paving[rr][q] != 0)) return false;
+        if (ti.paving[cc][q] != (q == cc ? 1 : 0) || to.paving[cc][q] != (q == cc ? 1 : 0)) return false;
+    }
+    if (ti.fitting[rr][0] != 1 || to.fitting[rr][0] != 1 || ti.fitting[cc][0] != 0 || to.fitting[cc][0] != 0) return false;
+    const int64_t S = ti.paving[rr][rr], m = to.paving[rr][rr], R0 = d.rep[rr];
+    if (frames > 1) {
+        if (ti.origin[rr] != 0 || to.origin[rr] != 0 || S < 1 || d.in[0].shape[rr] != S * R0 ||
+            d.out[0].shape[rr] != m * R0 || ti.pattern[0] > S)
+            return false;
+    }
+    if (frames * d.in[0].shape[rr] >= 2147483647LL || frames * d.out[0].shape[rr] >= 2147483647LL ||
+        frames * R0 >= 2147483647LL)
+        return false;
+    *o = d;
+    o->rep_rank = 2;
+    o->rep[0] = frames * R0;
+    o->rep[1] = d.rep[cc];
+    arol_array_desc* arrs[2] = {&o->in[0], &o->out[0]};
+    const arol_array_desc* src[2] = {&d.in[0], &d.out[0]};
+    for (int a = 0; a < 2; ++a) {
+        arrs[a]->rank = 2;
+        arrs[a]->shape[0] = frames * src[a]->shape[rr];
+        arrs[a]->shape[1] = src[a]->shape[cc];
+        arrs[a]->shape[2] = arrs[a]->shape[3] = 1;
+    }
+    arol_tiler* tls[2] = {&o->in_tiler[0], &o->out_tiler[0]};
+    const arol_tiler* tsrc[2] = {&ti, &to};
+    for (int a = 0; a < 2; ++a) {
+        arol_tiler& t = *tls[a];
+        const arol_tiler& u = *tsrc[a];
+        std::memset(&t, 0, sizeof t);
+        t.origin[0] = u.origin[rr];
+        t.origin[1] = u.origin[cc];
+        t.paving[0][0] = u.paving[rr][rr];
+        t.paving[1][1] = 1;
+        t.fitting[0][0] = 1;
+        t.pattern_rank = 1;
+        t.pattern[0] = u.pattern[0];
+    }
+    return true;
+}
+
 TaskDev make_taskdev_exact(const arol_task_desc& d);
 
 TaskDev make_taskdev(const arol_task_desc& d) {
@@ -354,6 +416,10 @@ TaskDev make_taskdev(const arol_task_desc& d) {
     if (flatten_frames(d, &flat)) {
         const TaskDev t = make_taskdev_exact(flat);
         if (t.rowfir) return t;
+    }
+    if (flatten_frames_col(d, &flat)) {
+        const TaskDev t = make_taskdev_exact(flat);
+        if (t.colfir) return t;
     }
     return make_taskdev_exact(d);
 }
@@ -404,6 +470,17 @@ TaskDev make_taskdev_exact(const arol_task_desc& d) {
         if (t.step < 1) t.rowfir = 0;
         t.wfull = t.step * (int32_t)(d.rep[1] > 0 ? d.rep[1] - 1 : 0) + d.fir_T;
         t.wfull_div = make_fastdiv((uint32_t)std::max(t.wfull, 1));
+    }
+    // Column FIR: one column per r1, step down the rows per r0, the pattern
+    // running down the rows, m consecutive output rows per repetition.
+    if (!t.rowfir && d.elem == AROL_ELEM_FIR && !t.wide && !t.in_bf16 && !t.out_bf16 && d.rep_rank == 2 &&
+        d.in[0].rank == 2 && d.out[0].rank == 2 && ti.pattern_rank == 1 && to.pattern_rank == 1 &&
+        ti.paving[0][0] >= 1 && ti.paving[0][1] == 0 && ti.paving[1][0] == 0 && ti.paving[1][1] == 1 &&
+        ti.fitting[0][0] == 1 && ti.fitting[1][0] == 0 && to.paving[0][0] == d.fir_m && to.paving[0][1] == 0 &&
+        to.paving[1][0] == 0 && to.paving[1][1] == 1 && to.fitting[0][0] == 1 && to.fitting[1][0] == 0 &&
+        d.fir_T <= 32 && d.fir_m <= 16 && d.in[0].shape[0] > 1 && d.out[0].shape[0] > 1) {
+        t.step = (int32_t)emod(ti.paving[0][0], d.in[0].shape[0]);
+        t.colfir = t.step >= 1 ? 1 : 0;
     }
     return t;
 }
@@ -1447,7 +1524,7 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
         size_t ntaps = 0;
         for (size_t i = 0; i < n; ++i) {
             ntaps += b->taps[i].size();
-            if (b->host_tasks[i].rowfir) ntaps += (size_t)b->host_tasks[i].T * 16;
+            if (b->host_tasks[i].rowfir || b->host_tasks[i].colfir) ntaps += (size_t)b->host_tasks[i].T * 16;
         }
         AROL_CUDA(cudaMalloc(&b->dev_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMalloc(task table)");
         AROL_CUDA(cudaMallocHost(&b->pinned_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMallocHost(task table)");
@@ -1464,7 +1541,7 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
                 off += b->taps[i].size();
             }
             TaskDev& td = b->host_tasks[i];
-            if (td.rowfir) {
+            if (td.rowfir || td.colfir) {
                 std::vector<float> ht((size_t)td.T * 16, 0.f);
                 for (int k = 0; k < td.T; ++k)
                     for (int j = 0; j < td.m; ++j) ht[(size_t)k * 16 + j] = b->taps[i][(size_t)j * td.T + k];

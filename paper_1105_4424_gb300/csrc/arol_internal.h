@@ -47,11 +47,13 @@ struct TaskDev {
     int32_t wide;           // 1 when repetition indices or base sums reach 2^31 (64-bit path)
     int32_t rowfir;         // 1: rank-2 row FIR (paving [[1,0],[0,step]], fitting [[0],[1]], output
                             //    paving [[1,0],[0,m]]) with step, T <= 32 and m <= 16: row-tile path
-    int32_t step;           // input paving along the row (reduced), row-FIR tasks
+    int32_t colfir;         // 1: rank-2 column FIR (paving [[step,0],[0,1]], fitting [[1],[0]], output
+                            //    paving [[m,0],[0,1]], fitting [[1],[0]]) with T <= 32 and m <= 16
+    int32_t step;           // input paving along the row (row FIR) or down the column (column FIR), reduced
     int32_t wfull;          // staged window of one whole row: step * (rep[3] - 1) + T
     FastDiv wfull_div;      // division by wfull
     const float* taps;      // m x T (fir)
-    const float* taps_t;    // row-FIR tasks in a batch: taps transposed, T x 16, zero padded
+    const float* taps_t;    // row- and column-FIR tasks in a batch: taps transposed, T x 16, zero padded
     const void* x;
     void* y;
 };

@@ -389,6 +389,85 @@ __device__ __forceinline__ void row_fir_dispatch(const TaskDev& t, const float* 
 #undef AROL_ROW_FIR_CASE
 }
 
+// ---------------------------------------------------------------------------
+// Column FIR tile (repetitions start .. start + count - 1 of a column-FIR
+// task, column fastest): repetition (r0, c) reads rows (o0 + step*r0 + k) mod
+// H of column (o1 + c) mod W and writes m consecutive output rows of one
+// column.  Consecutive threads take consecutive columns, so the loads of a
+// warp and its stores are contiguous; the input is read straight from global
+// memory (each element once when T <= step), the transposed taps from shared
+// memory.  Two repetitions per thread share every tap load.
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void col_fir_compute(const TaskDev& t, const float* ht, int64_t start, int count) {
+    constexpr int kHt = 16;
+    const int T = t.T;
+    const uint32_t S = (uint32_t)t.step, C = (uint32_t)t.rep[3];
+    const uint32_t hin = (uint32_t)t.in.shape[0], win = (uint32_t)t.in.shape[1];
+    const uint32_t hout = (uint32_t)t.out.shape[0], wout = (uint32_t)t.out.shape[1];
+    const float* x = static_cast<const float*>(t.x);
+    float* y = static_cast<float*>(t.y);
+    const int B = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < count; i0 += 2 * B) {
+        const int i1 = i0 + B < count ? i0 + B : i0;
+        uint32_t r0[2], col[2], row[2];
+        const uint32_t lr[2] = {(uint32_t)(start + i0), (uint32_t)(start + i1)};   // < 2^31: not wide
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            r0[a] = fast_div(lr[a], t.rep_div[3]);
+            const uint32_t c = lr[a] - r0[a] * C;
+            const uint32_t vr = t.in.origin[0] + S * r0[a];              // < 2^31: checked on the host
+            row[a] = vr - fast_div(vr, t.in.shape_div[0]) * hin;
+            const uint32_t vc = t.in.origin[1] + c;
+            col[a] = vc - fast_div(vc, t.in.shape_div[1]) * win;
+        }
+        float acc0[M], acc1[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc0[j] = acc1[j] = 0.f;
+#pragma unroll 2
+        for (int kk = 0; kk < T; ++kk) {
+            const float p0 = __ldg(x + (int64_t)row[0] * win + col[0]);
+            const float p1 = __ldg(x + (int64_t)row[1] * win + col[1]);
+            row[0] = row[0] + 1u == hin ? 0u : row[0] + 1u;
+            row[1] = row[1] + 1u == hin ? 0u : row[1] + 1u;
+            float h[M];
+            load_taps<M>(ht + kk * kHt, h);
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                acc0[j] = fmaf(h[j], p0, acc0[j]);
+                acc1[j] = fmaf(h[j], p1, acc1[j]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a == 1 && i1 == i0) break;
+            const uint32_t c = lr[a] - r0[a] * C;
+            const uint32_t vr = t.out.origin[0] + (uint32_t)M * r0[a];   // < 2^31: checked on the host
+            uint32_t orow = vr - fast_div(vr, t.out.shape_div[0]) * hout;
+            const uint32_t vc = t.out.origin[1] + c;
+            const uint32_t ocol = vc - fast_div(vc, t.out.shape_div[1]) * wout;
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                y[(int64_t)orow * wout + ocol] = a == 0 ? acc0[j] : acc1[j];
+                orow = orow + 1u == hout ? 0u : orow + 1u;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void col_fir_dispatch(const TaskDev& t, const float* ht, int64_t start, int count) {
+#define AROL_COL_FIR_CASE(M) \
+    case M: col_fir_compute<M>(t, ht, start, count); break;
+    switch (t.m) {
+        AROL_COL_FIR_CASE(1) AROL_COL_FIR_CASE(2) AROL_COL_FIR_CASE(3) AROL_COL_FIR_CASE(4)
+        AROL_COL_FIR_CASE(5) AROL_COL_FIR_CASE(6) AROL_COL_FIR_CASE(7) AROL_COL_FIR_CASE(8)
+        AROL_COL_FIR_CASE(9) AROL_COL_FIR_CASE(10) AROL_COL_FIR_CASE(11) AROL_COL_FIR_CASE(12)
+        AROL_COL_FIR_CASE(13) AROL_COL_FIR_CASE(14) AROL_COL_FIR_CASE(15)
+        default: col_fir_compute<16>(t, ht, start, count); break;
+    }
+#undef AROL_COL_FIR_CASE
+}
+
 // Shared memory of the batch kernel: a ring of three task records (the
 // TaskDev of the tile being computed, of the next tile, whose copies are in
 // flight, and of the one after, being copied), then two data slots, each the
@@ -418,6 +497,12 @@ __device__ __forceinline__ RowGeom row_geom(const TaskDev& t, int64_t start, int
     return g;
 }
 
+// Issues (cp.async, no wait) the copies of a task's transposed taps into a data slot.
+__device__ __forceinline__ void stage_taps(const TaskDev& t, float* slot) {
+    float* ht = slot + kWinPad;
+    for (int i = threadIdx.x; i < t.T * 16; i += blockDim.x) ptx::cp_async4(ht + i, t.taps_t + i);
+}
+
 // Issues (cp.async, no wait) the copies of a row tile's window and, unless
 // the slot already holds them, its task's transposed taps.
 __device__ __forceinline__ void stage_row_tile(const TaskDev& t, int64_t start, int count, float* slot,
@@ -438,10 +523,7 @@ __device__ __forceinline__ void stage_row_tile(const TaskDev& t, int64_t start, 
     } else {
         stage_window(t, g.row0, g.a0, t.step * (count - 1) + t.T, slot);
     }
-    if (need_taps) {
-        float* ht = slot + kWinPad;
-        for (int i = threadIdx.x; i < t.T * 16; i += blockDim.x) ptx::cp_async4(ht + i, t.taps_t + i);
-    }
+    if (need_taps) stage_taps(t, slot);
 }
 
 __device__ __forceinline__ void compute_row_tile(const TaskDev& t, int64_t start, int count, const float* slot) {
@@ -491,6 +573,9 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(cons
             if (m0.rowfir) {
                 stage_row_tile(m0, tl0.start, tl0.count, data, true);
                 slot_task[0] = tl0.task;
+            } else if (m0.colfir) {
+                stage_taps(m0, data);
+                slot_task[0] = tl0.task;
             }
         }
         ptx::cp_async_commit();
@@ -507,6 +592,9 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(cons
                 if (m1.rowfir) {
                     stage_row_tile(m1, tl1.start, tl1.count, data + nxt * kSlotFloats, slot_task[nxt] != tl1.task);
                     slot_task[nxt] = tl1.task;
+                } else if (m1.colfir) {
+                    if (slot_task[nxt] != tl1.task) stage_taps(m1, data + nxt * kSlotFloats);
+                    slot_task[nxt] = tl1.task;
                 }
             }
             if (ti + 2 * G < ntiles) stage_meta(tasks[tl2.task], meta + ((i + 2) % kMetaSlots) * kTaskFloats);
@@ -519,6 +607,10 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(cons
         const TaskDev* mcur = reinterpret_cast<const TaskDev*>(meta + (i % kMetaSlots) * kTaskFloats);
         if (kRows && mcur->rowfir) {
             compute_row_tile(*mcur, tile.start, tile.count, data + cur * kSlotFloats);
+            continue;
+        }
+        if (kRows && mcur->colfir) {
+            col_fir_dispatch(*mcur, data + cur * kSlotFloats + kWinPad, tile.start, tile.count);
             continue;
         }
         const TaskDev& t = tasks[tile.task];

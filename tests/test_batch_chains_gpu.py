@@ -154,3 +154,48 @@ def test_batch_mixes_bf16_and_row_tasks(arol):
     ref = O.run_task(tk_v, [xv])[0]
     got = W.bf16_bits_to_f32(host(outs[4])).astype(np.float64)
     assert np.all(np.abs(got - ref) <= FIR_RTOL * fir_scale(tk_v, xv) + 2.0 ** -8 * np.abs(ref) + 1e-38)
+
+
+def _col_task(g, h, w, T, m, S, origin=(0, 0), out_origin=(0, 0)):
+    """Column FIR: repetition (r0, c) reads rows origin0 + S*r0 + k (mod h) of
+    column origin1 + c (mod w); m consecutive output rows per repetition."""
+    R0 = -(-h // S)
+    taps = (g.standard_normal((m, T)) / T).astype(np.float32)
+    inp = W.port((h, w), origin, ((S, 0), (0, 1)), ((1,), (0,)), (T,))
+    out = W.port((m * R0, w), out_origin, ((m, 0), (0, 1)), ((1,), (0,)), (m,))
+    return W.task((R0, w), "fir", [inp], [out], taps)
+
+
+def test_batch_column_fir(arol):
+    """Column FIRs for every output count, with wrapping origins, steps below
+    and above T, and a framed column task whose windows overlap the next
+    frame (so it must not be merged into one tall array)."""
+    g = W.rng(124)
+    tasks, xs = [], []
+    for m in range(1, 17):
+        T = int(g.integers(m, 33))
+        S = int(g.integers(1, T + 3))
+        h, w = int(g.integers(8, 90)), int(g.integers(3, 300))
+        tk = _col_task(g, h, w, T, m, S, origin=(int(g.integers(-40, 40)), int(g.integers(-40, 40))),
+                       out_origin=(int(g.integers(0, 5)), int(g.integers(0, 7))))
+        tasks.append(tk)
+        xs.append(g.standard_normal((h, w)).astype(np.float32))
+    # frames with overlapping windows (T > S): rows wrap within each frame
+    F, h, w, T, m, S = 3, 24, 40, 6, 2, 4
+    taps = (g.standard_normal((m, T)) / T).astype(np.float32)
+    inp = W.port((F, h, w), (0, 0, 0), ((1, 0, 0), (0, S, 0), (0, 0, 1)), ((0,), (1,), (0,)), (T,))
+    out = W.port((F, m * h // S, w), (0, 0, 0), ((1, 0, 0), (0, m, 0), (0, 0, 1)), ((0,), (1,), (0,)), (m,))
+    tasks.append(W.task((F, h // S, w), "fir", [inp], [out], taps))
+    xs.append(g.standard_normal((F, h, w)).astype(np.float32))
+    b = arol.Batch(tasks)
+    ins = [dev(x) for x in xs]
+    outs, outs2 = b.empty_outputs(), b.empty_outputs()
+    b.run(ins, outs)
+    b.run_per_task(ins, outs2)
+    torch.cuda.synchronize()
+    for tk, x, y, y2 in zip(tasks, xs, outs, outs2):
+        y = host(y)
+        assert_fir_close(y, O.run_task(tk, [x])[0], fir_scale(tk, x), what=f"column fir {x.shape}")
+        np.testing.assert_array_equal(y, host(y2))
+        # the single-task path agrees
+        np.testing.assert_allclose(host(arol.Task(tk).run([dev(x)])), y, rtol=1e-6, atol=1e-6)
