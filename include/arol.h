@@ -142,8 +142,7 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out);
  * first task's inputs and the last task's output.  A chain whose tasks are a
  * separable block downscaler (horizontal then vertical fir with step == T, no
  * wrap) runs as one fused kernel that never writes the intermediate to HBM;
- * other chains run task by task through an intermediate the chain allocates
- * on first use. */
+ * other chains run stage by stage through intermediates the chain owns. */
 arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out);
 
 /* Replace the fir taps.  on_device = 0: `taps` is host memory, copied now.
@@ -155,7 +154,11 @@ arol_status arol_task_set_taps(arol_task t, const float* taps, int on_device);
 
 /* Run the task: in[k] is the device pointer of input port k, out[0] of the
  * output port.  Inputs are read-only (Sec. 6.3); they must not overlap the
- * output. */
+ * output.  Row- and column-FIR tasks and chains outside the fused kernel run
+ * on the batch engine as a one-member batch the handle owns (built at the
+ * first run, rebuilt after arol_task_set_taps); with taps on the device they
+ * take the per-repetition kernel.  A handle may be used from several streams:
+ * a change of buffers is ordered after its launches on any stream. */
 arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, void* stream);
 
 /* Same computation from HOST buffers: copies each input from host memory to

@@ -588,6 +588,9 @@ struct arol_task_s {
     int device = -1;
     // unfused chain intermediates
     std::vector<void*> mids;
+    // row/column-FIR tasks and unfused chains run as a one-member batch
+    arol_batch ib = nullptr;
+    bool ib_checked = false;
     // fused downscaler
     int64_t ds_frames = 0;
     int ds_H = 0, ds_W = 0;
@@ -870,6 +873,11 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
 arol_status arol_task_set_taps(arol_task t, const float* taps, int on_device) {
     if (!t || !taps) return fail(AROL_ERR_INVALID, "null argument");
     if (t->taps_host.empty()) return fail(AROL_ERR_INVALID, "task has no fir taps");
+    if (t->ib) {   // rebuilt with the new taps at the next run
+        arol_batch_destroy(t->ib);
+        t->ib = nullptr;
+    }
+    t->ib_checked = false;
     if (on_device) {
         t->taps_borrowed = taps;
     } else {
@@ -924,6 +932,41 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+
+// Row- and column-FIR tasks and unfused chains run on the batch engine, as a
+// one-member batch owned by the task (staged row tiles, column tiles, one
+// launch per chain stage, in one graph).  *used stays false when the task
+// does not qualify (other elementary tasks, taps on the device), and the
+// caller takes the per-repetition path.
+arol_status run_internal_batch(arol_task t, const void* const* in, void* const* out, cudaStream_t s, bool* used) {
+    *used = false;
+    if (t->taps_borrowed || !t->taps_ready) return AROL_OK;
+    if (!t->ib_checked) {
+        t->ib_checked = true;
+        bool want = true;
+        for (const arol_task_desc& d : t->descs)
+            if (d.elem != AROL_ELEM_FIR) want = false;
+        if (want && t->kind == 0) {
+            const TaskDev td = make_taskdev(t->descs[0]);
+            want = td.rowfir || td.colfir;
+        }
+        if (want) {
+            arol_task self = t;
+            if (arol_batch_create(&self, 1, &t->ib) != AROL_OK) t->ib = nullptr;
+        }
+    }
+    if (!t->ib) return AROL_OK;
+    *used = true;
+    return arol_batch_run(t->ib, in, out, s);
+}
+
+}  // namespace
+
+extern "C" {
+
 arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, void* stream) {
     if (!t || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
@@ -944,6 +987,9 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
                       "matmul kernel launch");
             return AROL_OK;
         }
+        bool used = false;
+        st = run_internal_batch(t, in, out, s, &used);
+        if (used) return st;
         return run_generic(d0, taps, in[0], out[0], s);
     }
     if (t->kernel == 1 && aligned16(in[0])) {
@@ -954,6 +1000,9 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
         AROL_CUDA(launch_downscale_fwd(p, s), "downscale kernel launch");
         return AROL_OK;
     }
+    bool used = false;
+    st = run_internal_batch(t, in, out, s, &used);
+    if (used) return st;
     // Unfused chain through intermediates owned by the chain.
     const size_t n = t->descs.size();
     const void* cur = in[0];
@@ -1261,6 +1310,7 @@ arol_status arol_task_sync_status(arol_task t, void* stream) {
 
 void arol_task_destroy(arol_task t) {
     if (!t) return;
+    if (t->ib) arol_batch_destroy(t->ib);
     if (t->device >= 0) {
         int cur = 0;
         cudaGetDevice(&cur);
@@ -1313,6 +1363,7 @@ struct arol_batch_s {
     TaskDev* dev_tasks = nullptr;
     TaskDev* pinned_tasks = nullptr;
     cudaEvent_t table_copied = nullptr;
+    cudaEvent_t launched = nullptr;   // after the latest launch: a new table waits for it, on any stream
     TileDev* dev_tiles = nullptr;
     int64_t tiles_cap = 0;
     int ntiles = 0;
@@ -1529,6 +1580,7 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
         AROL_CUDA(cudaMalloc(&b->dev_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMalloc(task table)");
         AROL_CUDA(cudaMallocHost(&b->pinned_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMallocHost(task table)");
         AROL_CUDA(cudaEventCreateWithFlags(&b->table_copied, cudaEventDisableTiming), "cudaEventCreate");
+        AROL_CUDA(cudaEventCreateWithFlags(&b->launched, cudaEventDisableTiming), "cudaEventCreate");
         AROL_CUDA(cudaMalloc(&b->counter, sizeof(unsigned)), "cudaMalloc(counter)");
         AROL_CUDA(cudaMalloc(&b->taps_dev, std::max<size_t>(ntaps, 1) * sizeof(float)), "cudaMalloc(taps)");
         size_t off = 0;
@@ -1583,6 +1635,8 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
             b->last_out[i] = out[i];
         }
         std::memcpy(b->pinned_tasks, b->host_tasks.data(), n * sizeof(TaskDev));
+        // launches on other streams may still read the old table
+        AROL_CUDA(cudaStreamWaitEvent(s, b->launched, 0), "wait for previous launches");
         AROL_CUDA(cudaMemcpyAsync(b->dev_tasks, b->pinned_tasks, n * sizeof(TaskDev), cudaMemcpyHostToDevice, s),
                   "upload task table");
         AROL_CUDA(cudaEventRecord(b->table_copied, s), "cudaEventRecord");
@@ -1660,6 +1714,7 @@ arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out
     if (st != AROL_OK) return st;
     if ((st = batch_capture(b)) != AROL_OK) return st;
     AROL_CUDA(cudaGraphLaunch(b->exec, s), "graph launch");
+    AROL_CUDA(cudaEventRecord(b->launched, s), "cudaEventRecord");
     return AROL_OK;
 }
 
@@ -1677,6 +1732,7 @@ arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* c
                                           std::min(cnt, cap), b->threads, b->max_m, s),
                   "tiler kernel launch");
     }
+    AROL_CUDA(cudaEventRecord(b->launched, s), "cudaEventRecord");
     return AROL_OK;
 }
 
@@ -1759,6 +1815,7 @@ void arol_batch_destroy(arol_batch b) {
         invalidate_graph(b);
         if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
         if (b->table_copied) cudaEventDestroy(b->table_copied);
+        if (b->launched) cudaEventDestroy(b->launched);
         if (b->pinned_tasks) cudaFreeHost(b->pinned_tasks);
         free_dev(b->dev_tasks);
         free_dev(b->dev_tiles);
