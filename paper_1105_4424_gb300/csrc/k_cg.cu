@@ -51,22 +51,23 @@ __device__ __forceinline__ double row_dot(const Csr& A, const double* __restrict
     double s = 0.0;
     if (row < A.n) {
         const int64_t a = __ldg(A.row_ptr + row), z = __ldg(A.row_ptr + row + 1);
-        for (int64_t k0 = a + sub; k0 < z; k0 += 4 * LPR) {
-            double w[4];
+        int64_t k0 = a + sub;
+        // whole steps of four products, all loads issued first ...
+        for (; k0 + 3 * LPR < z; k0 += 4 * LPR) {
+            double w[4], xv[4];
             int32_t c[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int64_t k = k0 + u * LPR;
-                w[u] = k < z ? __ldg(A.val + k) : 0.0;
-                c[u] = k < z ? __ldg(A.col + k) : -1;
+                w[u] = __ldg(A.val + k0 + u * LPR);
+                c[u] = __ldg(A.col + k0 + u * LPR);
             }
-            double xv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? __ldg(v + c[u]) : 0.0;
+            for (int u = 0; u < 4; ++u) xv[u] = __ldg(v + c[u]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (c[u] >= 0) s = fma(w[u], xv[u], s);
+            for (int u = 0; u < 4; ++u) s = fma(w[u], xv[u], s);
         }
+        // ... then the remaining products one by one, in the same order
+        for (; k0 < z; k0 += LPR) s = fma(__ldg(A.val + k0), __ldg(v + __ldg(A.col + k0)), s);
     }
 #pragma unroll
     for (int off = LPR / 2; off > 0; off >>= 1) s += __shfl_xor_sync(kFullMask, s, off, LPR);
