@@ -161,3 +161,19 @@ def test_batch_accepts_chain_members_and_rejects_matmul(B):
     assert e.value.status == 3
     for h in parts + [ch, one, mm]:
         B.arol_task_destroy(h)
+
+
+def test_batch_rejects_members_with_device_taps(B):
+    """Taps borrowed from device memory cannot be copied into a batch: the
+    creation fails with AROL_ERR_INVALID (the pointer is never read here)."""
+    single, _ = W.config0()
+    t = B.arol_task_create(single)
+    B.lib.arol_task_set_taps(t, ctypes.c_void_p(0x1000), 1)
+    with pytest.raises(B.ArolError) as e:
+        B.arol_batch_create([t])
+    assert e.value.status == 1
+    # host taps again: accepted
+    B.arol_task_set_taps(t, np.zeros((3, 8), np.float32), False)
+    b = B.arol_batch_create([t])
+    B.arol_batch_destroy(b)
+    B.arol_task_destroy(t)
