@@ -351,6 +351,27 @@ def bench_batched_chains(A, torch, stream, flush, reps):
             "launches": {"batched": 2, "per_task": 2 * len(chains), "fused_per_chain": len(chains)}}
 
 
+def bench_stencil(A, torch, stream, flush, reps, hbm):
+    """A 3x3 stencil as a repetitive task (2-D pattern, identity fitting,
+    origin (-1, -1) with wrap) on an 8192 x 8192 float32 image, one call."""
+    n = 8192
+    g = W.rng(5)
+    x = g.random((n, n), dtype=np.float32)
+    H = (g.standard_normal((1, 9)) / 9).astype(np.float32)
+    inp = W.port((n, n), (-1, -1), ((1, 0), (0, 1)), ((1, 0), (0, 1)), (3, 3))
+    out = W.port((n, n), (0, 0), ((1, 0), (0, 1)), ((0,), (0,)), (1,))
+    t = A.Task(W.task((n, n), "fir", [inp], [out], H))
+    xd = torch.from_numpy(x).cuda()
+    y = t.empty_output("cuda")
+    run = t.prepare([xd], y)
+    for _ in range(3):
+        run()
+    ms = statistics.median(time_each_flushed(run, reps, stream, flush))
+    nbytes = 8 * n * n
+    return {"workload": "3x3 stencil, 8192x8192 f32, wrap", "ms": ms, "unique_bytes": nbytes,
+            "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_of_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm}
+
+
 def bench_backward(A, torch, stream, flush, reps):
     chain, (x,), w = W.config4()
     c = A.Chain(chain)
@@ -593,6 +614,7 @@ def run_gpu(args):
         line["config0"] = bench_config0(A, torch, stream, 200)
         line["batched"] = bench_batched(A, torch, stream, flush, reps)
         line["batched_chains"] = bench_batched_chains(A, torch, stream, flush, reps)
+        line["stencil"] = bench_stencil(A, torch, stream, flush, reps, hbm)
         line["fwd_bwd"] = bench_backward(A, torch, stream, flush, reps)
         line["matmul"] = bench_matmul(A, torch, stream, flush, reps, bf16)
         line["bf16_storage"] = bench_bf16(A, torch, stream, flush, reps, hbm)
@@ -628,6 +650,8 @@ def run_case(args):
     warm_clocks(torch, flush.w)
     if args.case == "batched":
         out = bench_batched(A, torch, stream, flush, reps, tune=not args.no_tune)
+    elif args.case == "stencil":
+        out = bench_stencil(A, torch, stream, flush, reps, hbm)
     elif args.case == "chains":
         out = bench_batched_chains(A, torch, stream, flush, reps)
     elif args.case == "backward":
@@ -652,7 +676,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["batched", "chains", "backward", "matmul", "config0", "cg", "bf16"],
+    ap.add_argument("--case", choices=["batched", "chains", "stencil", "backward", "matmul", "config0", "cg", "bf16"],
                     help="run one extra measurement alone (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="batched case: keep the default launch shape")
     args = ap.parse_args(argv)

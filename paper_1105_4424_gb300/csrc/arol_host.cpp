@@ -482,6 +482,33 @@ TaskDev make_taskdev_exact(const arol_task_desc& d) {
         t.step = (int32_t)emod(ti.paving[0][0], d.in[0].shape[0]);
         t.colfir = t.step >= 1 ? 1 : 0;
     }
+    // FIR on a 2-D pattern: pattern dims map to the array dims in order
+    // (fitting identity), diagonal paving, m outputs along the output row.
+    if (d.elem == AROL_ELEM_FIR && !t.wide && !t.in_bf16 && !t.out_bf16 && d.rep_rank == 2 && d.in[0].rank == 2 &&
+        d.out[0].rank == 2 && ti.pattern_rank == 2 && to.pattern_rank == 1 && ti.fitting[0][0] == 1 &&
+        ti.fitting[0][1] == 0 && ti.fitting[1][0] == 0 && ti.fitting[1][1] == 1 && ti.paving[0][1] == 0 &&
+        ti.paving[1][0] == 0 && to.paving[0][0] == 1 && to.paving[0][1] == 0 && to.paving[1][0] == 0 &&
+        to.paving[1][1] == d.fir_m && (d.fir_m == 1 || (to.fitting[0][0] == 0 && to.fitting[1][0] == 1)) &&
+        d.fir_T <= 64 && d.fir_m <= 16 && elems_of(d.in[0]) > 0 && elems_of(d.out[0]) > 0) {
+        const int64_t s0 = emod(ti.paving[0][0], d.in[0].shape[0]), s1 = emod(ti.paving[1][1], d.in[0].shape[1]);
+        const int64_t p0 = ti.pattern[0], p1 = ti.pattern[1];
+        // tile of 16 x 64 repetitions, or 32 x 32, whose input window fits 8192 floats
+        const int shapes[2][2] = {{16, 64}, {32, 32}};
+        for (const auto& sh : shapes) {
+            const int64_t wh = s0 * (sh[0] - 1) + p0, ww = s1 * (sh[1] - 1) + p1;
+            const int64_t tiles = ((d.rep[0] + sh[0] - 1) / sh[0]) * ((d.rep[1] + sh[1] - 1) / sh[1]);
+            if (wh * ww <= 8192 && tiles < 2147483647LL) {
+                t.fir2d = 1;
+                t.s0 = (int32_t)s0;
+                t.s1 = (int32_t)s1;
+                t.p0 = (int32_t)p0;
+                t.p1 = (int32_t)p1;
+                t.bh = sh[0];
+                t.bw = sh[1];
+                break;
+            }
+        }
+    }
     return t;
 }
 
@@ -904,6 +931,10 @@ arol_status run_generic(const arol_task_desc& d, const float* taps, const void* 
     td.taps = taps;
     td.x = x;
     td.y = y;
+    if (td.fir2d) {
+        AROL_CUDA(launch_fir2d(td, s), "2-D FIR kernel launch");
+        return AROL_OK;
+    }
     AROL_CUDA(launch_tiler_generic(td, td.elem == ELEM_FIR ? td.m : 1, s), "tiler kernel launch");
     return AROL_OK;
 }

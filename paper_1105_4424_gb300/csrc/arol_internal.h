@@ -49,6 +49,10 @@ struct TaskDev {
                             //    paving [[1,0],[0,m]]) with step, T <= 32 and m <= 16: row-tile path
     int32_t colfir;         // 1: rank-2 column FIR (paving [[step,0],[0,1]], fitting [[1],[0]], output
                             //    paving [[m,0],[0,1]], fitting [[1],[0]]) with T <= 32 and m <= 16
+    int32_t fir2d;          // 1: rank-2 FIR on a 2-D pattern (paving [[s0,0],[0,s1]], fitting identity,
+                            //    outputs m consecutive along the row): 2-D window tiles
+    int32_t s0, s1, p0, p1; // fir2d: steps and pattern extents (rows, columns)
+    int32_t bh, bw;         // fir2d: repetitions per CTA tile (rows, columns)
     int32_t step;           // input paving along the row (row FIR) or down the column (column FIR), reduced
     int32_t wfull;          // staged window of one whole row: step * (rep[3] - 1) + T
     FastDiv wfull_div;      // division by wfull
@@ -87,6 +91,7 @@ struct DownscaleDev {
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s);
 // CTA b takes tiles b, b + grid, ... (a static schedule; `counter` is unused).
+cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s);
 cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, int ntiles,
                                     unsigned* counter, int grid, int threads, int max_m,
                                     cudaStream_t s);

@@ -468,6 +468,133 @@ __device__ __forceinline__ void col_fir_dispatch(const TaskDev& t, const float* 
 #undef AROL_COL_FIR_CASE
 }
 
+// ---------------------------------------------------------------------------
+// FIR on a 2-D pattern (a stencil when m = 1): repetition (r0, r1) reads the
+// p0 x p1 block of rows o0 + s0*r0 + a and columns o1 + s1*r1 + b (mod the
+// array shape) and writes m consecutive elements of output row (oo0 + r0)
+// from column oo1 + m*r1.  A CTA takes a bh x bw block of repetitions: it
+// stages the (s0*(bh-1) + p0) x (s1*(bw-1) + p1) input window (wrapped) and
+// the transposed taps in shared memory, then each thread computes
+// repetitions of one column of the block, reading the window with
+// consecutive columns in consecutive lanes.
+// ---------------------------------------------------------------------------
+constexpr int kFir2dThreads = 256;
+constexpr int kFir2dWin = 8192;   // window floats (host-checked)
+
+template <int M>
+__device__ __forceinline__ void fir2d_compute(const TaskDev& t, const float* win, int ww, const float* ht,
+                                              uint32_t r0a, uint32_t r1a) {
+    constexpr int kHt = 16;
+    // thread: column lr1 of the block and rows g, g + rs, g + 2 rs, g + 3 rs
+    // (bh = 4 rs, rs = blockDim.x / bw); the four share every tap load
+    const int bw = t.bw, rs = (int)blockDim.x / bw;
+    const int lr1 = (int)threadIdx.x % bw, g = (int)threadIdx.x / bw;
+    const int s0 = t.s0, s1 = t.s1, p0 = t.p0, p1 = t.p1;
+    const uint32_t R0 = (uint32_t)t.rep[2], R1 = (uint32_t)t.rep[3];
+    const uint32_t r1 = r1a + (uint32_t)lr1;
+    if (r1 >= R1) return;
+    float acc[4][M];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[u][j] = 0.f;
+    const float* w0 = win + (s0 * g) * ww + s1 * lr1;
+    const int du = s0 * rs * ww;   // window offset between the thread's rows
+    int k = 0;
+    for (int a = 0; a < p0; ++a) {
+        const float* wr = w0 + a * ww;
+        for (int b = 0; b < p1; ++b, ++k) {
+            float h[M];
+            load_taps<M>(ht + k * kHt, h);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float v = wr[u * du + b];
+#pragma unroll
+                for (int j = 0; j < M; ++j) acc[u][j] = fmaf(h[j], v, acc[u][j]);
+            }
+        }
+    }
+    const uint32_t hout = (uint32_t)t.out.shape[0], wout = (uint32_t)t.out.shape[1];
+    float* y = static_cast<float*>(t.y);
+    const uint64_t vc = (uint64_t)t.out.origin[1] + (uint64_t)M * r1;
+    const uint32_t c0 = vc < 0x7fffffffull ? (uint32_t)vc - fast_div((uint32_t)vc, t.out.shape_div[1]) * wout
+                                           : (uint32_t)(vc % wout);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint32_t r0 = r0a + (uint32_t)(g + u * rs);
+        if (r0 >= R0) break;
+        const uint32_t vr = t.out.origin[0] + r0;                      // < 2^31: checked on the host
+        const uint32_t orow = vr - fast_div(vr, t.out.shape_div[0]) * hout;
+        float* yrow = y + (int64_t)orow * wout;
+        uint32_t c = c0;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            yrow[c] = acc[u][j];
+            c = (c + 1u == wout) ? 0u : c + 1u;
+        }
+    }
+}
+
+// Issues (cp.async, no wait) the copies of tile `tile`'s input window:
+// rows (o0 + s0*r0a + i) mod H, columns (o1 + s1*r1a + j) mod W.
+__device__ __forceinline__ void fir2d_stage(const TaskDev& t, uint32_t r0a, uint32_t r1a, int wh, int ww, float* win) {
+    const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
+    const uint32_t vr = t.in.origin[0] + (uint32_t)t.s0 * r0a;      // < 2^31: checked on the host
+    const uint32_t rb = vr - fast_div(vr, t.in.shape_div[0]) * hin;
+    const uint32_t vc = t.in.origin[1] + (uint32_t)t.s1 * r1a;
+    const uint32_t cb = vc - fast_div(vc, t.in.shape_div[1]) * wi;
+    const float* x = static_cast<const float*>(t.x);
+    // element e = i * ww + j of the window, walked with an incremental (i, j)
+    const int B = (int)blockDim.x, di = B / ww, dj = B - di * ww;
+    int i = (int)threadIdx.x / ww, j = (int)threadIdx.x - i * ww;
+    for (int e = threadIdx.x; e < wh * ww; e += B) {
+        uint32_t row = rb + (uint32_t)i, col = cb + (uint32_t)j;
+        row -= fast_div(row, t.in.shape_div[0]) * hin;
+        col -= fast_div(col, t.in.shape_div[1]) * wi;
+        ptx::cp_async4(win + e, x + (int64_t)row * wi + col);
+        i += di;
+        j += dj;
+        if (j >= ww) {
+            j -= ww;
+            ++i;
+        }
+    }
+}
+
+// One CTA per tile (tile = ty * tiles_x + tx covers repetitions r0 in
+// [ty*bh, +bh), r1 in [tx*bw, +bw)); CTAs of different tiles overlap their
+// copies and compute on an SM.  kMaxM: the largest output count the
+// instantiation handles; the one for m <= 4 keeps to 64 registers so that
+// four CTAs share an SM.
+template <int kMaxM>
+__global__ void __launch_bounds__(kFir2dThreads, kMaxM <= 4 ? 4 : 2) fir2d_kernel(const TaskDev t, int tiles_x) {
+    extern __shared__ __align__(16) float f2[];
+    const int ww = t.s1 * (t.bw - 1) + t.p1, wh = t.s0 * (t.bh - 1) + t.p0;
+    float* win = f2;
+    float* ht = f2 + ((wh * ww + 3) & ~3);
+    const int tile = blockIdx.x, ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const uint32_t r0a = (uint32_t)(ty * t.bh), r1a = (uint32_t)(tx * t.bw);
+    fir2d_stage(t, r0a, r1a, wh, ww, win);
+    // taps transposed: ht[k * 16 + j] = H[j, k]
+    const int T = t.T, m = t.m;
+    for (int e = threadIdx.x; e < T * 16; e += blockDim.x) {
+        const int k = e >> 4, j = e & 15;
+        ht[e] = j < m ? __ldg(t.taps + j * T + k) : 0.f;
+    }
+    ptx::cp_async_wait_all();
+    __syncthreads();
+#define AROL_FIR2D_CASE(M) \
+    case M: fir2d_compute<(M <= kMaxM ? M : kMaxM)>(t, win, ww, ht, r0a, r1a); break;
+    switch (m) {
+        AROL_FIR2D_CASE(1) AROL_FIR2D_CASE(2) AROL_FIR2D_CASE(3) AROL_FIR2D_CASE(4)
+        AROL_FIR2D_CASE(5) AROL_FIR2D_CASE(6) AROL_FIR2D_CASE(7) AROL_FIR2D_CASE(8)
+        AROL_FIR2D_CASE(9) AROL_FIR2D_CASE(10) AROL_FIR2D_CASE(11) AROL_FIR2D_CASE(12)
+        AROL_FIR2D_CASE(13) AROL_FIR2D_CASE(14) AROL_FIR2D_CASE(15)
+        default: fir2d_compute<kMaxM>(t, win, ww, ht, r0a, r1a); break;
+    }
+#undef AROL_FIR2D_CASE
+}
+
 // Shared memory of the batch kernel: a ring of three task records (the
 // TaskDev of the tile being computed, of the next tile, whose copies are in
 // flight, and of the one after, being copied), then two data slots, each the
@@ -713,6 +840,24 @@ int device_sm_count() {
         if (sms <= 0) sms = 1;
     }
     return sms;
+}
+
+cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
+    static bool attr = false;
+    const int ww = t.s1 * (t.bw - 1) + t.p1, wh = t.s0 * (t.bh - 1) + t.p0;
+    const size_t smem = (size_t)(((wh * ww + 3) & ~3) + t.T * 16) * sizeof(float);
+    if (!attr) {
+        const int most = (int)((kFir2dWin + 64 * 16) * sizeof(float));
+        cudaError_t e = cudaFuncSetAttribute(fir2d_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fir2d_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t tiles_x = (t.rep[3] + t.bw - 1) / t.bw, tiles_y = (t.rep[2] + t.bh - 1) / t.bh;
+    const unsigned grid = (unsigned)(tiles_x * tiles_y);   // < 2^31: checked on the host
+    if (t.m <= 4) fir2d_kernel<4><<<grid, kFir2dThreads, smem, s>>>(t, (int)tiles_x);
+    else fir2d_kernel<16><<<grid, kFir2dThreads, smem, s>>>(t, (int)tiles_x);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s) {

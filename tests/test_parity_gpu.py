@@ -428,3 +428,28 @@ def test_three_task_chain_forward_and_backward(arol):
     for dH, sH in zip(dHs, sHs):
         assert_fir_close(got[off:off + dH.size].reshape(dH.shape), dH, sH, what="3-task chain dH")
         off += dH.size
+
+
+@pytest.mark.parametrize("case", [
+    # (H, W, p0, p1, s0, s1, m, origin, out_origin)
+    (37, 53, 3, 3, 1, 1, 1, (-1, -1), (0, 0)),      # 3x3 stencil with wrap
+    (300, 700, 5, 7, 1, 1, 1, (-2, -3), (3, 5)),    # larger stencil, shifted output
+    (64, 96, 4, 4, 4, 4, 2, (0, 0), (0, 0)),        # non-overlapping 4x4 blocks, 2 outputs
+    (90, 200, 3, 8, 2, 3, 5, (7, -11), (1, 2)),     # strided, overlapping, 5 outputs
+    (9, 5, 6, 6, 1, 1, 3, (4, 1), (0, 0)),          # pattern wider than the array
+    (40, 4000, 2, 2, 1, 40, 16, (0, 0), (0, 0)),    # window too wide for a tile: per-repetition path
+])
+def test_fir_2d_pattern_tiles(arol, case):
+    """FIR on 2-D patterns (the 2-D window path, or the per-repetition path
+    when the window does not fit): every output element against the oracle."""
+    H, W_, p0, p1, s0, s1, m, origin, oo = case
+    g = W.rng(hash(case) % 1000)
+    R0, R1 = -(-H // s0), -(-W_ // s1)
+    taps = (g.standard_normal((m, p0 * p1)) / (p0 * p1)).astype(np.float32)
+    inp = W.port((H, W_), origin, ((s0, 0), (0, s1)), ((1, 0), (0, 1)), (p0, p1))
+    out = W.port((R0, m * R1), oo, ((1, 0), (0, m)), ((0,), (1,)), (m,))
+    tk = W.task((R0, R1), "fir", [inp], [out], taps)
+    x = g.standard_normal((H, W_)).astype(np.float32)
+    t, y = run1(arol, tk, [x])
+    ref = (C.run_task if H * W_ > 20000 else O.run_task)(tk, [x])[0]
+    assert_fir_close(y, ref, fir_scale(tk, x, C.run_chain if H * W_ > 20000 else O.run_chain), what=f"2-D FIR {case}")
