@@ -547,6 +547,22 @@ __device__ __forceinline__ void fir2d_stage(const TaskDev& t, uint32_t r0a, uint
     // element e = i * ww + j of the window, walked with an incremental (i, j)
     const int B = (int)blockDim.x, di = B / ww, dj = B - di * ww;
     int i = (int)threadIdx.x / ww, j = (int)threadIdx.x - i * ww;
+    if ((uint32_t)wh <= hin && (uint32_t)ww <= wi) {
+        // the window wraps at most once in each dimension
+        for (int e = threadIdx.x; e < wh * ww; e += B) {
+            uint32_t row = rb + (uint32_t)i, col = cb + (uint32_t)j;
+            row = row >= hin ? row - hin : row;
+            col = col >= wi ? col - wi : col;
+            ptx::cp_async4(win + e, x + (int64_t)row * wi + col);
+            i += di;
+            j += dj;
+            if (j >= ww) {
+                j -= ww;
+                ++i;
+            }
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < wh * ww; e += B) {
         uint32_t row = rb + (uint32_t)i, col = cb + (uint32_t)j;
         row -= fast_div(row, t.in.shape_div[0]) * hin;
@@ -593,6 +609,65 @@ __global__ void __launch_bounds__(kFir2dThreads, kMaxM <= 4 ? 4 : 2) fir2d_kerne
         default: fir2d_compute<kMaxM>(t, win, ww, ht, r0a, r1a); break;
     }
 #undef AROL_FIR2D_CASE
+}
+
+// Stencil specialisation (steps 1, one output, a P0 x P1 pattern): a CTA
+// takes 32 x 64 repetitions; thread (column c, strip g) computes the 8
+// consecutive output rows 8 g .. 8 g + 7 of column c.  It walks the window
+// down one row at a time, holding that row's P1 values and the taps in
+// registers, and adds the row into every output it belongs to, so each
+// window value is read from shared memory once per thread.
+constexpr int kStencilBh = 32, kStencilBw = 64, kStencilRows = 8;
+
+template <int P0, int P1>
+__global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev t, int tiles_x) {
+    constexpr int ww = kStencilBw + P1 - 1, wh = kStencilBh + P0 - 1;
+    __shared__ __align__(16) float win[wh * ww];
+    const int tile = blockIdx.x, ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const uint32_t r0a = (uint32_t)(ty * kStencilBh), r1a = (uint32_t)(tx * kStencilBw);
+    fir2d_stage(t, r0a, r1a, wh, ww, win);
+    float h[P0][P1];
+#pragma unroll
+    for (int a = 0; a < P0; ++a)
+#pragma unroll
+        for (int b = 0; b < P1; ++b) h[a][b] = __ldg(t.taps + a * P1 + b);
+    ptx::cp_async_wait_all();
+    __syncthreads();
+    const int c = (int)threadIdx.x % kStencilBw, g = (int)threadIdx.x / kStencilBw;
+    const uint32_t R0 = (uint32_t)t.rep[2], R1 = (uint32_t)t.rep[3];
+    const uint32_t r1 = r1a + (uint32_t)c;
+    if (r1 >= R1) return;
+    float acc[kStencilRows];
+#pragma unroll
+    for (int r = 0; r < kStencilRows; ++r) acc[r] = 0.f;
+    const float* w0 = win + (g * kStencilRows) * ww + c;
+#pragma unroll
+    for (int i = 0; i < kStencilRows + P0 - 1; ++i) {
+        float v[P1];
+#pragma unroll
+        for (int b = 0; b < P1; ++b) v[b] = w0[i * ww + b];
+        // window row i feeds output rows r = i - a for pattern rows a, in a order per output
+#pragma unroll
+        for (int a = 0; a < P0; ++a) {
+            const int r = i - a;
+            if (r >= 0 && r < kStencilRows) {
+#pragma unroll
+                for (int b = 0; b < P1; ++b) acc[r] = fmaf(h[a][b], v[b], acc[r]);
+            }
+        }
+    }
+    const uint32_t hout = (uint32_t)t.out.shape[0], wout = (uint32_t)t.out.shape[1];
+    float* y = static_cast<float*>(t.y);
+    const uint32_t vc = t.out.origin[1] + r1;                           // < 2^31: checked on the host
+    const uint32_t ocol = vc - fast_div(vc, t.out.shape_div[1]) * wout;
+#pragma unroll
+    for (int r = 0; r < kStencilRows; ++r) {
+        const uint32_t r0 = r0a + (uint32_t)(g * kStencilRows + r);
+        if (r0 >= R0) break;
+        const uint32_t vr = t.out.origin[0] + r0;
+        const uint32_t orow = vr - fast_div(vr, t.out.shape_div[0]) * hout;
+        y[(int64_t)orow * wout + ocol] = acc[r];
+    }
 }
 
 // Shared memory of the batch kernel: a ring of three task records (the
@@ -852,6 +927,13 @@ cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fir2d_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (e != cudaSuccess) return e;
         attr = true;
+    }
+    if (t.m == 1 && t.s0 == 1 && t.s1 == 1 && t.p0 == t.p1 && (t.p0 == 3 || t.p0 == 5)) {
+        const int64_t sx = (t.rep[3] + kStencilBw - 1) / kStencilBw, sy = (t.rep[2] + kStencilBh - 1) / kStencilBh;
+        const unsigned sgrid = (unsigned)(sx * sy);   // fewer tiles than the general tiling: < 2^31
+        if (t.p0 == 3) stencil_kernel<3, 3><<<sgrid, kFir2dThreads, 0, s>>>(t, (int)sx);
+        else stencil_kernel<5, 5><<<sgrid, kFir2dThreads, 0, s>>>(t, (int)sx);
+        return cudaGetLastError();
     }
     const int64_t tiles_x = (t.rep[3] + t.bw - 1) / t.bw, tiles_y = (t.rep[2] + t.bh - 1) / t.bh;
     const unsigned grid = (unsigned)(tiles_x * tiles_y);   // < 2^31: checked on the host
