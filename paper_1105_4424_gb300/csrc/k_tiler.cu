@@ -619,13 +619,47 @@ __global__ void __launch_bounds__(kFir2dThreads, kMaxM <= 4 ? 4 : 2) fir2d_kerne
 // window value is read from shared memory once per thread.
 constexpr int kStencilBh = 32, kStencilBw = 64, kStencilRows = 8;
 
+// Copies rows (rb + i) mod H, i < wh, columns c0 .. c0 + 4 nq - 1 (c0 a
+// multiple of 4, W a multiple of 4, so no 16-byte chunk straddles the wrap)
+// of x into win (row stride 4 nq) with 16-byte cp.async.
+__device__ __forceinline__ void stage_rows16(const float* x, uint32_t hin, uint32_t wi, uint32_t rb, uint32_t c0,
+                                             int wh, int nq, float* win) {
+    const int B = (int)blockDim.x, di = B / nq, dj = B - di * nq;
+    int i = (int)threadIdx.x / nq, j = (int)threadIdx.x - i * nq;
+    for (int e = threadIdx.x; e < wh * nq; e += B) {
+        uint32_t row = rb + (uint32_t)i, col = c0 + 4u * (uint32_t)j;
+        row = row >= hin ? row - hin : row;
+        col = col >= wi ? col - wi : col;
+        ptx::cp_async16(win + 4 * e, x + (int64_t)row * wi + col);
+        i += di;
+        j += dj;
+        if (j >= nq) {
+            j -= nq;
+            ++i;
+        }
+    }
+}
+
 template <int P0, int P1>
 __global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev t, int tiles_x) {
     constexpr int ww = kStencilBw + P1 - 1, wh = kStencilBh + P0 - 1;
-    __shared__ __align__(16) float win[wh * ww];
+    constexpr int nq = (ww + 3 + 3) / 4;   // 16-byte chunks per row when the start is rounded down to 4
+    __shared__ __align__(16) float win[wh * nq * 4];
     const int tile = blockIdx.x, ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const uint32_t r0a = (uint32_t)(ty * kStencilBh), r1a = (uint32_t)(tx * kStencilBw);
-    fir2d_stage(t, r0a, r1a, wh, ww, win);
+    const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
+    int rs = ww, delta = 0;   // staged row stride and the window's first column within it
+    if ((wi & 3u) == 0u && ((uintptr_t)t.x & 15u) == 0u && (uint32_t)wh <= hin && (uint32_t)(4 * nq) <= wi) {
+        const uint32_t vr = t.in.origin[0] + r0a;                        // < 2^31: checked on the host
+        const uint32_t rb = vr - fast_div(vr, t.in.shape_div[0]) * hin;
+        const uint32_t vc = t.in.origin[1] + r1a;
+        const uint32_t cb = vc - fast_div(vc, t.in.shape_div[1]) * wi;
+        delta = (int)(cb & 3u);
+        rs = 4 * nq;
+        stage_rows16(static_cast<const float*>(t.x), hin, wi, rb, cb - (uint32_t)delta, wh, nq, win);
+    } else {
+        fir2d_stage(t, r0a, r1a, wh, ww, win);
+    }
     float h[P0][P1];
 #pragma unroll
     for (int a = 0; a < P0; ++a)
@@ -640,12 +674,12 @@ __global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev
     float acc[kStencilRows];
 #pragma unroll
     for (int r = 0; r < kStencilRows; ++r) acc[r] = 0.f;
-    const float* w0 = win + (g * kStencilRows) * ww + c;
+    const float* w0 = win + (g * kStencilRows) * rs + delta + c;
 #pragma unroll
     for (int i = 0; i < kStencilRows + P0 - 1; ++i) {
         float v[P1];
 #pragma unroll
-        for (int b = 0; b < P1; ++b) v[b] = w0[i * ww + b];
+        for (int b = 0; b < P1; ++b) v[b] = w0[i * rs + b];
         // window row i feeds output rows r = i - a for pattern rows a, in a order per output
 #pragma unroll
         for (int a = 0; a < P0; ++a) {
@@ -660,13 +694,14 @@ __global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev
     float* y = static_cast<float*>(t.y);
     const uint32_t vc = t.out.origin[1] + r1;                           // < 2^31: checked on the host
     const uint32_t ocol = vc - fast_div(vc, t.out.shape_div[1]) * wout;
+    const uint32_t r00 = r0a + (uint32_t)(g * kStencilRows);
+    const uint32_t vr = t.out.origin[0] + r00;
+    uint32_t orow = vr - fast_div(vr, t.out.shape_div[0]) * hout;
 #pragma unroll
     for (int r = 0; r < kStencilRows; ++r) {
-        const uint32_t r0 = r0a + (uint32_t)(g * kStencilRows + r);
-        if (r0 >= R0) break;
-        const uint32_t vr = t.out.origin[0] + r0;
-        const uint32_t orow = vr - fast_div(vr, t.out.shape_div[0]) * hout;
+        if (r00 + (uint32_t)r >= R0) break;
         y[(int64_t)orow * wout + ocol] = acc[r];
+        orow = orow + 1u == hout ? 0u : orow + 1u;
     }
 }
 
