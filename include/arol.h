@@ -195,6 +195,15 @@ void arol_task_destroy(arol_task t);
 arol_status arol_tiler_cover(const arol_array_desc* array, const arol_tiler* tiler,
                              int rep_rank, const int64_t* rep, int64_t* count_min, int64_t* count_max);
 
+/* Self-test of failure detection (no counterpart in the paper).  Launches a
+ * kernel whose thread waits on an mbarrier that nothing completes, through
+ * the same bounded wait the pipelined kernels use: the wait gives up after
+ * its limit (about 2 s), sets an error word and the kernel returns.  Returns
+ * AROL_ERR_TIMEOUT when that happens (the expected result), AROL_OK if the
+ * wait completed.  No trap or fault is involved; the context stays usable.
+ * Synchronizes the stream. */
+arol_status arol_selftest_wait_timeout(void* stream);
+
 /* ---- batches of independent tasks ---------------------------------------- */
 
 /* Build a batch of n independent members (uneven shapes allowed).  A member

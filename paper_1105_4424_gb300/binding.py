@@ -67,6 +67,7 @@ def _load():
         "arol_task_info": [c_vp, P(TaskInfo)],
         "arol_task_sync_status": [c_vp, c_vp],
         "arol_tiler_cover": [P(ArrayDesc), P(Tiler), ctypes.c_int, P(c_i64), P(c_i64), P(c_i64)],
+        "arol_selftest_wait_timeout": [c_vp],
         "arol_batch_create": [P(c_vp), ctypes.c_int, P(c_vp)],
         "arol_batch_run": [c_vp, P(c_vp), P(c_vp), c_vp],
         "arol_batch_run_per_task": [c_vp, P(c_vp), P(c_vp), c_vp],
@@ -262,6 +263,10 @@ def arol_tiler_cover(shape, port, rep) -> tuple:
     lo, hi = c_i64(), c_i64()
     _check(lib.arol_tiler_cover(ctypes.byref(a), ctypes.byref(tl), len(rep), r, ctypes.byref(lo), ctypes.byref(hi)))
     return lo.value, hi.value
+
+
+def arol_selftest_wait_timeout(stream=None):
+    _check(lib.arol_selftest_wait_timeout(_stream(stream)))
 
 
 def arol_batch_create(tasks) -> int:

@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace arol;
 
 namespace arol {
@@ -51,6 +53,36 @@ arol_status cuda_fail(cudaError_t e, const char* what) {
         cudaError_t e_ = (call);                     \
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
+
+// An NVTX range named after the ABI call, for the duration of the call
+// (shown by Nsight tools; nearly free without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define AROL_TRACE() NvtxRange arol_nvtx_range_(__func__)
+
+// AROL_LOG=1: one line on stderr for each kernel-path decision (task and
+// chain creation, one-member batches, batch layout).
+bool log_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("AROL_LOG");
+        return v && v[0] && v[0] != '0';
+    }();
+    return on;
+}
+
+void log_line(const char* fmt, ...) {
+    if (!log_enabled()) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::fprintf(stderr, "arol: %s\n", buf);
+}
 
 int64_t emod(int64_t a, int64_t s) {
     int64_t r = a % s;
@@ -652,11 +684,23 @@ arol_status remember_device(arol_task t) {
     return AROL_OK;
 }
 
+// Device allocations go through here.  AROL_FAIL_ALLOC=1 makes every one
+// fail as if the device were out of memory (failure injection for tests;
+// nothing is allocated), so callers' error paths can be exercised on the host.
+cudaError_t arol_malloc(void** p, size_t bytes) {
+    const char* v = std::getenv("AROL_FAIL_ALLOC");
+    if (v && v[0] == '1') {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 arol_status dev_alloc(arol_task t, void** p, size_t bytes, const char* what) {
     arol_status st = remember_device(t);
     if (st != AROL_OK) return st;
     if (*p) return AROL_OK;
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    cudaError_t e = arol_malloc(p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
         *p = nullptr;
         return cuda_fail(e, what);
@@ -789,8 +833,25 @@ arol_status arol_last_error(char* buf, size_t len) {
     return AROL_OK;
 }
 
+arol_status arol_selftest_wait_timeout(void* stream) {
+    AROL_TRACE();
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* err = nullptr;
+    AROL_CUDA(arol_malloc((void**)&err, sizeof(unsigned)), "cudaMalloc(error word)");
+    unsigned host = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_wait_selftest(err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(err);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+    if (host) return fail(AROL_ERR_TIMEOUT, "wait self-test: the bounded wait gave up as designed");
+    return AROL_OK;
+}
+
 arol_status arol_tiler_cover(const arol_array_desc* array, const arol_tiler* tiler, int rep_rank, const int64_t* rep,
                              int64_t* count_min, int64_t* count_max) {
+    AROL_TRACE();
     if (!array || !tiler || !rep || !count_min || !count_max) return fail(AROL_ERR_INVALID, "null argument");
     if (rep_rank < 1 || rep_rank > AROL_MAX_RANK) return fail(AROL_ERR_INVALID, "rep_rank %d not in [1,4]", rep_rank);
     for (int q = 0; q < rep_rank; ++q)
@@ -809,6 +870,7 @@ arol_status arol_tiler_cover(const arol_array_desc* array, const arol_tiler* til
 }
 
 arol_status arol_task_create(const arol_task_desc* desc, arol_task* out) {
+    AROL_TRACE();
     if (!desc || !out) return fail(AROL_ERR_INVALID, "null argument");
     *out = nullptr;
     arol_status st = validate_desc(*desc);
@@ -831,11 +893,21 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out) {
         t->mm_K = K;
     }
     fill_info_single(t);
+    if (log_enabled()) {
+        const TaskDev td = make_taskdev(t->descs[0]);
+        const char* path = t->kernel == 2 ? (M % 256 == 0 && N % 256 == 0 ? "tcgen05 matmul, CTA pairs" : "tcgen05 matmul")
+                           : td.rowfir ? "row FIR (staged row tiles)"
+                           : td.colfir ? "column FIR (column tiles)"
+                           : td.fir2d ? "2-D window FIR"
+                                      : "per-repetition walk";
+        log_line("task %p: rank %d, %lld repetitions, %s", (void*)t, desc->in[0].rank, (long long)reps_of(*desc), path);
+    }
     *out = t;
     return AROL_OK;
 }
 
 arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
+    AROL_TRACE();
     if (!tasks || !out || n < 2) return fail(AROL_ERR_INVALID, "a chain needs at least 2 tasks");
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
@@ -893,6 +965,8 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     const arol_task_desc &first = t->descs.front(), &last = t->descs.back();
     in.unique_bytes = elems_of(first.in[0]) * esize_of(first.in[0].dtype) + elems_of(last.out[0]) * esize_of(last.out[0].dtype);
     t->mids.assign(n - 1, nullptr);
+    log_line("chain %p: %d tasks, %s", (void*)t, n,
+             t->kernel == 1 ? "fused separable downscaler" : "stage by stage through a one-member batch");
     *out = t;
     return AROL_OK;
 }
@@ -988,6 +1062,7 @@ arol_status run_internal_batch(arol_task t, const void* const* in, void* const* 
             arol_task self = t;
             if (arol_batch_create(&self, 1, &t->ib) != AROL_OK) t->ib = nullptr;
         }
+        log_line("task %p: %s", (void*)t, t->ib ? "runs as a one-member batch" : "runs its per-task kernel");
     }
     if (!t->ib) return AROL_OK;
     *used = true;
@@ -999,6 +1074,7 @@ arol_status run_internal_batch(arol_task t, const void* const* in, void* const* 
 extern "C" {
 
 arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, void* stream) {
+    AROL_TRACE();
     if (!t || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const arol_task_desc& d0 = t->descs[0];
@@ -1115,6 +1191,7 @@ arol_status run_host_pipelined(arol_task t, const void* hin, void* hout, cudaStr
 extern "C" {
 
 arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* const* host_out, void* stream) {
+    AROL_TRACE();
     if (!t || !host_in || !host_out) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const arol_task_desc& d0 = t->descs[0];
@@ -1238,6 +1315,7 @@ extern "C" {
 
 arol_status arol_task_backward(arol_task t, const void* grad_out, const void* const* saved_in, void* grad_in,
                                float* grad_taps, void* stream) {
+    AROL_TRACE();
     if (!t || !grad_out || !saved_in || !saved_in[0]) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     for (const arol_task_desc& d : t->descs) {
@@ -1301,6 +1379,7 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
 
 arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* grad_out, void* out, void* grad_in,
                               float* grad_taps, void* stream) {
+    AROL_TRACE();
     if (!t || !in || !in[0] || !grad_out || !out) return fail(AROL_ERR_INVALID, "null argument");
     if (!(t->kind == 1 && t->kernel == 1) || t->ds_in_bf16 || t->ds_mid_bf16 || t->ds_out_bf16)
         return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd is implemented for the float32 fused separable downscaler chain only");
@@ -1575,8 +1654,8 @@ arol_status build_tiles(arol_batch b) {
         free_dev(b->dev_tiles);
         free_dev(b->dev_tiles_pt);
         b->dev_tiles = b->dev_tiles_pt = nullptr;
-        AROL_CUDA(cudaMalloc(&b->dev_tiles, std::max<size_t>(tiles.size(), 1) * sizeof(TileDev)), "cudaMalloc(tiles)");
-        AROL_CUDA(cudaMalloc(&b->dev_tiles_pt, std::max<size_t>(tiles.size(), 1) * sizeof(TileDev)), "cudaMalloc(tiles)");
+        AROL_CUDA(arol_malloc((void**)&b->dev_tiles, std::max<size_t>(tiles.size(), 1) * sizeof(TileDev)), "cudaMalloc(tiles)");
+        AROL_CUDA(arol_malloc((void**)&b->dev_tiles_pt, std::max<size_t>(tiles.size(), 1) * sizeof(TileDev)), "cudaMalloc(tiles)");
         b->tiles_cap = (int64_t)tiles.size();
     }
     if (!tiles.empty()) {
@@ -1608,12 +1687,18 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
             ntaps += b->taps[i].size();
             if (b->host_tasks[i].rowfir || b->host_tasks[i].colfir) ntaps += (size_t)b->host_tasks[i].T * 16;
         }
-        AROL_CUDA(cudaMalloc(&b->dev_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMalloc(task table)");
-        AROL_CUDA(cudaMallocHost(&b->pinned_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMallocHost(task table)");
-        AROL_CUDA(cudaEventCreateWithFlags(&b->table_copied, cudaEventDisableTiming), "cudaEventCreate");
-        AROL_CUDA(cudaEventCreateWithFlags(&b->launched, cudaEventDisableTiming), "cudaEventCreate");
-        AROL_CUDA(cudaMalloc(&b->counter, sizeof(unsigned)), "cudaMalloc(counter)");
-        AROL_CUDA(cudaMalloc(&b->taps_dev, std::max<size_t>(ntaps, 1) * sizeof(float)), "cudaMalloc(taps)");
+        // each resource is made once: a call that failed part-way (say, out of
+        // memory) is retried without leaking what it had already made
+        if (!b->dev_tasks)
+            AROL_CUDA(arol_malloc((void**)&b->dev_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMalloc(task table)");
+        if (!b->pinned_tasks)
+            AROL_CUDA(cudaMallocHost(&b->pinned_tasks, std::max<size_t>(n, 1) * sizeof(TaskDev)), "cudaMallocHost(task table)");
+        if (!b->table_copied)
+            AROL_CUDA(cudaEventCreateWithFlags(&b->table_copied, cudaEventDisableTiming), "cudaEventCreate");
+        if (!b->launched) AROL_CUDA(cudaEventCreateWithFlags(&b->launched, cudaEventDisableTiming), "cudaEventCreate");
+        if (!b->counter) AROL_CUDA(arol_malloc((void**)&b->counter, sizeof(unsigned)), "cudaMalloc(counter)");
+        if (!b->taps_dev)
+            AROL_CUDA(arol_malloc((void**)&b->taps_dev, std::max<size_t>(ntaps, 1) * sizeof(float)), "cudaMalloc(taps)");
         size_t off = 0;
         for (size_t i = 0; i < n; ++i) {
             if (!b->taps[i].empty()) {
@@ -1644,8 +1729,8 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
             const arol_array_desc& o = b->descs[j].out[0];
             arena += ((size_t)elems_of(o) * esize_of(o.dtype) + 255) / 256 * 256;
         }
-        if (arena) AROL_CUDA(cudaMalloc(&b->arena, arena), "cudaMalloc(chain intermediates)");
-        AROL_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        if (arena && !b->arena) AROL_CUDA(arol_malloc((void**)&b->arena, arena), "cudaMalloc(chain intermediates)");
+        if (!b->cap_stream) AROL_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         arol_status st = build_tiles(b);
         if (st != AROL_OK) return st;
         b->tables_built = true;
@@ -1704,6 +1789,7 @@ arol_status batch_capture(arol_batch b) {
 extern "C" {
 
 arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out) {
+    AROL_TRACE();
     if (!tasks || !out || n < 1) return fail(AROL_ERR_INVALID, "a batch needs at least one task");
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
@@ -1734,11 +1820,21 @@ arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out) {
             if (d.elem == AROL_ELEM_FIR) b->max_m = std::max(b->max_m, d.fir_m);
         }
     }
+    if (log_enabled()) {
+        int rows = 0, cols = 0;
+        for (const TaskDev& td : b->host_tasks) {
+            rows += td.rowfir;
+            cols += td.colfir;
+        }
+        log_line("batch %p: %d members, %zu tasks in %d stage(s): %d row FIR, %d column FIR, %zu per-repetition",
+                 (void*)b, n, b->host_tasks.size(), b->nstages, rows, cols, b->host_tasks.size() - rows - cols);
+    }
     *out = b;
     return AROL_OK;
 }
 
 arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out, void* stream) {
+    AROL_TRACE();
     if (!b || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     arol_status st = batch_prepare(b, in, out, s);
@@ -1750,6 +1846,7 @@ arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out
 }
 
 arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* const* out, void* stream) {
+    AROL_TRACE();
     if (!b || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     arol_status st = batch_prepare(b, in, out, s);
@@ -1776,6 +1873,7 @@ arol_status arol_batch_config(arol_batch b, int64_t* tile_reps, int32_t* ctas_pe
 }
 
 arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* out, void* stream, int force) {
+    AROL_TRACE();
     if (!b || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     arol_status st = batch_prepare(b, in, out, s);

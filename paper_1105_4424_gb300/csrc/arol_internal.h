@@ -92,6 +92,7 @@ struct DownscaleDev {
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s);
 // CTA b takes tiles b, b + grid, ... (a static schedule; `counter` is unused).
 cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s);
+cudaError_t launch_wait_selftest(unsigned* err, cudaStream_t s);
 cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, int ntiles,
                                     unsigned* counter, int grid, int threads, int max_m,
                                     cudaStream_t s);

@@ -952,6 +952,25 @@ int device_sm_count() {
     return sms;
 }
 
+// Self-test of the bounded waits the pipelined kernels use: thread 0 waits
+// on an mbarrier that nothing ever completes; the wait gives up after its
+// limit and the kernel records it in *err and returns.
+__global__ void wait_selftest_kernel(unsigned* err) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t a = ptx::smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(a, 1);
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !ptx::mbar_wait(a, 0)) atomicOr(err, 1u);
+}
+
+cudaError_t launch_wait_selftest(unsigned* err, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
     static bool attr = false;
     const int ww = t.s1 * (t.bw - 1) + t.p1, wh = t.s0 * (t.bh - 1) + t.p0;
