@@ -282,6 +282,14 @@ typedef struct arol_cg_s* arol_cg;
 arol_status arol_csr_spmv(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                           const double* vals, const double* x, double* y, void* stream);
 
+/* Check a CSR matrix on the device: row_ptr[0] == 0, row_ptr[n_rows] == nnz,
+ * row_ptr non-decreasing, every col_idx in [0, n_rows).  Returns
+ * AROL_ERR_INVALID (with the failed rule in arol_cg_last_error) for a
+ * malformed matrix, AROL_ERR_UNSUPPORTED for n_rows >= 2^31.  Device
+ * pointers; synchronizes the stream.  arol_cg_create runs it; arol_csr_spmv
+ * does not (call it once per matrix). */
+arol_status arol_csr_check(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx, void* stream);
+
 /* Prepare conjugate gradient on A: allocates five float64 work vectors, the
  * reduction scratch and the device-side state, and captures a CUDA graph of
  * eight iterations.  The matrix buffers must stay alive and unchanged while

@@ -77,6 +77,7 @@ def _load():
         "arol_downscale_backward_noalloc": [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp],
         "arol_csr_spmv": [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
         "arol_cg_create": [c_i64, c_i64, c_vp, c_vp, c_vp, P(c_vp)],
+        "arol_csr_check": [c_i64, c_i64, c_vp, c_vp, c_vp],
         "arol_cg_solve": [c_vp, c_vp, c_vp, ctypes.c_double, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double), c_vp],
         "arol_cg_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     }
@@ -319,6 +320,10 @@ def _check_cg(st):
 def arol_csr_spmv(n_rows, nnz, row_ptr, col_idx, vals, x, y, stream=None):
     _check_cg(lib.arol_csr_spmv(int(n_rows), int(nnz), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(x), _ptr(y),
                                 _stream(stream)))
+
+
+def arol_csr_check(n_rows, nnz, row_ptr, col_idx, stream=None):
+    _check_cg(lib.arol_csr_check(int(n_rows), int(nnz), _ptr(row_ptr), _ptr(col_idx), _stream(stream)))
 
 
 def arol_cg_create(n_rows, nnz, row_ptr, col_idx, vals) -> int:

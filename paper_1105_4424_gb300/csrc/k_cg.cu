@@ -239,6 +239,21 @@ __global__ void __launch_bounds__(kCgThreads) cg_direction_kernel(int64_t n, con
     }
 }
 
+// CSR structure check: row_ptr[0] == 0, row_ptr[n] == nnz, row_ptr
+// non-decreasing, every column index in [0, n).  Bits of *bad: 1 ends, 2
+// order, 4 column range.
+__global__ void __launch_bounds__(kCgThreads) csr_check_kernel(const Csr A, int64_t nnz, unsigned* bad) {
+    const int64_t stride = (int64_t)gridDim.x * kCgThreads;
+    const int64_t t0 = (int64_t)blockIdx.x * kCgThreads + threadIdx.x;
+    if (t0 == 0 && (__ldg(A.row_ptr) != 0 || __ldg(A.row_ptr + A.n) != nnz)) atomicOr(bad, 1u);
+    for (int64_t i = t0; i < A.n; i += stride)
+        if (__ldg(A.row_ptr + i + 1) < __ldg(A.row_ptr + i)) atomicOr(bad, 2u);
+    for (int64_t k = t0; k < nnz; k += stride) {
+        const int32_t c = __ldg(A.col + k);
+        if (c < 0 || (int64_t)c >= A.n) atomicOr(bad, 4u);
+    }
+}
+
 // Lanes per row: AROL_SPMV_LPR (1, 2, 4 or 8) when set, else about 8 to 16
 // products per lane from the mean row length (on the 27-point system, mean 26,
 // two lanes per row beat one, four and eight).  Fixed per matrix, so results
@@ -328,12 +343,44 @@ arol_status arol_csr_spmv(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, c
     return AROL_OK;
 }
 
+arol_status arol_csr_check(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx, void* stream) {
+    if (n_rows < 0 || nnz < 0) return cg_fail(AROL_ERR_INVALID, "negative size");
+    if (!row_ptr || (nnz > 0 && !col_idx)) return cg_fail(AROL_ERR_INVALID, "null pointer");
+    if (n_rows >= 2147483647LL) return cg_fail(AROL_ERR_UNSUPPORTED, "column indices are 32-bit: n_rows < 2^31");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* bad = nullptr;
+    CG_CUDA(cudaMalloc(&bad, sizeof(unsigned)), "cudaMalloc(check word)");
+    unsigned host = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        const int64_t work = n_rows > nnz ? n_rows : nnz;
+        int64_t grid = (work + kCgThreads - 1) / kCgThreads;
+        const int64_t cap = (int64_t)device_sm_count() * 8;
+        grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
+        csr_check_kernel<<<(int)grid, kCgThreads, 0, s>>>(Csr{row_ptr, col_idx, nullptr, n_rows}, nnz, bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(bad);
+    if (e != cudaSuccess) return cg_fail(AROL_ERR_CUDA, std::string("csr check: ") + cudaGetErrorString(e));
+    if (host & 1u) return cg_fail(AROL_ERR_INVALID, "csr: row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+    if (host & 2u) return cg_fail(AROL_ERR_INVALID, "csr: row_ptr must not decrease");
+    if (host & 4u) return cg_fail(AROL_ERR_INVALID, "csr: a column index is outside [0, n)");
+    return AROL_OK;
+}
+
 arol_status arol_cg_create(int64_t n_rows, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                            const double* vals, arol_cg* out) {
     if (!out) return cg_fail(AROL_ERR_INVALID, "null handle pointer");
     *out = nullptr;
     if (n_rows < 1 || nnz < 0 || !row_ptr || (nnz > 0 && (!col_idx || !vals)))
         return cg_fail(AROL_ERR_INVALID, "bad matrix");
+    // the products index x by col_idx: a malformed matrix is refused here
+    {
+        const arol_status cs = arol_csr_check(n_rows, nnz, row_ptr, col_idx, nullptr);
+        if (cs != AROL_OK) return cs;
+    }
     arol_cg h = new (std::nothrow) arol_cg_s();
     if (!h) return cg_fail(AROL_ERR_INVALID, "out of host memory");
     h->A = Csr{row_ptr, col_idx, vals, n_rows};

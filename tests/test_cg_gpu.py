@@ -88,3 +88,21 @@ def test_cg_small_grid_matches_direct_solve_and_respects_limits(arol):
     x0 = torch.from_numpy(np.linalg.solve(A, b)).cuda()               # already solved: no iteration
     x, iters, rel = solver.solve(bd, x0.clone(), tol=1e-8, max_iter=50)
     assert iters == 0
+
+
+def test_malformed_csr_is_refused(arol):
+    """A column index outside [0, n), a decreasing row_ptr or a wrong end
+    value is refused before any product runs (AROL_ERR_INVALID)."""
+    row_ptr, col, vals, b = W.stencil27_csr(5, seed=1)
+    good = _dev(row_ptr, col, vals)
+    arol.arol_csr_check(len(row_ptr) - 1, len(vals), good[0], good[1])
+    bad_col = col.copy()
+    bad_col[17] = len(row_ptr) - 1                      # == n: out of range
+    bad_rp = row_ptr.copy()
+    bad_rp[10], bad_rp[11] = bad_rp[11], bad_rp[10]      # decreasing
+    bad_end = row_ptr.copy()
+    bad_end[-1] -= 1                                     # row_ptr[n] != nnz
+    for rp, c in ((row_ptr, bad_col), (bad_rp, col), (bad_end, col)):
+        with pytest.raises(arol.ArolError) as e:
+            arol.ConjugateGradient(*_dev(rp, c, vals))
+        assert e.value.status == 1
