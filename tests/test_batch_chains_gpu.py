@@ -249,3 +249,21 @@ def test_task_handle_on_two_streams(arol):
     torch.cuda.synchronize()
     for x, y in zip(xs, ys):
         assert_fir_close(host(y), C.run_task(tk, [x])[0], fir_scale(tk, x, C.run_chain), what="two streams")
+
+
+def test_batched_chains_full_size(arol):
+    """The bench's 128 two-stage chains of uneven frames, in the bench's
+    launch configuration (one graph, default tiles): every eighth member
+    against the C oracle's chain, all members against one fused launch each."""
+    chains, xs = W.chain_batch()
+    b = arol.Batch(chains)
+    ins = [dev(x) for x in xs]
+    outs = b.empty_outputs()
+    b.run(ins, outs)
+    torch.cuda.synchronize()
+    for i, (chain, x, y) in enumerate(zip(chains, xs, outs)):
+        y = host(y)
+        if i % 8 == 0:
+            assert_fir_close(y, C.run_chain(chain, [x])[0], fir_scale(chain, x, C.run_chain), what=f"chain {i}")
+        yf = host(arol.Chain(chain).run([ins[i]]))
+        np.testing.assert_allclose(y, yf, rtol=1e-5, atol=1e-6)

@@ -457,3 +457,24 @@ def test_fir_2d_pattern_tiles(arol, case):
     t, y = run1(arol, tk, [x])
     ref = (C.run_task if H * W_ > 20000 else O.run_task)(tk, [x])[0]
     assert_fir_close(y, ref, fir_scale(tk, x, C.run_chain if H * W_ > 20000 else O.run_chain), what=f"2-D FIR {case}")
+
+
+def test_stencil_8192_full_size(arol):
+    """The bench's 3x3 stencil on 8192x8192 with wrap, every element against
+    the numpy.roll closed form (sum over a, b of H[a, b] x[i + a - 1, j + b - 1])."""
+    n = 8192
+    g = W.rng(5)
+    x = g.random((n, n), dtype=np.float32)
+    H = (g.standard_normal((1, 9)) / 9).astype(np.float32)
+    inp = W.port((n, n), (-1, -1), ((1, 0), (0, 1)), ((1, 0), (0, 1)), (3, 3))
+    out = W.port((n, n), (0, 0), ((1, 0), (0, 1)), ((0,), (0,)), (1,))
+    _, y = run1(arol, W.task((n, n), "fir", [inp], [out], H), [x])
+    x64 = x.astype(np.float64)
+    ref = np.zeros((n, n))
+    scale = np.zeros((n, n))
+    for a in range(3):
+        for b in range(3):
+            sh = np.roll(x64, (1 - a, 1 - b), axis=(0, 1))
+            ref += float(H[0, 3 * a + b]) * sh
+            scale += abs(float(H[0, 3 * a + b])) * np.abs(sh)
+    assert_fir_close(y, ref, scale, what="8192^2 stencil")
