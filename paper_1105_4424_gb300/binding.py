@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libarol.so")
+# AROL_LIB selects another build of the library (e.g. libarol_debug.so)
+LIB_PATH = os.environ.get("AROL_LIB") or os.path.join(_PKG, "libarol.so")
 
 c_i32, c_i64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
 

@@ -78,5 +78,42 @@ def build(force: bool = False, extra_flags=None, verbose: bool = False) -> str:
     return LIB
 
 
+DEBUG_LIB = os.path.join(PKG, "libarol_debug.so")
+DEBUG_SOURCES = ("k_tiler.cu",)   # the units whose AROL_DEBUG checks differ
+
+
+def build_debug(verbose: bool = False) -> str:
+    """libarol_debug.so: the release objects, except that the units in
+    DEBUG_SOURCES are compiled with -DAROL_DEBUG (device-side bounds checks
+    on every index of the per-repetition walk, reported as AROL_ERR_OOB).
+    Load it with AROL_LIB=<path> before importing the package."""
+    build()
+    dbgdir = os.path.join(OBJDIR, "debug")
+    os.makedirs(dbgdir, exist_ok=True)
+    objs = []
+    for src in _sources():
+        name = os.path.basename(src)
+        if name in DEBUG_SOURCES:
+            obj = os.path.join(dbgdir, name + ".o")
+            if _stale(obj, [src] + _headers()):
+                cmd = [NVCC] + ARCH + FLAGS + ["-DAROL_DEBUG", "-c", src, "-o", obj]
+                r = subprocess.run(cmd, capture_output=True, text=True)
+                if r.returncode != 0:
+                    raise RuntimeError(f"nvcc failed on {name}:\n{r.stdout}\n{r.stderr}")
+            objs.append(obj)
+        else:
+            objs.append(os.path.join(OBJDIR, name + ".o"))
+    if _stale(DEBUG_LIB, objs):
+        tmp = DEBUG_LIB + f".tmp{os.getpid()}"
+        cmd = [NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, DEBUG_LIB)
+    if verbose:
+        print(f"built {DEBUG_LIB}")
+    return DEBUG_LIB
+
+
 if __name__ == "__main__":
     build(verbose=True)

@@ -474,6 +474,8 @@ TaskDev make_taskdev_exact(const arol_task_desc& d) {
         }
     }
     t.nreps = reps_of(d);
+    t.in_elems = elems_of(d.in[0]);
+    t.out_elems = elems_of(d.out[0]);
     for (int q = 0; q < 4; ++q) t.rep_div[q] = make_fastdiv((uint32_t)t.rep[q]);
     make_port(d.in[0], dd.in_tiler[0], 4, t.in);
     make_port(d.out[0], dd.out_tiler[0], 4, t.out);
@@ -1000,11 +1002,13 @@ arol_status arol_task_info(arol_task t, arol_task_info_t* info) {
 
 namespace {
 
-arol_status run_generic(const arol_task_desc& d, const float* taps, const void* x, void* y, cudaStream_t s) {
+arol_status run_generic(const arol_task_desc& d, const float* taps, const void* x, void* y, cudaStream_t s,
+                        unsigned* err = nullptr) {
     TaskDev td = make_taskdev(d);
     td.taps = taps;
     td.x = x;
     td.y = y;
+    td.err = err;
     if (td.fir2d) {
         AROL_CUDA(launch_fir2d(td, s), "2-D FIR kernel launch");
         return AROL_OK;
@@ -1097,7 +1101,8 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
         bool used = false;
         st = run_internal_batch(t, in, out, s, &used);
         if (used) return st;
-        return run_generic(d0, taps, in[0], out[0], s);
+        if ((st = ensure_err(t, s)) != AROL_OK) return st;
+        return run_generic(d0, taps, in[0], out[0], s, t->err_flag);
     }
     if (t->kernel == 1 && aligned16(in[0])) {
         if ((st = ensure_err(t, s)) != AROL_OK) return st;
@@ -1122,7 +1127,8 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
         }
         if (reps_of(t->descs[i]) > 0) {
             const float* tp = taps ? taps + t->tap_off[i] : nullptr;
-            if ((st = run_generic(t->descs[i], tp, cur, dst, s)) != AROL_OK) return st;
+            if ((st = ensure_err(t, s)) != AROL_OK) return st;
+            if ((st = run_generic(t->descs[i], tp, cur, dst, s, t->err_flag)) != AROL_OK) return st;
         }
         cur = dst;
     }
@@ -1412,6 +1418,9 @@ arol_status arol_task_sync_status(arol_task t, void* stream) {
         AROL_CUDA(cudaMemcpy(&flag, t->err_flag, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
         if (flag) {
             cudaMemset(t->err_flag, 0, sizeof(unsigned));
+            if (flag & 0x300u)
+                return fail(AROL_ERR_OOB, "a device-side index was out of range (%s; flags 0x%x)",
+                            (flag & 0x100u) ? "input" : "output", flag);
             return fail(AROL_ERR_TIMEOUT, "a bounded device-side wait gave up (flags 0x%x)", flag);
         }
     }

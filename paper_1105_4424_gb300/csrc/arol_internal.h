@@ -60,6 +60,8 @@ struct TaskDev {
     const float* taps_t;    // row- and column-FIR tasks in a batch: taps transposed, T x 16, zero padded
     const void* x;
     void* y;
+    int64_t in_elems, out_elems;   // array sizes, for the bounds checks of AROL_DEBUG builds
+    unsigned* err;                 // AROL_DEBUG builds: bit 0x100 (input) / 0x200 (output) on an out-of-range index
 };
 
 // One unit of work of a batch: repetitions [start, start + count) of a task.

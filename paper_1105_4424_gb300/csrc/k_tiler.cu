@@ -126,6 +126,27 @@ struct RowWalk {
     __device__ __forceinline__ void next() { c = (c + 1u == extent) ? 0u : c + 1u; }
 };
 
+// AROL_DEBUG builds check every index the per-repetition walk computes
+// against its array before the access; an index out of range is skipped and
+// recorded in *t.err, bit 0x100 (input) or 0x200 (output), which
+// arol_task_sync_status reports as AROL_ERR_OOB.
+// Release builds compile the checks away.
+#ifdef AROL_DEBUG
+__device__ __forceinline__ bool in_ok(const TaskDev& t, int64_t off) {
+    if ((uint64_t)off < (uint64_t)t.in_elems) return true;
+    if (t.err) atomicOr(t.err, 0x100u);
+    return false;
+}
+__device__ __forceinline__ bool out_ok(const TaskDev& t, int64_t off) {
+    if ((uint64_t)off < (uint64_t)t.out_elems) return true;
+    if (t.err) atomicOr(t.err, 0x200u);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_ok(const TaskDev&, int64_t) { return true; }
+__device__ __forceinline__ constexpr bool out_ok(const TaskDev&, int64_t) { return true; }
+#endif
+
 template <int MAXM>
 __device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_t bi[4], const uint32_t bo[4]) {
     RowWalk wi, wo;
@@ -137,7 +158,7 @@ __device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_
             const uint32_t* x = static_cast<const uint32_t*>(t.x);
             uint32_t* y = static_cast<uint32_t*>(t.y);
             for (int k = 0; k < n; ++k) {
-                y[wo.off()] = __ldg(x + wi.off());
+                if (in_ok(t, wi.off()) && out_ok(t, wo.off())) y[wo.off()] = __ldg(x + wi.off());
                 wi.next();
                 wo.next();
             }
@@ -145,7 +166,7 @@ __device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_
             const uint16_t* x = static_cast<const uint16_t*>(t.x);
             uint16_t* y = static_cast<uint16_t*>(t.y);
             for (int k = 0; k < n; ++k) {
-                y[wo.off()] = __ldg(x + wi.off());
+                if (in_ok(t, wi.off()) && out_ok(t, wo.off())) y[wo.off()] = __ldg(x + wi.off());
                 wi.next();
                 wo.next();
             }
@@ -157,7 +178,7 @@ __device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) acc[j] = 0.f;
     for (int k = 0; k < n; ++k) {
-        const float p = load_value(t, wi.off());
+        const float p = in_ok(t, wi.off()) ? load_value(t, wi.off()) : 0.f;
         wi.next();
         const float* h = t.taps + k;
 #pragma unroll
@@ -167,7 +188,7 @@ __device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
         if (j < m) {
-            store_value(t, wo.off(), acc[j]);
+            if (out_ok(t, wo.off())) store_value(t, wo.off(), acc[j]);
             wo.next();
         }
     }
@@ -193,7 +214,8 @@ __device__ __forceinline__ void process_rep(const TaskDev& t, int64_t lr) {
             const uint32_t* x = static_cast<const uint32_t*>(t.x);
             uint32_t* y = static_cast<uint32_t*>(t.y);
             for (int k = 0; k < n; ++k) {
-                y[offset_of(t.out, wo.cur)] = __ldg(x + offset_of(t.in, wi.cur));
+                const int64_t oi = offset_of(t.in, wi.cur), oo = offset_of(t.out, wo.cur);
+                if (in_ok(t, oi) && out_ok(t, oo)) y[oo] = __ldg(x + oi);
                 wi.next(t.in);
                 wo.next(t.out);
             }
@@ -201,7 +223,8 @@ __device__ __forceinline__ void process_rep(const TaskDev& t, int64_t lr) {
             const uint16_t* x = static_cast<const uint16_t*>(t.x);
             uint16_t* y = static_cast<uint16_t*>(t.y);
             for (int k = 0; k < n; ++k) {
-                y[offset_of(t.out, wo.cur)] = __ldg(x + offset_of(t.in, wi.cur));
+                const int64_t oi = offset_of(t.in, wi.cur), oo = offset_of(t.out, wo.cur);
+                if (in_ok(t, oi) && out_ok(t, oo)) y[oo] = __ldg(x + oi);
                 wi.next(t.in);
                 wo.next(t.out);
             }
@@ -214,7 +237,8 @@ __device__ __forceinline__ void process_rep(const TaskDev& t, int64_t lr) {
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) acc[j] = 0.f;
     for (int k = 0; k < n; ++k) {
-        const float p = load_value(t, offset_of(t.in, wi.cur));
+        const int64_t oi = offset_of(t.in, wi.cur);
+        const float p = in_ok(t, oi) ? load_value(t, oi) : 0.f;
         wi.next(t.in);
         const float* h = t.taps + k;
 #pragma unroll
@@ -224,7 +248,8 @@ __device__ __forceinline__ void process_rep(const TaskDev& t, int64_t lr) {
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
         if (j < m) {
-            store_value(t, offset_of(t.out, wo.cur), acc[j]);
+            const int64_t oo = offset_of(t.out, wo.cur);
+            if (out_ok(t, oo)) store_value(t, oo, acc[j]);
             wo.next(t.out);
         }
     }
