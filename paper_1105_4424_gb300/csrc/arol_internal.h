@@ -99,7 +99,7 @@ cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, 
                                     unsigned* counter, int grid, int threads, int max_m,
                                     cudaStream_t s);
 constexpr int kBatchThreads = 128;                  // threads of the batch kernel (its launch bound)
-constexpr int kRowTile = 1024;                      // at most this many repetitions per row tile
+constexpr int kRowTile = 2048;                      // at most this many repetitions per row tile
 // Staged input window of a row tile.  A tile that is a piece of one row holds
 // at most min(kRowTile, (kWinFloats - T) / step + 1) repetitions, so its
 // window (step * (count - 1) + T words) always fits.

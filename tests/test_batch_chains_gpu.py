@@ -90,8 +90,8 @@ def test_batch_rejects_matmul_members(arol):
 
 def _row_cases():
     """Row-FIR tasks that reach every exact-m template and both tile layouts
-    at their capacity edges (4096-float windows; whole rows up to 2048
-    words), with origins that wrap."""
+    at their capacity edges (4096-float windows, 2048 repetitions; whole
+    rows up to 2048 words), with origins that wrap."""
     g = W.rng(122)
     cases = []
     for m in range(1, 17):                          # every output count, T up to 32
@@ -103,6 +103,12 @@ def _row_cases():
         cases.append((2, w, 32, 3, 32))
     for w in (2047, 2048, 2049):                    # whole rows: two per tile, then one
         cases.append((5, w, 9, 2, 5))
+    # step 1: pieces capped at 2048 repetitions; whole rows capped at 2048
+    # repetitions per tile (two rows of 1024, then one row of 1025)
+    for w in (2048, 2049, 4100):
+        cases.append((3, w, 4, 1, 1))
+    for w in (1024, 1025):
+        cases.append((5, w, 4, 1, 1))
     cases.append((3, 2, 7, 1, 1))                   # a row shorter than its pattern
     tasks, xs = [], []
     for (h, w, T, m, S) in cases:
