@@ -283,11 +283,12 @@ __device__ __forceinline__ int padw(int w) { return w + (w >> 5); }
 //    holds the rows themselves, W words each (a contiguous copy), and
 //    repetition (k, r1) walks columns (o1 + step*r1 + kk) mod W with one
 //    compare per step.
-// Each thread computes two repetitions, i and i + blockDim.x, so every tap
-// fetch feeds both; the exact output count M is a template parameter (taps
-// are read from the transposed block as float4 / float2 / float pieces, no
-// padded FMAs), and a repetition's M outputs go to consecutive columns with
-// one wrap test each.
+// Each thread computes two repetitions, i and i + blockDim.x (in a tile's
+// last chunk of fewer than 2 blockDim.x repetitions, i and i + half of the
+// chunk), so every tap fetch feeds both; the exact output count M is a
+// template parameter (taps are read from the transposed block as float4 /
+// float2 / float pieces, no padded FMAs), and a repetition's M outputs go to
+// consecutive columns with one wrap test each.
 template <int M>
 __device__ __forceinline__ void load_taps(const float* hrow, float (&h)[M]) {
 #pragma unroll
@@ -332,8 +333,14 @@ __device__ __forceinline__ void row_fir_compute(const TaskDev& t, const float* w
     const uint32_t R1 = (uint32_t)t.rep[3];
     const uint32_t wi = (uint32_t)t.in.shape[1];
     const int B = blockDim.x;
-    for (int i0 = threadIdx.x; i0 < count; i0 += 2 * B) {
-        const int i1 = i0 + B < count ? i0 + B : i0;   // a missing second repetition recomputes the first
+    for (int base = 0; base < count; base += 2 * B) {
+        // a chunk of 2B repetitions: thread t takes base + t and base + t + B;
+        // the last, shorter chunk pairs t with t + ceil(rem / 2) instead, so
+        // only an odd remainder recomputes one repetition
+        const int rem = count - base, half = rem >= 2 * B ? B : (rem + 1) >> 1;
+        if ((int)threadIdx.x >= half) break;
+        const int i0 = base + (int)threadIdx.x;
+        const int i1 = i0 + half < count ? i0 + half : i0;
         float acc0[M], acc1[M];
 #pragma unroll
         for (int j = 0; j < M; ++j) acc0[j] = acc1[j] = 0.f;
@@ -433,8 +440,12 @@ __device__ __forceinline__ void col_fir_compute(const TaskDev& t, const float* h
     const float* x = static_cast<const float*>(t.x);
     float* y = static_cast<float*>(t.y);
     const int B = blockDim.x;
-    for (int i0 = threadIdx.x; i0 < count; i0 += 2 * B) {
-        const int i1 = i0 + B < count ? i0 + B : i0;
+    for (int base = 0; base < count; base += 2 * B) {
+        // repetition pairs as in the row FIR: (t, t + B), the last chunk (t, t + ceil(rem / 2))
+        const int rem = count - base, half = rem >= 2 * B ? B : (rem + 1) >> 1;
+        if ((int)threadIdx.x >= half) break;
+        const int i0 = base + (int)threadIdx.x;
+        const int i1 = i0 + half < count ? i0 + half : i0;
         uint32_t r0[2], col[2], row[2];
         const uint32_t lr[2] = {(uint32_t)(start + i0), (uint32_t)(start + i1)};   // < 2^31: not wide
 #pragma unroll
