@@ -647,13 +647,13 @@ __global__ void __launch_bounds__(kFir2dThreads, kMaxM <= 4 ? 4 : 2) fir2d_kerne
 #undef AROL_FIR2D_CASE
 }
 
-// Stencil specialisation (steps 1, one output, a P0 x P1 pattern): a CTA
-// takes 32 x 64 repetitions; thread (column c, strip g) computes the 8
-// consecutive output rows 8 g .. 8 g + 7 of column c.  It walks the window
+// Stencil specialisation (steps 1, one output, a P0 x P1 pattern): a tile
+// is 32 x 128 repetitions; thread (column c, strip g) computes the 16
+// consecutive output rows 16 g .. 16 g + 15 of column c.  It walks the window
 // down one row at a time, holding that row's P1 values and the taps in
 // registers, and adds the row into every output it belongs to, so each
 // window value is read from shared memory once per thread.
-constexpr int kStencilBh = 32, kStencilBw = 64, kStencilRows = 8;
+constexpr int kStencilBh = 32, kStencilBw = 128, kStencilRows = 16;
 
 // Copies rows (rb + i) mod H, i < wh, columns c0 .. c0 + 4 nq - 1 (c0 a
 // multiple of 4, W a multiple of 4, so no 16-byte chunk straddles the wrap)
@@ -676,36 +676,36 @@ __device__ __forceinline__ void stage_rows16(const float* x, uint32_t hin, uint3
     }
 }
 
+// Stages the window of stencil tile (ty, tx) (repetitions r0 in
+// [kStencilBh ty, +kStencilBh), r1 in [kStencilBw tx, +kStencilBw)) into win
+// and returns the window's first column within a staged row.  fast: 16-byte
+// copies of 4-aligned row pieces (row stride 4 nq); otherwise element copies
+// (row stride ww).
 template <int P0, int P1>
-__global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev t, int tiles_x) {
+__device__ __forceinline__ int stencil_stage(const TaskDev& t, bool fast, uint32_t ty, uint32_t tx, float* win) {
     constexpr int ww = kStencilBw + P1 - 1, wh = kStencilBh + P0 - 1;
-    constexpr int nq = (ww + 3 + 3) / 4;   // 16-byte chunks per row when the start is rounded down to 4
-    __shared__ __align__(16) float win[wh * nq * 4];
-    const int tile = blockIdx.x, ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const uint32_t r0a = (uint32_t)(ty * kStencilBh), r1a = (uint32_t)(tx * kStencilBw);
-    const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
-    int rs = ww, delta = 0;   // staged row stride and the window's first column within it
-    if ((wi & 3u) == 0u && ((uintptr_t)t.x & 15u) == 0u && (uint32_t)wh <= hin && (uint32_t)(4 * nq) <= wi) {
-        const uint32_t vr = t.in.origin[0] + r0a;                        // < 2^31: checked on the host
-        const uint32_t rb = vr - fast_div(vr, t.in.shape_div[0]) * hin;
-        const uint32_t vc = t.in.origin[1] + r1a;
-        const uint32_t cb = vc - fast_div(vc, t.in.shape_div[1]) * wi;
-        delta = (int)(cb & 3u);
-        rs = 4 * nq;
-        stage_rows16(static_cast<const float*>(t.x), hin, wi, rb, cb - (uint32_t)delta, wh, nq, win);
-    } else {
+    constexpr int nq = (ww + 3 + 3) / 4;
+    const uint32_t r0a = ty * (uint32_t)kStencilBh, r1a = tx * (uint32_t)kStencilBw;
+    if (!fast) {
         fir2d_stage(t, r0a, r1a, wh, ww, win);
+        return 0;
     }
-    float h[P0][P1];
-#pragma unroll
-    for (int a = 0; a < P0; ++a)
-#pragma unroll
-        for (int b = 0; b < P1; ++b) h[a][b] = __ldg(t.taps + a * P1 + b);
-    ptx::cp_async_wait_all();
-    __syncthreads();
+    const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
+    const uint32_t vr = t.in.origin[0] + r0a;                        // < 2^31: checked on the host
+    const uint32_t rb = vr - fast_div(vr, t.in.shape_div[0]) * hin;
+    const uint32_t vc = t.in.origin[1] + r1a;
+    const uint32_t cb = vc - fast_div(vc, t.in.shape_div[1]) * wi;
+    stage_rows16(static_cast<const float*>(t.x), hin, wi, rb, cb & ~3u, wh, nq, win);
+    return (int)(cb & 3u);
+}
+
+// Computes and stores stencil tile (ty, tx) from its staged window.
+template <int P0, int P1>
+__device__ __forceinline__ void stencil_tile(const TaskDev& t, const float* win, int rs, int delta, uint32_t ty,
+                                             uint32_t tx, const float (&h)[P0][P1]) {
     const int c = (int)threadIdx.x % kStencilBw, g = (int)threadIdx.x / kStencilBw;
     const uint32_t R0 = (uint32_t)t.rep[2], R1 = (uint32_t)t.rep[3];
-    const uint32_t r1 = r1a + (uint32_t)c;
+    const uint32_t r1 = tx * (uint32_t)kStencilBw + (uint32_t)c;
     if (r1 >= R1) return;
     float acc[kStencilRows];
 #pragma unroll
@@ -715,7 +715,8 @@ __global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev
     for (int i = 0; i < kStencilRows + P0 - 1; ++i) {
         float v[P1];
 #pragma unroll
-        for (int b = 0; b < P1; ++b) v[b] = w0[i * rs + b];
+        for (int b = 0; b < P1; ++b) v[b] = w0[b];
+        w0 += rs;
         // window row i feeds output rows r = i - a for pattern rows a, in a order per output
 #pragma unroll
         for (int a = 0; a < P0; ++a) {
@@ -727,17 +728,71 @@ __global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev
         }
     }
     const uint32_t hout = (uint32_t)t.out.shape[0], wout = (uint32_t)t.out.shape[1];
-    float* y = static_cast<float*>(t.y);
     const uint32_t vc = t.out.origin[1] + r1;                           // < 2^31: checked on the host
     const uint32_t ocol = vc - fast_div(vc, t.out.shape_div[1]) * wout;
-    const uint32_t r00 = r0a + (uint32_t)(g * kStencilRows);
+    const uint32_t r00 = ty * (uint32_t)kStencilBh + (uint32_t)(g * kStencilRows);
     const uint32_t vr = t.out.origin[0] + r00;
     uint32_t orow = vr - fast_div(vr, t.out.shape_div[0]) * hout;
+    float* yp = static_cast<float*>(t.y) + (int64_t)orow * wout + ocol;
+    if (orow + (uint32_t)kStencilRows <= hout && r00 + (uint32_t)kStencilRows <= R0) {
+        // the strip neither wraps nor runs past the last repetition row
+#pragma unroll
+        for (int r = 0; r < kStencilRows; ++r) {
+            *yp = acc[r];
+            yp += wout;
+        }
+        return;
+    }
+    float* y = static_cast<float*>(t.y);
 #pragma unroll
     for (int r = 0; r < kStencilRows; ++r) {
         if (r00 + (uint32_t)r >= R0) break;
         y[(int64_t)orow * wout + ocol] = acc[r];
         orow = orow + 1u == hout ? 0u : orow + 1u;
+    }
+}
+
+// Persistent over tiles (static schedule: CTA b takes tiles b, b + grid, ...,
+// grid <= ntiles; tile = ty * tiles_x + tx), with two window buffers: the
+// copies of a CTA's next tile are in flight while it computes the current
+// one.
+template <int P0, int P1>
+__global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev t, uint32_t tiles_x, uint32_t ntiles) {
+    constexpr int ww = kStencilBw + P1 - 1, wh = kStencilBh + P0 - 1;
+    constexpr int nq = (ww + 3 + 3) / 4;   // 16-byte chunks per row when the start is rounded down to 4
+    constexpr int kBuf = wh * nq * 4;
+    __shared__ __align__(16) float win[2 * kBuf];
+    const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
+    const bool fast = (wi & 3u) == 0u && ((uintptr_t)t.x & 15u) == 0u && (uint32_t)wh <= hin && (uint32_t)(4 * nq) <= wi;
+    const int rs = fast ? 4 * nq : ww;   // staged row stride
+    float h[P0][P1];
+#pragma unroll
+    for (int a = 0; a < P0; ++a)
+#pragma unroll
+        for (int b = 0; b < P1; ++b) h[a][b] = __ldg(t.taps + a * P1 + b);
+    // tile coordinates advance by the grid: (gq, gr) = divmod(grid, tiles_x)
+    const uint32_t gq = gridDim.x / tiles_x, gr = gridDim.x - gq * tiles_x;
+    uint32_t tile = blockIdx.x, ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    int delta = stencil_stage<P0, P1>(t, fast, ty, tx, win);
+    ptx::cp_async_commit();
+    for (int k = 0; tile < ntiles; ++k) {
+        const uint32_t next = tile + gridDim.x;   // < 2^32: both below 2^31
+        uint32_t ny = ty + gq, nx = tx + gr;
+        if (nx >= tiles_x) {
+            nx -= tiles_x;
+            ++ny;
+        }
+        int delta_next = 0;
+        if (next < ntiles) delta_next = stencil_stage<P0, P1>(t, fast, ny, nx, win + ((k + 1) & 1) * kBuf);
+        ptx::cp_async_commit();
+        ptx::cp_async_wait_group<1>();   // the current tile's copies have landed
+        __syncthreads();
+        stencil_tile<P0, P1>(t, win + (k & 1) * kBuf, rs, delta, ty, tx, h);
+        __syncthreads();                 // the buffer is free for the tile after next
+        tile = next;
+        ty = ny;
+        tx = nx;
+        delta = delta_next;
     }
 }
 
@@ -1020,9 +1075,19 @@ cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
     }
     if (t.m == 1 && t.s0 == 1 && t.s1 == 1 && t.p0 == t.p1 && (t.p0 == 3 || t.p0 == 5)) {
         const int64_t sx = (t.rep[3] + kStencilBw - 1) / kStencilBw, sy = (t.rep[2] + kStencilBh - 1) / kStencilBh;
-        const unsigned sgrid = (unsigned)(sx * sy);   // fewer tiles than the general tiling: < 2^31
-        if (t.p0 == 3) stencil_kernel<3, 3><<<sgrid, kFir2dThreads, 0, s>>>(t, (int)sx);
-        else stencil_kernel<5, 5><<<sgrid, kFir2dThreads, 0, s>>>(t, (int)sx);
+        const uint32_t ntiles = (uint32_t)(sx * sy);   // fewer tiles than the general tiling: < 2^31
+        static int occ3 = 0, occ5 = 0;
+        int& occ = t.p0 == 3 ? occ3 : occ5;
+        if (occ == 0) {
+            int n = 0;
+            cudaError_t e = t.p0 == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<3, 3>, kFir2dThreads, 0)
+                                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<5, 5>, kFir2dThreads, 0);
+            if (e != cudaSuccess) return e;
+            occ = n > 0 ? n : 1;
+        }
+        const uint32_t grid = (uint32_t)std::min<int64_t>((int64_t)device_sm_count() * occ, ntiles);
+        if (t.p0 == 3) stencil_kernel<3, 3><<<grid, kFir2dThreads, 0, s>>>(t, (uint32_t)sx, ntiles);
+        else stencil_kernel<5, 5><<<grid, kFir2dThreads, 0, s>>>(t, (uint32_t)sx, ntiles);
         return cudaGetLastError();
     }
     const int64_t tiles_x = (t.rep[3] + t.bw - 1) / t.bw, tiles_y = (t.rep[2] + t.bh - 1) / t.bh;

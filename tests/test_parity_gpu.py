@@ -436,8 +436,13 @@ def test_three_task_chain_forward_and_backward(arol):
     (70, 130, 5, 5, 1, 1, 1, (-2, -2), (1, 3)),     # 5x5 stencil, shifted output (register-blocked kernel)
     (33, 65, 3, 3, 1, 1, 2, (-1, -1), (0, 0)),      # 3x3 pattern with two outputs (general kernel)
     (50, 256, 3, 3, 1, 1, 1, (-1, -1), (0, 0)),     # rows a multiple of 4: 16-byte window copies, wrap
-    (40, 96, 5, 5, 1, 1, 1, (-2, 93), (2, 1)),      # 16-byte copies, window start near the row end
+    (40, 160, 5, 5, 1, 1, 1, (-2, 157), (2, 1)),    # 16-byte copies, window start near the row end
     (300, 700, 5, 7, 1, 1, 1, (-2, -3), (3, 5)),    # larger stencil, shifted output
+    # more 32x128 stencil tiles (1152, 1024) than CTAs resident on a GB300
+    # (152 SMs x 4), so CTAs take several tiles through both buffers
+    (4096, 1030, 3, 3, 1, 1, 1, (-1, -1), (5, 7)),  # element window copies, ragged last tile column
+    (2048, 2048, 5, 5, 1, 1, 1, (-2, -2), (0, 0)),  # 16-byte window copies
+    (1000, 520, 3, 3, 1, 1, 1, (-1, -1), (998, 0)), # output strips that wrap and a ragged last tile row
     (64, 96, 4, 4, 4, 4, 2, (0, 0), (0, 0)),        # non-overlapping 4x4 blocks, 2 outputs
     (90, 200, 3, 8, 2, 3, 5, (7, -11), (1, 2)),     # strided, overlapping, 5 outputs
     (9, 5, 6, 6, 1, 1, 3, (4, 1), (0, 0)),          # pattern wider than the array
