@@ -431,6 +431,22 @@ def bench_bf16(A, torch, stream, flush, reps, hbm):
             "unique_bytes": nbytes, "gbs": gbs, "frac_of_hbm": gbs / hbm}
 
 
+def bench_f16(A, torch, stream, flush, reps, hbm):
+    """The same 64x1080x1920 chain with IEEE half frames and output (f32
+    arithmetic and intermediate)."""
+    chain, (x,) = W.config1_f16(seed=3)
+    c = A.Chain(chain)
+    xd = torch.from_numpy(x).cuda()
+    y = c.run([xd])
+    for _ in range(3):
+        c.run([xd], y)
+    ms = statistics.median(time_each_flushed(lambda: c.run([xd], y), reps, stream, flush))
+    nbytes = 2 * FRAMES * HEIGHT * WIDTH + 2 * FRAMES * (HEIGHT // 8 * 3) * (WIDTH // 8 * 3)
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": "64x1080x1920 f16 -> 64x405x720 f16", "ms": ms, "elems_per_s": chain_units(FRAMES) / (ms * 1e-3),
+            "unique_bytes": nbytes, "gbs": gbs, "frac_of_hbm": gbs / hbm}
+
+
 def bench_cg(A, torch, stream, flush, reps, hbm):
     """Conjugate gradient of the case study on a synthetic SPD matrix with the
     paper's N and NNZ (27-point stencil on 51^3), tol 1e-10, float64."""
@@ -618,6 +634,7 @@ def run_gpu(args):
         line["fwd_bwd"] = bench_backward(A, torch, stream, flush, reps)
         line["matmul"] = bench_matmul(A, torch, stream, flush, reps, bf16)
         line["bf16_storage"] = bench_bf16(A, torch, stream, flush, reps, hbm)
+        line["f16_storage"] = bench_f16(A, torch, stream, flush, reps, hbm)
         line["cg"] = bench_cg(A, torch, stream, flush, reps, hbm)
         del flush
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -662,6 +679,8 @@ def run_case(args):
         out = bench_cg(A, torch, stream, flush, reps, hbm)
     elif args.case == "bf16":
         out = bench_bf16(A, torch, stream, flush, reps, hbm)
+    elif args.case == "f16":
+        out = bench_f16(A, torch, stream, flush, reps, hbm)
     else:
         out = bench_config0(A, torch, stream, reps)
     print(json.dumps({"case": args.case, **out}))
@@ -676,7 +695,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["batched", "chains", "stencil", "backward", "matmul", "config0", "cg", "bf16"],
+    ap.add_argument("--case", choices=["batched", "chains", "stencil", "backward", "matmul", "config0", "cg", "bf16", "f16"],
                     help="run one extra measurement alone (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="batched case: keep the default launch shape")
     args = ap.parse_args(argv)

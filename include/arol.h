@@ -59,7 +59,16 @@ typedef enum {
     AROL_ERR_OOB = 6             /* a device-side bounds check fired (checked builds only) */
 } arol_status;
 
-typedef enum { AROL_F32 = 0, AROL_BF16 = 1 } arol_dtype;
+/* Element storage (Sec. 5 typeAllocation).  FIR arithmetic is f32 for every
+ * storage type: 16-bit inputs are widened exactly, 16-bit outputs (and a
+ * 16-bit chain intermediate) are rounded to nearest even.  Copy tasks move
+ * raw bits of any type; matmul inputs are bfloat16 only; backward passes take
+ * float32 storage only. */
+typedef enum {
+    AROL_F32 = 0,    /* IEEE binary32 */
+    AROL_BF16 = 1,   /* bfloat16: the upper 16 bits of a binary32 */
+    AROL_F16 = 2     /* IEEE binary16 (half) */
+} arol_dtype;
 
 typedef enum {
     AROL_ELEM_COPY = 0,    /* y[j] = p[j]: raw bits, NaN payloads kept */

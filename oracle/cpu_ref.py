@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cpu_ref.c")
 _LIB = os.path.join(_HERE, "_cpu_ref.so")
-_DT = {"f32": 0, "bf16": 1, "f64": 2}
+_DT = {"f32": 0, "bf16": 1, "f64": 2, "f16": 1}   # f16 ports: 16-bit words moved by a copy, never decoded in C
 _ELEM = {"copy": 0, "fir": 1, "matmul": 2}
 
 
@@ -108,10 +108,19 @@ def _dtype_of(x, declared):
     return declared
 
 
+def _half_input(x, p, elem):
+    """IEEE half inputs (float16 arrays, or uint16 words on an f16 port): a
+    copy moves their 16-bit words; arithmetic reads their values, which
+    float64 holds exactly, so the C code never decodes binary16 itself."""
+    if x.dtype == np.float16 or (x.dtype == np.uint16 and p["dtype"] == "f16"):
+        return x.view(np.uint16) if elem == "copy" else x.view(np.float16).astype(np.float64)
+    return x
+
+
 def run_task(tk, inputs):
     """One task.  Returns [Y]: float64 for fir/matmul, raw bits for copy."""
     L = lib()
-    ins = [np.ascontiguousarray(x) for x in inputs]
+    ins = [_half_input(np.ascontiguousarray(x), p, tk["elem"]) for x, p in zip(inputs, tk["inputs"])]
     ports = (OrefPort * 2)(*[_port(p, _dtype_of(x, p["dtype"])) for p, x in zip(tk["inputs"], ins)])
     ptrs = (ctypes.c_void_p * 2)(*[x.ctypes.data for x in ins])
     op = tk["outputs"][0]

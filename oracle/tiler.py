@@ -112,10 +112,16 @@ def elem_matmul(pa, pb, a_shape, b_shape):
 # --------------------------------------------------------------------------
 
 def _as_values(x, dtype):
-    """Element values the task reads.  bf16 arrays are given as uint16 bit
-    patterns and widened exactly to float64."""
+    """Element values the task reads (Sec. 5 typeAllocation).  bf16 arrays
+    are given as uint16 bit patterns: a bfloat16 is the upper half of a
+    binary32, so shifting the bits up 16 places gives its value exactly.  f16
+    arrays are IEEE binary16 (numpy float16, or its uint16 bit patterns);
+    every binary16 value is exact in float64."""
     if dtype == "bf16":
         return (np.asarray(x, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    if dtype == "f16":
+        x = np.asarray(x)
+        return (x.view(np.float16) if x.dtype == np.uint16 else x.astype(np.float16)).astype(np.float64)
     return np.asarray(x, dtype=np.float64)
 
 

@@ -8,7 +8,7 @@ import torch
 
 from . import binding as B
 
-_TORCH_DTYPE = {"f32": torch.float32, "bf16": torch.bfloat16}
+_TORCH_DTYPE = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
 
 
 def _out_port(spec):

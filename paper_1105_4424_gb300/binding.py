@@ -18,9 +18,9 @@ LIB_PATH = os.environ.get("AROL_LIB") or os.path.join(_PKG, "libarol.so")
 
 c_i32, c_i64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
 
-AROL_F32, AROL_BF16 = 0, 1
+AROL_F32, AROL_BF16, AROL_F16 = 0, 1, 2
 ELEM = {"copy": 0, "fir": 1, "matmul": 2}
-DTYPE = {"f32": AROL_F32, "bf16": AROL_BF16}
+DTYPE = {"f32": AROL_F32, "bf16": AROL_BF16, "f16": AROL_F16}
 STATUS = {0: "AROL_OK", 1: "AROL_ERR_INVALID", 2: "AROL_ERR_NOT_PARTITION", 3: "AROL_ERR_UNSUPPORTED",
           4: "AROL_ERR_CUDA", 5: "AROL_ERR_TIMEOUT", 6: "AROL_ERR_OOB"}
 

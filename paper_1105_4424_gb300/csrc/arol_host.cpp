@@ -95,7 +95,7 @@ int64_t elems_of(const arol_array_desc& a) {
     return n;
 }
 
-int esize_of(int dtype) { return dtype == AROL_BF16 ? 2 : 4; }
+int esize_of(int dtype) { return dtype == AROL_BF16 || dtype == AROL_F16 ? 2 : 4; }
 
 int64_t pattern_size(const arol_tiler& t) {
     int64_t n = 1;
@@ -113,7 +113,8 @@ constexpr int64_t kMaxDim = (int64_t(1) << 31) - 1;
 
 arol_status check_array(const arol_array_desc& a, const char* name) {
     if (a.rank < 1 || a.rank > AROL_MAX_RANK) return fail(AROL_ERR_INVALID, "%s: rank %d not in [1,4]", name, a.rank);
-    if (a.dtype != AROL_F32 && a.dtype != AROL_BF16) return fail(AROL_ERR_INVALID, "%s: unknown dtype %d", name, a.dtype);
+    if (a.dtype != AROL_F32 && a.dtype != AROL_BF16 && a.dtype != AROL_F16)
+        return fail(AROL_ERR_INVALID, "%s: unknown dtype %d", name, a.dtype);
     double total = 1;
     for (int k = 0; k < a.rank; ++k) {
         if (a.shape[k] < 0 || a.shape[k] > kMaxDim)
@@ -483,8 +484,8 @@ TaskDev make_taskdev_exact(const arol_task_desc& d) {
     t.T = (int32_t)pattern_size(d.in_tiler[0]);
     t.m = (int32_t)pattern_size(d.out_tiler[0]);
     t.esize = esize_of(d.in[0].dtype);
-    t.in_bf16 = d.elem == AROL_ELEM_FIR && d.in[0].dtype == AROL_BF16 ? 1 : 0;
-    t.out_bf16 = d.elem == AROL_ELEM_FIR && d.out[0].dtype == AROL_BF16 ? 1 : 0;
+    t.in_dt = d.elem == AROL_ELEM_FIR ? d.in[0].dtype : kStF32;
+    t.out_dt = d.elem == AROL_ELEM_FIR ? d.out[0].dtype : kStF32;
     arol_task_desc full = dd;
     full.rep_rank = 4;
     for (int q = 0; q < 4; ++q) full.rep[q] = t.rep[q];
@@ -492,7 +493,7 @@ TaskDev make_taskdev_exact(const arol_task_desc& d) {
     // Row FIR: one row per r0, step along the row per r1, one contiguous
     // pattern of T taps, m contiguous outputs per repetition.
     const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
-    if (d.elem == AROL_ELEM_FIR && !t.wide && !t.in_bf16 && !t.out_bf16 && d.rep_rank == 2 && d.in[0].rank == 2 &&
+    if (d.elem == AROL_ELEM_FIR && !t.wide && t.in_dt == kStF32 && t.out_dt == kStF32 && d.rep_rank == 2 && d.in[0].rank == 2 &&
         d.out[0].rank == 2 &&
         ti.pattern_rank == 1 && to.pattern_rank == 1 && ti.paving[0][0] == 1 && ti.paving[0][1] == 0 &&
         ti.paving[1][0] == 0 && ti.fitting[0][0] == 0 && ti.fitting[1][0] == 1 && to.paving[0][0] == 1 &&
@@ -507,7 +508,7 @@ TaskDev make_taskdev_exact(const arol_task_desc& d) {
     }
     // Column FIR: one column per r1, step down the rows per r0, the pattern
     // running down the rows, m consecutive output rows per repetition.
-    if (!t.rowfir && d.elem == AROL_ELEM_FIR && !t.wide && !t.in_bf16 && !t.out_bf16 && d.rep_rank == 2 &&
+    if (!t.rowfir && d.elem == AROL_ELEM_FIR && !t.wide && t.in_dt == kStF32 && t.out_dt == kStF32 && d.rep_rank == 2 &&
         d.in[0].rank == 2 && d.out[0].rank == 2 && ti.pattern_rank == 1 && to.pattern_rank == 1 &&
         ti.paving[0][0] >= 1 && ti.paving[0][1] == 0 && ti.paving[1][0] == 0 && ti.paving[1][1] == 1 &&
         ti.fitting[0][0] == 1 && ti.fitting[1][0] == 0 && to.paving[0][0] == d.fir_m && to.paving[0][1] == 0 &&
@@ -518,7 +519,7 @@ TaskDev make_taskdev_exact(const arol_task_desc& d) {
     }
     // FIR on a 2-D pattern: pattern dims map to the array dims in order
     // (fitting identity), diagonal paving, m outputs along the output row.
-    if (d.elem == AROL_ELEM_FIR && !t.wide && !t.in_bf16 && !t.out_bf16 && d.rep_rank == 2 && d.in[0].rank == 2 &&
+    if (d.elem == AROL_ELEM_FIR && !t.wide && t.in_dt == kStF32 && t.out_dt == kStF32 && d.rep_rank == 2 && d.in[0].rank == 2 &&
         d.out[0].rank == 2 && ti.pattern_rank == 2 && to.pattern_rank == 1 && ti.fitting[0][0] == 1 &&
         ti.fitting[0][1] == 0 && ti.fitting[1][0] == 0 && ti.fitting[1][1] == 1 && ti.paving[0][1] == 0 &&
         ti.paving[1][0] == 0 && to.paving[0][0] == 1 && to.paving[0][1] == 0 && to.paving[1][0] == 0 &&
@@ -655,7 +656,7 @@ struct arol_task_s {
     // fused downscaler
     int64_t ds_frames = 0;
     int ds_H = 0, ds_W = 0;
-    bool ds_in_bf16 = false, ds_mid_bf16 = false, ds_out_bf16 = false;
+    bool ds_in16 = false, ds_mid16 = false, ds_out16 = false, ds_half16 = false;
     // matmul
     int mm_M = 0, mm_N = 0, mm_K = 0;
     unsigned* err_flag = nullptr;        // device word: bounded waits that gave up
@@ -939,19 +940,21 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     if (n == 2 && match_pass(t->descs[0], 2, &h) && match_pass(t->descs[1], 1, &v) && h.S == 8 && h.T == 8 &&
         h.m == 3 && v.S == 8 && v.T == 8 && v.m == 3 && v.F == h.F && v.H == h.H && v.W == h.W / 8 * 3 &&
         h.W % 8 == 0 && h.H % 8 == 0 && (double)h.F * (h.H / 8) * (h.W / 4) < 2147483647.0) {
-        // fused storage combinations: all f32, or bf16 frames with an f32 or
-        // bf16 intermediate and output; others run task by task
-        const bool in_bf16 = t->descs[0].in[0].dtype == AROL_BF16;
-        const bool mid_bf16 = t->descs[0].out[0].dtype == AROL_BF16;
-        const bool out_bf16 = t->descs[1].out[0].dtype == AROL_BF16;
-        if (in_bf16 || (!mid_bf16 && !out_bf16)) {
+        // fused storage combinations: all f32, or 16-bit frames (bfloat16 or
+        // IEEE half) with an intermediate and an output each f32 or of the
+        // frames' type; others run task by task
+        const int di = t->descs[0].in[0].dtype, dm = t->descs[0].out[0].dtype, dy = t->descs[1].out[0].dtype;
+        const bool fused = di == AROL_F32 ? dm == AROL_F32 && dy == AROL_F32
+                                          : (dm == AROL_F32 || dm == di) && (dy == AROL_F32 || dy == di);
+        if (fused) {
             t->kernel = 1;
             t->ds_frames = h.F;
             t->ds_H = (int)h.H;
             t->ds_W = (int)h.W;
-            t->ds_in_bf16 = in_bf16;
-            t->ds_mid_bf16 = mid_bf16;
-            t->ds_out_bf16 = out_bf16;
+            t->ds_in16 = di != AROL_F32;
+            t->ds_mid16 = dm != AROL_F32;
+            t->ds_out16 = dy != AROL_F32;
+            t->ds_half16 = di == AROL_F16;
         }
     }
     arol_task_info_t& in = t->info;
@@ -1021,9 +1024,10 @@ DownscaleDev ds_params(arol_task t, const float* taps) {
     DownscaleDev p;
     std::memset(&p, 0, sizeof p);
     p.err = t->err_flag;
-    p.in_bf16 = t->ds_in_bf16;
-    p.mid_bf16 = t->ds_mid_bf16;
-    p.out_bf16 = t->ds_out_bf16;
+    p.in16 = t->ds_in16;
+    p.mid16 = t->ds_mid16;
+    p.out16 = t->ds_out16;
+    p.half16 = t->ds_half16;
     p.taps = taps;
     p.frames = t->ds_frames;
     p.H = t->ds_H;
@@ -1203,7 +1207,7 @@ arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* co
     const arol_task_desc& d0 = t->descs[0];
     const arol_array_desc& od = t->descs.back().out[0];
     arol_status st;
-    const bool pipelined = t->kind == 1 && t->kernel == 1 && t->ds_frames >= 2 && !t->ds_in_bf16 && !t->ds_out_bf16;
+    const bool pipelined = t->kind == 1 && t->kernel == 1 && t->ds_frames >= 2 && !t->ds_in16 && !t->ds_out16;
     void* dins[2] = {nullptr, nullptr};
     for (int i = 0; i < d0.n_in; ++i) {
         if (!host_in[i]) return fail(AROL_ERR_INVALID, "null input pointer %d", i);
@@ -1387,7 +1391,7 @@ arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* gr
                               float* grad_taps, void* stream) {
     AROL_TRACE();
     if (!t || !in || !in[0] || !grad_out || !out) return fail(AROL_ERR_INVALID, "null argument");
-    if (!(t->kind == 1 && t->kernel == 1) || t->ds_in_bf16 || t->ds_mid_bf16 || t->ds_out_bf16)
+    if (!(t->kind == 1 && t->kernel == 1) || t->ds_in16 || t->ds_mid16 || t->ds_out16)
         return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd is implemented for the float32 fused separable downscaler chain only");
     if (!aligned16(in[0]) || !aligned16(grad_in) || !aligned16(grad_out))
         return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd needs 16-byte aligned input, output-gradient and input-gradient buffers");

@@ -33,6 +33,9 @@ struct PortDev {
 
 enum ElemCode : int32_t { ELEM_COPY = 0, ELEM_FIR = 1 };
 
+// Element storage of a FIR task's arrays: the arol_dtype codes.
+enum StorageCode : int32_t { kStF32 = 0, kStBf16 = 1, kStF16 = 2 };
+
 // A copy or fir task for the generic tiler kernel (and one entry of a batch).
 struct TaskDev {
     int32_t rep[4];         // repetition space, last dimension fastest; unused = 1
@@ -42,8 +45,8 @@ struct TaskDev {
     int32_t T, m;           // fir: pattern size and outputs; copy: both = pattern size
     int32_t elem;           // ElemCode
     int32_t esize;          // copy: element size in bytes (2 or 4)
-    int32_t in_bf16;        // fir: input stored as bfloat16 (widened exactly to f32)
-    int32_t out_bf16;       // fir: output stored as bfloat16 (round to nearest even)
+    int32_t in_dt;          // fir: input storage, a StorageCode (16-bit values widen exactly to f32)
+    int32_t out_dt;         // fir: output storage, a StorageCode (16-bit stores round to nearest even)
     int32_t wide;           // 1 when repetition indices or base sums reach 2^31 (64-bit path)
     int32_t rowfir;         // 1: rank-2 row FIR (paving [[1,0],[0,step]], fitting [[0],[1]], output
                             //    paving [[1,0],[0,m]]) with step, T <= 32 and m <= 16: row-tile path
@@ -81,9 +84,10 @@ struct DownscaleDev {
     float* gx;              // backward: dL/dx
     float* partials;        // backward: per-CTA tap-gradient partials (48 floats each)
     unsigned* err;          // nullable: bit set when a bounded wait gives up
-    int32_t in_bf16;        // forward: x stored as bfloat16
-    int32_t mid_bf16;       // forward: the intermediate array is declared bfloat16 (rounded)
-    int32_t out_bf16;       // forward: y stored as bfloat16
+    int32_t in16;           // forward: x stored in 16 bits
+    int32_t mid16;          // forward: the intermediate array is declared 16-bit (rounded)
+    int32_t out16;          // forward: y stored in 16 bits
+    int32_t half16;         // forward: the 16-bit arrays are IEEE half (else bfloat16)
     float* grad_taps;       // backward: 48 tap gradients, written by the last CTA (nullable)
     unsigned* ticket;       // backward: CTAs done (zero before the launch; the last CTA resets it)
     int64_t frames;

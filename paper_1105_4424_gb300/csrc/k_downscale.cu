@@ -25,6 +25,7 @@
 #include <cstring>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "arol_internal.h"
 #include "ptx.h"
@@ -692,23 +693,36 @@ bool use_register_variant() {
 }
 
 // ---------------------------------------------------------------------------
-// bfloat16 frames (Sec. 5 typeAllocation): the same bulk-copy ring, now with
-// one consumer thread per 8x8 block (one 16-byte shared load holds 8 pixels
-// of a row, so no lane pairs and no shuffles).  The arithmetic is f32; an
-// intermediate declared bfloat16 is rounded to nearest even exactly where the
-// unfused chain would store it; the output is stored as f32 or bfloat16.
+// 16-bit frames, bfloat16 or IEEE half (Sec. 5 typeAllocation): the same
+// bulk-copy ring, now with one consumer thread per 8x8 block (one 16-byte
+// shared load holds 8 pixels of a row, so no lane pairs and no shuffles).
+// The arithmetic is f32; an intermediate declared 16-bit is rounded to
+// nearest even exactly where the unfused chain would store it; the output is
+// stored as f32 or in the frames' 16-bit type.
 // ---------------------------------------------------------------------------
 constexpr int kB16Stages = 4;
 constexpr int kB16CWarps = 4;
 constexpr int kB16Threads = (kB16CWarps + 1) * 32;
 
-__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+// Storage policies: the two halves of a 32-bit word widened exactly to f32,
+// rounding to nearest even, and a 16-bit store.
+struct Bf16Storage {
+    __device__ static float lo(uint32_t w) { return __uint_as_float(w << 16); }
+    __device__ static float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+    __device__ static float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    __device__ static void store(void* y, int64_t i, float v) { static_cast<__nv_bfloat16*>(y)[i] = __float2bfloat16_rn(v); }
+};
+struct HalfStorage {
+    __device__ static float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+    __device__ static float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    __device__ static float round(float v) { return __half2float(__float2half_rn(v)); }
+    __device__ static void store(void* y, int64_t i, float v) { static_cast<__half*>(y)[i] = __float2half_rn(v); }
+};
 
-template <bool kRoundMid, bool kOutBf16>
-__global__ void __launch_bounds__(kB16Threads, 3) downscale_bf16_kernel(const DownscaleDev p, int Wc, int nch) {
+template <class St, bool kRoundMid, bool kOut16>
+__device__ __forceinline__ void downscale16(const DownscaleDev& p, int Wc, int nch) {
     extern __shared__ __align__(128) unsigned short smb[];
-    const int sf = 8 * Wc;                                   // bf16 elements per stage
+    const int sf = 8 * Wc;                                   // 16-bit elements per stage
     uint64_t* bars = reinterpret_cast<uint64_t*>(smb + kB16Stages * sf);
     const uint32_t full0 = ptx::smem_addr(bars), empty0 = ptx::smem_addr(bars + kB16Stages);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -785,14 +799,14 @@ __global__ void __launch_bounds__(kB16Threads, 3) downscale_bf16_kernel(const Do
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const uint4 q = *reinterpret_cast<const uint4*>(src + r * Wc + 8 * b);
-                const float xr[8] = {bf16_lo(q.x), bf16_hi(q.x), bf16_lo(q.y), bf16_hi(q.y),
-                                     bf16_lo(q.z), bf16_hi(q.z), bf16_lo(q.w), bf16_hi(q.w)};
+                const float xr[8] = {St::lo(q.x), St::hi(q.x), St::lo(q.y), St::hi(q.y),
+                                     St::lo(q.z), St::hi(q.z), St::lo(q.w), St::hi(q.w)};
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     float mid = hh[j][0] * xr[0];
 #pragma unroll
                     for (int k = 1; k < 8; ++k) mid = fmaf(hh[j][k], xr[k], mid);
-                    if (kRoundMid) mid = __bfloat162float(__float2bfloat16_rn(mid));
+                    if (kRoundMid) mid = St::round(mid);
 #pragma unroll
                     for (int jv = 0; jv < 3; ++jv) y[jv][j] = fmaf(hv[jv][r], mid, y[jv][j]);
                 }
@@ -802,8 +816,7 @@ __global__ void __launch_bounds__(kB16Threads, 3) downscale_bf16_kernel(const Do
             for (int jv = 0; jv < 3; ++jv)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    if (kOutBf16) static_cast<__nv_bfloat16*>(static_cast<void*>(p.y))[ob + (int64_t)jv * Wo + j] =
-                        __float2bfloat16_rn(y[jv][j]);
+                    if (kOut16) St::store(p.y, ob + (int64_t)jv * Wo + j, y[jv][j]);
                     else p.y[ob + (int64_t)jv * Wo + j] = y[jv][j];
                 }
         }
@@ -812,32 +825,49 @@ __global__ void __launch_bounds__(kB16Threads, 3) downscale_bf16_kernel(const Do
     }
 }
 
-// Column chunk of the bf16 variant: at most 1024 columns, a multiple of 64.
-int bf16_chunk(int W) {
+template <bool kRoundMid, bool kOut16>
+__global__ void __launch_bounds__(kB16Threads, 3) downscale_bf16_kernel(const DownscaleDev p, int Wc, int nch) {
+    downscale16<Bf16Storage, kRoundMid, kOut16>(p, Wc, nch);
+}
+
+template <bool kRoundMid, bool kOut16>
+__global__ void __launch_bounds__(kB16Threads, 3) downscale_f16_kernel(const DownscaleDev p, int Wc, int nch) {
+    downscale16<HalfStorage, kRoundMid, kOut16>(p, Wc, nch);
+}
+
+// Column chunk of the 16-bit variants: at most 1024 columns, a multiple of 64.
+int chunk16(int W) {
     const int n = (W + 1023) / 1024;
     const int wc = (W + n - 1) / n;
     return (wc + 63) / 64 * 64;
 }
 
-template <bool kRoundMid, bool kOutBf16>
-cudaError_t launch_bf16_variant(const DownscaleDev& p, cudaStream_t s) {
-    const int Wc = bf16_chunk(p.W);
+template <bool kHalf, bool kRoundMid, bool kOut16>
+cudaError_t launch_16bit_variant(const DownscaleDev& p, cudaStream_t s) {
+    void (*kern)(const DownscaleDev, int, int) =
+        kHalf ? downscale_f16_kernel<kRoundMid, kOut16> : downscale_bf16_kernel<kRoundMid, kOut16>;
+    const int Wc = chunk16(p.W);
     const int nch = (p.W + Wc - 1) / Wc;
     const size_t smem = (size_t)kB16Stages * 8 * Wc * 2 + 2 * kB16Stages * 8;
     static int last_wc = -1, per_sm = 1;
     if (Wc != last_wc) {
-        cudaError_t e = cudaFuncSetAttribute(downscale_bf16_kernel<kRoundMid, kOutBf16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, downscale_bf16_kernel<kRoundMid, kOutBf16>, kB16Threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kB16Threads, smem);
         per_sm = n > 0 ? n : 1;
         last_wc = Wc;
     }
     const uint32_t units = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * (uint32_t)nch;
     const uint32_t cap = (uint32_t)(device_sm_count() * per_sm);
-    downscale_bf16_kernel<kRoundMid, kOutBf16><<<(int)(units < cap ? units : cap), kB16Threads, smem, s>>>(p, Wc, nch);
+    kern<<<(int)(units < cap ? units : cap), kB16Threads, smem, s>>>(p, Wc, nch);
     return cudaGetLastError();
+}
+
+template <bool kHalf>
+cudaError_t launch_16bit(const DownscaleDev& p, cudaStream_t s) {
+    if (p.mid16) return p.out16 ? launch_16bit_variant<kHalf, true, true>(p, s) : launch_16bit_variant<kHalf, true, false>(p, s);
+    return p.out16 ? launch_16bit_variant<kHalf, false, true>(p, s) : launch_16bit_variant<kHalf, false, false>(p, s);
 }
 
 int fwd_grid(uint32_t items) {
@@ -884,10 +914,7 @@ int downscale_bwd_partials(int sm_count, int W) {
 cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s) {
     const uint32_t items = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * ((uint32_t)p.W >> 2);
     if (items == 0) return cudaSuccess;
-    if (p.in_bf16) {
-        if (p.mid_bf16) return p.out_bf16 ? launch_bf16_variant<true, true>(p, s) : launch_bf16_variant<true, false>(p, s);
-        return p.out_bf16 ? launch_bf16_variant<false, true>(p, s) : launch_bf16_variant<false, false>(p, s);
-    }
+    if (p.in16) return p.half16 ? launch_16bit<true>(p, s) : launch_16bit<false>(p, s);
     if (!use_register_variant()) {
         const int Wc = bulk_chunk(p.W);
         const uint32_t units = (uint32_t)p.frames * ((uint32_t)p.H >> 3) * (uint32_t)((p.W + Wc - 1) / Wc);

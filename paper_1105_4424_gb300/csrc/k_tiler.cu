@@ -8,6 +8,7 @@
 // walks the pattern by adding fitting columns with one conditional subtract
 // per dimension (strength-reduced modulo), all in 32-bit registers.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "arol_internal.h"
 #include "ptx.h"
@@ -100,15 +101,18 @@ __device__ __forceinline__ void decode_rep(const TaskDev& t, int64_t lr, bool wi
 }
 
 // One repetition of a copy or fir task: gather, elementary task, scatter.
-// FIR storage: f32, or bfloat16 widened exactly on load and rounded to
-// nearest even on store; the arithmetic is f32 either way.
+// FIR storage: f32, bfloat16 or IEEE half; 16-bit values are widened
+// exactly on load and rounded to nearest even on store; the arithmetic is f32
+// either way.
 __device__ __forceinline__ float load_value(const TaskDev& t, int64_t off) {
-    if (t.in_bf16) return __uint_as_float((uint32_t)__ldg(static_cast<const unsigned short*>(t.x) + off) << 16);
+    if (t.in_dt == kStBf16) return __uint_as_float((uint32_t)__ldg(static_cast<const unsigned short*>(t.x) + off) << 16);
+    if (t.in_dt == kStF16) return __half2float(__ushort_as_half(__ldg(static_cast<const unsigned short*>(t.x) + off)));
     return __ldg(static_cast<const float*>(t.x) + off);
 }
 
 __device__ __forceinline__ void store_value(const TaskDev& t, int64_t off, float v) {
-    if (t.out_bf16) static_cast<__nv_bfloat16*>(t.y)[off] = __float2bfloat16_rn(v);
+    if (t.out_dt == kStBf16) static_cast<__nv_bfloat16*>(t.y)[off] = __float2bfloat16_rn(v);
+    else if (t.out_dt == kStF16) static_cast<__half*>(t.y)[off] = __float2half_rn(v);
     else static_cast<float*>(t.y)[off] = v;
 }
 

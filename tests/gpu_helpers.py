@@ -14,7 +14,8 @@ FIR_ATOL = 1e-30
 
 
 def dev(a: np.ndarray) -> torch.Tensor:
-    """numpy -> CUDA tensor; uint16 arrays are bfloat16 bit patterns."""
+    """numpy -> CUDA tensor; uint16 arrays are bfloat16 bit patterns, float16
+    arrays IEEE half."""
     a = np.ascontiguousarray(a)
     if a.dtype == np.uint16:
         return torch.from_numpy(a.view(np.int16)).cuda().view(torch.bfloat16)

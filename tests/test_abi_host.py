@@ -101,6 +101,36 @@ def test_partition_check_matches_oracle(B):
                 assert e.value.status == 2
 
 
+def test_16bit_storage_descriptors(B):
+    """IEEE half storage (arol_dtype 2) is accepted next to f32 and bfloat16;
+    an unknown dtype is a malformed descriptor; matmul takes bfloat16 only;
+    the fused chain needs its 16-bit arrays to share one type."""
+    tk, _ = W.config0()
+    f16 = W.task(tk["rep"], "fir", [dict(tk["inputs"][0], dtype="f16")], [dict(tk["outputs"][0], dtype="f16")],
+                 tk["taps"])
+    h = B.arol_task_create(f16)
+    assert B.arol_task_info(h)["unique_bytes"] == 2 * (64 * 64 + 64 * 48)
+    B.arol_task_destroy(h)
+    d, keep = B.task_desc(f16)
+    d.in_[0].dtype = 3
+    with pytest.raises(B.ArolError) as e:
+        B.arol_task_create(d)
+    assert e.value.status == 1
+    mm = W.matmul_task(256, 256, 128)
+    mm = dict(mm, inputs=[dict(p, dtype="f16") for p in mm["inputs"]])
+    assert _err(B, mm) == 3
+    Hh = np.ones((3, 8), np.float32)
+    for dts, kernel in [(("f16", "f16", "f16"), 1), (("f16", "f32", "f16"), 1), (("f16", "f16", "f32"), 1),
+                        (("bf16", "bf16", "bf16"), 1), (("f16", "bf16", "f32"), 3), (("bf16", "f32", "f16"), 3),
+                        (("f32", "f16", "f32"), 3)]:
+        chain = W.downscale_chain(2, 16, 64, Hh, Hh, dtypes=dts)
+        subs = [B.arol_task_create(s) for s in chain]
+        h = B.arol_chain_create(subs)
+        assert B.arol_task_info(h)["kernel"] == kernel, dts
+        for x in subs + [h]:
+            B.arol_task_destroy(x)
+
+
 def test_info_counts_the_downscaler_chain(B):
     Hh = np.ones((3, 8), np.float32)
     chain = W.downscale_chain(64, 1080, 1920, Hh, Hh)

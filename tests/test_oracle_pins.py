@@ -231,6 +231,46 @@ def test_bf16_round_known_values():
     np.testing.assert_array_equal(W.bf16_round(v), np.array([0x3F80, 0x3F80, 0x3F82, 0xC000, 0x3F81], np.uint16))
 
 
+def test_f16_round_known_values():
+    """IEEE binary16 rounding of the input generator, values worked by hand:
+    ties go to the even significand, 65520 (halfway to 2^16) overflows, and
+    the subnormal step is 2^-24."""
+    v = np.array([1.0, 1.0 + 2 ** -11, 1.0 + 3 * 2 ** -11, -2.0, 65504.0, 65520.0,
+                  2 ** -24, 2 ** -25, 3 * 2 ** -26], dtype=np.float32)
+    want = np.array([0x3C00, 0x3C00, 0x3C02, 0xC000, 0x7BFF, 0x7C00, 0x0001, 0x0000, 0x0001], np.uint16)
+    np.testing.assert_array_equal(W.f16_round(v).view(np.uint16), want)
+
+
+def test_oracle_reads_f16_values():
+    """The oracle's f16 reads against values decoded by hand from binary16
+    fields (sign, 5-bit exponent with bias 15, 10-bit fraction)."""
+    bits = np.array([0x3C00, 0x3555, 0x0001, 0x8400, 0x7BFF, 0x03FF], np.uint16)
+    want = [1.0, 1365 / 4096, 2.0 ** -24, -(2.0 ** -14), 65504.0, 1023 * 2.0 ** -24]
+    got = O._as_values(bits, "f16")
+    assert got.dtype == np.float64 and list(got) == want
+    assert list(O._as_values(bits.view(np.float16), "f16")) == want
+
+
+def test_f16_fir_and_copy_through_both_oracles():
+    """An f16 FIR reads the exact half values (the same as an f32 task on the
+    widened values); an f16 copy moves the 16-bit words unchanged."""
+    from oracle import cpu_ref as C
+    g = W.rng(41)
+    tk = W.random_tiler_task(g, "fir", max_side=8)
+    x = W.f16_round(g.standard_normal(tk["inputs"][0]["shape"]).astype(np.float32))
+    t16 = dict(tk, inputs=[dict(tk["inputs"][0], dtype="f16")])
+    ref = O.run_task(tk, [x.astype(np.float64)])[0]
+    np.testing.assert_array_equal(O.run_task(t16, [x])[0], ref)
+    np.testing.assert_allclose(C.run_task(t16, [x])[0], ref, rtol=1e-13, atol=1e-300)
+    tc = W.random_tiler_task(g, "copy", max_side=8)
+    tc = dict(tc, inputs=[dict(tc["inputs"][0], dtype="f16")], outputs=[dict(tc["outputs"][0], dtype="f16")])
+    xc = W.f16_round(g.standard_normal(tc["inputs"][0]["shape"]).astype(np.float32))
+    yo = O.run_task(tc, [xc])[0]
+    yc = C.run_task(tc, [xc])[0]
+    np.testing.assert_array_equal(yo.view(np.uint16), yc.view(np.uint16))
+    assert set(yo.view(np.uint16).ravel()) <= set(xc.view(np.uint16).ravel())
+
+
 # ----------------------------------------------------------------- adjoints
 
 def _inner(a, b):

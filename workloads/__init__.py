@@ -29,8 +29,8 @@ import numpy as np
 
 __all__ = [
     "rng", "port", "task", "fir_row_task", "downscale_chain",
-    "config0", "config1", "config1_bf16", "config2", "config3", "config4",
-    "bf16_round", "bf16_bits_to_f32", "random_tiler_task", "stencil27_csr",
+    "config0", "config1", "config1_bf16", "config1_f16", "config2", "config3", "config4",
+    "bf16_round", "bf16_bits_to_f32", "f16_round", "random_tiler_task", "stencil27_csr",
 ]
 
 
@@ -113,6 +113,16 @@ def config1_bf16(seed=0, frames=64, height=1080, width=1920, mid="f32", out="bf1
     return downscale_chain(frames, height, width, Hh, Hv, dtypes=("bf16", mid, out)), [x]
 
 
+def config1_f16(seed=0, frames=64, height=1080, width=1920, mid="f32", out="f16"):
+    """The chained downscaler with IEEE half frames: X drawn as in config1
+    (U[0,1) float32), then rounded to float16 (RNE); returns float16 arrays."""
+    g = rng(seed)
+    x = f16_round(g.random((frames, height, width), dtype=np.float32))
+    Hh = _taps(g, 3, 8)
+    Hv = _taps(g, 3, 8)
+    return downscale_chain(frames, height, width, Hh, Hv, dtypes=("f16", mid, out)), [x]
+
+
 def _taps(g, m, T):
     return (g.standard_normal((m, T), dtype=np.float64) / T).astype(np.float32)
 
@@ -150,6 +160,13 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
     b = ((u + bias) >> 16).astype(np.uint16)
     b[nan] = 0x7FC0
     return b
+
+
+def f16_round(x: np.ndarray) -> np.ndarray:
+    """float32 -> IEEE half (numpy float16), round to nearest even; values
+    from 65520 (halfway between the largest half, 65504, and 2^16) up round
+    to infinity."""
+    return np.ascontiguousarray(x, dtype=np.float32).astype(np.float16)
 
 
 def bf16_bits_to_f32(b: np.ndarray) -> np.ndarray:
