@@ -464,7 +464,9 @@ __device__ __forceinline__ void col_fir_compute(const TaskDev& t, const float* h
         float acc0[M], acc1[M];
 #pragma unroll
         for (int j = 0; j < M; ++j) acc0[j] = acc1[j] = 0.f;
-#pragma unroll 2
+        // unrolled by 4: the taps' global loads are independent of the FMAs,
+        // so more of them are in flight per thread
+#pragma unroll 4
         for (int kk = 0; kk < T; ++kk) {
             const float p0 = __ldg(x + (int64_t)row[0] * win + col[0]);
             const float p1 = __ldg(x + (int64_t)row[1] * win + col[1]);
