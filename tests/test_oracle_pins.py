@@ -475,3 +475,29 @@ def test_2d_fir_patterns_c_oracle_and_adjoint():
         G = g.standard_normal(tk["outputs"][0]["shape"])
         dX, dH = O.task_vjp(tk, [x], G)
         assert abs(_inner(y, G) - _inner(x, dX)) <= 1e-10 * (1 + abs(_inner(y, G)))
+
+
+def test_2d_fir_is_a_sum_of_rolled_arrays():
+    """A FIR on a 2-D pattern (fitting identity, diagonal paving (s0, s1),
+    m outputs along the output row) against its closed form as a sum of
+    shifted arrays: y[r0, m r1 + j] = sum_{a,b} H[j, a p1 + b] x[(s0 r0 + a + o0)
+    mod H, (s1 r1 + b + o1) mod W], i.e. numpy.roll then a strided slice."""
+    g = W.rng(17)
+    cases = [(12, 10, 3, 3, 1, 1, 1, (-1, -1)),    # 3x3 stencil with wrap
+             (9, 14, 2, 5, 3, 2, 2, (4, -7)),      # strided, overlapping, 2 outputs
+             (7, 7, 5, 5, 1, 1, 3, (-2, 30))]      # pattern as wide as the array, origin past the edge
+    for (Hh, Ww, p0, p1, s0, s1, m, o) in cases:
+        R0, R1 = -(-Hh // s0), -(-Ww // s1)
+        inp = W.port((Hh, Ww), o, ((s0, 0), (0, s1)), ((1, 0), (0, 1)), (p0, p1))
+        out = W.port((R0, m * R1), (0, 0), ((1, 0), (0, m)), ((0,), (1,)), (m,))
+        tk = W.task((R0, R1), "fir", [inp], [out], g.standard_normal((m, p0 * p1)))
+        taps = tk["taps"].astype(np.float64)
+        x = g.standard_normal((Hh, Ww))
+        want = np.zeros((R0, m * R1))
+        for j in range(m):
+            acc = np.zeros((Hh, Ww))
+            for a in range(p0):
+                for b in range(p1):
+                    acc += taps[j, a * p1 + b] * np.roll(x, (-(a + o[0]), -(b + o[1])), axis=(0, 1))
+            want[:, j::m] = acc[::s0, ::s1]
+        np.testing.assert_allclose(O.run_task(tk, [x])[0], want, rtol=1e-12, atol=1e-12)
