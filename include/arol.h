@@ -150,8 +150,10 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out);
  * they may be destroyed afterwards.  Its run, backward and fwd_bwd take the
  * first task's inputs and the last task's output.  A chain whose tasks are a
  * separable block downscaler (horizontal then vertical fir with step == T, no
- * wrap) runs as one fused kernel that never writes the intermediate to HBM;
- * other chains run stage by stage through intermediates the chain owns. */
+ * wrap) runs as one fused kernel that never writes the intermediate to HBM,
+ * when its storage is all f32, or 16-bit frames (bf16 or f16) with an
+ * intermediate and an output each f32 or of the frames' type; other chains
+ * run stage by stage through intermediates the chain owns. */
 arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out);
 
 /* Replace the fir taps.  on_device = 0: `taps` is host memory, copied now.
