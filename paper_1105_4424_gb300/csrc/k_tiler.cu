@@ -758,16 +758,24 @@ __device__ __forceinline__ void stencil_tile(const TaskDev& t, const float* win,
     }
 }
 
+// Window floats of one stencil tile buffer (rows of 4 nq floats).
+template <int P0, int P1>
+constexpr int stencil_buf_floats() {
+    return (kStencilBh + P0 - 1) * ((kStencilBw + P1 - 1 + 3 + 3) / 4) * 4;
+}
+
 // Persistent over tiles (static schedule: CTA b takes tiles b, b + grid, ...,
-// grid <= ntiles; tile = ty * tiles_x + tx), with two window buffers: the
-// copies of a CTA's next tile are in flight while it computes the current
-// one.
+// grid <= ntiles; tile = ty * tiles_x + tx), with three window buffers in
+// dynamic shared memory: while a CTA computes tile k, the copies of tiles
+// k + 1 and k + 2 are in flight.  One barrier per tile suffices: the buffer
+// refilled after it was last read by the previous tile, which every thread
+// finished before the barrier.
 template <int P0, int P1>
 __global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev t, uint32_t tiles_x, uint32_t ntiles) {
     constexpr int ww = kStencilBw + P1 - 1, wh = kStencilBh + P0 - 1;
     constexpr int nq = (ww + 3 + 3) / 4;   // 16-byte chunks per row when the start is rounded down to 4
-    constexpr int kBuf = wh * nq * 4;
-    __shared__ __align__(16) float win[2 * kBuf];
+    constexpr int kBuf = stencil_buf_floats<P0, P1>();
+    extern __shared__ __align__(16) float swin[];
     const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
     const bool fast = (wi & 3u) == 0u && ((uintptr_t)t.x & 15u) == 0u && (uint32_t)wh <= hin && (uint32_t)(4 * nq) <= wi;
     const int rs = fast ? 4 * nq : ww;   // staged row stride
@@ -778,28 +786,40 @@ __global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev
         for (int b = 0; b < P1; ++b) h[a][b] = __ldg(t.taps + a * P1 + b);
     // tile coordinates advance by the grid: (gq, gr) = divmod(grid, tiles_x)
     const uint32_t gq = gridDim.x / tiles_x, gr = gridDim.x - gq * tiles_x;
-    uint32_t tile = blockIdx.x, ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    int delta = stencil_stage<P0, P1>(t, fast, ty, tx, win);
-    ptx::cp_async_commit();
-    for (int k = 0; tile < ntiles; ++k) {
-        const uint32_t next = tile + gridDim.x;   // < 2^32: both below 2^31
-        uint32_t ny = ty + gq, nx = tx + gr;
-        if (nx >= tiles_x) {
-            nx -= tiles_x;
-            ++ny;
-        }
-        int delta_next = 0;
-        if (next < ntiles) delta_next = stencil_stage<P0, P1>(t, fast, ny, nx, win + ((k + 1) & 1) * kBuf);
-        ptx::cp_async_commit();
-        ptx::cp_async_wait_group<1>();   // the current tile's copies have landed
-        __syncthreads();
-        stencil_tile<P0, P1>(t, win + (k & 1) * kBuf, rs, delta, ty, tx, h);
-        __syncthreads();                 // the buffer is free for the tile after next
-        tile = next;
-        ty = ny;
-        tx = nx;
-        delta = delta_next;
+    // the tile a CTA computes now (0), and the next two (1, 2); indices are
+    // 64-bit so that tile + 2 grid cannot wrap
+    uint64_t t0 = blockIdx.x, t1 = t0 + gridDim.x;
+    uint32_t y0 = (uint32_t)t0 / tiles_x, x0 = (uint32_t)t0 - y0 * tiles_x;
+    uint32_t y1 = y0 + gq, x1 = x0 + gr;
+    if (x1 >= tiles_x) {
+        x1 -= tiles_x;
+        ++y1;
     }
+    int b0 = 0, b1 = 1, b2 = 2;   // buffers of tiles 0, 1, 2
+    int d0 = stencil_stage<P0, P1>(t, fast, y0, x0, swin);
+    ptx::cp_async_commit();
+    int d1 = 0;
+    if (t1 < ntiles) d1 = stencil_stage<P0, P1>(t, fast, y1, x1, swin + kBuf);
+    ptx::cp_async_commit();
+    while (t0 < ntiles) {
+        ptx::cp_async_wait_group<1>();   // tile 0's copies have landed (tile 1's may be in flight)
+        __syncthreads();
+        const uint64_t t2 = t1 + gridDim.x;
+        uint32_t y2 = y1 + gq, x2 = x1 + gr;
+        if (x2 >= tiles_x) {
+            x2 -= tiles_x;
+            ++y2;
+        }
+        int d2 = 0;
+        if (t2 < ntiles) d2 = stencil_stage<P0, P1>(t, fast, y2, x2, swin + b2 * kBuf);
+        ptx::cp_async_commit();
+        stencil_tile<P0, P1>(t, swin + b0 * kBuf, rs, d0, y0, x0, h);
+        const int bf = b0;
+        t0 = t1; y0 = y1; x0 = x1; d0 = d1; b0 = b1;
+        t1 = t2; y1 = y2; x1 = x2; d1 = d2; b1 = b2;
+        b2 = bf;
+    }
+    ptx::cp_async_wait_all();
 }
 
 // Shared memory of the batch kernel: a ring of three task records (the
@@ -1084,16 +1104,17 @@ cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
         const uint32_t ntiles = (uint32_t)(sx * sy);   // fewer tiles than the general tiling: < 2^31
         static int occ3 = 0, occ5 = 0;
         int& occ = t.p0 == 3 ? occ3 : occ5;
+        void (*kern)(const TaskDev, uint32_t, uint32_t) = t.p0 == 3 ? stencil_kernel<3, 3> : stencil_kernel<5, 5>;
+        const size_t ssmem = 3 * sizeof(float) * (size_t)(t.p0 == 3 ? stencil_buf_floats<3, 3>() : stencil_buf_floats<5, 5>());
         if (occ == 0) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem);
             int n = 0;
-            cudaError_t e = t.p0 == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<3, 3>, kFir2dThreads, 0)
-                                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<5, 5>, kFir2dThreads, 0);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kFir2dThreads, ssmem);
             if (e != cudaSuccess) return e;
             occ = n > 0 ? n : 1;
         }
         const uint32_t grid = (uint32_t)std::min<int64_t>((int64_t)device_sm_count() * occ, ntiles);
-        if (t.p0 == 3) stencil_kernel<3, 3><<<grid, kFir2dThreads, 0, s>>>(t, (uint32_t)sx, ntiles);
-        else stencil_kernel<5, 5><<<grid, kFir2dThreads, 0, s>>>(t, (uint32_t)sx, ntiles);
+        kern<<<grid, kFir2dThreads, ssmem, s>>>(t, (uint32_t)sx, ntiles);
         return cudaGetLastError();
     }
     const int64_t tiles_x = (t.rep[3] + t.bw - 1) / t.bw, tiles_y = (t.rep[2] + t.bh - 1) / t.bh;
