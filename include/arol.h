@@ -246,7 +246,10 @@ arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* c
  * candidates on the given buffers (outputs are overwritten).  Results are
  * cached per process by batch signature and device, and persisted as JSON in
  * the file named by the AROL_TUNE_CACHE environment variable when it is set.
- * force = 1 re-times even when a cached choice exists.  Synchronizes. */
+ * force = 1 re-times even when a cached choice exists.  Synchronizes.
+ * The AROL_TUNE environment variable overrides: "off" returns AROL_OK at once
+ * and keeps the current launch shape (no device work, buffers not read),
+ * "force" re-times as force = 1 does. */
 arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* out, void* stream, int force);
 
 /* The tile size (repetitions per tile) and CTAs per SM in use. */

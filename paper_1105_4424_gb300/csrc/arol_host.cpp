@@ -1888,6 +1888,16 @@ arol_status arol_batch_config(arol_batch b, int64_t* tile_reps, int32_t* ctas_pe
 arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* out, void* stream, int force) {
     AROL_TRACE();
     if (!b || !in || !out) return fail(AROL_ERR_INVALID, "null argument");
+    // AROL_TUNE: "off" keeps the current launch shape (nothing is timed or
+    // read), "force" re-times as force = 1 does, anything else is the default
+    if (const char* mode = std::getenv("AROL_TUNE")) {
+        if (std::strcmp(mode, "off") == 0) {
+            log_line("batch tune: AROL_TUNE=off, keeping tile_reps %lld, %d CTAs per SM", (long long)b->tile_reps,
+                     b->ctas_per_sm);
+            return AROL_OK;
+        }
+        if (std::strcmp(mode, "force") == 0) force = 1;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     arol_status st = batch_prepare(b, in, out, s);
     if (st != AROL_OK) return st;

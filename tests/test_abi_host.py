@@ -207,3 +207,25 @@ def test_batch_rejects_members_with_device_taps(B):
     b = B.arol_batch_create([t])
     B.arol_batch_destroy(b)
     B.arol_task_destroy(t)
+
+
+def test_tune_off_keeps_the_launch_shape_without_device_work(B):
+    """AROL_TUNE=off: arol_batch_tune returns at once with the launch shape
+    unchanged and touches no buffer (the pointers here are not device memory,
+    and no GPU is needed)."""
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1105_4424_gb300 import binding as B\n"
+        "import workloads as W\n"
+        "tk, _ = W.config0()\n"
+        "h = B.arol_task_create(tk)\n"
+        "b = B.arol_batch_create([h])\n"
+        "before = B.arol_batch_config(b)\n"
+        "B.arol_batch_tune(b, [16], [32], stream=0)\n"
+        "assert B.arol_batch_config(b) == before, (before, B.arol_batch_config(b))\n"
+        "print('ok')\n" % ROOT)
+    env = dict(os.environ, AROL_TUNE="off")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr
