@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define AROL_VERSION 100            /* 1.0.0 */
+#define AROL_VERSION 101            /* 1.0.1: arol_task_info_t.path */
 #define AROL_MAX_RANK 4             /* array rank and repetition-space rank */
 #define AROL_MAX_PATTERN_RANK 2     /* pattern rank */
 #define AROL_MAX_FIR_M 32           /* outputs per pattern of a FIR bank */
@@ -130,14 +130,19 @@ typedef struct {
     int64_t unique_bytes;      /* algorithmic bytes: every external input element read once,
                                   every final output element written once */
     double flops;              /* arithmetic of the elementary tasks (2 per multiply-add) */
+    int32_t path;              /* a single task with kernel 0 and taps given on the host: 0 per-repetition
+                                  walk, 1 row-FIR tiles, 2 column-FIR tiles, 3 2-D window tiles,
+                                  4 register-blocked stencil (3x3 or 5x5, steps 1, one output); -1 otherwise */
+    int32_t reserved_;
 } arol_task_info_t;
 
 /* ---- tasks --------------------------------------------------------------- */
 
 /* Validate `desc` and build a task handle.  Host only: touches no GPU state.
  * Checks ranks, shapes, the elementary-task/pattern/dtype combination (copy:
- * same dtype and pattern size in and out; fir: f32 in and out, pattern size T,
- * output pattern size m; matmul: bf16 inputs with the panel tilers of a tiled
+ * same dtype and pattern size in and out; fir: f32, bf16 or f16 in and out,
+ * pattern size T, output pattern size m; matmul: bf16 inputs with the panel
+ * tilers of a tiled
  * product, f32 output) and that the output tiler partitions its array
  * (AROL_ERR_NOT_PARTITION otherwise).  On success *out owns a copy of the
  * descriptor and of the taps. */

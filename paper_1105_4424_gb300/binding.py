@@ -42,7 +42,8 @@ class TaskDesc(ctypes.Structure):
 
 class TaskInfo(ctypes.Structure):
     _fields_ = [("kind", c_i32), ("kernel", c_i32), ("reps", c_i64), ("gathered_elems", c_i64),
-                ("scattered_elems", c_i64), ("unique_bytes", c_i64), ("flops", ctypes.c_double)]
+                ("scattered_elems", c_i64), ("unique_bytes", c_i64), ("flops", ctypes.c_double),
+                ("path", c_i32), ("reserved_", c_i32)]
 
 
 class ArolError(RuntimeError):
@@ -246,7 +247,7 @@ def arol_task_fwd_bwd(t, ins, grad_out, out, grad_in=None, grad_taps=None, strea
 def arol_task_info(t) -> dict:
     info = TaskInfo()
     _check(lib.arol_task_info(t, ctypes.byref(info)))
-    return {f: getattr(info, f) for f, _ in TaskInfo._fields_}
+    return {f: getattr(info, f) for f, _ in TaskInfo._fields_ if not f.endswith("_")}
 
 
 def arol_task_sync_status(t, stream=None):

@@ -806,6 +806,12 @@ void fill_info_single(arol_task t) {
     else if (d.elem == AROL_ELEM_MATMUL)
         in.flops = 2.0 * (double)d.in_tiler[0].pattern[0] * d.in_tiler[0].pattern[1] * d.in_tiler[1].pattern[1] * (double)in.reps;
     else in.flops = 0;
+    in.path = -1;
+    if (t->kernel == 0 && d.elem != AROL_ELEM_MATMUL) {
+        const TaskDev td = make_taskdev(d);
+        in.path = td.rowfir ? 1 : td.colfir ? 2 : td.fir2d ? (fir2d_uses_stencil(td) ? 4 : 3) : 0;
+    }
+    in.reserved_ = 0;
 }
 
 void free_dev(void* p) {
@@ -901,7 +907,7 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out) {
         const char* path = t->kernel == 2 ? (M % 256 == 0 && N % 256 == 0 ? "tcgen05 matmul, CTA pairs" : "tcgen05 matmul")
                            : td.rowfir ? "row FIR (staged row tiles)"
                            : td.colfir ? "column FIR (column tiles)"
-                           : td.fir2d ? "2-D window FIR"
+                           : td.fir2d ? (fir2d_uses_stencil(td) ? "register-blocked stencil" : "2-D window FIR")
                                       : "per-repetition walk";
         log_line("task %p: rank %d, %lld repetitions, %s", (void*)t, desc->in[0].rank, (long long)reps_of(*desc), path);
     }
@@ -960,6 +966,8 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     arol_task_info_t& in = t->info;
     in.kind = 1;
     in.kernel = t->kernel;
+    in.path = -1;
+    in.reserved_ = 0;
     for (int i = 0; i < n; ++i) {
         const arol_task_info_t& s = tasks[i]->info;
         in.reps += s.reps;

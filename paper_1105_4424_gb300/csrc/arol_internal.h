@@ -98,6 +98,9 @@ struct DownscaleDev {
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s);
 // CTA b takes tiles b, b + grid, ... (a static schedule; `counter` is unused).
 cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s);
+// A 2-D window task that launch_fir2d runs on the register-blocked stencil
+// kernel (steps 1, one output, a 3x3 or 5x5 pattern).
+bool fir2d_uses_stencil(const TaskDev& t);
 cudaError_t launch_wait_selftest(unsigned* err, cudaStream_t s);
 cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, int ntiles,
                                     unsigned* counter, int grid, int threads, int max_m,

@@ -1088,6 +1088,10 @@ cudaError_t launch_wait_selftest(unsigned* err, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+bool fir2d_uses_stencil(const TaskDev& t) {
+    return t.fir2d && t.m == 1 && t.s0 == 1 && t.s1 == 1 && t.p0 == t.p1 && (t.p0 == 3 || t.p0 == 5);
+}
+
 cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
     static bool attr = false;
     const int ww = t.s1 * (t.bw - 1) + t.p1, wh = t.s0 * (t.bh - 1) + t.p0;
@@ -1099,7 +1103,7 @@ cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (t.m == 1 && t.s0 == 1 && t.s1 == 1 && t.p0 == t.p1 && (t.p0 == 3 || t.p0 == 5)) {
+    if (fir2d_uses_stencil(t)) {
         const int64_t sx = (t.rep[3] + kStencilBw - 1) / kStencilBw, sy = (t.rep[2] + kStencilBh - 1) / kStencilBh;
         const uint32_t ntiles = (uint32_t)(sx * sy);   // fewer tiles than the general tiling: < 2^31
         static int occ3 = 0, occ5 = 0;

@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(B):
 def test_struct_layout_matches(B):
     for i, cls in enumerate((B.ArrayDesc, B.Tiler, B.TaskDesc, B.TaskInfo)):
         assert B.lib.arol_abi_struct_size(i) == ctypes.sizeof(cls)
-    assert B.arol_version() == 100
+    assert B.arol_version() == 101
 
 
 def _err(B, spec):
@@ -229,3 +229,49 @@ def test_tune_off_keeps_the_launch_shape_without_device_work(B):
     env = dict(os.environ, AROL_TUNE="off")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr
+
+
+def _path(B, spec):
+    h = B.arol_task_create(spec)
+    try:
+        return B.arol_task_info(h)["path"]
+    finally:
+        B.arol_task_destroy(h)
+
+
+def _fir2d(n0, n1, p0, p1, s0=1, s1=1, m=1, dtype="f32"):
+    R0, R1 = -(-n0 // s0), -(-n1 // s1)
+    inp = W.port((n0, n1), (-(p0 // 2), -(p1 // 2)), ((s0, 0), (0, s1)), ((1, 0), (0, 1)), (p0, p1), dtype)
+    out = W.port((R0, m * R1), (0, 0), ((1, 0), (0, m)), ((0,), (1,)), (m,), dtype)
+    return W.task((R0, R1), "fir", [inp], [out], np.ones((m, p0 * p1), np.float32))
+
+
+def test_info_reports_the_kernel_path(B):
+    """Which kernel a single task takes, decided on the host: the staged row
+    and column FIR tiles, the 2-D window tiles and the register-blocked
+    stencil are f32-only paths; 16-bit storage, copies and anything else take
+    the per-repetition walk."""
+    tk, _ = W.config0()
+    assert _path(B, tk) == 1                                              # row FIR, step 4, wrap
+    assert _path(B, dict(tk, inputs=[dict(tk["inputs"][0], dtype="f16")])) == 0
+    assert _path(B, dict(tk, outputs=[dict(tk["outputs"][0], dtype="bf16")])) == 0
+    col = W.task((16, 64), "fir", [W.port((64, 64), (0, 0), ((4, 0), (0, 1)), ((1,), (0,)), (8,))],
+                 [W.port((48, 64), (0, 0), ((3, 0), (0, 1)), ((1,), (0,)), (3,))], np.ones((3, 8), np.float32))
+    assert _path(B, col) == 2                                             # column FIR
+    assert _path(B, _fir2d(8192, 8192, 3, 3)) == 4                        # the bench's 3x3 stencil
+    assert _path(B, _fir2d(70, 130, 5, 5)) == 4
+    assert _path(B, _fir2d(64, 96, 3, 3, m=2)) == 3                       # two outputs: 2-D window tiles
+    assert _path(B, _fir2d(300, 700, 5, 7)) == 3                          # not square
+    assert _path(B, _fir2d(90, 200, 3, 3, s0=2)) == 3                     # strided
+    assert _path(B, _fir2d(8192, 8192, 3, 3, dtype="f16")) == 0           # 16-bit storage
+    cp = W.random_tiler_task(W.rng(3), "copy")
+    assert _path(B, cp) == 0
+    mm = B.arol_task_create(W.matmul_task(256, 256, 128))
+    assert B.arol_task_info(mm)["kernel"] == 2 and B.arol_task_info(mm)["path"] == -1
+    B.arol_task_destroy(mm)
+    chain = W.downscale_chain(2, 16, 64, np.ones((3, 8), np.float32), np.ones((3, 8), np.float32))
+    subs = [B.arol_task_create(s) for s in chain]
+    h = B.arol_chain_create(subs)
+    assert B.arol_task_info(h)["path"] == -1
+    for x in subs + [h]:
+        B.arol_task_destroy(x)
