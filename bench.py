@@ -5,12 +5,20 @@ on 64 float32 frames of 1080x1920 -> 64 x 405 x 720, one fused kernel launch
 through the C ABI.  Metric: tiler elements per second (pattern elements
 gathered + elements scattered, both tasks) and the fraction of the measured
 HBM copy bandwidth reached by the kernel on its algorithmic bytes (input read
-once, output written once).  The same JSON line also reports the batched
-uneven workload (512 tasks, one graph launch vs one launch per task), the
-backward pass (fwd+bwd over fwd, 16 frames) and the tensor-core matmul task
-(4096^3 bf16 -> f32).
+once, output written once).  The same JSON line also reports, with L2
+emptied before each timed call:
+
+  * the 64x64 task's latency per call;
+  * the batched uneven workload (512 tasks, one graph launch vs one launch
+    per task) and 128 batched two-stage chains;
+  * the 3x3 stencil on 8192x8192 (a FIR on a 2-D pattern);
+  * the backward pass (fwd+bwd over fwd, 16 frames);
+  * the tensor-core matmul task (4096^3 bf16 -> f32);
+  * the chain with bf16 and with IEEE half storage;
+  * the conjugate-gradient solve and its SpMV.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --case batched|chains|stencil|backward|matmul|config0|cg|bf16|f16
 
 Under torchrun every rank runs its own 64 frames (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
