@@ -348,21 +348,36 @@ arol_status arol_cg_last_error(char* buf, size_t len);
  * must be multiples of 8.
  *
  * Nothing is allocated: not by cudaMalloc, cudaFree or any allocating library
- * routine.  The only scratch (one 48-float partial per CTA) is a static device
- * array of 1024 partials (192 KiB) that every GPU loading this library keeps
- * until the process exits; a device that would launch more CTAs than that gets
- * AROL_ERR_UNSUPPORTED, as do frames * height/8 * width/4 >= 2^31 work items.
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.  All
- * calls share the array: every CTA overwrites its partials before they are
- * read, so nothing needs clearing, but calls that overlap on the GPU (two
- * streams, or two host threads) race on it and must be serialized by the
- * caller.  Returns AROL_ERR_INVALID for null inputs, unaligned buffers or
- * sizes not multiples of 8; this entry point does not record a message for
- * arol_last_error. */
+ * routine.  The only scratch (one 48-float partial per CTA, a ticket word and
+ * an error word) is a static device array of 1024 partials (192 KiB) that
+ * every GPU loading this library keeps until the process exits; the launch
+ * uses at most 1024 CTAs (the kernels stride over the work, so a device that
+ * could hold more still gets the whole result).  frames * height/8 * width/4
+ * >= 2^31 work items gives AROL_ERR_UNSUPPORTED.  The first call on each
+ * device looks up the array's device address (with that device current);
+ * make that first call before any stream capture.  All calls share the array:
+ * every CTA overwrites its partials before they are read and every launch
+ * leaves the ticket at zero, so nothing needs clearing, but calls that
+ * overlap on the GPU (two streams, or two host threads) race on it and must
+ * be serialized by the caller.  Returns AROL_ERR_INVALID for null inputs,
+ * unaligned buffers or sizes not multiples of 8; this entry point does not
+ * record a message for arol_last_error.
+ *
+ * Device-side timeouts: every wait inside the kernel is bounded; a wait that
+ * gives up sets the array's error word and leaves the gradients incomplete.
+ * The call itself returns before the kernel runs, so it cannot see that;
+ * arol_downscale_backward_noalloc_status reports it. */
 arol_status arol_downscale_backward_noalloc(const float* x, const float* grad_out, const float* taps,
                                             int64_t frames, int32_t height, int32_t width,
                                             float* grad_in, float* grad_taps, void* stream);
+
+/* Status of the no-allocation backward on the current device (the paper has
+ * no counterpart either): synchronizes `stream`, then returns
+ * AROL_ERR_TIMEOUT if a bounded wait of any arol_downscale_backward_noalloc
+ * launch gave up since the last query (clearing the error word), else
+ * AROL_OK; AROL_ERR_CUDA if the copy fails.  Allocates nothing; it is a
+ * synchronizing call, so it does not belong inside a stream capture. */
+arol_status arol_downscale_backward_noalloc_status(void* stream);
 
 #ifdef __cplusplus
 }

@@ -77,6 +77,7 @@ def _load():
         "arol_batch_config": [c_vp, P(c_i64), P(c_i32), P(c_i32)],
         "arol_last_error": [ctypes.c_char_p, ctypes.c_size_t],
         "arol_downscale_backward_noalloc": [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp],
+        "arol_downscale_backward_noalloc_status": [c_vp],
         "arol_csr_spmv": [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
         "arol_cg_create": [c_i64, c_i64, c_vp, c_vp, c_vp, P(c_vp)],
         "arol_csr_check": [c_i64, c_i64, c_vp, c_vp, c_vp],
@@ -310,6 +311,14 @@ def arol_downscale_backward_noalloc(x, grad_out, taps, frames, height, width, gr
                                              int(width), _ptr(grad_in), _ptr(grad_taps), _stream(stream))
     if st != 0:
         raise ArolError(st, "arol_downscale_backward_noalloc rejected the call")
+
+
+def arol_downscale_backward_noalloc_status(stream=None):
+    """Synchronizes the stream; raises ArolError (AROL_ERR_TIMEOUT) if a bounded
+    wait of the no-allocation backward gave up since the last query."""
+    st = lib.arol_downscale_backward_noalloc_status(_stream(stream))
+    if st != 0:
+        raise ArolError(st, "arol_downscale_backward_noalloc: a device-side wait gave up")
 
 
 def _check_cg(st):

@@ -969,14 +969,32 @@ cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int ca
 namespace arol {
 namespace {
 
-constexpr int kNoAllocMaxParts = 1024;   // CTAs whose partials fit: 1024 x 48 floats = 192 KiB
-// the 48-float partial of each CTA, then one word: the CTAs-done ticket of the
-// last-CTA reduction (zero at load; every launch leaves it at zero)
+constexpr int kNoAllocMaxParts = 1024;   // CTA partials the array holds: 1024 x 48 floats = 192 KiB
+constexpr int kNoAllocTicket = kNoAllocMaxParts * kTapGrads;   // word: CTAs done (each launch leaves it at 0)
+constexpr int kNoAllocErr = kNoAllocTicket + 1;                 // word: bounded waits that gave up (sticky)
+// the 48-float partial of each CTA, then the ticket of the last-CTA reduction
+// and the error word (both zero at load)
 static __device__ __align__(256) float g_noalloc_partials[kNoAllocMaxParts * kTapGrads + 4];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 float* g_noalloc_ptr[kMaxDevices] = {};
+
+// The device address of the static array on the current device, looked up
+// once per device with that device current (host code only knows a host-side
+// stand-in for the array; the device address comes from the runtime).
+arol_status noalloc_scratch(float** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AROL_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return AROL_ERR_CUDA;
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return AROL_OK;
+}
 
 }  // namespace
 
@@ -991,42 +1009,44 @@ extern "C" arol_status arol_downscale_backward_noalloc(const float* x, const flo
     if ((double)frames * (height / 8) * (width / 4) >= 2147483647.0) return AROL_ERR_UNSUPPORTED;
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(grad_in) | reinterpret_cast<uintptr_t>(grad_out)) & 15u)
         return AROL_ERR_INVALID;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AROL_ERR_CUDA;
     float* scratch = nullptr;
-    {
-        // One-time set-up per device, with that device current: host code only
-        // knows a host-side stand-in for the array; the device address comes
-        // from the runtime.
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return AROL_ERR_CUDA;
-            g_noalloc_ptr[dev] = static_cast<float*>(p);
-        }
-        scratch = g_noalloc_ptr[dev];
-    }
-    const int nparts = downscale_bwd_partials(device_sm_count(), width);
-    if (nparts > kNoAllocMaxParts) return AROL_ERR_UNSUPPORTED;   // more CTAs than the static scratch holds
+    const arol_status st = noalloc_scratch(&scratch);
+    if (st != AROL_OK) return st;
     if (frames == 0 || height == 0 || width == 0) {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         if (grad_taps && cudaMemsetAsync(grad_taps, 0, kTapGrads * sizeof(float), s) != cudaSuccess) return AROL_ERR_CUDA;
         return AROL_OK;
     }
-    DownscaleDev p;
+    DownscaleDev p{};
     p.x = x;
-    p.y = nullptr;
     p.taps = taps;
     p.gy = grad_out;
     p.gx = grad_in;
-    p.err = nullptr;
-    p.grad_taps = nullptr;
+    p.err = reinterpret_cast<unsigned*>(scratch + kNoAllocErr);
     p.partials = scratch;   // every CTA overwrites its own 48 slots before the reduction reads them
-    p.ticket = reinterpret_cast<unsigned*>(scratch + kNoAllocMaxParts * kTapGrads);
+    p.ticket = reinterpret_cast<unsigned*>(scratch + kNoAllocTicket);
     p.frames = frames;
     p.H = height;
     p.W = width;
-    if (launch_downscale_bwd(p, grad_taps, nparts, false, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    // at most kNoAllocMaxParts CTAs: the kernels stride over the work, so a
+    // smaller grid than the device could hold still covers it
+    if (launch_downscale_bwd(p, grad_taps, kNoAllocMaxParts, false, static_cast<cudaStream_t>(stream)) != cudaSuccess)
         return AROL_ERR_CUDA;
     return AROL_OK;
+}
+
+extern "C" arol_status arol_downscale_backward_noalloc_status(void* stream) {
+    using namespace arol;
+    float* scratch = nullptr;
+    arol_status st = noalloc_scratch(&scratch);
+    if (st != AROL_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned word = 0;
+    if (cudaMemcpyAsync(&word, scratch + kNoAllocErr, sizeof word, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return AROL_ERR_CUDA;
+    if (!word) return AROL_OK;
+    if (cudaMemsetAsync(scratch + kNoAllocErr, 0, sizeof word, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return AROL_ERR_CUDA;
+    return AROL_ERR_TIMEOUT;
 }

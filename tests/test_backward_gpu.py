@@ -84,6 +84,30 @@ def test_backward_config4_full_size(arol):
     check_chain_grads(arol, chain, x, w.astype(np.float64), vjp=C.chain_vjp)
 
 
+def test_fwd_bwd_config4_full_size_against_oracle(arol):
+    """The fused forward+backward entry at the size it is timed at (16 frames
+    of 1080 x 1920): output, dX and both tap gradients element by element
+    against the C oracle's FP64 forward and adjoint."""
+    chain, (x,), w = W.config4()
+    c = arol.Chain(chain)
+    xd, wd = dev(x), dev(w)
+    y = torch.empty(chain[-1]["outputs"][0]["shape"], device="cuda")
+    gx = torch.empty_like(xd)
+    gt = torch.empty(48, device="cuda")
+    c.fwd_bwd([xd], wd, y, gx, gt)
+    c.sync_status()
+    assert c.info["kernel"] == 1
+    w64 = w.astype(np.float64)
+    assert_fir_close(host(y), C.run_chain(chain, [x])[0],
+                     C.run_chain(_abs_chain(chain), [np.abs(x).astype(np.float64)])[0], RTOL, "fwd_bwd y")
+    dX, (dHh, dHv) = C.chain_vjp(chain, [x], w64)
+    sX, (sHh, sHv) = C.chain_vjp(_abs_chain(chain), [np.abs(x)], np.abs(w64))
+    assert_fir_close(host(gx), dX, sX, RTOL, "fwd_bwd dX")
+    g = host(gt)
+    assert_fir_close(g[:24].reshape(3, 8), dHh, sHh, RTOL, "fwd_bwd dHh")
+    assert_fir_close(g[24:].reshape(3, 8), dHv, sHv, RTOL, "fwd_bwd dHv")
+
+
 def test_fwd_bwd_equals_separate_calls_and_is_deterministic(arol):
     chain, (x,), w = W.config4(frames=2, height=64, width=128)
     c = arol.Chain(chain)

@@ -241,6 +241,19 @@ def test_f16_round_known_values():
     np.testing.assert_array_equal(W.f16_round(v).view(np.uint16), want)
 
 
+def test_oracle_reads_bf16_values():
+    """The oracle's bf16 reads against values decoded by hand from bfloat16
+    fields (sign, 8-bit exponent with bias 127, 7-bit fraction):
+    0x4049 = +2^(128-127) * (1 + 73/128), 0xC2F7 = -2^6 * (1 + 119/128),
+    0x3EAB = 2^-2 * (1 + 43/128), 0x0001 and 0x007F the smallest and largest
+    subnormals (fraction/128 * 2^-126), 0x7F7F the largest finite value."""
+    bits = np.array([0x3F80, 0x4049, 0xC2F7, 0x3EAB, 0x0001, 0x007F, 0x7F7F, 0x8000], np.uint16)
+    want = [1.0, 3.140625, -123.5, 0.333984375, 2.0 ** -133, 127 * 2.0 ** -133, 255 * 2.0 ** 120, 0.0]
+    got = O._as_values(bits, "bf16")
+    assert got.dtype == np.float64 and list(got) == want
+    assert np.signbit(got[-1]) and not np.signbit(got[0])   # 0x8000 is -0
+
+
 def test_oracle_reads_f16_values():
     """The oracle's f16 reads against values decoded by hand from binary16
     fields (sign, 5-bit exponent with bias 15, 10-bit fraction)."""

@@ -260,11 +260,12 @@ def test_batch_config3_matches_per_task_and_oracle(arol):
     outs2 = b.empty_outputs()
     b.run_per_task(ins, outs2)
     torch.cuda.synchronize()
+    # every instance against the C oracle (the per-task launches run the same
+    # kernel body, so equality with them alone would check the path against itself)
     for i, (tk, x) in enumerate(zip(tasks, xs)):
         y = host(outs[i])
+        assert_fir_close(y, C.run_task(tk, [x])[0], fir_scale(tk, x, C.run_chain), what=f"instance {i}")
         np.testing.assert_array_equal(y, host(outs2[i]))
-        if i % 8 == 0:
-            assert_fir_close(y, C.run_task(tk, [x])[0], fir_scale(tk, x, C.run_chain), what=f"instance {i}")
     # the autotuner changes the tiling, not the results; new buffers refresh the table
     b.tune(ins, outs, force=True)
     outs3 = b.empty_outputs()
