@@ -48,6 +48,11 @@ WORKLOAD = "downscale chain 64x1080x1920 f32 -> 64x405x720 (8-tap->3 FIR, step 8
 L2_BYTES = 126 * 1024 * 1024
 
 
+# FP32 FMA peak derived from the part's unit counts and clock: 152 SMs x 128
+# FP32 lanes x 2 flops x 2.07 GHz (the maximum SM clock).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def chain_units(frames, height=HEIGHT, width=WIDTH):
     """Tiler elements of one pass of the chain: gathered + scattered, both tasks."""
     wr, hr = width // 8, height // 8
@@ -318,10 +323,15 @@ def bench_batched(A, torch, stream, flush, reps, tune=True):
     nbytes = sum(4 * x.size for x in xs) + sum(4 * int(np.prod(t["outputs"][0]["shape"])) for t in tasks)
     units = sum(t["rep"][0] * t["rep"][1] * (t["inputs"][0]["pattern"][0] + t["outputs"][0]["pattern"][0])
                 for t in tasks)
+    # FIR multiply-adds: repetitions x m x T per task
+    fma = sum(t["rep"][0] * t["rep"][1] * t["taps"].size for t in tasks)
     tb, tp = statistics.median(batched), statistics.median(per_task)
+    b.sync_status()
     return {"tasks": len(tasks), "unique_bytes": nbytes, "tiler_elems": units,
             "batched_ms": tb, "per_task_ms": tp, "speedup": tp / tb,
             "batched_gbs": nbytes / (tb * 1e-3) / 1e9, "batched_elems_per_s": units / (tb * 1e-3),
+            "fma": fma, "fp32_tflops": 2 * fma / (tb * 1e-3) / 1e12,
+            "fp32_frac_of_derived_peak": 2 * fma / (tb * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
             "launches_batched": 1, "launches_per_task": len(tasks), "autotuned": cfg}
 
 

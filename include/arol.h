@@ -228,9 +228,12 @@ arol_status arol_selftest_wait_timeout(void* stream);
  * one per stage, without the fused chain kernels.  The batch copies the
  * descriptors and host taps (the handles may be destroyed afterwards), owns
  * one device arena for every chain intermediate, a device work list of
- * (task, repetition range) tiles grouped by stage, built on first run, and a
- * CUDA graph that launches one persistent kernel per stage: stage k of every
- * chain runs after stage k - 1 of every chain.  Matmul tasks and tasks whose
+ * tiles grouped by stage, built on first run, and a CUDA graph that launches
+ * the persistent kernels of each stage: stage k of every chain runs after
+ * stage k - 1 of every chain.  Row-FIR tasks (one row per repetition row,
+ * step <= 32 along it, T <= 32, m <= 16, f32) run as tiles of whole rows or
+ * row pieces on the row-FIR kernel; the others as repetition ranges on the
+ * general persistent kernel.  Matmul tasks and tasks whose
  * taps live on the device are rejected (AROL_ERR_UNSUPPORTED /
  * AROL_ERR_INVALID). */
 arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out);
@@ -247,8 +250,11 @@ arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out
  * tile counter (for comparison with arol_batch_run). */
 arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* const* out, void* stream);
 
-/* Autotune the batch's tile size and persistent-grid shape by timing
- * candidates on the given buffers (outputs are overwritten).  Results are
+/* Autotune the batch's tile shapes and grid sizes by timing candidates on
+ * the given buffers (outputs are overwritten): for row-FIR tasks the shared
+ * memory a row tile may fill and the CTAs per SM of the row-FIR kernel, for
+ * the other tasks the repetitions per tile and CTAs per SM of the persistent
+ * kernel.  Results are
  * cached per process by batch signature and device, and persisted as JSON in
  * the file named by the AROL_TUNE_CACHE environment variable when it is set.
  * force = 1 re-times even when a cached choice exists.  Synchronizes.
@@ -259,6 +265,11 @@ arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* ou
 
 /* The tile size (repetitions per tile) and CTAs per SM in use. */
 arol_status arol_batch_config(arol_batch b, int64_t* tile_reps, int32_t* ctas_per_sm, int32_t* threads);
+
+/* Synchronizes `stream`, then reports AROL_ERR_TIMEOUT if a bounded wait
+ * inside the batch's kernels gave up since the last query (the word is
+ * cleared), else AROL_OK. */
+arol_status arol_batch_sync_status(arol_batch b, void* stream);
 
 void arol_batch_destroy(arol_batch b);
 

@@ -133,8 +133,8 @@ class Chain(Task):
 
 class Batch:
     """Independent copy/fir tasks and chains of them, run by one graph
-    launch: one persistent launch per chain stage over every member's tiles
-    of that stage.  A member is a task spec or a list of specs (a chain,
+    launch: the persistent launches of each chain stage over every member's
+    tiles of that stage.  A member is a task spec or a list of specs (a chain,
     whose intermediates the batch allocates); its input is the first task's
     input, its output the last task's output."""
 
@@ -189,6 +189,10 @@ class Batch:
     def tune(self, ins, outs, stream=None, force=False):
         B.arol_batch_tune(self.handle, list(ins), list(outs), stream, force)
         return self.config
+
+    def sync_status(self, stream=None):
+        """Synchronizes; raises ArolError if a bounded device wait gave up."""
+        B.arol_batch_sync_status(self.handle, stream)
 
     @property
     def config(self):

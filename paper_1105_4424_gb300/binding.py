@@ -75,6 +75,7 @@ def _load():
         "arol_batch_run_per_task": [c_vp, P(c_vp), P(c_vp), c_vp],
         "arol_batch_tune": [c_vp, P(c_vp), P(c_vp), c_vp, ctypes.c_int],
         "arol_batch_config": [c_vp, P(c_i64), P(c_i32), P(c_i32)],
+        "arol_batch_sync_status": [c_vp, c_vp],
         "arol_last_error": [ctypes.c_char_p, ctypes.c_size_t],
         "arol_downscale_backward_noalloc": [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp],
         "arol_downscale_backward_noalloc_status": [c_vp],
@@ -296,6 +297,10 @@ def arol_batch_config(b) -> dict:
     tile, ctas, thr = c_i64(), c_i32(), c_i32()
     _check(lib.arol_batch_config(b, ctypes.byref(tile), ctypes.byref(ctas), ctypes.byref(thr)))
     return {"tile_reps": tile.value, "ctas_per_sm": ctas.value, "threads": thr.value}
+
+
+def arol_batch_sync_status(b, stream=None):
+    _check(lib.arol_batch_sync_status(b, _stream(stream)))
 
 
 def arol_batch_destroy(b):

@@ -503,8 +503,6 @@ TaskDev make_taskdev_exact(const arol_task_desc& d) {
         t.rowfir = 1;
         t.step = (int32_t)emod(ti.paving[1][1], d.in[0].shape[1]);
         if (t.step < 1) t.rowfir = 0;
-        t.wfull = t.step * (int32_t)(d.rep[1] > 0 ? d.rep[1] - 1 : 0) + d.fir_T;
-        t.wfull_div = make_fastdiv((uint32_t)std::max(t.wfull, 1));
     }
     // Column FIR: one column per r1, step down the rows per r0, the pattern
     // running down the rows, m consecutive output rows per repetition.
@@ -1425,6 +1423,10 @@ arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* gr
 arol_status arol_task_sync_status(arol_task t, void* stream) {
     if (!t) return fail(AROL_ERR_INVALID, "null task");
     AROL_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
+    if (t->ib) {
+        const arol_status bs = arol_batch_sync_status(t->ib, stream);
+        if (bs != AROL_OK) return bs;
+    }
     if (t->err_flag) {
         unsigned flag = 0;
         AROL_CUDA(cudaMemcpy(&flag, t->err_flag, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
@@ -1500,6 +1502,16 @@ struct arol_batch_s {
     int ntiles = 0;
     TileDev* dev_tiles_pt = nullptr;      // the same tiles grouped by task, for one launch per task
     std::vector<int> pt_off, pt_cnt;
+    // row-FIR tiles (k_rowfir.cu): by stage, and the same grouped by task
+    std::vector<RowTileDev> rtiles, rtiles_pt;
+    std::vector<int> rstage_off, rstage_cnt, rpt_off, rpt_cnt;
+    RowTileDev* dev_rtiles = nullptr;
+    RowTileDev* dev_rtiles_pt = nullptr;
+    RowTileDev* pinned_rtiles = nullptr;  // both lists back to back, for the upload
+    int64_t rtiles_cap = 0;
+    int row_budget = kRowSlotFloats;      // slot floats a row tile may fill (autotuned)
+    int row_ctas = 0;                     // row-FIR CTAs per SM (0: as many as fit; autotuned)
+    unsigned* err = nullptr;              // bounded device waits that gave up (bits)
     unsigned* counter = nullptr;
     float* taps_dev = nullptr;
     bool tables_built = false;
@@ -1545,7 +1557,8 @@ std::string batch_signature(arol_batch b) {
     return buf;
 }
 
-// The cache file is a flat JSON object: {"<signature>": [tile, threads, ctas], ...}
+// The cache file is a flat JSON object:
+// {"<signature>": [tile, threads, ctas, row_budget, row_ctas], ...}
 void tune_cache_load() {
     if (g_tune_loaded) return;
     g_tune_loaded = true;
@@ -1561,12 +1574,11 @@ void tune_cache_load() {
         size_t end = s.find('"', pos + 1);
         if (end == std::string::npos) break;
         std::string key = s.substr(pos + 1, end - pos - 1);
-        long long a = 0, b2 = 0, c = 0;
+        long long v[5] = {0, 0, 0, 0, 0};
         size_t lb = s.find('[', end);
         if (lb == std::string::npos) break;
-        if (std::sscanf(s.c_str() + lb, "[%lld , %lld , %lld]", &a, &b2, &c) == 3 ||
-            std::sscanf(s.c_str() + lb, "[%lld, %lld, %lld]", &a, &b2, &c) == 3)
-            g_tune_cache[key] = {a, b2, c};
+        if (std::sscanf(s.c_str() + lb, "[%lld , %lld , %lld , %lld , %lld]", &v[0], &v[1], &v[2], &v[3], &v[4]) == 5)
+            g_tune_cache[key] = {v[0], v[1], v[2], v[3], v[4]};
         pos = s.find(']', lb);
         if (pos == std::string::npos) break;
     }
@@ -1581,8 +1593,9 @@ void tune_cache_save() {
     f << "{";
     bool first = true;
     for (auto& kv : g_tune_cache) {
-        f << (first ? "\n" : ",\n") << "  \"" << kv.first << "\": [" << kv.second[0] << ", " << kv.second[1] << ", "
-          << kv.second[2] << "]";
+        f << (first ? "\n" : ",\n") << "  \"" << kv.first << "\": [";
+        for (size_t q = 0; q < kv.second.size(); ++q) f << (q ? ", " : "") << kv.second[q];
+        f << "]";
         first = false;
     }
     f << "\n}\n";
@@ -1597,6 +1610,91 @@ void invalidate_graph(arol_batch b) {
     b->graph = nullptr;
 }
 
+// Shared-memory bank conflict degree of one warp of the row-FIR kernel that
+// covers a rows x 32/a consecutive repetitions: lane (k, j) reads word
+// 4 ((k >> 2) & 7) + (k W mod 4) + S j (mod 32) of its tile at every tap
+// (row slot placement and 16-byte-preserving bulk copies; the tile's first
+// row and column shift every lane alike).
+int rowfir_conflicts(int a, int64_t W, int S) {
+    int count[32] = {0}, worst = 0;
+    for (int k = 0; k < a; ++k)
+        for (int j = 0; j < 32 / a; ++j) {
+            const int bank = (int)((4 * ((k >> 2) & 7) + (int)((k * W) & 3) + S * j) & 31);
+            worst = std::max(worst, ++count[bank]);
+        }
+    return worst;
+}
+
+// Row tiles of a row-FIR task: rows per warp unit (a), repetitions per row
+// piece (cnt) and rows per tile (<= 32) are chosen for the fewest bank
+// conflicts per useful lane, within `budget` slot floats per tile.
+void build_row_tiles(const TaskDev& t, int task, int budget, std::vector<RowTileDev>& out) {
+    const int S = t.step, T = t.T, M = t.m;
+    const int64_t W = t.in.shape[1], H = t.in.shape[0], Wo = t.out.shape[1], Ho = t.out.shape[0];
+    const int64_t R0 = t.rep[2], R1 = t.rep[3];
+    if (R0 <= 0 || R1 <= 0) return;
+    auto ss_of = [&](int64_t cnt) { return (int)((S * (cnt - 1) + T + 6 + 31) & ~int64_t(31)); };
+    double best = 1e300;
+    int ba = 1;
+    int64_t bcnt = 1, brows = 1;
+    for (int a = 1; a <= 32; a *= 2) {
+        if (a > 1 && a > R0) break;
+        const int b = 32 / a;
+        const int64_t cmax = ((budget / a) - T - 37) / S + 1;   // ss_of(cmax) * a <= budget
+        if (cmax < 1) break;
+        int64_t cnt = std::min<int64_t>(R1, cmax);
+        const int64_t pieces = (R1 + cnt - 1) / cnt;
+        cnt = (R1 + pieces - 1) / pieces;
+        int64_t rows = std::min<int64_t>({32, R0, (int64_t)(budget / ss_of(cnt))});
+        rows = rows / a * a;
+        if (rows < a) continue;
+        const double used = (double)cnt / (double)(b * ((cnt + b - 1) / b));
+        const double score = rowfir_conflicts(a, W, S) / used;
+        if (score < best * 0.999 || (score <= best * 1.001 && rows * cnt > brows * bcnt)) {
+            best = score;
+            ba = a;
+            bcnt = cnt;
+            brows = rows;
+        }
+    }
+    for (int64_t r0 = 0; r0 < R0; r0 += brows)
+        for (int64_t a0 = 0; a0 < R1; a0 += bcnt) {
+            RowTileDev rt;
+            std::memset(&rt, 0, sizeof rt);
+            const int64_t cnt = std::min<int64_t>(bcnt, R1 - a0);
+            rt.W = (int32_t)W;
+            rt.H = (int32_t)H;
+            rt.Wout = (int32_t)Wo;
+            rt.Hout = (int32_t)Ho;
+            rt.row0 = (int32_t)(((int64_t)t.in.origin[0] + r0) % H);
+            rt.orow0 = (int32_t)(((int64_t)t.out.origin[0] + r0) % Ho);
+            rt.nrows = (int32_t)std::min<int64_t>(brows, R0 - r0);
+            rt.c0 = (int32_t)(((int64_t)t.in.origin[1] + (int64_t)S * a0) % W);
+            rt.oc0 = (int32_t)(((int64_t)t.out.origin[1] + (int64_t)M * a0) % Wo);
+            rt.cnt = (int32_t)cnt;
+            rt.S = S;
+            rt.T = T;
+            rt.M = M;
+            rt.lw = (int32_t)(S * (cnt - 1) + T);
+            rt.ss = ss_of(cnt);
+            rt.a = ba;
+            rt.out_wrap = rt.oc0 + M * cnt > Wo ? 1 : 0;
+            rt.task = task;
+            out.push_back(rt);
+        }
+}
+
+// Row tiles carry their task's current buffers and transposed taps.
+void fill_row_tile_ptrs(arol_batch b) {
+    for (std::vector<RowTileDev>* v : {&b->rtiles, &b->rtiles_pt})
+        for (RowTileDev& rt : *v) {
+            const TaskDev& t = b->host_tasks[rt.task];
+            rt.x = static_cast<const float*>(t.x);
+            rt.y = static_cast<float*>(t.y);
+            rt.taps_t = t.taps_t;
+        }
+}
+
 // Tiles of at most tile_reps repetitions, grouped by chain stage (stage k of
 // every chain runs in the k-th launch, after stage k-1 has finished), most
 // expensive tasks first within a stage (a longest-processing-time order for
@@ -1607,49 +1705,22 @@ arol_status build_tiles(arol_batch b) {
         return (double)t.nreps * (t.T + t.m);
     };
     std::vector<TileDev> tiles;
+    std::vector<RowTileDev> rtiles;
     b->stage_off.assign(b->nstages, 0);
     b->stage_cnt.assign(b->nstages, 0);
+    b->rstage_off.assign(b->nstages, 0);
+    b->rstage_cnt.assign(b->nstages, 0);
     for (int stage = 0; stage < b->nstages; ++stage) {
         b->stage_off[stage] = (int)std::min<size_t>(tiles.size(), 2147483647);
         std::vector<int> order;
         for (size_t i = 0; i < b->host_tasks.size(); ++i)
             if (b->stage_of[i] == stage) order.push_back((int)i);
         std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+        b->rstage_off[stage] = (int)std::min<size_t>(rtiles.size(), 2147483647);
         for (int i : order) {
             const TaskDev& t = b->host_tasks[i];
             if (t.rowfir) {
-                // Row tiles: pieces of at most cmax repetitions of a long row
-                // (their window, step * (count - 1) + T words, fits kWinFloats),
-                // or as many whole short rows as fit kRowTile repetitions and a
-                // staged window of kWinFloats floats.
-                const int64_t R1 = t.rep[3];
-                const int64_t cmax = std::min<int64_t>(kRowTile, (kWinFloats - t.T) / t.step + 1);
-                if (R1 > cmax) {
-                    for (int64_t r0 = 0; r0 < t.rep[2]; ++r0)
-                        for (int64_t a = 0; a < R1; a += cmax) {
-                            TileDev td;
-                            td.task = i;
-                            td.start = r0 * R1 + a;
-                            td.count = (int32_t)std::min<int64_t>(cmax, R1 - a);
-                            tiles.push_back(td);
-                        }
-                } else if (R1 > 0) {
-                    // Whole rows per tile: at most kRowTile repetitions, the rows
-                    // themselves (W words each) within the staged window, no row
-                    // twice (rows <= H), and extents below 2^30 so that column
-                    // sums stay inside the 31-bit division.
-                    const int64_t W = t.in.shape[1], H = t.in.shape[0];
-                    int64_t per = std::min<int64_t>(kRowTile / R1, kWinFloats / W);
-                    per = std::min<int64_t>(per, H);
-                    if (H >= (1 << 30) || W >= (1 << 30) || per < 2) per = 1;
-                    for (int64_t r0 = 0; r0 < t.rep[2]; r0 += per) {
-                        TileDev td;
-                        td.task = i;
-                        td.start = r0 * R1;
-                        td.count = (int32_t)(std::min<int64_t>(per, t.rep[2] - r0) * R1);
-                        tiles.push_back(td);
-                    }
-                }
+                build_row_tiles(t, i, b->row_budget, rtiles);
                 continue;
             }
             for (int64_t s = 0; s < t.nreps; s += b->tile_reps) {
@@ -1661,8 +1732,40 @@ arol_status build_tiles(arol_batch b) {
             }
         }
         b->stage_cnt[stage] = (int)std::min<size_t>(tiles.size() - b->stage_off[stage], 2147483647);
+        b->rstage_cnt[stage] = (int)std::min<size_t>(rtiles.size() - b->rstage_off[stage], 2147483647);
     }
-    if ((int64_t)tiles.size() >= 2147483647LL) return fail(AROL_ERR_UNSUPPORTED, "batch: too many tiles");
+    if ((int64_t)tiles.size() >= 2147483647LL || (int64_t)rtiles.size() >= 2147483647LL)
+        return fail(AROL_ERR_UNSUPPORTED, "batch: too many tiles");
+    // row tiles: the same list grouped by task, for one launch per task
+    b->rtiles = rtiles;
+    b->rtiles_pt = rtiles;
+    std::stable_sort(b->rtiles_pt.begin(), b->rtiles_pt.end(),
+                     [](const RowTileDev& x, const RowTileDev& y) { return x.task < y.task; });
+    b->rpt_off.assign(b->host_tasks.size(), 0);
+    b->rpt_cnt.assign(b->host_tasks.size(), 0);
+    for (size_t k = 0; k < b->rtiles_pt.size(); ++k)
+        if (b->rpt_cnt[b->rtiles_pt[k].task]++ == 0) b->rpt_off[b->rtiles_pt[k].task] = (int)k;
+    if ((int64_t)rtiles.size() > b->rtiles_cap) {
+        free_dev(b->dev_rtiles);
+        free_dev(b->dev_rtiles_pt);
+        if (b->pinned_rtiles) cudaFreeHost(b->pinned_rtiles);
+        b->dev_rtiles = b->dev_rtiles_pt = b->pinned_rtiles = nullptr;
+        b->rtiles_cap = 0;
+        const size_t bytes = std::max<size_t>(rtiles.size(), 1) * sizeof(RowTileDev);
+        AROL_CUDA(arol_malloc((void**)&b->dev_rtiles, bytes), "cudaMalloc(row tiles)");
+        AROL_CUDA(arol_malloc((void**)&b->dev_rtiles_pt, bytes), "cudaMalloc(row tiles)");
+        AROL_CUDA(cudaMallocHost((void**)&b->pinned_rtiles, 2 * bytes), "cudaMallocHost(row tiles)");
+        b->rtiles_cap = (int64_t)rtiles.size();
+    }
+    fill_row_tile_ptrs(b);
+    if (!b->rtiles.empty()) {
+        AROL_CUDA(cudaMemcpy(b->dev_rtiles, b->rtiles.data(), b->rtiles.size() * sizeof(RowTileDev),
+                             cudaMemcpyHostToDevice),
+                  "upload row tiles");
+        AROL_CUDA(cudaMemcpy(b->dev_rtiles_pt, b->rtiles_pt.data(), b->rtiles_pt.size() * sizeof(RowTileDev),
+                             cudaMemcpyHostToDevice),
+                  "upload row tiles");
+    }
     b->ntiles = (int)tiles.size();
     std::vector<TileDev> by_task(tiles);
     std::stable_sort(by_task.begin(), by_task.end(), [](const TileDev& x, const TileDev& y) { return x.task < y.task; });
@@ -1706,7 +1809,7 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
         size_t ntaps = 0;
         for (size_t i = 0; i < n; ++i) {
             ntaps += b->taps[i].size();
-            if (b->host_tasks[i].rowfir || b->host_tasks[i].colfir) ntaps += (size_t)b->host_tasks[i].T * 16;
+            if (b->host_tasks[i].rowfir || b->host_tasks[i].colfir) ntaps += 3 + (size_t)b->host_tasks[i].T * 16;
         }
         // each resource is made once: a call that failed part-way (say, out of
         // memory) is retried without leaking what it had already made
@@ -1718,6 +1821,10 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
             AROL_CUDA(cudaEventCreateWithFlags(&b->table_copied, cudaEventDisableTiming), "cudaEventCreate");
         if (!b->launched) AROL_CUDA(cudaEventCreateWithFlags(&b->launched, cudaEventDisableTiming), "cudaEventCreate");
         if (!b->counter) AROL_CUDA(arol_malloc((void**)&b->counter, sizeof(unsigned)), "cudaMalloc(counter)");
+        if (!b->err) {
+            AROL_CUDA(arol_malloc((void**)&b->err, sizeof(unsigned)), "cudaMalloc(error word)");
+            AROL_CUDA(cudaMemset(b->err, 0, sizeof(unsigned)), "clear error word");
+        }
         if (!b->taps_dev)
             AROL_CUDA(arol_malloc((void**)&b->taps_dev, std::max<size_t>(ntaps, 1) * sizeof(float)), "cudaMalloc(taps)");
         size_t off = 0;
@@ -1731,6 +1838,7 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
             }
             TaskDev& td = b->host_tasks[i];
             if (td.rowfir || td.colfir) {
+                off = (off + 3) & ~size_t(3);   // 16-byte aligned: the row-FIR kernel bulk-copies these
                 std::vector<float> ht((size_t)td.T * 16, 0.f);
                 for (int k = 0; k < td.T; ++k)
                     for (int j = 0; j < td.m; ++j) ht[(size_t)k * 16 + j] = b->taps[i][(size_t)j * td.T + k];
@@ -1772,10 +1880,23 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
             b->last_out[i] = out[i];
         }
         std::memcpy(b->pinned_tasks, b->host_tasks.data(), n * sizeof(TaskDev));
+        fill_row_tile_ptrs(b);
+        const size_t nr = b->rtiles.size();
+        if (nr) {
+            std::memcpy(b->pinned_rtiles, b->rtiles.data(), nr * sizeof(RowTileDev));
+            std::memcpy(b->pinned_rtiles + nr, b->rtiles_pt.data(), nr * sizeof(RowTileDev));
+        }
         // launches on other streams may still read the old table
         AROL_CUDA(cudaStreamWaitEvent(s, b->launched, 0), "wait for previous launches");
         AROL_CUDA(cudaMemcpyAsync(b->dev_tasks, b->pinned_tasks, n * sizeof(TaskDev), cudaMemcpyHostToDevice, s),
                   "upload task table");
+        if (nr) {
+            AROL_CUDA(cudaMemcpyAsync(b->dev_rtiles, b->pinned_rtiles, nr * sizeof(RowTileDev), cudaMemcpyHostToDevice, s),
+                      "upload row tiles");
+            AROL_CUDA(cudaMemcpyAsync(b->dev_rtiles_pt, b->pinned_rtiles + nr, nr * sizeof(RowTileDev),
+                                      cudaMemcpyHostToDevice, s),
+                      "upload row tiles");
+        }
         AROL_CUDA(cudaEventRecord(b->table_copied, s), "cudaEventRecord");
     }
     return AROL_OK;
@@ -1787,9 +1908,12 @@ arol_status batch_capture(arol_batch b) {
     AROL_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     // one launch per chain stage; stage k reads what stage k - 1 wrote
     cudaError_t le = cudaSuccess;
+    const int rgrid = b->row_ctas > 0 ? device_sm_count() * b->row_ctas : 0;
     for (int k = 0; k < b->nstages && le == cudaSuccess; ++k) {
+        if (b->rstage_cnt[k] > 0)
+            le = launch_rowfir_batch(b->dev_rtiles + b->rstage_off[k], b->rstage_cnt[k], rgrid, b->err, b->cap_stream);
         const int cnt = b->stage_cnt[k];
-        if (cnt == 0) continue;
+        if (cnt == 0 || le != cudaSuccess) continue;
         le = launch_batch_persistent(b->dev_tasks, b->dev_tiles + b->stage_off[k], cnt, b->counter,
                                      std::min(grid, cnt), b->threads, b->max_m, b->cap_stream);
     }
@@ -1874,7 +1998,11 @@ arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* c
     if (st != AROL_OK) return st;
     // one launch of the batch kernel per task, over that task's tiles only
     const int cap = device_sm_count() * b->ctas_per_sm;
+    const int rgrid = b->row_ctas > 0 ? device_sm_count() * b->row_ctas : 0;
     for (size_t i = 0; i < b->host_tasks.size(); ++i) {
+        if (b->rpt_cnt[i] > 0)
+            AROL_CUDA(launch_rowfir_batch(b->dev_rtiles_pt + b->rpt_off[i], b->rpt_cnt[i], rgrid, b->err, s),
+                      "row-FIR kernel launch");
         const int cnt = b->pt_cnt[i];
         if (cnt == 0) continue;
         AROL_CUDA(launch_batch_persistent(b->dev_tasks, b->dev_tiles_pt + b->pt_off[i], cnt, nullptr,
@@ -1914,56 +2042,107 @@ arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* ou
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_cache_load();
         auto it = g_tune_cache.find(sig);
-        if (!force && it != g_tune_cache.end()) {
+        if (!force && it != g_tune_cache.end() && it->second.size() == 5) {
             b->tile_reps = it->second[0];
             b->threads = (int)it->second[1];
             b->ctas_per_sm = (int)it->second[2];
+            b->row_budget = (int)it->second[3];
+            b->row_ctas = (int)it->second[4];
             return build_tiles(b);
         }
+    }
+    bool has_rows = false, has_other = false;
+    for (const TaskDev& t : b->host_tasks) {
+        if (t.nreps == 0) continue;
+        if (t.rowfir) has_rows = true;
+        else has_other = true;
     }
     cudaEvent_t e0, e1;
     AROL_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
     AROL_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
-    float best = 1e30f;
-    int64_t best_tile = b->tile_reps;
-    int best_thr = b->threads, best_ctas = b->ctas_per_sm;
-    const int64_t tiles[] = {512, 1024, 2048, 4096, 8192, 16384};
-    const int thrs[] = {kBatchThreads};
-    const int ctas[] = {2, 4, 6, 8};
+    // one candidate: tiles rebuilt (when their shape changed), graph
+    // captured, one warm-up launch, three timed
+    auto time_it = [&](bool rebuild, float* ms) -> arol_status {
+        arol_status r = AROL_OK;
+        if (rebuild && (r = build_tiles(b)) != AROL_OK) return r;
+        invalidate_graph(b);
+        if ((r = batch_capture(b)) != AROL_OK) return r;
+        cudaGraphLaunch(b->exec, s);
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; ++rep) cudaGraphLaunch(b->exec, s);
+        cudaEventRecord(e1, s);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) return cuda_fail(ce, "autotune run");
+        cudaEventElapsedTime(ms, e0, e1);
+        return AROL_OK;
+    };
     st = AROL_OK;
-    for (int64_t tile : tiles) {
-        b->tile_reps = tile;
-        if ((st = build_tiles(b)) != AROL_OK) break;
-        for (int thr : thrs)
-            for (int c : ctas) {
-                if ((int64_t)thr * c > 2048) continue;
-                b->threads = thr;
-                b->ctas_per_sm = c;
-                invalidate_graph(b);
-                if ((st = batch_capture(b)) != AROL_OK) break;
-                cudaGraphLaunch(b->exec, s);   // warm-up
-                cudaEventRecord(e0, s);
-                for (int rep = 0; rep < 3; ++rep) cudaGraphLaunch(b->exec, s);
-                cudaEventRecord(e1, s);
-                cudaError_t ce = cudaEventSynchronize(e1);
-                if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune run"); break; }
+    // row-FIR tiles: slot floats per tile and CTAs per SM
+    if (has_rows) {
+        float best = 1e30f;
+        int best_budget = b->row_budget, best_rc = b->row_ctas;
+        const int budgets[] = {1536, 3072, kRowSlotFloats};
+        const int rcs[] = {1, 2};
+        for (int bud : budgets) {
+            b->row_budget = bud;
+            bool rebuilt = false;
+            for (int rc : rcs) {
+                b->row_ctas = rc;
                 float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; best_tile = tile; best_thr = thr; best_ctas = c; }
+                if ((st = time_it(!rebuilt, &ms)) != AROL_OK) break;
+                rebuilt = true;
+                if (ms < best) { best = ms; best_budget = bud; best_rc = rc; }
             }
-        if (st != AROL_OK) break;
+            if (st != AROL_OK) break;
+        }
+        b->row_budget = best_budget;
+        b->row_ctas = best_rc;
+    }
+    // other tiles: repetitions per tile and CTAs per SM of the persistent kernel
+    if (st == AROL_OK && has_other) {
+        float best = 1e30f;
+        int64_t best_tile = b->tile_reps;
+        int best_ctas = b->ctas_per_sm;
+        const int64_t tiles[] = {512, 1024, 2048, 4096, 8192, 16384};
+        const int ctas[] = {2, 4, 6, 8};
+        for (int64_t tile : tiles) {
+            b->tile_reps = tile;
+            bool rebuilt = false;
+            for (int c : ctas) {
+                if ((int64_t)b->threads * c > 2048) continue;
+                b->ctas_per_sm = c;
+                float ms = 0;
+                if ((st = time_it(!rebuilt, &ms)) != AROL_OK) break;
+                rebuilt = true;
+                if (ms < best) { best = ms; best_tile = tile; best_ctas = c; }
+            }
+            if (st != AROL_OK) break;
+        }
+        b->tile_reps = best_tile;
+        b->ctas_per_sm = best_ctas;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != AROL_OK) return st;
-    b->tile_reps = best_tile;
-    b->threads = best_thr;
-    b->ctas_per_sm = best_ctas;
     if ((st = build_tiles(b)) != AROL_OK) return st;
+    log_line("batch tune: tile_reps %lld, %d CTAs per SM; row tiles of %d slot floats, %d CTAs per SM",
+             (long long)b->tile_reps, b->ctas_per_sm, b->row_budget, b->row_ctas);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[sig] = {best_tile, best_thr, best_ctas};
+    g_tune_cache[sig] = {b->tile_reps, (int64_t)b->threads, (int64_t)b->ctas_per_sm, (int64_t)b->row_budget,
+                         (int64_t)b->row_ctas};
     tune_cache_save();
     return AROL_OK;
+}
+
+arol_status arol_batch_sync_status(arol_batch b, void* stream) {
+    if (!b) return fail(AROL_ERR_INVALID, "null batch");
+    AROL_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
+    if (!b->err) return AROL_OK;
+    unsigned flag = 0;
+    AROL_CUDA(cudaMemcpy(&flag, b->err, sizeof flag, cudaMemcpyDeviceToHost), "read error word");
+    if (!flag) return AROL_OK;
+    cudaMemset(b->err, 0, sizeof(unsigned));
+    return fail(AROL_ERR_TIMEOUT, "a bounded device-side wait of the batch kernels gave up (flags 0x%x)", flag);
 }
 
 void arol_batch_destroy(arol_batch b) {
@@ -1980,6 +2159,10 @@ void arol_batch_destroy(arol_batch b) {
         free_dev(b->dev_tasks);
         free_dev(b->dev_tiles);
         free_dev(b->dev_tiles_pt);
+        free_dev(b->dev_rtiles);
+        free_dev(b->dev_rtiles_pt);
+        if (b->pinned_rtiles) cudaFreeHost(b->pinned_rtiles);
+        free_dev(b->err);
         free_dev(b->counter);
         free_dev(b->taps_dev);
         free_dev(b->arena);

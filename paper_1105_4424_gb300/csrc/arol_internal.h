@@ -57,8 +57,6 @@ struct TaskDev {
     int32_t s0, s1, p0, p1; // fir2d: steps and pattern extents (rows, columns)
     int32_t bh, bw;         // fir2d: repetitions per CTA tile (rows, columns)
     int32_t step;           // input paving along the row (row FIR) or down the column (column FIR), reduced
-    int32_t wfull;          // staged window of one whole row: step * (rep[3] - 1) + T
-    FastDiv wfull_div;      // division by wfull
     const float* taps;      // m x T (fir)
     const float* taps_t;    // row- and column-FIR tasks in a batch: taps transposed, T x 16, zero padded
     const void* x;
@@ -73,6 +71,36 @@ struct TileDev {
     int32_t count;
     int64_t start;
 };
+
+// One tile of a row-FIR task in a batch (see k_rowfir.cu): rows row0 ..
+// row0 + nrows - 1 (mod H) of the input, repetitions a0 .. a0 + cnt - 1 of
+// each row.  Built on the host; x, y and taps_t are filled in when the
+// batch's buffers are known.
+struct RowTileDev {
+    const float* x;         // input array, rows of W floats
+    float* y;               // output array, rows of Wout floats
+    const float* taps_t;    // the task's taps transposed, T x 16, zero padded (16-byte aligned)
+    int32_t W, H;           // input row length and row count
+    int32_t Wout, Hout;     // output row length and row count
+    int32_t row0, orow0;    // input and output row of the tile's first row (reduced)
+    int32_t nrows;          // rows in the tile, 1..32
+    int32_t c0;             // window's first input column: (o1 + S a0) mod W
+    int32_t oc0;            // first output column: (oo1 + M a0) mod Wout
+    int32_t cnt;            // repetitions per row
+    int32_t S, T, M;        // step (1..32), taps (<= 32), outputs per repetition (<= 16)
+    int32_t lw;             // window words per row: S (cnt - 1) + T
+    int32_t ss;             // row slot stride in floats: a multiple of 32, >= lw + 6
+    int32_t a;              // rows per warp unit: 1, 2, 4, ..., 32 (the unit has 32 / a repetitions per row)
+    int32_t out_wrap;       // 1 when the tile's output columns wrap at Wout
+    int32_t task;           // the batch task this tile belongs to (host bookkeeping)
+};
+// Shared-memory stage of the row-FIR kernel (floats): the tile record, the
+// transposed taps, then row slots; a tile's slots take nrows * ss floats, at
+// most kRowSlotFloats.
+constexpr int kRowStageFloats = 5120;
+constexpr int kRowSlotFloats = kRowStageFloats - 32 - 32 * 16 - 28;
+cudaError_t launch_rowfir_batch(const RowTileDev* tiles, int ntiles, int grid, unsigned* err, cudaStream_t s);
+int rowfir_ctas_per_sm();
 
 // Parameters of the fused separable downscaler chain (8-tap -> 3-output on
 // both axes, step 8, no wrap): x (frames, H, W) -> y (frames, 3H/8, 3W/8).
@@ -106,11 +134,6 @@ cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, 
                                     unsigned* counter, int grid, int threads, int max_m,
                                     cudaStream_t s);
 constexpr int kBatchThreads = 128;                  // threads of the batch kernel (its launch bound)
-constexpr int kRowTile = 2048;                      // at most this many repetitions per row tile
-// Staged input window of a row tile.  A tile that is a piece of one row holds
-// at most min(kRowTile, (kWinFloats - T) / step + 1) repetitions, so its
-// window (step * (count - 1) + T words) always fits.
-constexpr int kWinFloats = 4096;
 cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s);
 cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int nparts, bool with_fwd,
                                  cudaStream_t s);

@@ -266,33 +266,8 @@ __global__ void __launch_bounds__(kThreads) tiler_generic_kernel(const TaskDev t
         process_rep<MAXM>(t, lr);
 }
 
-// ---------------------------------------------------------------------------
-// Row tile of a row-FIR task: repetitions (r0, a .. a+count-1) read the input
-// window of row r0 covering columns o1 + step*a .. o1 + step*(a+count-1) + T-1
-// (mod the row length).  The window is staged once into shared memory with
-// coalesced loads (one extra word every 32 so that lanes reading at stride
-// `step` spread over the banks); the taps are staged transposed so that one
-// 128-bit shared load feeds four outputs.
-// ---------------------------------------------------------------------------
-constexpr int kWinPad = kWinFloats + kWinFloats / 32;
-
-__device__ __forceinline__ int padw(int w) { return w + (w >> 5); }
-
-// Row tiles come in two layouts (chosen by the host when it builds tiles):
-//  * window: part of one long row (count <= kRowTile repetitions from column
-//    step a0); shared memory holds the window o1 + step*a0 + w, w <
-//    step*(count-1) + T, already wrapped, and repetition i reads words
-//    step*i .. step*i + T - 1;
-//  * rows: whole short rows (a0 == 0, rows * W <= kWinFloats); shared memory
-//    holds the rows themselves, W words each (a contiguous copy), and
-//    repetition (k, r1) walks columns (o1 + step*r1 + kk) mod W with one
-//    compare per step.
-// Each thread computes two repetitions, i and i + blockDim.x (in a tile's
-// last chunk of fewer than 2 blockDim.x repetitions, i and i + half of the
-// chunk), so every tap fetch feeds both; the exact output count M is a
-// template parameter (taps are read from the transposed block as float4 /
-// float2 / float pieces, no padded FMAs), and a repetition's M outputs go to
-// consecutive columns with one wrap test each.
+// Taps of one tap index k for M outputs, from the transposed block
+// ht[k * 16 + j] = H[j, k], as float4 / float2 / float pieces.
 template <int M>
 __device__ __forceinline__ void load_taps(const float* hrow, float (&h)[M]) {
 #pragma unroll
@@ -310,119 +285,6 @@ __device__ __forceinline__ void load_taps(const float* hrow, float (&h)[M]) {
         h[j0 + 1] = v.y;
     }
     if ((M - j0) & 1) h[M - 1] = hrow[M - 1];
-}
-
-template <int M>
-__device__ __forceinline__ void store_outputs(const TaskDev& t, uint32_t r0, uint32_t k, uint32_t r1, const float (&acc)[M]) {
-    const uint32_t hout = (uint32_t)t.out.shape[0], wout = (uint32_t)t.out.shape[1];
-    // output row (o0 + r0 + k) mod H_out and first column (o1 + m*r1) mod W_out
-    const uint32_t ov = t.out.origin[0] + r0 + k;            // < 2^31: checked on the host
-    const uint32_t orow = ov - fast_div(ov, t.out.shape_div[0]) * hout;
-    const uint64_t v = (uint64_t)t.out.origin[1] + (uint64_t)M * r1;
-    uint32_t c = v < 0x7fffffffull ? (uint32_t)v - fast_div((uint32_t)v, t.out.shape_div[1]) * wout
-                                   : (uint32_t)(v % wout);
-    float* yrow = static_cast<float*>(t.y) + (int64_t)orow * wout;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        yrow[c] = acc[j];
-        c = (c + 1u == wout) ? 0u : c + 1u;
-    }
-}
-
-template <int M, bool kRowsLayout>
-__device__ __forceinline__ void row_fir_compute(const TaskDev& t, const float* win, const float* ht, int count,
-                                                uint32_t r0, uint32_t a0, uint32_t cb) {
-    constexpr int kHt = 16;   // ht row stride (floats)
-    const int T = t.T, S = t.step;
-    const uint32_t R1 = (uint32_t)t.rep[3];
-    const uint32_t wi = (uint32_t)t.in.shape[1];
-    const int B = blockDim.x;
-    for (int base = 0; base < count; base += 2 * B) {
-        // a chunk of 2B repetitions: thread t takes base + t and base + t + B;
-        // the last, shorter chunk pairs t with t + ceil(rem / 2) instead, so
-        // only an odd remainder recomputes one repetition
-        const int rem = count - base, half = rem >= 2 * B ? B : (rem + 1) >> 1;
-        if ((int)threadIdx.x >= half) break;
-        const int i0 = base + (int)threadIdx.x;
-        const int i1 = i0 + half < count ? i0 + half : i0;
-        float acc0[M], acc1[M];
-#pragma unroll
-        for (int j = 0; j < M; ++j) acc0[j] = acc1[j] = 0.f;
-        uint32_t k0, k1, r10, r11;
-        if (kRowsLayout) {
-            k0 = fast_div((uint32_t)i0, t.rep_div[3]);
-            k1 = fast_div((uint32_t)i1, t.rep_div[3]);
-            r10 = (uint32_t)i0 - k0 * R1;
-            r11 = (uint32_t)i1 - k1 * R1;
-            uint32_t c0 = cb + (uint32_t)S * r10, c1 = cb + (uint32_t)S * r11;   // < 2^31: extents below 2^30
-            c0 -= fast_div(c0, t.in.shape_div[1]) * wi;
-            c1 -= fast_div(c1, t.in.shape_div[1]) * wi;
-            const int ro0 = (int)(k0 * wi), ro1 = (int)(k1 * wi);
-#pragma unroll 2
-            for (int kk = 0; kk < T; ++kk) {
-                const float p0 = win[padw(ro0 + (int)c0)], p1 = win[padw(ro1 + (int)c1)];
-                c0 = (c0 + 1u == wi) ? 0u : c0 + 1u;
-                c1 = (c1 + 1u == wi) ? 0u : c1 + 1u;
-                float h[M];
-                load_taps<M>(ht + kk * kHt, h);
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    acc0[j] = fmaf(h[j], p0, acc0[j]);
-                    acc1[j] = fmaf(h[j], p1, acc1[j]);
-                }
-            }
-        } else {
-            k0 = k1 = 0;
-            r10 = a0 + (uint32_t)i0;
-            r11 = a0 + (uint32_t)i1;
-            const int b0 = S * i0, b1 = S * i1;
-#pragma unroll 2
-            for (int kk = 0; kk < T; ++kk) {
-                const float p0 = win[padw(b0 + kk)], p1 = win[padw(b1 + kk)];
-                float h[M];
-                load_taps<M>(ht + kk * kHt, h);
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    acc0[j] = fmaf(h[j], p0, acc0[j]);
-                    acc1[j] = fmaf(h[j], p1, acc1[j]);
-                }
-            }
-        }
-        store_outputs<M>(t, r0, k0, r10, acc0);
-        if (i1 != i0) store_outputs<M>(t, r0, k1, r11, acc1);
-    }
-}
-
-// Stages the window layout: words (o1 + step*a + w) mod W of input row r, w < len.
-__device__ __forceinline__ void stage_window(const TaskDev& t, uint32_t row, uint32_t a, int len, float* win) {
-    const uint32_t wi = (uint32_t)t.in.shape[1];
-    uint32_t v = t.in.origin[1] + (uint32_t)t.step * a;       // < 2^31: checked on the host
-    const uint32_t cb = v - fast_div(v, t.in.shape_div[1]) * wi;
-    const float* xr = static_cast<const float*>(t.x) + (int64_t)row * wi;
-    if ((int)wi >= len) {
-        for (int w = threadIdx.x; w < len; w += blockDim.x) {
-            uint32_t c = cb + (uint32_t)w;
-            c = c >= wi ? c - wi : c;
-            ptx::cp_async4(win + padw(w), xr + c);
-        }
-    } else {
-        for (int w = threadIdx.x; w < len; w += blockDim.x) ptx::cp_async4(win + padw(w), xr + (cb + (uint32_t)w) % wi);
-    }
-}
-
-template <bool kRowsLayout>
-__device__ __forceinline__ void row_fir_dispatch(const TaskDev& t, const float* win, const float* ht, int count,
-                                                 uint32_t r0, uint32_t a0, uint32_t cb) {
-#define AROL_ROW_FIR_CASE(M) \
-    case M: row_fir_compute<M, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
-    switch (t.m) {
-        AROL_ROW_FIR_CASE(1) AROL_ROW_FIR_CASE(2) AROL_ROW_FIR_CASE(3) AROL_ROW_FIR_CASE(4)
-        AROL_ROW_FIR_CASE(5) AROL_ROW_FIR_CASE(6) AROL_ROW_FIR_CASE(7) AROL_ROW_FIR_CASE(8)
-        AROL_ROW_FIR_CASE(9) AROL_ROW_FIR_CASE(10) AROL_ROW_FIR_CASE(11) AROL_ROW_FIR_CASE(12)
-        AROL_ROW_FIR_CASE(13) AROL_ROW_FIR_CASE(14) AROL_ROW_FIR_CASE(15)
-        default: row_fir_compute<16, kRowsLayout>(t, win, ht, count, r0, a0, cb); break;
-    }
-#undef AROL_ROW_FIR_CASE
 }
 
 // ---------------------------------------------------------------------------
@@ -823,68 +685,17 @@ __global__ void __launch_bounds__(kFir2dThreads, 4) stencil_kernel(const TaskDev
 }
 
 // Shared memory of the batch kernel: a ring of three task records (the
-// TaskDev of the tile being computed, of the next tile, whose copies are in
-// flight, and of the one after, being copied), then two data slots, each the
-// staged window followed by the taps of the tile's task transposed and zero
-// padded (ht[k * 16 + j] = H[j, k], k < 32).
+// TaskDev of the tile being computed, of the next tile, and of the one after,
+// being copied), then two slots for the transposed, zero-padded taps of a
+// column-FIR tile's task (ht[k * 16 + j] = H[j, k], k < 32).
 constexpr int kTaskFloats = (int)((sizeof(TaskDev) + 15) / 16 * 4);
 constexpr int kMetaSlots = 3;
-constexpr int kSlotFloats = kWinPad + 32 * 16;
+constexpr int kSlotFloats = 32 * 16;
 static_assert(sizeof(TaskDev) % 4 == 0, "TaskDev is copied in 4-byte words");
-
-struct RowGeom {
-    uint32_t r0, a0, row0;
-    bool rows_layout;
-};
-
-__device__ __forceinline__ RowGeom row_geom(const TaskDev& t, int64_t start, int count) {
-    RowGeom g;
-    const uint32_t R1 = (uint32_t)t.rep[3];
-    g.r0 = fast_div((uint32_t)start, t.rep_div[3]);
-    g.a0 = (uint32_t)start - g.r0 * R1;
-    const uint32_t v = t.in.origin[0] + g.r0;               // < 2^31: checked on the host
-    g.row0 = v - fast_div(v, t.in.shape_div[0]) * (uint32_t)t.in.shape[0];
-    // The host builds multi-row tiles only as whole rows (count = rows * R1,
-    // rows >= 2, rows <= H, rows * W <= kWinFloats); every other row tile lies
-    // within one row (count <= R1).
-    g.rows_layout = g.a0 == 0u && (uint32_t)count > R1;
-    return g;
-}
 
 // Issues (cp.async, no wait) the copies of a task's transposed taps into a data slot.
 __device__ __forceinline__ void stage_taps(const TaskDev& t, float* slot) {
-    float* ht = slot + kWinPad;
-    for (int i = threadIdx.x; i < t.T * 16; i += blockDim.x) ptx::cp_async4(ht + i, t.taps_t + i);
-}
-
-// Issues (cp.async, no wait) the copies of a row tile's window and, unless
-// the slot already holds them, its task's transposed taps.
-__device__ __forceinline__ void stage_row_tile(const TaskDev& t, int64_t start, int count, float* slot,
-                                               bool need_taps) {
-    const RowGeom g = row_geom(t, start, count);
-    if (g.rows_layout) {
-        const uint32_t hin = (uint32_t)t.in.shape[0], wi = (uint32_t)t.in.shape[1];
-        const int rows = (int)((uint32_t)count / (uint32_t)t.rep[3]);
-        const float* x = static_cast<const float*>(t.x);
-        const int64_t plane = (int64_t)hin * wi;
-        const int64_t g0 = (int64_t)g.row0 * wi;
-        const int total = rows * (int)wi;
-        for (int w = threadIdx.x; w < total; w += blockDim.x) {
-            int64_t gofs = g0 + w;
-            if (gofs >= plane) gofs -= plane;
-            ptx::cp_async4(slot + padw(w), x + gofs);
-        }
-    } else {
-        stage_window(t, g.row0, g.a0, t.step * (count - 1) + t.T, slot);
-    }
-    if (need_taps) stage_taps(t, slot);
-}
-
-__device__ __forceinline__ void compute_row_tile(const TaskDev& t, int64_t start, int count, const float* slot) {
-    const RowGeom g = row_geom(t, start, count);
-    const float* ht = slot + kWinPad;
-    if (g.rows_layout) row_fir_dispatch<true>(t, slot, ht, count, g.r0, 0u, t.in.origin[1]);
-    else row_fir_dispatch<false>(t, slot, ht, count, g.r0, g.a0, 0u);
+    for (int i = threadIdx.x; i < t.T * 16; i += blockDim.x) ptx::cp_async4(slot + i, t.taps_t + i);
 }
 
 // Copies (cp.async, no wait) task record `t` into a meta slot.
@@ -893,21 +704,22 @@ __device__ __forceinline__ void stage_meta(const TaskDev& t, float* meta) {
     for (int w = threadIdx.x; w < (int)(sizeof(TaskDev) / 4); w += blockDim.x) ptx::cp_async4(meta + w, src + w);
 }
 
-// Persistent batched kernel.  CTA b takes tiles b, b + gridDim.x, ... (the
-// host orders tiles by cost).  Two pipelines run ahead of the compute: the
-// task record of tile i + 2 is copied into shared memory while tile i is
-// computed, and the window and taps of tile i + 1, whose addresses come from
-// its record already in shared memory, fill the other data slot.  So no
-// global load stands between a barrier and the compute.  Row tiles of row-FIR
-// tasks use the staged data; other tiles run the generic per-repetition path.
-// No CTA ever waits on another.
+// Persistent batched kernel for the tiles that are not row-FIR tiles (those
+// run on the row-FIR kernel).  CTA b takes tiles b, b + gridDim.x, ... (the
+// host orders tiles by cost).  The task record of tile i + 2 is copied into
+// shared memory while tile i is computed, and the taps of tile i + 1 (a
+// column-FIR tile), whose address comes from its record already in shared
+// memory, fill the other data slot, so no global load stands between a
+// barrier and the compute.  Column-FIR tiles read their columns from global
+// memory; other tiles run the generic per-repetition path.  No CTA ever waits
+// on another.
 template <int MAXM>
 __global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(const TaskDev* __restrict__ tasks,
                                                                   const TileDev* __restrict__ tiles, int ntiles) {
-    constexpr bool kRows = MAXM <= 16;
+    constexpr bool kCols = MAXM <= 16;
     extern __shared__ __align__(16) float dsm[];
     float* meta = dsm;                                  // kMetaSlots task records
-    float* data = dsm + kMetaSlots * kTaskFloats;       // two data slots
+    float* data = dsm + kMetaSlots * kTaskFloats;       // two tap slots
     const int G = gridDim.x;
     int slot_task[2] = {-1, -1};   // task whose taps each data slot holds (the same in every thread)
     // records of tiles i, i + 1, i + 2 (registers), valid when the index < ntiles
@@ -916,7 +728,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(cons
     if (t0 < ntiles) tl0 = tiles[t0];
     if (t0 + G < ntiles) tl1 = tiles[t0 + G];
     if (t0 + 2 * G < ntiles) tl2 = tiles[t0 + 2 * G];
-    if (kRows) {
+    if (kCols) {
         if (t0 < ntiles) stage_meta(tasks[tl0.task], meta);
         if (t0 + G < ntiles) stage_meta(tasks[tl1.task], meta + kTaskFloats);
         ptx::cp_async_commit();
@@ -924,10 +736,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(cons
         __syncthreads();
         if (t0 < ntiles) {
             const TaskDev& m0 = *reinterpret_cast<const TaskDev*>(meta);
-            if (m0.rowfir) {
-                stage_row_tile(m0, tl0.start, tl0.count, data, true);
-                slot_task[0] = tl0.task;
-            } else if (m0.colfir) {
+            if (m0.colfir) {
                 stage_taps(m0, data);
                 slot_task[0] = tl0.task;
             }
@@ -936,17 +745,14 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(cons
     }
     for (int i = 0, ti = t0; ti < ntiles; ++i, ti += G) {
         const int cur = i & 1, nxt = cur ^ 1;
-        if (kRows) {
-            // data of tile i and the record of tile i + 1 have landed; every
+        if (kCols) {
+            // taps of tile i and the record of tile i + 1 have landed; every
             // thread is done with tile i - 1 (its data slot and its record)
             ptx::cp_async_wait_group<0>();
             __syncthreads();
             if (ti + G < ntiles) {
                 const TaskDev& m1 = *reinterpret_cast<const TaskDev*>(meta + ((i + 1) % kMetaSlots) * kTaskFloats);
-                if (m1.rowfir) {
-                    stage_row_tile(m1, tl1.start, tl1.count, data + nxt * kSlotFloats, slot_task[nxt] != tl1.task);
-                    slot_task[nxt] = tl1.task;
-                } else if (m1.colfir) {
+                if (m1.colfir) {
                     if (slot_task[nxt] != tl1.task) stage_taps(m1, data + nxt * kSlotFloats);
                     slot_task[nxt] = tl1.task;
                 }
@@ -959,12 +765,8 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_persistent_kernel(cons
         tl1 = tl2;
         if (ti + 3 * G < ntiles) tl2 = tiles[ti + 3 * G];   // used at the next iteration
         const TaskDev* mcur = reinterpret_cast<const TaskDev*>(meta + (i % kMetaSlots) * kTaskFloats);
-        if (kRows && mcur->rowfir) {
-            compute_row_tile(*mcur, tile.start, tile.count, data + cur * kSlotFloats);
-            continue;
-        }
-        if (kRows && mcur->colfir) {
-            col_fir_dispatch(*mcur, data + cur * kSlotFloats + kWinPad, tile.start, tile.count);
+        if (kCols && mcur->colfir) {
+            col_fir_dispatch(*mcur, data + cur * kSlotFloats, tile.start, tile.count);
             continue;
         }
         const TaskDev& t = tasks[tile.task];
