@@ -1626,14 +1626,19 @@ int rowfir_conflicts(int a, int64_t W, int S) {
 }
 
 // Row tiles of a row-FIR task: rows per warp unit (a), repetitions per row
-// piece (cnt) and rows per tile (<= 32) are chosen for the fewest bank
-// conflicts per useful lane, within `budget` slot floats per tile.
+// piece (cnt) and rows per tile (<= 32), within `budget` slot floats per
+// tile, chosen by a cost model in warp instructions: a fixed cost per tile
+// (record, waits, set-up), a cost per unit (addresses, stores) and per unit
+// and tap the shared-memory wavefronts of the window load (its bank
+// conflict degree) plus m FMAs, lanes past a tile's edge included.
 void build_row_tiles(const TaskDev& t, int task, int budget, std::vector<RowTileDev>& out) {
     const int S = t.step, T = t.T, M = t.m;
     const int64_t W = t.in.shape[1], H = t.in.shape[0], Wo = t.out.shape[1], Ho = t.out.shape[0];
     const int64_t R0 = t.rep[2], R1 = t.rep[3];
     if (R0 <= 0 || R1 <= 0) return;
     auto ss_of = [&](int64_t cnt) { return (int)((S * (cnt - 1) + T + 6 + 31) & ~int64_t(31)); };
+    budget = std::min(budget, kRowSlotFloats - 32 * (T - 1));   // the taps sit at the stage's end
+    constexpr double kTile = 400, kUnit = 40;
     double best = 1e300;
     int ba = 1;
     int64_t bcnt = 1, brows = 1;
@@ -1648,10 +1653,11 @@ void build_row_tiles(const TaskDev& t, int task, int budget, std::vector<RowTile
         int64_t rows = std::min<int64_t>({32, R0, (int64_t)(budget / ss_of(cnt))});
         rows = rows / a * a;
         if (rows < a) continue;
-        const double used = (double)cnt / (double)(b * ((cnt + b - 1) / b));
-        const double score = rowfir_conflicts(a, W, S) / used;
-        if (score < best * 0.999 || (score <= best * 1.001 && rows * cnt > brows * bcnt)) {
-            best = score;
+        const double tiles = (double)((R0 + rows - 1) / rows) * (double)pieces;
+        const double units = tiles * (double)(rows / a) * (double)((cnt + b - 1) / b);
+        const double cost = tiles * kTile + units * (kUnit + T * (double)(rowfir_conflicts(a, W, S) + M));
+        if (cost < best) {
+            best = cost;
             ba = a;
             bcnt = cnt;
             brows = rows;
@@ -1809,7 +1815,8 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
         size_t ntaps = 0;
         for (size_t i = 0; i < n; ++i) {
             ntaps += b->taps[i].size();
-            if (b->host_tasks[i].rowfir || b->host_tasks[i].colfir) ntaps += 3 + (size_t)b->host_tasks[i].T * 16;
+            if (b->host_tasks[i].rowfir) ntaps += 3 + (size_t)b->host_tasks[i].T * 32;
+            else if (b->host_tasks[i].colfir) ntaps += 3 + (size_t)b->host_tasks[i].T * 16;
         }
         // each resource is made once: a call that failed part-way (say, out of
         // memory) is retried without leaking what it had already made
@@ -1839,9 +1846,14 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
             TaskDev& td = b->host_tasks[i];
             if (td.rowfir || td.colfir) {
                 off = (off + 3) & ~size_t(3);   // 16-byte aligned: the row-FIR kernel bulk-copies these
-                std::vector<float> ht((size_t)td.T * 16, 0.f);
+                // column FIR: ht[k * 16 + j] = H[j, k]; row FIR: each tap twice,
+                // ht[k * 32 + 2 j + e] = H[j, k] (pairs for paired FMAs)
+                const int dup = td.rowfir ? 2 : 1;
+                std::vector<float> ht((size_t)td.T * 16 * dup, 0.f);
                 for (int k = 0; k < td.T; ++k)
-                    for (int j = 0; j < td.m; ++j) ht[(size_t)k * 16 + j] = b->taps[i][(size_t)j * td.T + k];
+                    for (int j = 0; j < td.m; ++j)
+                        for (int e = 0; e < dup; ++e)
+                            ht[((size_t)k * 16 + j) * dup + e] = b->taps[i][(size_t)j * td.T + k];
                 AROL_CUDA(cudaMemcpy(b->taps_dev + off, ht.data(), ht.size() * sizeof(float), cudaMemcpyHostToDevice),
                           "upload taps");
                 td.taps_t = b->taps_dev + off;
@@ -2081,7 +2093,7 @@ arol_status arol_batch_tune(arol_batch b, const void* const* in, void* const* ou
     if (has_rows) {
         float best = 1e30f;
         int best_budget = b->row_budget, best_rc = b->row_ctas;
-        const int budgets[] = {1536, 3072, kRowSlotFloats};
+        const int budgets[] = {kRowSlotFloats / 2, kRowSlotFloats * 3 / 4, kRowSlotFloats};
         const int rcs[] = {1, 2};
         for (int bud : budgets) {
             b->row_budget = bud;

@@ -58,7 +58,8 @@ struct TaskDev {
     int32_t bh, bw;         // fir2d: repetitions per CTA tile (rows, columns)
     int32_t step;           // input paving along the row (row FIR) or down the column (column FIR), reduced
     const float* taps;      // m x T (fir)
-    const float* taps_t;    // row- and column-FIR tasks in a batch: taps transposed, T x 16, zero padded
+    const float* taps_t;    // column-FIR tasks in a batch: taps transposed, T x 16, zero padded;
+                            // row-FIR tasks: transposed and doubled, T x 32 (see RowTileDev)
     const void* x;
     void* y;
     int64_t in_elems, out_elems;   // array sizes, for the bounds checks of AROL_DEBUG builds
@@ -79,7 +80,8 @@ struct TileDev {
 struct RowTileDev {
     const float* x;         // input array, rows of W floats
     float* y;               // output array, rows of Wout floats
-    const float* taps_t;    // the task's taps transposed, T x 16, zero padded (16-byte aligned)
+    const float* taps_t;    // the task's taps transposed and doubled, T x 32: [k * 32 + 2 j + e] = H[j, k]
+                            // (e = 0, 1; zero for j >= m), 16-byte aligned
     int32_t W, H;           // input row length and row count
     int32_t Wout, Hout;     // output row length and row count
     int32_t row0, orow0;    // input and output row of the tile's first row (reduced)
@@ -94,11 +96,15 @@ struct RowTileDev {
     int32_t out_wrap;       // 1 when the tile's output columns wrap at Wout
     int32_t task;           // the batch task this tile belongs to (host bookkeeping)
 };
-// Shared-memory stage of the row-FIR kernel (floats): the tile record, the
-// transposed taps, then row slots; a tile's slots take nrows * ss floats, at
-// most kRowSlotFloats.
-constexpr int kRowStageFloats = 5120;
-constexpr int kRowSlotFloats = kRowStageFloats - 32 - 32 * 16 - 28;
+// Shared-memory stage of the row-FIR kernel (floats): the tile record, a
+// table of its rows, the row slots, and the taps (32 T floats) at its end; a
+// tile's slots take nrows * ss floats, at most kRowSlotFloats - 32 (T - 1)
+// (kRowSlotFloats leaves room for T = 1).
+#ifndef AROL_ROW_STAGE_FLOATS
+#define AROL_ROW_STAGE_FLOATS 3456
+#endif
+constexpr int kRowStageFloats = AROL_ROW_STAGE_FLOATS;
+constexpr int kRowSlotFloats = kRowStageFloats - 32 - 32 * 4 - 32 - 28;
 cudaError_t launch_rowfir_batch(const RowTileDev* tiles, int ntiles, int grid, unsigned* err, cudaStream_t s);
 int rowfir_ctas_per_sm();
 
