@@ -34,10 +34,19 @@
 namespace arol {
 namespace {
 
-constexpr int kRfCWarps = 4;                        // consumer warps
+#ifndef AROL_ROW_SHARE
+#define AROL_ROW_SHARE 2
+#endif
+#ifndef AROL_ROW_UNROLL
+#define AROL_ROW_UNROLL 4
+#endif
+constexpr int kRfShare = AROL_ROW_SHARE;            // consumer warps per tile
+constexpr int kRfUnroll = AROL_ROW_UNROLL;          // tap-loop unroll
+constexpr int kRfGroups = 4;                        // consumer groups (kRfShare warps each)
+constexpr int kRfCWarps = kRfGroups * kRfShare;     // consumer warps
 constexpr int kRfPWarps = 2;                        // producer warps
 constexpr int kRfThreads = (kRfCWarps + kRfPWarps) * 32;
-constexpr int kRfStages = 8;                       // two per consumer warp
+constexpr int kRfStages = 2 * kRfGroups;            // two per consumer group
 constexpr int kRfRecs = 8;                         // tile records read ahead by the producers
 static_assert(kRfRecs % kRfPWarps == 0 && kRfStages % kRfPWarps == 0, "each producer owns its stages and slots");
 // Stage layout (floats): the tile record, the row table, the row slots, and
@@ -158,7 +167,7 @@ __device__ __forceinline__ void unit_group(const RowTileDev& h, const UnitPos (&
         for (int j = 0; j < G; ++j) acc[q][j] = make_float2(0.f, 0.f);
     const float* hp = ht + 2 * j0;
     const int T = h.T;
-#pragma unroll 4
+#pragma unroll kRfUnroll
     for (int kk = 0; kk < T; ++kk) {
         float2 v[P];
 #pragma unroll
@@ -224,14 +233,28 @@ __device__ __forceinline__ void units(const RowTileDev& h, const TileGeom& g, co
 // fastest, four at a time, the last U mod 4 two at a time.  A unit is a rows
 // x 32/a repetitions; lanes past the tile's edge compute from slot 0 and
 // store nothing.
-__device__ __forceinline__ void tile_compute(const RowTileDev& h, const float* stage, int lane) {
+__device__ __forceinline__ void tile_compute(const RowTileDev& h, const float* stage, int lane, int sub) {
     const RowInfo* rows = reinterpret_cast<const RowInfo*>(stage + kRfRecFloats);
     const float* ht = stage_taps(stage, h.T);
     const float* slots = stage + kRfSlotBase;
     const TileGeom g = tile_geom(h, lane);
-    int grp = 0, blk = 0, u = 0;
-    for (; u + 4 <= g.U; u += 4) units<4>(h, g, rows, slots, ht, grp, blk);
-    for (; u < g.U; u += 2) units<2>(h, g, rows, slots, ht, grp, blk);
+    // the kRfShare warps of a group take alternate chunks of units
+    int grp = 0, blk = 0, u = 0, c = 0;
+    auto skip = [&](int n) {
+        blk += n;
+        while (blk >= g.nb) {
+            blk -= g.nb;
+            ++grp;
+        }
+    };
+    for (; u + 4 <= g.U; u += 4, ++c) {
+        if (c % kRfShare == sub) units<4>(h, g, rows, slots, ht, grp, blk);
+        else skip(4);
+    }
+    for (; u < g.U; u += 2, ++c) {
+        if (c % kRfShare == sub) units<2>(h, g, rows, slots, ht, grp, blk);
+        else skip(2);
+    }
 }
 
 // Producer: issues the copies of tile record `src` (its fields in h) into
@@ -319,8 +342,8 @@ __device__ __forceinline__ void produce_tile(const RowTileDev& h, const RowTileD
 }
 
 // Persistent over the tile list: CTA b takes tiles b, b + gridDim.x, ...;
-// its i-th tile goes to stage i % kRfStages and consumer warp i % kRfCWarps
-// (two stages per consumer warp: one computed, one filling).  The producer
+// its i-th tile goes to stage i % kRfStages and consumer group i % kRfGroups
+// (two stages per group: one computed, one filling).  The producer
 // reads each tile's record from a ring of kRfRecs records in shared memory
 // that bulk copies fill kRfRecs tiles ahead, so no global load latency stands
 // between two tiles.
@@ -338,7 +361,7 @@ __global__ void __launch_bounds__(kRfThreads, AROL_ROW_MIN_CTAS) rowfir_batch_ke
     if (threadIdx.x == 0) {
         for (int st = 0; st < kRfStages; ++st) {
             ptx::mbar_init(full0 + 8 * st, 32);
-            ptx::mbar_init(empty0 + 8 * st, 1);
+            ptx::mbar_init(empty0 + 8 * st, kRfShare);
         }
         for (int q = 0; q < kRfRecs; ++q) ptx::mbar_init(rec0 + 8 * q, 1);
         ptx::fence_barrier_init();
@@ -401,7 +424,8 @@ __global__ void __launch_bounds__(kRfThreads, AROL_ROW_MIN_CTAS) rowfir_batch_ke
         ptx::cp_async_wait_all();
         return;
     }
-    for (int i = warp, t = blockIdx.x + warp * G; t < ntiles; i += kRfCWarps, t += kRfCWarps * G) {
+    const int group = warp / kRfShare, sub = warp - group * kRfShare;
+    for (int i = group, t = blockIdx.x + group * G; t < ntiles; i += kRfGroups, t += kRfGroups * G) {
         const int st = i % kRfStages;
         if (!ptx::mbar_wait(full0 + 8 * st, (uint32_t)(i / kRfStages) & 1u)) {
             if (lane == 0) flag(err, 2u);
@@ -409,7 +433,7 @@ __global__ void __launch_bounds__(kRfThreads, AROL_ROW_MIN_CTAS) rowfir_batch_ke
         }
         const float* stage = rsm + st * kRowStageFloats;
         const RowTileDev h = *reinterpret_cast<const RowTileDev*>(stage);
-        tile_compute(h, stage, lane);
+        tile_compute(h, stage, lane, sub);
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(empty0 + 8 * st);
     }
