@@ -18,7 +18,7 @@ emptied before each timed call:
   * the conjugate-gradient solve and its SpMV.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-    python bench.py --case batched|chains|stencil|backward|matmul|config0|cg|bf16|f16
+    python bench.py --case batched|chains|chain5to2|config0_scaled|generic|stencil|backward|matmul|config0|cg|bf16|f16
 
 Under torchrun every rank runs its own 64 frames (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
@@ -369,6 +369,54 @@ def bench_batched_chains(A, torch, stream, flush, reps):
             "launches": {"batched": 2, "per_task": 2 * len(chains), "fused_per_chain": len(chains)}}
 
 
+def _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, kernel_name):
+    t = A.Task(tk) if isinstance(tk, dict) else A.Chain(tk)
+    ins = [torch.from_numpy(x).cuda() for x in xs]
+    last = tk if isinstance(tk, dict) else tk[-1]
+    out = torch.empty(tuple(last["outputs"][0]["shape"]), dtype=torch.float32, device="cuda")
+    call = t.prepare(ins, out)
+    for _ in range(3):
+        call()
+    ms = statistics.median(time_each_flushed(call, reps, stream, flush))
+    t.sync_status()
+    nbytes = sum(4 * x.size for x in xs) + 4 * out.numel()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return t, ms, {"ms": ms, "unique_bytes": nbytes, "gbs": gbs, "frac_of_hbm": gbs / hbm, "kernel": kernel_name,
+                   "info_kernel": t.info["kernel"], "path": t.info.get("path")}
+
+
+def bench_chain_5to2(A, torch, stream, flush, reps, hbm):
+    """The 5-tap -> 2 step-4 downscaler chain on 64 x 1080 x 1920: the fused
+    separable chain kernel against the same chain stage by stage (a
+    one-member batch: two launches, the intermediate through HBM)."""
+    chain, xs = W.config1_5to2()
+    _, ms, out = _task_gbs(A, torch, stream, flush, reps, hbm, chain, xs, "sepchain_kernel")
+    b = A.Batch([chain])
+    ins = [torch.from_numpy(x).cuda() for x in xs]
+    outs = b.empty_outputs()
+    run, _ = b.prepare(ins, outs)
+    for _ in range(3):
+        run()
+    out["staged_ms"] = statistics.median(time_each_flushed(run, reps, stream, flush))
+    out["fused_speedup"] = out["staged_ms"] / ms
+    out["roofline"] = {"bound": "hbm", "achieved": out["gbs"], "peak": hbm, "unit": "GB/s", "frac": out["frac_of_hbm"]}
+    return out
+
+
+def bench_config0_scaled(A, torch, stream, flush, reps, hbm):
+    """The 64 x 64 task's step-4 wrapping 8 -> 3 tiler on 64 x 1080 x 1920 (a
+    row-FIR task: the row-FIR batch kernel, as a one-member batch)."""
+    tk, xs = W.config0_scaled()
+    return _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, "rowfir_batch_kernel")[2]
+
+
+def bench_generic(A, torch, stream, flush, reps, hbm):
+    """A tiler no specialised kernel takes (diagonal 8-element patterns) on
+    64 x 1080 x 1920: the per-repetition walk."""
+    tk, xs = W.diagonal_fir()
+    return _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, "tiler_generic_kernel")[2]
+
+
 def bench_stencil(A, torch, stream, flush, reps, hbm):
     """A 3x3 stencil as a repetitive task (2-D pattern, identity fitting,
     origin (-1, -1) with wrap) on an 8192 x 8192 float32 image, one call."""
@@ -649,6 +697,9 @@ def run_gpu(args):
         line["batched"] = bench_batched(A, torch, stream, flush, reps)
         line["batched_chains"] = bench_batched_chains(A, torch, stream, flush, reps)
         line["stencil"] = bench_stencil(A, torch, stream, flush, reps, hbm)
+        line["chain_5to2"] = bench_chain_5to2(A, torch, stream, flush, reps, hbm)
+        line["config0_scaled"] = bench_config0_scaled(A, torch, stream, flush, reps, hbm)
+        line["generic_diagonal"] = bench_generic(A, torch, stream, flush, reps, hbm)
         line["fwd_bwd"] = bench_backward(A, torch, stream, flush, reps)
         line["matmul"] = bench_matmul(A, torch, stream, flush, reps, bf16)
         line["bf16_storage"] = bench_bf16(A, torch, stream, flush, reps, hbm)
@@ -689,6 +740,12 @@ def run_case(args):
         out = bench_stencil(A, torch, stream, flush, reps, hbm)
     elif args.case == "chains":
         out = bench_batched_chains(A, torch, stream, flush, reps)
+    elif args.case == "chain5to2":
+        out = bench_chain_5to2(A, torch, stream, flush, reps, hbm)
+    elif args.case == "config0_scaled":
+        out = bench_config0_scaled(A, torch, stream, flush, reps, hbm)
+    elif args.case == "generic":
+        out = bench_generic(A, torch, stream, flush, reps, hbm)
     elif args.case == "backward":
         out = bench_backward(A, torch, stream, flush, reps)
     elif args.case == "matmul":
@@ -713,7 +770,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["batched", "chains", "stencil", "backward", "matmul", "config0", "cg", "bf16", "f16"],
+    ap.add_argument("--case", choices=["batched", "chains", "chain5to2", "config0_scaled", "generic", "stencil", "backward",
+                                       "matmul", "config0", "cg", "bf16", "f16"],
                     help="run one extra measurement alone (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="batched case: keep the default launch shape")
     args = ap.parse_args(argv)

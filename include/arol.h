@@ -123,7 +123,8 @@ typedef struct arol_batch_s* arol_batch;
 /* What the library chose for a task (filled by arol_task_info). */
 typedef struct {
     int32_t kind;              /* 0 single task, 1 chain */
-    int32_t kernel;            /* 0 generic tiler, 1 fused separable downscaler, 2 tcgen05 matmul, 3 unfused chain */
+    int32_t kernel;            /* 0 generic tiler, 1 fused separable downscaler (8 -> 3, step 8), 2 tcgen05 matmul,
+                                  3 unfused chain, 4 fused separable chain (any row and column passes) */
     int64_t reps;              /* repetitions of the task (sum over a chain's tasks) */
     int64_t gathered_elems;    /* pattern elements gathered over all inputs (and tasks) */
     int64_t scattered_elems;   /* elements scattered (sum over a chain's tasks) */
@@ -153,12 +154,18 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out);
  * of tasks[k] is the input array of tasks[k+1] (same shape and dtype,
  * AROL_ERR_INVALID otherwise).  The chain copies what it needs from the tasks;
  * they may be destroyed afterwards.  Its run, backward and fwd_bwd take the
- * first task's inputs and the last task's output.  A chain whose tasks are a
- * separable block downscaler (horizontal then vertical fir with step == T, no
- * wrap) runs as one fused kernel that never writes the intermediate to HBM,
- * when its storage is all f32, or 16-bit frames (bf16 or f16) with an
- * intermediate and an output each f32 or of the frames' type; other chains
- * run stage by stage through intermediates the chain owns. */
+ * first task's inputs and the last task's output.  Fused chains never write
+ * their intermediates to HBM:
+ *  - the separable 8 -> 3 block downscaler (horizontal then vertical fir,
+ *    step 8, no wrap) runs on its own kernel (kernel 1) when its storage is
+ *    all f32, or 16-bit frames (bf16 or f16) with an intermediate and an
+ *    output each f32 or of the frames' type;
+ *  - any other f32 chain of 2 to 4 row passes (a fir along each row) and
+ *    column passes (down each column), each identity on the other axis and
+ *    the frames, with T <= 32, m <= 16, any step and input origin (wrap
+ *    included), runs on the fused separable chain kernel (kernel 4): tiles of
+ *    the last array, every pass in shared memory;
+ * other chains run stage by stage through intermediates the chain owns. */
 arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out);
 
 /* Replace the fir taps.  on_device = 0: `taps` is host memory, copied now.
@@ -194,9 +201,10 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
 
 /* Forward and reverse mode in one pass when grad_out is known before the
  * forward runs (e.g. loss = sum(W * out)): writes out, grad_in and grad_taps
- * as arol_task_run followed by arol_task_backward would, reading the inputs
- * once.  Only the fused separable downscaler chain supports it
- * (AROL_ERR_UNSUPPORTED otherwise). */
+ * as arol_task_run followed by arol_task_backward would.  The f32 fused
+ * separable downscaler (kernel 1, 16-byte aligned buffers) does both in one
+ * kernel that reads the inputs once; every other fir task or chain runs the
+ * forward, then the backward, on `stream`. */
 arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* grad_out, void* out,
                               void* grad_in, float* grad_taps, void* stream);
 

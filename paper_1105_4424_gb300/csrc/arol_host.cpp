@@ -4,6 +4,7 @@
 // autotuner) and the C ABI declared in include/arol.h.
 #include "arol.h"
 #include "arol_internal.h"
+#include "sepchain.h"
 
 #include <algorithm>
 #include <cinttypes>
@@ -629,6 +630,147 @@ bool match_pass(const arol_task_desc& d, int axis, Pass* ps) {
     return true;
 }
 
+// One task of a separable chain: a f32 fir along the columns of each row
+// (row pass, axis 1) or down the rows of each column (column pass, axis 0) of
+// a rank-2 array or of every frame of a rank-3 one: along its axis input
+// paving S, fitting 1, any origin, output paving m, fitting 1, origin 0; the
+// other axis and the frames identity.  Fills the pass (taps offset left 0)
+// and the frame count and input/output extents.
+bool match_sep_pass(const arol_task_desc& d, SepPassDev* p, int64_t* F, int64_t in_hw[2], int64_t out_hw[2]) {
+    if (d.elem != AROL_ELEM_FIR || d.n_in != 1) return false;
+    const arol_array_desc &a = d.in[0], &o = d.out[0];
+    if (a.dtype != AROL_F32 || o.dtype != AROL_F32) return false;
+    const int r = a.rank;
+    if ((r != 2 && r != 3) || o.rank != r || d.rep_rank != r) return false;
+    const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
+    if (ti.pattern_rank != 1 || to.pattern_rank != 1 || ti.pattern[0] > 32 || to.pattern[0] > 16) return false;
+    if (r == 3) {   // frames
+        if (a.shape[0] != d.rep[0] || o.shape[0] != d.rep[0] || ti.origin[0] || to.origin[0] || ti.fitting[0][0] ||
+            to.fitting[0][0])
+            return false;
+        for (int q = 0; q < 3; ++q)
+            if (ti.paving[0][q] != (q == 0) || to.paving[0][q] != (q == 0) || (q > 0 && (ti.paving[q][0] || to.paving[q][0])))
+                return false;
+    }
+    const int ar = r - 2, ac = r - 1;
+    int axis = -1;
+    if (ti.fitting[ac][0] == 1 && ti.fitting[ar][0] == 0) axis = 1;
+    else if (ti.fitting[ar][0] == 1 && ti.fitting[ac][0] == 0) axis = 0;
+    else return false;
+    const int ax = axis == 1 ? ac : ar, ot = axis == 1 ? ar : ac;
+    if (to.fitting[ax][0] != 1 || to.fitting[ot][0] != 0) return false;
+    if (ti.paving[ax][ot] || ti.paving[ot][ax] || ti.paving[ot][ot] != 1 || to.paving[ax][ot] || to.paving[ot][ax] ||
+        to.paving[ot][ot] != 1 || ti.origin[ot] || to.origin[ot] || to.origin[ax])
+        return false;
+    const int64_t n_in = a.shape[ax], R = d.rep[ax], m = to.pattern[0];
+    if (to.paving[ax][ax] != m || o.shape[ax] != m * R || d.rep[ot] != a.shape[ot] || o.shape[ot] != a.shape[ot]) return false;
+    if (n_in < 1 || R < 1 || n_in >= (1 << 30) || m * R >= (1 << 30) || a.shape[ot] >= (1 << 30)) return false;
+    const int64_t S = emod(ti.paving[ax][ax], n_in);
+    if (S < 1) return false;
+    std::memset(p, 0, sizeof *p);
+    p->axis = axis;
+    p->T = (int32_t)ti.pattern[0];
+    p->m = (int32_t)m;
+    p->S = (int32_t)S;
+    p->o = (int32_t)emod(ti.origin[ax], n_in);
+    p->n_in = (int32_t)n_in;
+    p->n_out = (int32_t)(m * R);
+    p->R = (int32_t)R;
+    *F = r == 3 ? a.shape[0] : 1;
+    in_hw[0] = a.shape[ar];
+    in_hw[1] = a.shape[ac];
+    out_hw[0] = o.shape[ar];
+    out_hw[1] = o.shape[ac];
+    return true;
+}
+
+// Plans a fused separable chain: the passes, the stage extents and the tile
+// of the last stage.  Region sizes separate into a row part (depending on
+// the tile row only) and a column part (tile column only), so the largest
+// shared buffer and the total work of a tile shape take one pass over tile
+// rows and one over tile columns.  Among the shapes whose shared memory
+// (taps and two buffers) fits kSepSmemFloats, the one with the least work
+// (elements of every stage's regions, halos included, weighted up for narrow
+// tiles whose row segments use DRAM sectors poorly) wins; shapes with fewer
+// tiles than kSepFillTiles pay for the idle SMs.
+constexpr int kSepSmemFloats = 12 * 1024;   // 48 KB: four CTAs per SM
+constexpr double kSepFillTiles = 4.0 * 152;  // four tiles per SM of a 152-SM GB300 (planning stays host-only)
+
+bool plan_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out) {
+    const int K = (int)descs.size();
+    if (K < 2 || K > kSepMaxPasses) return false;
+    SepChainDev d;
+    std::memset(&d, 0, sizeof d);
+    d.K = K;
+    int64_t F0 = -1, ntaps = 0;
+    for (int k = 0; k < K; ++k) {
+        int64_t F, ihw[2], ohw[2];
+        if (!match_sep_pass(descs[k], &d.p[k], &F, ihw, ohw)) return false;
+        if (k == 0) {
+            F0 = F;
+            d.H[0] = (int32_t)ihw[0];
+            d.W[0] = (int32_t)ihw[1];
+        } else if (F != F0 || ihw[0] != d.H[k] || ihw[1] != d.W[k]) {
+            return false;
+        }
+        d.H[k + 1] = (int32_t)ohw[0];
+        d.W[k + 1] = (int32_t)ohw[1];
+        d.p[k].tap_off = (int32_t)ntaps;
+        ntaps += (int64_t)d.p[k].m * d.p[k].T;
+    }
+    d.F = F0;
+    d.ntaps = (int32_t)ntaps;
+    const int taps4 = (d.ntaps + 3) & ~3;
+    static const int bhs[] = {4, 8, 16, 32, 64, 128};
+    static const int bws[] = {16, 32, 64, 128, 256, 512};
+    double best = 1e300;
+    bool found = false;
+    for (int bh : bhs)
+        for (int bw : bws) {
+            SepChainDev c = d;
+            c.BH = std::min<int32_t>(bh, std::max<int32_t>(d.H[K], 1));
+            c.BW = std::min<int32_t>(bw, std::max<int32_t>(d.W[K], 1));
+            c.tiles_y = (int32_t)((d.H[K] + c.BH - 1) / c.BH);
+            c.tiles_x = (int32_t)((d.W[K] + c.BW - 1) / c.BW);
+            if (c.tiles_y == 0 || c.tiles_x == 0) continue;
+            int64_t rmax[kSepMaxPasses + 1] = {}, cmax[kSepMaxPasses + 1] = {};
+            double rsum[kSepMaxPasses + 1] = {}, csum[kSepMaxPasses + 1] = {};
+            SepRange rows[kSepMaxPasses + 1], cols[kSepMaxPasses + 1];
+            for (int ty = 0; ty < c.tiles_y; ++ty) {
+                sep_regions(c, ty, 0, rows, cols);
+                for (int k = 0; k <= K; ++k) {
+                    rmax[k] = std::max<int64_t>(rmax[k], rows[k].len);
+                    rsum[k] += rows[k].len;
+                }
+            }
+            for (int tx = 0; tx < c.tiles_x; ++tx) {
+                sep_regions(c, 0, tx, rows, cols);
+                for (int k = 0; k <= K; ++k) {
+                    cmax[k] = std::max<int64_t>(cmax[k], cols[k].len);
+                    csum[k] += cols[k].len;
+                }
+            }
+            int64_t buf = 0;
+            double work = 0;
+            for (int k = 0; k < K; ++k) {
+                buf = std::max<int64_t>(buf, rmax[k] * cmax[k]);
+                work += rsum[k + 1] * csum[k + 1] + (k == 0 ? rsum[0] * csum[0] : 0);
+            }
+            if (taps4 + 2 * buf > kSepSmemFloats) continue;
+            const double tiles = (double)d.F * c.tiles_y * c.tiles_x;
+            const double fill = kSepFillTiles;
+            // narrow tiles read short row segments: a sector-efficiency factor
+            const double cost = work * std::max(1.0, fill / tiles) * (1.0 + 16.0 / c.BW);
+            if (cost < best) {
+                best = cost;
+                c.buf = (int32_t)((buf + 3) & ~int64_t(3));
+                *out = c;
+                found = true;
+            }
+        }
+    return found;
+}
+
 }  // namespace
 
 // ===================================================================== tasks
@@ -657,6 +799,8 @@ struct arol_task_s {
     bool ds_in16 = false, ds_mid16 = false, ds_out16 = false, ds_half16 = false;
     // matmul
     int mm_M = 0, mm_N = 0, mm_K = 0;
+    // fused separable chain (kernel 4)
+    SepChainDev sc{};
     unsigned* err_flag = nullptr;        // device word: bounded waits that gave up
     // backward scratch and inverse maps
     float* partials = nullptr;
@@ -961,6 +1105,9 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
             t->ds_half16 = di == AROL_F16;
         }
     }
+    // Any other chain of 2 .. 4 row and column passes (f32): the general
+    // fused separable chain kernel, when a tile shape fits shared memory.
+    if (t->kernel == 3 && plan_sepchain(t->descs, &t->sc)) t->kernel = 4;
     arol_task_info_t& in = t->info;
     in.kind = 1;
     in.kernel = t->kernel;
@@ -977,7 +1124,12 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     in.unique_bytes = elems_of(first.in[0]) * esize_of(first.in[0].dtype) + elems_of(last.out[0]) * esize_of(last.out[0].dtype);
     t->mids.assign(n - 1, nullptr);
     log_line("chain %p: %d tasks, %s", (void*)t, n,
-             t->kernel == 1 ? "fused separable downscaler" : "stage by stage through a one-member batch");
+             t->kernel == 1 ? "fused separable downscaler"
+             : t->kernel == 4 ? "fused separable chain (shared-memory tiles)"
+                              : "stage by stage through a one-member batch");
+    if (t->kernel == 4)
+        log_line("chain %p: tiles of %d x %d, %lld tiles per frame, %zu B of shared memory", (void*)t, t->sc.BH,
+                 t->sc.BW, (long long)t->sc.tiles_y * t->sc.tiles_x, sepchain_smem(t->sc));
     *out = t;
     return AROL_OK;
 }
@@ -1120,6 +1272,14 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
         p.x = (const float*)in[0];
         p.y = (float*)out[0];
         AROL_CUDA(launch_downscale_fwd(p, s), "downscale kernel launch");
+        return AROL_OK;
+    }
+    if (t->kernel == 4) {
+        SepChainDev d = t->sc;
+        d.x = (const float*)in[0];
+        d.y = (float*)out[0];
+        d.taps = taps;
+        AROL_CUDA(launch_sepchain(d, s), "fused chain kernel launch");
         return AROL_OK;
     }
     bool used = false;
@@ -1397,11 +1557,15 @@ arol_status arol_task_fwd_bwd(arol_task t, const void* const* in, const void* gr
                               float* grad_taps, void* stream) {
     AROL_TRACE();
     if (!t || !in || !in[0] || !grad_out || !out) return fail(AROL_ERR_INVALID, "null argument");
-    if (!(t->kind == 1 && t->kernel == 1) || t->ds_in16 || t->ds_mid16 || t->ds_out16)
-        return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd is implemented for the float32 fused separable downscaler chain only");
-    if (!aligned16(in[0]) || !aligned16(grad_in) || !aligned16(grad_out))
-        return fail(AROL_ERR_UNSUPPORTED, "fwd_bwd needs 16-byte aligned input, output-gradient and input-gradient buffers");
     cudaStream_t s = (cudaStream_t)stream;
+    if (!(t->kind == 1 && t->kernel == 1) || t->ds_in16 || t->ds_mid16 || t->ds_out16 || !aligned16(in[0]) ||
+        !aligned16(grad_in) || !aligned16(grad_out)) {
+        // every other task: the forward, then the backward (same results)
+        void* outs[1] = {out};
+        arol_status st = arol_task_run(t, in, outs, stream);
+        if (st != AROL_OK) return st;
+        return arol_task_backward(t, grad_out, in, grad_in, grad_taps, stream);
+    }
     const float* taps = nullptr;
     arol_status st = remember_device(t);
     if (st != AROL_OK) return st;

@@ -145,6 +145,11 @@ cudaError_t launch_downscale_bwd(const DownscaleDev& p, float* grad_taps, int np
                                  cudaStream_t s);
 int downscale_bwd_partials(int sm_count, int W);   // per-CTA partial slots the backward uses for width W
 
+// Fused chains of separable FIR passes (sepchain.h).
+struct SepChainDev;
+cudaError_t launch_sepchain(const SepChainDev& d, cudaStream_t s);
+size_t sepchain_smem(const SepChainDev& d);
+
 // tcgen05 matmul: C (M x N, f32) = A (M x K, bf16 row-major) . B (K x N, bf16 row-major).
 cudaError_t launch_matmul_tc(const void* A, const void* B, float* C, int M, int N, int K,
                              unsigned* err_flag, cudaStream_t s);

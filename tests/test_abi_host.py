@@ -143,15 +143,30 @@ def test_info_counts_the_downscaler_chain(B):
     assert info["scattered_elems"] == 64 * 1080 * 720 + 64 * 405 * 720
     for x in subs + [h]:
         B.arol_task_destroy(x)
-    # a chain that is not a block downscaler (overlapping step 4) runs unfused
+    # row passes with overlap (step 4 < T = 8) and wrap: the general fused chain
     tk, _ = W.config0()
     nxt = W.task((64, 16), "fir", [W.port((64, 48), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))],
                  [W.port((64, 16), (0, 0), ((1, 0), (0, 1)), ((0,), (1,)), (1,))], np.ones((1, 3), np.float32))
     subs = [B.arol_task_create(tk), B.arol_task_create(nxt)]
     h = B.arol_chain_create(subs)
+    assert B.arol_task_info(h)["kernel"] == 4
+    for x in subs + [h]:
+        B.arol_task_destroy(x)
+    # a task on a 2-D pattern is no row or column pass: stage by stage
+    subs = [B.arol_task_create(t) for t in unfusable_chain()]
+    h = B.arol_chain_create(subs)
     assert B.arol_task_info(h)["kernel"] == 3
     for x in subs + [h]:
         B.arol_task_destroy(x)
+
+
+def unfusable_chain():
+    """A 3 x 3 pattern FIR (one output per repetition), then a row pass."""
+    t1 = W.task((16, 16), "fir", [W.port((16, 16), (-1, -1), ((1, 0), (0, 1)), ((1, 0), (0, 1)), (3, 3))],
+                [W.port((16, 16), (0, 0), ((1, 0), (0, 1)), ((0,), (1,)), (1,))], np.ones((1, 9), np.float32))
+    t2 = W.task((16, 8), "fir", [W.port((16, 16), (0, 0), ((1, 0), (0, 2)), ((0,), (1,)), (2,))],
+                [W.port((16, 8), (0, 0), ((1, 0), (0, 1)), ((0,), (1,)), (1,))], np.ones((1, 2), np.float32))
+    return [t1, t2]
 
 
 def test_chain_rejects_mismatched_arrays(B):

@@ -130,16 +130,26 @@ def test_config1_full_size(arol):
     assert_fir_close(y, ref, fir_scale(chain, x, C.run_chain), what="config1 full")
 
 
-def test_unfused_chain_with_overlap_and_wrap(arol):
+def test_fused_chain_with_overlap_and_wrap(arol):
     tk, (x,) = W.config0(seed=3)
     g = W.rng(107)
     nxt = W.task((64, 16), "fir", [W.port((64, 48), (0, 0), ((1, 0), (0, 3)), ((0,), (1,)), (3,))],
                  [W.port((64, 16), (0, 0), ((1, 0), (0, 1)), ((0,), (1,)), (1,))],
                  g.standard_normal((1, 3)).astype(np.float32))
     c = arol.Chain([tk, nxt])
+    assert c.info["kernel"] == 4
+    y = host(c.run([dev(x)]))
+    assert_fir_close(y, O.run_chain([tk, nxt], [x])[0], fir_scale([tk, nxt], x), what="fused overlapping chain")
+
+
+def test_unfused_chain(arol):
+    from tests.test_abi_host import unfusable_chain
+    chain = unfusable_chain()
+    x = W.rng(108).standard_normal((16, 16)).astype(np.float32)
+    c = arol.Chain(chain)
     assert c.info["kernel"] == 3
     y = host(c.run([dev(x)]))
-    assert_fir_close(y, O.run_chain([tk, nxt], [x])[0], fir_scale([tk, nxt], x), what="unfused chain")
+    assert_fir_close(y, O.run_chain(chain, [x])[0], fir_scale(chain, x), what="unfused chain")
 
 
 def test_misaligned_input_takes_the_unfused_path(arol):
@@ -413,7 +423,7 @@ def test_three_task_chain_forward_and_backward(arol):
     chain = _three_task_chain(g)
     x = g.standard_normal((24, 32)).astype(np.float32)
     c = arol.Chain(chain)
-    assert c.info["kernel"] == 3
+    assert c.info["kernel"] == 4
     y = host(c.run([dev(x)]))
     assert_fir_close(y, O.run_chain(chain, [x])[0], fir_scale(chain, x), what="3-task chain")
     G = g.standard_normal((12, 8)).astype(np.float32)

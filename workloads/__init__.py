@@ -29,7 +29,8 @@ import numpy as np
 
 __all__ = [
     "rng", "port", "task", "fir_row_task", "downscale_chain",
-    "config0", "config1", "config1_bf16", "config1_f16", "config2", "config3", "config4",
+    "config0", "config1", "config1_bf16", "config1_f16", "config1_5to2", "config2", "config3", "config4",
+    "config0_scaled", "diagonal_fir", "separable_pass", "random_separable_chain",
     "bf16_round", "bf16_bits_to_f32", "f16_round", "random_tiler_task", "stencil27_csr",
 ]
 
@@ -362,6 +363,94 @@ def ragged_csr(n=3000, seed=0, max_row=70):
     col = np.concatenate(cols).astype(np.int32) if n else np.zeros(0, np.int32)
     vals = g.standard_normal(int(row_ptr[-1]))
     return row_ptr, col, vals
+
+
+def config1_5to2(seed=0, frames=64, height=1080, width=1920):
+    """The chained downscaler with 5-tap -> 2-output banks at step 4 on both
+    axes (overlapping windows that wrap at the right and bottom edges):
+    (frames, height, width) -> (frames, height / 2, width / 2).  Draw order:
+    X U[0,1), taps_h (2 x 5) N(0,1)/5, taps_v (2 x 5) N(0,1)/5."""
+    g = rng(seed)
+    x = g.random((frames, height, width), dtype=np.float32)
+    Hh = _taps(g, 2, 5)
+    Hv = _taps(g, 2, 5)
+    return downscale_chain(frames, height, width, Hh, Hv, step_h=4, step_v=4), [x]
+
+
+def config0_scaled(seed=0, frames=64, height=1080, width=1920):
+    """The 64 x 64 task's tiler (8-tap -> 3-output bank, step 4 along the row,
+    windows overlapping two-fold and wrapping at the row end) on frames x
+    height x width float32.  Draw order: X U[0,1), taps (3 x 8) N(0,1)/8."""
+    g = rng(seed)
+    x = g.random((frames, height, width), dtype=np.float32)
+    H = _taps(g, 3, 8)
+    reps = width // 4
+    t = task((frames, height, reps), "fir",
+             [port((frames, height, width), (0, 0, 0), ((1, 0, 0), (0, 1, 0), (0, 0, 4)), ((0,), (0,), (1,)), (8,))],
+             [port((frames, height, 3 * reps), (0, 0, 0), ((1, 0, 0), (0, 1, 0), (0, 0, 3)), ((0,), (0,), (1,)), (3,))],
+             H)
+    return t, [x]
+
+
+def diagonal_fir(seed=0, frames=64, height=1080, width=1920):
+    """A tiler that none of the specialised kernels takes: repetition (f, r0,
+    r1) reads the 8-element diagonal X[f, r0 + i, 8 r1 + i] (i < 8, rows mod
+    height), so every element is read exactly once but a pattern advances
+    along both array dimensions; an 8-tap -> 3-output bank writes 3
+    consecutive outputs per repetition: (frames, height, width) ->
+    (frames, height, 3 width / 8).  Draw order: X U[0,1), taps (3 x 8)."""
+    g = rng(seed)
+    x = g.random((frames, height, width), dtype=np.float32)
+    H = _taps(g, 3, 8)
+    reps = width // 8
+    t = task((frames, height, reps), "fir",
+             [port((frames, height, width), (0, 0, 0), ((1, 0, 0), (0, 1, 0), (0, 0, 8)), ((0,), (1,), (1,)), (8,))],
+             [port((frames, height, 3 * reps), (0, 0, 0), ((1, 0, 0), (0, 1, 0), (0, 0, 3)), ((0,), (0,), (1,)), (3,))],
+             H)
+    return t, [x]
+
+
+def separable_pass(in_shape, axis, T, m, step, origin, reps, taps):
+    """One pass of a separable chain on rank-2 (rows, cols) or rank-3
+    (frames, rows, cols) arrays: a fir along the columns of every row (axis
+    1) or down the rows of every column (axis 0), input paving `step` and
+    origin `origin` along that axis, `reps` repetitions there (windows wrap
+    modulo the extent), m outputs per repetition; identity on the other axis
+    and on the frames."""
+    d = len(in_shape)
+    ax = d - 1 if axis == 1 else d - 2
+    rep = tuple(reps if k == ax else in_shape[k] for k in range(d))
+    out_shape = tuple(m * reps if k == ax else in_shape[k] for k in range(d))
+    pin = tuple(tuple((step if k == ax else 1) if q == k else 0 for q in range(d)) for k in range(d))
+    pout = tuple(tuple((m if k == ax else 1) if q == k else 0 for q in range(d)) for k in range(d))
+    fit = tuple((1,) if k == ax else (0,) for k in range(d))
+    org = tuple(origin if k == ax else 0 for k in range(d))
+    return task(rep, "fir", [port(in_shape, org, pin, fit, (T,))],
+                [port(out_shape, (0,) * d, pout, fit, (m,))], taps)
+
+
+def random_separable_chain(g: np.random.Generator, max_side=40, frames=None):
+    """2 to 4 passes of random axis, taps T in 1..12, outputs m in 1..5,
+    step 1..9, origin, and repetitions (ceil(n / step), or up to three times
+    the extent: windows that wrap several times), on frames x rows x cols
+    (rank 2 when frames is 1).  Draw order: frames, rows, cols, then per pass
+    axis, T, m, step, the repetition rule, reps, origin, taps N(0,1)/T.
+    Returns (chain, input shape)."""
+    F = int(g.integers(1, 4)) if frames is None else frames
+    shape = (int(g.integers(1, max_side + 1)), int(g.integers(1, max_side + 1)))
+    if F > 1:
+        shape = (F,) + shape
+    chain, cur = [], shape
+    for _ in range(int(g.integers(2, 5))):
+        axis = int(g.integers(0, 2))
+        n = cur[-1] if axis == 1 else cur[-2]
+        T, m, step = int(g.integers(1, 13)), int(g.integers(1, 6)), int(g.integers(1, 10))
+        reps = -(-n // step) if g.random() < 0.6 else int(g.integers(1, 3 * n + 3))
+        origin = int(g.integers(0, n))
+        t = separable_pass(cur, axis, T, m, step, origin, reps, _taps(g, m, T))
+        chain.append(t)
+        cur = t["outputs"][0]["shape"]
+    return chain, shape
 
 
 def chain_batch(seed=0, n=128):
