@@ -666,7 +666,7 @@ bool match_sep_pass(const arol_task_desc& d, SepPassDev* p, int64_t* F, int64_t 
     if (to.paving[ax][ax] != m || o.shape[ax] != m * R || d.rep[ot] != a.shape[ot] || o.shape[ot] != a.shape[ot]) return false;
     if (n_in < 1 || R < 1 || n_in >= (1 << 30) || m * R >= (1 << 30) || a.shape[ot] >= (1 << 30)) return false;
     const int64_t S = emod(ti.paving[ax][ax], n_in);
-    if (S < 1) return false;
+    if (S < 1 || S * R >= (1 << 30) || S * 8 >= (1 << 30)) return false;   // the kernel's 32-bit window arithmetic
     std::memset(p, 0, sizeof *p);
     p->axis = axis;
     p->T = (int32_t)ti.pattern[0];
@@ -690,10 +690,11 @@ bool match_sep_pass(const arol_task_desc& d, SepPassDev* p, int64_t* F, int64_t 
 // shared buffer and the total work of a tile shape take one pass over tile
 // rows and one over tile columns.  Among the shapes whose shared memory
 // (taps and two buffers) fits kSepSmemFloats, the one with the least work
-// (elements of every stage's regions, halos included, weighted up for narrow
-// tiles whose row segments use DRAM sectors poorly) wins; shapes with fewer
-// tiles than kSepFillTiles pay for the idle SMs.
-constexpr int kSepSmemFloats = 12 * 1024;   // 48 KB: four CTAs per SM
+// wins: staging the window, and T multiply-adds per output of every pass
+// (halos included) divided by the pass's lane use, weighted up for narrow
+// tiles whose row segments use DRAM sectors poorly; shapes with fewer tiles
+// than kSepFillTiles pay for the idle SMs.
+constexpr int kSepSmemFloats = 14 * 1024;   // 56 KB: four CTAs per SM
 constexpr double kSepFillTiles = 4.0 * 152;  // four tiles per SM of a 152-SM GB300 (planning stays host-only)
 
 bool plan_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out) {
@@ -720,8 +721,21 @@ bool plan_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out) {
     }
     d.F = F0;
     d.ntaps = (int32_t)ntaps;
-    const int taps4 = (d.ntaps + 3) & ~3;
-    static const int bhs[] = {4, 8, 16, 32, 64, 128};
+    int max_m = 1;
+    for (int k = 0; k < K; ++k) max_m = std::max(max_m, (int)d.p[k].m);
+    const int taps4 = kSepMaxPasses * 32 * (max_m <= 4 ? 4 : 16);   // every pass's taps, transposed
+    // tile heights: powers of two, and those whose window, through the first
+    // column pass, is just under a multiple of 32 rows (the row passes' lanes
+    // walk rows 32 at a time)
+    std::vector<int> bhs = {4, 8, 16, 32, 64, 128};
+    for (int k = 0; k < K; ++k) {
+        if (d.p[k].axis != 0) continue;
+        for (int rows = 32; rows <= 128; rows += 32) {
+            const int reps = (rows - d.p[k].T) / d.p[k].S + 1;
+            if (reps >= 1) bhs.push_back(reps * d.p[k].m);
+        }
+        break;
+    }
     static const int bws[] = {16, 32, 64, 128, 256, 512};
     double best = 1e300;
     bool found = false;
@@ -750,20 +764,28 @@ bool plan_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out) {
                     csum[k] += cols[k].len;
                 }
             }
-            int64_t buf = 0;
-            double work = 0;
+            int64_t buf[2] = {0, 0};
+            double work = 2.0 * rsum[0] * csum[0];   // staging the window
             for (int k = 0; k < K; ++k) {
-                buf = std::max<int64_t>(buf, rmax[k] * cmax[k]);
-                work += rsum[k + 1] * csum[k + 1] + (k == 0 ? rsum[0] * csum[0] : 0);
+                // rows of an odd stride (cols | 1), whole 16-byte units per buffer
+                buf[k & 1] = std::max<int64_t>(buf[k & 1], (rmax[k] * (cmax[k] | 1) + 3) & ~int64_t(3));
+                // a pass's lanes walk the region's rows (row pass) or columns
+                // (column pass) 32 at a time: T multiply-adds per output,
+                // lanes past the region's edge idle
+                const int64_t lanes = d.p[k].axis == 1 ? rmax[k] : cmax[k];
+                const double util = (double)lanes / (32.0 * (double)((lanes + 31) / 32));
+                work += d.p[k].T * rsum[k + 1] * csum[k + 1] / util;
             }
-            if (taps4 + 2 * buf > kSepSmemFloats) continue;
+            if (taps4 + buf[0] + buf[1] > kSepSmemFloats) continue;
             const double tiles = (double)d.F * c.tiles_y * c.tiles_x;
+            if (tiles >= 2147483647.0) continue;   // the kernel counts tiles in 32 bits
             const double fill = kSepFillTiles;
             // narrow tiles read short row segments: a sector-efficiency factor
-            const double cost = work * std::max(1.0, fill / tiles) * (1.0 + 16.0 / c.BW);
+            const double cost = work * std::max(1.0, fill / tiles) * (1.0 + 8.0 / c.BW);
             if (cost < best) {
                 best = cost;
-                c.buf = (int32_t)((buf + 3) & ~int64_t(3));
+                c.buf = (int32_t)buf[0];
+                c.buf1 = (int32_t)buf[1];
                 *out = c;
                 found = true;
             }
@@ -799,8 +821,11 @@ struct arol_task_s {
     bool ds_in16 = false, ds_mid16 = false, ds_out16 = false, ds_half16 = false;
     // matmul
     int mm_M = 0, mm_N = 0, mm_K = 0;
-    // fused separable chain (kernel 4)
+    // fused separable chain (kernel 4): parameters and region tables (rows
+    // per tile row, then columns per tile column), on the host and the device
     SepChainDev sc{};
+    std::vector<int32_t> sc_tab;
+    int32_t* sc_tab_dev = nullptr;
     unsigned* err_flag = nullptr;        // device word: bounded waits that gave up
     // backward scratch and inverse maps
     float* partials = nullptr;
@@ -1107,7 +1132,28 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     }
     // Any other chain of 2 .. 4 row and column passes (f32): the general
     // fused separable chain kernel, when a tile shape fits shared memory.
-    if (t->kernel == 3 && plan_sepchain(t->descs, &t->sc)) t->kernel = 4;
+    if (t->kernel == 3 && plan_sepchain(t->descs, &t->sc)) {
+        t->kernel = 4;
+        const SepChainDev& c = t->sc;
+        const int K1 = c.K + 1;
+        t->sc_tab.assign((size_t)2 * K1 * (c.tiles_y + c.tiles_x), 0);
+        SepRange rows[kSepMaxPasses + 1], cols[kSepMaxPasses + 1];
+        for (int ty = 0; ty < c.tiles_y; ++ty) {
+            sep_regions(c, ty, 0, rows, cols);
+            for (int k = 0; k < K1; ++k) {
+                t->sc_tab[(size_t)2 * (ty * K1 + k)] = rows[k].start;
+                t->sc_tab[(size_t)2 * (ty * K1 + k) + 1] = rows[k].len;
+            }
+        }
+        const size_t coff = (size_t)2 * K1 * c.tiles_y;
+        for (int tx = 0; tx < c.tiles_x; ++tx) {
+            sep_regions(c, 0, tx, rows, cols);
+            for (int k = 0; k < K1; ++k) {
+                t->sc_tab[coff + (size_t)2 * (tx * K1 + k)] = cols[k].start;
+                t->sc_tab[coff + (size_t)2 * (tx * K1 + k) + 1] = cols[k].len;
+            }
+        }
+    }
     arol_task_info_t& in = t->info;
     in.kind = 1;
     in.kernel = t->kernel;
@@ -1275,10 +1321,20 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
         return AROL_OK;
     }
     if (t->kernel == 4) {
+        if (!t->sc_tab_dev) {
+            if ((st = dev_alloc(t, (void**)&t->sc_tab_dev, t->sc_tab.size() * sizeof(int32_t), "cudaMalloc(chain tiles)")) !=
+                AROL_OK)
+                return st;
+            AROL_CUDA(cudaMemcpyAsync(t->sc_tab_dev, t->sc_tab.data(), t->sc_tab.size() * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, s),
+                      "upload chain tiles");
+        }
         SepChainDev d = t->sc;
         d.x = (const float*)in[0];
         d.y = (float*)out[0];
         d.taps = taps;
+        d.row_tab = t->sc_tab_dev;
+        d.col_tab = t->sc_tab_dev + (size_t)2 * (d.K + 1) * d.tiles_y;
         AROL_CUDA(launch_sepchain(d, s), "fused chain kernel launch");
         return AROL_OK;
     }
@@ -1613,6 +1669,7 @@ void arol_task_destroy(arol_task t) {
         cudaGetDevice(&cur);
         if (cur != t->device) cudaSetDevice(t->device);
         free_dev(t->taps_dev);
+        free_dev(t->sc_tab_dev);
         for (void* p : t->mids) free_dev(p);
         free_dev(t->err_flag);
         free_dev(t->partials);

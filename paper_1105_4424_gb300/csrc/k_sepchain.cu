@@ -3,18 +3,24 @@
 // downscaler (Sec. 5 associatedParts; repetitive tasks on the GPU, Sec. 7).
 //
 // One CTA per tile of the last stage.  It loads the tile's stage-0 window
-// (rows and columns from sep_regions, wrapped at the array edges) into shared
+// (rows and columns from sep_regions, tabulated by the host per tile row and
+// per tile column, wrapped at the array edges) into shared
 // memory, then runs the passes in order between two shared buffers; the last
 // pass writes the tile to global memory.  The intermediate arrays never
 // reach HBM: only halos (the T - S overlap of neighbouring tiles' windows)
 // are read twice, mostly from L2.
 //
-// A pass's thread computes all m outputs of one repetition (one row of a row
-// pass, one column of a column pass), the m accumulators in registers (m is a
-// template parameter), the taps in shared memory (one broadcast load per tap
-// and output).  Column passes give consecutive threads consecutive columns:
-// conflict-free shared loads and coalesced global stores.
+// In a pass, a warp takes one repetition at a time (its index arithmetic is
+// the same for every lane) and its lanes take the region's rows (row pass)
+// or columns (column pass); a thread computes the m outputs of its row or
+// column, the m accumulators in registers (m is a template parameter), the
+// taps transposed in shared memory (one broadcast load feeds m FMAs).  Region rows have an odd stride,
+// so both kinds of pass read shared memory without bank conflicts; column
+// passes store consecutive columns from consecutive lanes.
+#include <algorithm>
+
 #include "arol_internal.h"
+#include "ptx.h"
 #include "sepchain.h"
 
 namespace arol {
@@ -27,77 +33,119 @@ __device__ __forceinline__ int wrap_pos(int v, int n) {
     return v;
 }
 
-// Row pass k: input region (rows ri, cols ci) in `in` (row stride ci.len),
-// output region (rows ri, cols co) to `out` (row stride ldo; a global tile
-// when `global`).
-template <int M>
-__device__ void row_pass(const SepPassDev& p, const float* hk, const float* in, SepRange ri, SepRange ci,
-                         SepRange co, float* out, int64_t ldo) {
+// Row stride (floats) of a region of `cols` columns in shared memory: odd,
+// so lanes that walk down a column of the region hit distinct banks.
+__device__ __forceinline__ int ld_of(int cols) { return cols | 1; }
+
+// Walks the repetitions ra + w, ra + w + nw, ... of a pass (w: this warp,
+// nw: the warps of the CTA) and keeps, for the current one, where it reads
+// the input region (`base`, a local index) and where its m outputs start in
+// the output region (`first`; some may fall outside).  Each step adds nw
+// repetitions with one conditional subtract; only a step past repetition
+// R - 1 recomputes from the definition.  Warp-uniform.
+struct RepWalk {
+    int ur, r, base, first;
+    int step_base, step_first;
+    __device__ __forceinline__ void set(const SepPassDev& p, SepRange in, SepRange out) {
+        r = ur % p.R;
+        // o + S r - start fits 32 bits: the host keeps S R and the extents below 2^30
+        const int b = (p.o + p.S * r - in.start) % p.n_in;
+        base = b < 0 ? b + p.n_in : b;
+        first = sep_upos(p, ur) - out.start;
+    }
+    __device__ __forceinline__ void start(const SepPassDev& p, int ur0, int nw, SepRange in, SepRange out) {
+        ur = ur0;
+        step_base = (p.S * nw) % p.n_in;
+        step_first = p.m * nw;
+        set(p, in, out);
+    }
+    __device__ __forceinline__ void next(const SepPassDev& p, int nw, SepRange in, SepRange out) {
+        ur += nw;
+        if (r + nw >= p.R) {
+            set(p, in, out);
+            return;
+        }
+        r += nw;
+        base += step_base;
+        if (base >= p.n_in) base -= p.n_in;
+        first += step_first;
+    }
+};
+
+// Row pass: warps take repetitions, lanes take the region's rows (all rows
+// of a row pass share the repetition's columns).  Input rows of stride
+// ld_of(ci.len), output rows of stride ldo; ht: the pass's taps transposed,
+// ht[kk * G + j] = H[j, kk] (G: the kernel's tap row, >= m).
+template <int M, int G>
+__device__ void row_pass(const SepPassDev& p, const float* ht, const float* in, SepRange ri, SepRange ci, SepRange co,
+                         float* out, int64_t ldo) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int ra = co.start / M;   // the first output position is < n_out
     const int nrep = sep_urep(p, co.start + co.len - 1) - ra + 1;
-    const int n = ri.len * nrep;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int i = e / nrep, ur = ra + (e - i * nrep);
-        const int r = ur % p.R;
-        int base = (int)(((int64_t)p.o + (int64_t)p.S * r - ci.start) % p.n_in);
-        if (base < 0) base += p.n_in;
-        const float* src = in + (int64_t)i * ci.len + base;
-        float acc[M];
+    const int ldi = ld_of(ci.len), T = p.T;
+    RepWalk w;
+    w.start(p, ra + warp, nwarps, ci, co);
+    for (int rr = warp; rr < nrep; rr += nwarps, w.next(p, nwarps, ci, co)) {
+        for (int i = lane; i < ri.len; i += 32) {
+            const float* src = in + i * ldi + w.base;
+            float acc[M];
 #pragma unroll
-        for (int j = 0; j < M; ++j) acc[j] = 0.f;
-        for (int kk = 0; kk < p.T; ++kk) {
-            const float v = src[kk];
+            for (int j = 0; j < M; ++j) acc[j] = 0.f;
+#pragma unroll 4
+            for (int kk = 0; kk < T; ++kk) {
+                const float v = src[kk];
+                const float* h = ht + kk * G;
 #pragma unroll
-            for (int j = 0; j < M; ++j) acc[j] = fmaf(hk[j * p.T + kk], v, acc[j]);
-        }
-        const int q0 = sep_upos(p, ur) - co.start;
+                for (int j = 0; j < M; ++j) acc[j] = fmaf(h[j], v, acc[j]);
+            }
+            float* o = out + (int64_t)i * ldo + w.first;
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            const int q = q0 + j;
-            if (q >= 0 && q < co.len) out[(int64_t)i * ldo + q] = acc[j];
+            for (int j = 0; j < M; ++j)
+                if (w.first + j >= 0 && w.first + j < co.len) o[j] = acc[j];
         }
     }
 }
 
-// Column pass k: input region (rows ri, cols ci), output region (rows ro,
-// cols ci).
-template <int M>
-__device__ void col_pass(const SepPassDev& p, const float* hk, const float* in, SepRange ri, SepRange ci,
-                         SepRange ro, float* out, int64_t ldo) {
+// Column pass: warps take repetitions, lanes take the region's columns.
+template <int M, int G>
+__device__ void col_pass(const SepPassDev& p, const float* ht, const float* in, SepRange ri, SepRange ci, SepRange ro,
+                         float* out, int64_t ldo) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int ra = ro.start / M;
     const int nrep = sep_urep(p, ro.start + ro.len - 1) - ra + 1;
-    const int n = nrep * ci.len;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int rr = e / ci.len, q = e - rr * ci.len;
-        const int ur = ra + rr;
-        const int r = ur % p.R;
-        int base = (int)(((int64_t)p.o + (int64_t)p.S * r - ri.start) % p.n_in);
-        if (base < 0) base += p.n_in;
-        const float* src = in + (int64_t)base * ci.len + q;
-        float acc[M];
+    const int ldi = ld_of(ci.len), T = p.T;
+    RepWalk w;
+    w.start(p, ra + warp, nwarps, ri, ro);
+    for (int rr = warp; rr < nrep; rr += nwarps, w.next(p, nwarps, ri, ro)) {
+        for (int c = lane; c < ci.len; c += 32) {
+            const float* src = in + w.base * ldi + c;
+            float acc[M];
 #pragma unroll
-        for (int j = 0; j < M; ++j) acc[j] = 0.f;
-        for (int kk = 0; kk < p.T; ++kk) {
-            const float v = src[(int64_t)kk * ci.len];
+            for (int j = 0; j < M; ++j) acc[j] = 0.f;
+#pragma unroll 4
+            for (int kk = 0; kk < T; ++kk) {
+                const float v = src[kk * ldi];
+                const float* h = ht + kk * G;
 #pragma unroll
-            for (int j = 0; j < M; ++j) acc[j] = fmaf(hk[j * p.T + kk], v, acc[j]);
-        }
-        const int i0 = sep_upos(p, ur) - ro.start;
+                for (int j = 0; j < M; ++j) acc[j] = fmaf(h[j], v, acc[j]);
+            }
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            const int i = i0 + j;
-            if (i >= 0 && i < ro.len) out[(int64_t)i * ldo + q] = acc[j];
+            for (int j = 0; j < M; ++j) {
+                const int i = w.first + j;
+                if (i >= 0 && i < ro.len) out[(int64_t)i * ldo + c] = acc[j];
+            }
         }
     }
 }
 
-template <bool kRow>
+template <bool kRow, int kMaxM>
 __device__ void run_pass(const SepPassDev& p, const float* hk, const float* in, SepRange ri, SepRange ci, SepRange ro,
                          SepRange co, float* out, int64_t ldo) {
-#define AROL_SEP_CASE(M)                                              \
-    case M:                                                           \
-        if (kRow) row_pass<M>(p, hk, in, ri, ci, co, out, ldo);      \
-        else col_pass<M>(p, hk, in, ri, ci, ro, out, ldo);           \
+    constexpr int G = kMaxM <= 4 ? 4 : 16;   // the kernel's transposed-tap row (kMaxM >= every m)
+#define AROL_SEP_CASE(M)                                                                          \
+    case M:                                                                                       \
+        if (kRow) row_pass<(M <= kMaxM ? M : kMaxM), G>(p, hk, in, ri, ci, co, out, ldo);       \
+        else col_pass<(M <= kMaxM ? M : kMaxM), G>(p, hk, in, ri, ci, ro, out, ldo);            \
         break;
     switch (p.m) {
         AROL_SEP_CASE(1) AROL_SEP_CASE(2) AROL_SEP_CASE(3) AROL_SEP_CASE(4)
@@ -109,47 +157,79 @@ __device__ void run_pass(const SepPassDev& p, const float* hk, const float* in, 
 #undef AROL_SEP_CASE
 }
 
-__global__ void __launch_bounds__(kSepThreads) sepchain_kernel(const SepChainDev d) {
-    extern __shared__ __align__(16) float ssm[];
-    float* taps = ssm;
-    float* buf[2] = {ssm + ((d.ntaps + 3) & ~3), ssm + ((d.ntaps + 3) & ~3) + d.buf};
-    for (int i = threadIdx.x; i < d.ntaps; i += blockDim.x) taps[i] = __ldg(d.taps + i);
-    const int K = d.K;
-    const int64_t ntile = (int64_t)d.tiles_y * d.tiles_x;
-    for (int64_t t = blockIdx.x; t < d.F * ntile; t += gridDim.x) {
-        const int64_t f = t / ntile;
-        const int tt = (int)(t - f * ntile);
-        const int ty = tt / d.tiles_x, tx = tt - ty * d.tiles_x;
-        SepRange rows[kSepMaxPasses + 1], cols[kSepMaxPasses + 1];
-        sep_regions(d, ty, tx, rows, cols);
-        // stage 0 window: rows (rs + i) mod H0, columns (cs + q) mod W0
-        {
-            const float* xf = d.x + f * (int64_t)d.H[0] * d.W[0];
-            const int nr = rows[0].len, nc = cols[0].len;
-            float* dst = buf[0];
-            for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
-                const int i = e / nc, q = e - i * nc;
-                const int gr = wrap_pos(rows[0].start + i, d.H[0]), gc = wrap_pos(cols[0].start + q, d.W[0]);
-                dst[e] = __ldg(xf + (int64_t)gr * d.W[0] + gc);
-            }
+// Stage-0 window: rows (rs + i) mod H0, columns (cs + q) mod W0, one warp per
+// row, lanes along it with 4-byte asynchronous copies (each row a run of at
+// most a few contiguous pieces, split where it wraps).
+__device__ void stage_window(const float* xf, int H0, int W0, SepRange rows, SepRange cols, float* dst) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int ld = ld_of(cols.len);
+    for (int i = warp; i < rows.len; i += nwarps) {
+        int gr = rows.start + i;
+        while (gr >= H0) gr -= H0;
+        const float* src = xf + (int64_t)gr * W0;
+        float* d = dst + i * ld;
+        // pieces [q0, q1) of the window that are contiguous in the row
+        int q0 = 0, c = cols.start;
+        while (q0 < cols.len) {
+            while (c >= W0) c -= W0;
+            const int q1 = min(cols.len, q0 + (W0 - c));
+            for (int q = q0 + lane; q < q1; q += 32) ptx::cp_async4(d + q, src + c + (q - q0));
+            c += q1 - q0;
+            q0 = q1;
         }
+    }
+    ptx::cp_async_wait_all();
+}
+
+// kMaxM: the largest m of the chain's passes the instantiation handles (the
+// one for m <= 4 keeps to 64 registers, four CTAs per SM).
+template <int kMaxM>
+__global__ void __launch_bounds__(kSepThreads, kMaxM <= 4 ? 4 : 2) sepchain_kernel(const SepChainDev d) {
+    extern __shared__ __align__(16) float ssm[];
+    // each pass's taps transposed: ht_k[kk * G + j] = H_k[j, kk], G = 4 (m <= 4) or 16
+    constexpr int G = kMaxM <= 4 ? 4 : 16;
+    float* taps = ssm;
+    float* buf[2] = {ssm + kSepMaxPasses * 32 * G, ssm + kSepMaxPasses * 32 * G + d.buf};
+    for (int k = 0; k < d.K; ++k)
+        for (int e = threadIdx.x; e < 32 * G; e += blockDim.x) {
+            const int kk = e / G, j = e - kk * G;
+            taps[k * 32 * G + e] = (kk < d.p[k].T && j < d.p[k].m) ? __ldg(d.taps + d.p[k].tap_off + j * d.p[k].T + kk) : 0.f;
+        }
+    const int K = d.K;
+    const uint32_t ntile = (uint32_t)d.tiles_y * (uint32_t)d.tiles_x;   // F * ntile < 2^31 (host)
+    const uint32_t total = (uint32_t)d.F * ntile;
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const uint32_t f = t / ntile;
+        const uint32_t tt = t - f * ntile;
+        const int ty = (int)(tt / (uint32_t)d.tiles_x), tx = (int)(tt - (uint32_t)ty * (uint32_t)d.tiles_x);
+        SepRange rows[kSepMaxPasses + 1], cols[kSepMaxPasses + 1];
+        const int2* rt = reinterpret_cast<const int2*>(d.row_tab) + ty * (K + 1);
+        const int2* ct = reinterpret_cast<const int2*>(d.col_tab) + tx * (K + 1);
+        for (int k = 0; k <= K; ++k) {
+            const int2 a = __ldg(rt + k), b = __ldg(ct + k);
+            rows[k].start = a.x;
+            rows[k].len = a.y;
+            cols[k].start = b.x;
+            cols[k].len = b.y;
+        }
+        __syncthreads();   // the previous tile's last pass is done with the buffers
+        stage_window(d.x + (int64_t)f * d.H[0] * d.W[0], d.H[0], d.W[0], rows[0], cols[0], buf[0]);
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kSepMaxPasses; ++k) {
-            if (k >= K) break;
+        for (int k = 0; k < K; ++k) {
             const SepPassDev& p = d.p[k];
             const float* in = buf[k & 1];
             float* out;
             int64_t ldo;
             if (k + 1 == K) {
-                out = d.y + (f * d.H[K] + rows[K].start) * (int64_t)d.W[K] + cols[K].start;
+                out = d.y + ((int64_t)f * d.H[K] + rows[K].start) * (int64_t)d.W[K] + cols[K].start;
                 ldo = d.W[K];
             } else {
                 out = buf[(k + 1) & 1];
-                ldo = cols[k + 1].len;
+                ldo = ld_of(cols[k + 1].len);
             }
-            if (p.axis == 1) run_pass<true>(p, taps + p.tap_off, in, rows[k], cols[k], rows[k + 1], cols[k + 1], out, ldo);
-            else run_pass<false>(p, taps + p.tap_off, in, rows[k], cols[k], rows[k + 1], cols[k + 1], out, ldo);
+            const float* ht = taps + k * 32 * G;
+            if (p.axis == 1) run_pass<true, kMaxM>(p, ht, in, rows[k], cols[k], rows[k + 1], cols[k + 1], out, ldo);
+            else run_pass<false, kMaxM>(p, ht, in, rows[k], cols[k], rows[k + 1], cols[k + 1], out, ldo);
             __syncthreads();
         }
     }
@@ -158,25 +238,35 @@ __global__ void __launch_bounds__(kSepThreads) sepchain_kernel(const SepChainDev
 }  // namespace
 
 size_t sepchain_smem(const SepChainDev& d) {
-    return ((size_t)((d.ntaps + 3) & ~3) + 2 * (size_t)d.buf) * sizeof(float);
+    int max_m = 1;
+    for (int k = 0; k < d.K; ++k) max_m = std::max(max_m, (int)d.p[k].m);
+    return ((size_t)kSepMaxPasses * 32 * (max_m <= 4 ? 4 : 16) + (size_t)d.buf + (size_t)d.buf1) * sizeof(float);
+}
+
+template <int kMaxM>
+cudaError_t launch_sepchain_m(const SepChainDev& d, int64_t work, cudaStream_t s) {
+    const size_t smem = sepchain_smem(d);
+    static size_t attr = 0;
+    static int occ = 0;
+    if (smem > attr || occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(sepchain_kernel<kMaxM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)std::max(smem, attr));
+        if (e != cudaSuccess) return e;
+        attr = std::max(smem, attr);
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sepchain_kernel<kMaxM>, kSepThreads, smem);
+    const int64_t cap = (int64_t)device_sm_count() * (occ > 0 ? occ : 1);
+    sepchain_kernel<kMaxM><<<(int)(work < cap ? work : cap), kSepThreads, smem, s>>>(d);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sepchain(const SepChainDev& d, cudaStream_t s) {
     const int64_t work = d.F * (int64_t)d.tiles_y * d.tiles_x;
     if (work <= 0) return cudaSuccess;
-    const size_t smem = sepchain_smem(d);
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(sepchain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = smem;
-    }
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sepchain_kernel, kSepThreads, smem);
-    if (occ < 1) occ = 1;
-    const int64_t cap = (int64_t)device_sm_count() * occ;
-    sepchain_kernel<<<(int)(work < cap ? work : cap), kSepThreads, smem, s>>>(d);
-    return cudaGetLastError();
+    if (!d.row_tab || !d.col_tab) return cudaErrorInvalidValue;
+    int max_m = 1;
+    for (int k = 0; k < d.K; ++k) max_m = std::max(max_m, (int)d.p[k].m);
+    return max_m <= 4 ? launch_sepchain_m<4>(d, work, s) : launch_sepchain_m<16>(d, work, s);
 }
 
 }  // namespace arol

@@ -41,10 +41,16 @@ struct SepChainDev {
     int32_t K;         // passes, 2 .. kSepMaxPasses
     int32_t BH, BW;    // tile of the last stage
     int32_t tiles_y, tiles_x;
-    int32_t buf;       // floats of one shared region buffer (the largest region of stages 0 .. K - 1)
+    int32_t buf;       // floats of shared buffer 0: the largest region of the even stages < K (row stride odd)
+    int32_t buf1;      // floats of shared buffer 1: the largest region of the odd stages < K
     int32_t ntaps;     // floats of all passes' taps
     int32_t H[kSepMaxPasses + 1], W[kSepMaxPasses + 1];
     SepPassDev p[kSepMaxPasses];
+    // sep_regions, tabulated by the host: the rows of stages 0 .. K for every
+    // tile row (row_tab[ty * (K + 1) + k]) and the columns for every tile
+    // column (col_tab[tx * (K + 1) + k]); each is a SepRange (start, len)
+    const int32_t* row_tab;
+    const int32_t* col_tab;
 };
 
 // Range of one axis of one stage: local index i of the region holds the
