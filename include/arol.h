@@ -168,6 +168,24 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out);
  * other chains run stage by stage through intermediates the chain owns. */
 arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out);
 
+/* Equal partition of a task over devices (Sec. 7: the generated host code
+ * spreads the repetitive tasks equally over 1, 2 or 4 GPUs; every repetition
+ * is independent, so the parts need no exchange).  Host only.  `desc` must
+ * have a frame dimension: in every port, array dimension 0 is repetition
+ * dimension 0 (extent rep[0], paving 1 on it and 0 elsewhere, fitting 0,
+ * origin 0).  Part `part` (0 <= part < parts) gets frames [*first_frame,
+ * *first_frame + count), count = rep[0] / parts, plus one for the first
+ * rep[0] % parts parts; *out is `desc` on those frames alone (rep[0] and
+ * every port's dimension 0 set to count), whose arrays are the frame slices
+ * of the full ones: the part's device holds only its slices.  A chain is
+ * sharded task by task with the same part.  Taps are not copied (the
+ * fir_taps_host pointer is kept).  The tap gradients of a backward are
+ * partial sums per part: their sum over the parts (an all-reduce) is the
+ * full gradient; grad_in is the part's slice.  AROL_ERR_UNSUPPORTED without
+ * a frame dimension, AROL_ERR_INVALID for a bad part. */
+arol_status arol_task_shard_frames(const arol_task_desc* desc, int parts, int part, arol_task_desc* out,
+                                   int64_t* first_frame);
+
 /* Replace the fir taps.  on_device = 0: `taps` is host memory, copied now.
  * on_device = 1: `taps` is a device pointer the caller keeps alive and
  * unchanged while runs that use it are in flight (it is read, never written).

@@ -75,6 +75,7 @@ def _load():
         "arol_batch_run_per_task": [c_vp, P(c_vp), P(c_vp), c_vp],
         "arol_batch_tune": [c_vp, P(c_vp), P(c_vp), c_vp, ctypes.c_int],
         "arol_batch_config": [c_vp, P(c_i64), P(c_i32), P(c_i32)],
+        "arol_task_shard_frames": [P(TaskDesc), ctypes.c_int, ctypes.c_int, P(TaskDesc), P(c_i64)],
         "arol_batch_sync_status": [c_vp, c_vp],
         "arol_last_error": [ctypes.c_char_p, ctypes.c_size_t],
         "arol_downscale_backward_noalloc": [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp],
@@ -199,6 +200,35 @@ def task_desc(spec) -> tuple:
         d.fir_m, d.fir_T = keep.shape
         d.fir_taps_host = keep.ctypes.data
     return d, keep
+
+
+def spec_of_desc(d, taps=None) -> dict:
+    """The task dict of a TaskDesc (the inverse of task_desc; taps given
+    separately, since a descriptor only points at them)."""
+    inv = {v: k for k, v in DTYPE.items()}
+
+    def port_of(a, t):
+        r = a.rank
+        return {"shape": tuple(int(a.shape[k]) for k in range(r)), "dtype": inv[a.dtype],
+                "origin": tuple(int(t.origin[k]) for k in range(r)),
+                "paving": tuple(tuple(int(t.paving[k][q]) for q in range(d.rep_rank)) for k in range(r)),
+                "fitting": tuple(tuple(int(t.fitting[k][i]) for i in range(t.pattern_rank)) for k in range(r)),
+                "pattern": tuple(int(t.pattern[i]) for i in range(t.pattern_rank))}
+    return {"rep": tuple(int(d.rep[q]) for q in range(d.rep_rank)),
+            "elem": {v: k for k, v in ELEM.items()}[d.elem],
+            "inputs": [port_of(d.in_[i], d.in_tiler[i]) for i in range(d.n_in)],
+            "outputs": [port_of(d.out[0], d.out_tiler[0])],
+            "taps": taps}
+
+
+def arol_task_shard_frames(spec: dict, parts: int, part: int):
+    """(spec of part `part` of `parts`, its first frame): see include/arol.h."""
+    d, keep = task_desc(spec)
+    out = TaskDesc()
+    first = c_i64()
+    _check(lib.arol_task_shard_frames(ctypes.byref(d), int(parts), int(part), ctypes.byref(out), ctypes.byref(first)))
+    del keep
+    return spec_of_desc(out, spec.get("taps")), first.value
 
 
 # ------------------------------------------------------------ entry points

@@ -1180,6 +1180,39 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     return AROL_OK;
 }
 
+arol_status arol_task_shard_frames(const arol_task_desc* desc, int parts, int part, arol_task_desc* out,
+                                   int64_t* first_frame) {
+    if (!desc || !out || !first_frame) return fail(AROL_ERR_INVALID, "null argument");
+    if (parts < 1 || part < 0 || part >= parts) return fail(AROL_ERR_INVALID, "part %d of %d", part, parts);
+    const arol_task_desc& d = *desc;
+    if (d.rep_rank < 1 || d.n_in < 1 || d.n_in > 2 || d.n_out != 1) return fail(AROL_ERR_INVALID, "malformed descriptor");
+    const int64_t F = d.rep[0];
+    // every port: array dimension 0 is repetition dimension 0 (the frames)
+    auto frame_port = [&](const arol_array_desc& a, const arol_tiler& t) {
+        if (a.rank < 2 || a.shape[0] != F || t.origin[0] != 0) return false;
+        for (int q = 0; q < d.rep_rank; ++q)
+            if (t.paving[0][q] != (q == 0 ? 1 : 0)) return false;
+        for (int k = 1; k < a.rank; ++k)
+            if (t.paving[k][0] != 0) return false;
+        for (int i = 0; i < t.pattern_rank; ++i)
+            if (t.fitting[0][i] != 0) return false;
+        return true;
+    };
+    for (int i = 0; i < d.n_in; ++i)
+        if (!frame_port(d.in[i], d.in_tiler[i]))
+            return fail(AROL_ERR_UNSUPPORTED, "shard: input %d has no frame dimension (array dim 0 = repetition dim 0)", i);
+    if (!frame_port(d.out[0], d.out_tiler[0]))
+        return fail(AROL_ERR_UNSUPPORTED, "shard: the output has no frame dimension (array dim 0 = repetition dim 0)");
+    const int64_t base = F / parts, extra = F % parts;
+    const int64_t count = base + (part < extra ? 1 : 0);
+    *first_frame = part * base + std::min<int64_t>(part, extra);
+    *out = d;
+    out->rep[0] = count;
+    for (int i = 0; i < d.n_in; ++i) out->in[i].shape[0] = count;
+    out->out[0].shape[0] = count;
+    return AROL_OK;
+}
+
 arol_status arol_task_set_taps(arol_task t, const float* taps, int on_device) {
     if (!t || !taps) return fail(AROL_ERR_INVALID, "null argument");
     if (t->taps_host.empty()) return fail(AROL_ERR_INVALID, "task has no fir taps");
