@@ -476,9 +476,20 @@ def bench_matmul(A, torch, stream, flush, reps, peak_tf):
     ms = statistics.median(time_each_flushed(lambda: t.run([ad, bd], c), reps, stream, flush))
     ref = statistics.median(time_each_flushed(lambda: torch.matmul(ad, bd), reps, stream, flush))
     flops = 2.0 * 4096 ** 3
-    return {"mnk": [4096, 4096, 4096], "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
-            "frac_of_bf16_peak": flops / (ms * 1e-3) / 1e12 / peak_tf,
-            "torch_matmul_bf16_out_ms": ref, "torch_tflops": flops / (ref * 1e-3) / 1e12}
+    out = {"mnk": [4096, 4096, 4096], "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+           "frac_of_bf16_peak": flops / (ms * 1e-3) / 1e12 / peak_tf,
+           "torch_matmul_bf16_out_ms": ref, "torch_tflops": flops / (ref * 1e-3) / 1e12}
+    # like for like: cuBLAS with a float32 C, as this task writes it
+    c32 = torch.empty((4096, 4096), dtype=torch.float32, device="cuda")
+    try:
+        torch.mm(ad, bd, out_dtype=torch.float32, out=c32)
+        ref32 = statistics.median(time_each_flushed(lambda: torch.mm(ad, bd, out_dtype=torch.float32, out=c32),
+                                                    reps, stream, flush))
+        out.update(torch_mm_f32_out_ms=ref32, torch_mm_f32_out_tflops=flops / (ref32 * 1e-3) / 1e12,
+                   ratio_vs_cublas_f32_out=ref32 / ms)
+    except (TypeError, RuntimeError) as e:
+        out["torch_mm_f32_out"] = f"unavailable: {type(e).__name__}"
+    return out
 
 
 def bench_bf16(A, torch, stream, flush, reps, hbm):
