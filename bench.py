@@ -51,6 +51,8 @@ L2_BYTES = 126 * 1024 * 1024
 # FP32 FMA peak derived from the part's unit counts and clock: 152 SMs x 128
 # FP32 lanes x 2 flops x 2.07 GHz (the maximum SM clock).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 peak: the part's nominal dense float64 rate (not measured here)
+FP64_PEAK_TFLOPS = 1.25
 
 
 def chain_units(frames, height=HEIGHT, width=WIDTH):
@@ -553,7 +555,12 @@ def bench_cg(A, torch, stream, flush, reps, hbm):
     return {"n": n, "nnz": nnz, "tol": 1e-10, "iterations": iters, "rel_residual": rel, "solve_ms": solve_s * 1e3,
             "ms_per_iteration": solve_s * 1e3 / max(iters, 1), "spmv_us_after_l2_flush": spmv_hbm * 1e3,
             "spmv_gbs_after_l2_flush": nbytes / (spmv_hbm * 1e-3) / 1e9, "spmv_frac_of_hbm": nbytes / (spmv_hbm * 1e-3) / 1e9 / hbm,
-            "spmv_us_l2_resident": spmv_l2 * 1e3, "oracle_cpu_s": cpu_s, "oracle_iterations": k_cpu,
+            "spmv_us_l2_resident": spmv_l2 * 1e3,
+            # the float64 side of the SpMV roofline: one multiply-add per nonzero
+            "spmv_fp64": {"bound": "fp64", "achieved": 2 * nnz / (spmv_hbm * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                          "unit": "TFLOP/s", "frac": 2 * nnz / (spmv_hbm * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                          "frac_l2_resident": 2 * nnz / (spmv_l2 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
+            "oracle_cpu_s": cpu_s, "oracle_iterations": k_cpu,
             "paper_table1_context": {"hardware": "Tesla T10 (OpenCL, 1 GPU) / Core 2 Duo (Matlab pcg), FP64",
                                      "opencl_1gpu_s": 0.659, "matlab_pcg_s": 3.17, "iterations": 116}}
 
