@@ -445,7 +445,55 @@ bool flatten_frames_col(const arol_task_desc& d, arol_task_desc* o) {
 
 TaskDev make_taskdev_exact(const arol_task_desc& d);
 
-TaskDev make_taskdev(const arol_task_desc& d) {
+// One frame of a rank-3 fir task whose dimension 0 is frames (origin 0,
+// paving 1 on its own repetition dimension, fitting 0, the same extent in
+// and out): the rank-2 task on (rows, cols).
+bool strip_frame(const arol_task_desc& d, arol_task_desc* o) {
+    if (d.elem != AROL_ELEM_FIR || d.in[0].rank != 3 || d.out[0].rank != 3 || d.rep_rank != 3 || d.n_in != 1) return false;
+    const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
+    if (ti.pattern_rank != 1 || to.pattern_rank != 1) return false;
+    if (d.in[0].shape[0] != d.rep[0] || d.out[0].shape[0] != d.rep[0] || ti.origin[0] || to.origin[0] ||
+        ti.fitting[0][0] || to.fitting[0][0])
+        return false;
+    for (int q = 0; q < 3; ++q)
+        if (ti.paving[0][q] != (q == 0) || to.paving[0][q] != (q == 0) || (q > 0 && (ti.paving[q][0] || to.paving[q][0])))
+            return false;
+    *o = d;
+    o->rep_rank = 2;
+    o->rep[0] = d.rep[1];
+    o->rep[1] = d.rep[2];
+    o->rep[2] = o->rep[3] = 0;
+    arol_array_desc* arrs[2] = {&o->in[0], &o->out[0]};
+    const arol_array_desc* src[2] = {&d.in[0], &d.out[0]};
+    for (int a = 0; a < 2; ++a) {
+        arrs[a]->rank = 2;
+        arrs[a]->shape[0] = src[a]->shape[1];
+        arrs[a]->shape[1] = src[a]->shape[2];
+        arrs[a]->shape[2] = arrs[a]->shape[3] = 1;
+    }
+    arol_tiler* tls[2] = {&o->in_tiler[0], &o->out_tiler[0]};
+    const arol_tiler* tsrc[2] = {&ti, &to};
+    for (int a = 0; a < 2; ++a) {
+        arol_tiler& t = *tls[a];
+        const arol_tiler& u = *tsrc[a];
+        std::memset(&t, 0, sizeof t);
+        for (int k = 0; k < 2; ++k) {
+            t.origin[k] = u.origin[k + 1];
+            t.fitting[k][0] = u.fitting[k + 1][0];
+            for (int q = 0; q < 2; ++q) t.paving[k][q] = u.paving[k + 1][q + 1];
+        }
+        t.pattern_rank = 1;
+        t.pattern[0] = u.pattern[0];
+    }
+    return true;
+}
+
+// batch_form: the form the batch engine runs (a column FIR over frames that
+// cannot merge keeps the column-FIR path with frames as an outer
+// repetition; its ports then describe one frame, so only the batch kernels'
+// column-FIR path may take it).  Otherwise the exact or frame-merged form
+// that the per-repetition kernels take.
+TaskDev make_taskdev(const arol_task_desc& d, bool batch_form = false) {
     arol_task_desc flat;
     if (flatten_frames(d, &flat)) {
         const TaskDev t = make_taskdev_exact(flat);
@@ -454,6 +502,23 @@ TaskDev make_taskdev(const arol_task_desc& d) {
     if (flatten_frames_col(d, &flat)) {
         const TaskDev t = make_taskdev_exact(flat);
         if (t.colfir) return t;
+    }
+    // A column FIR on each frame of a rank-3 array whose frames cannot merge
+    // into rows (windows that overlap or wrap within a frame): the column-FIR
+    // path over one frame's ports, with the frame as an outer repetition.
+    if (batch_form && strip_frame(d, &flat)) {
+        TaskDev t = make_taskdev_exact(flat);
+        if (t.colfir && (int64_t)t.nreps * d.rep[0] < 2147483647LL) {
+            t.cf_frames = (int32_t)d.rep[0];
+            t.rep[1] = t.cf_frames;
+            t.rep_div[1] = make_fastdiv((uint32_t)t.cf_frames);
+            t.cf_in_frame = elems_of(flat.in[0]);
+            t.cf_out_frame = elems_of(flat.out[0]);
+            t.nreps *= d.rep[0];
+            t.in_elems = elems_of(d.in[0]);
+            t.out_elems = elems_of(d.out[0]);
+            return t;
+        }
     }
     return make_taskdev_exact(d);
 }
@@ -975,7 +1040,7 @@ void fill_info_single(arol_task t) {
     else in.flops = 0;
     in.path = -1;
     if (t->kernel == 0 && d.elem != AROL_ELEM_MATMUL) {
-        const TaskDev td = make_taskdev(d);
+        const TaskDev td = make_taskdev(d, true);
         in.path = td.rowfir ? 1 : td.colfir ? 2 : td.fir2d ? (fir2d_uses_stencil(td) ? 4 : 3) : 0;
     }
     in.reserved_ = 0;
@@ -1070,7 +1135,7 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out) {
     }
     fill_info_single(t);
     if (log_enabled()) {
-        const TaskDev td = make_taskdev(t->descs[0]);
+        const TaskDev td = make_taskdev(t->descs[0], true);
         const char* path = t->kernel == 2 ? (M % 256 == 0 && N % 256 == 0 ? "tcgen05 matmul, CTA pairs" : "tcgen05 matmul")
                            : td.rowfir ? "row FIR (staged row tiles)"
                            : td.colfir ? "column FIR (column tiles)"
@@ -1300,7 +1365,7 @@ arol_status run_internal_batch(arol_task t, const void* const* in, void* const* 
         for (const arol_task_desc& d : t->descs)
             if (d.elem != AROL_ELEM_FIR) want = false;
         if (want && t->kind == 0) {
-            const TaskDev td = make_taskdev(t->descs[0]);
+            const TaskDev td = make_taskdev(t->descs[0], true);
             want = td.rowfir || td.colfir;
         }
         if (want) {
@@ -2225,12 +2290,19 @@ arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out) {
             const size_t z = t->kind == 0 || k + 1 == len ? t->taps_host.size() : (size_t)t->tap_off[k + 1];
             b->descs.push_back(d);
             b->taps.emplace_back(t->taps_host.begin() + a, t->taps_host.begin() + z);
-            b->host_tasks.push_back(make_taskdev(d));
+            b->host_tasks.push_back(make_taskdev(d, true));
             b->member_of.push_back(i);
             b->stage_of.push_back(k);
             if (d.elem == AROL_ELEM_FIR) b->max_m = std::max(b->max_m, d.fir_m);
         }
     }
+    // The persistent kernel's column-FIR path serves output counts up to 16;
+    // a batch with a larger m runs other tiles on the per-repetition walk,
+    // which needs every task's full ports: frame-stripped column FIRs go back
+    // to their exact form there.
+    if (b->max_m > 16)
+        for (size_t j = 0; j < b->host_tasks.size(); ++j)
+            if (b->host_tasks[j].cf_frames > 0) b->host_tasks[j] = make_taskdev_exact(b->descs[j]);
     if (log_enabled()) {
         int rows = 0, cols = 0;
         for (const TaskDev& td : b->host_tasks) {

@@ -57,6 +57,8 @@ struct TaskDev {
     int32_t s0, s1, p0, p1; // fir2d: steps and pattern extents (rows, columns)
     int32_t bh, bw;         // fir2d: repetitions per CTA tile (rows, columns)
     int32_t step;           // input paving along the row (row FIR) or down the column (column FIR), reduced
+    int32_t cf_frames;      // column FIR: frames (rep[1]); the ports describe one frame
+    int64_t cf_in_frame, cf_out_frame;   // column FIR: input and output elements per frame
     const float* taps;      // m x T (fir)
     const float* taps_t;    // column-FIR tasks in a batch: taps transposed, T x 16, zero padded;
                             // row-FIR tasks: transposed and doubled, T x 32 (see RowTileDev)

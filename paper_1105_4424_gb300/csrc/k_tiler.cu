@@ -289,9 +289,10 @@ __device__ __forceinline__ void load_taps(const float* hrow, float (&h)[M]) {
 
 // ---------------------------------------------------------------------------
 // Column FIR tile (repetitions start .. start + count - 1 of a column-FIR
-// task, column fastest): repetition (r0, c) reads rows (o0 + step*r0 + k) mod
-// H of column (o1 + c) mod W and writes m consecutive output rows of one
-// column.  Consecutive threads take consecutive columns, so the loads of a
+// task, column fastest, frames outermost): repetition (f, r0, c) reads rows
+// (o0 + step*r0 + k) mod H of column (o1 + c) mod W of frame f and writes m
+// consecutive output rows of one column of frame f (a task without frames
+// has one).  Consecutive threads take consecutive columns, so the loads of a
 // warp and its stores are contiguous; the input is read straight from global
 // memory (each element once when T <= step), the transposed taps from shared
 // memory.  Two repetitions per thread share every tap load.
@@ -312,12 +313,15 @@ __device__ __forceinline__ void col_fir_compute(const TaskDev& t, const float* h
         if ((int)threadIdx.x >= half) break;
         const int i0 = base + (int)threadIdx.x;
         const int i1 = i0 + half < count ? i0 + half : i0;
-        uint32_t r0[2], col[2], row[2];
+        uint32_t r0[2], col[2], row[2], fr[2];
         const uint32_t lr[2] = {(uint32_t)(start + i0), (uint32_t)(start + i1)};   // < 2^31: not wide
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-            r0[a] = fast_div(lr[a], t.rep_div[3]);
-            const uint32_t c = lr[a] - r0[a] * C;
+            // repetition (frame, r0, c): c fastest, frames outermost
+            const uint32_t q = fast_div(lr[a], t.rep_div[3]);
+            const uint32_t c = lr[a] - q * C;
+            fr[a] = fast_div(q, t.rep_div[2]);
+            r0[a] = q - fr[a] * (uint32_t)t.rep[2];
             const uint32_t vr = t.in.origin[0] + S * r0[a];              // < 2^31: checked on the host
             row[a] = vr - fast_div(vr, t.in.shape_div[0]) * hin;
             const uint32_t vc = t.in.origin[1] + c;
@@ -328,10 +332,12 @@ __device__ __forceinline__ void col_fir_compute(const TaskDev& t, const float* h
         for (int j = 0; j < M; ++j) acc0[j] = acc1[j] = 0.f;
         // unrolled by 4: the taps' global loads are independent of the FMAs,
         // so more of them are in flight per thread
+        const float* x0 = x + (int64_t)fr[0] * t.cf_in_frame;
+        const float* x1 = x + (int64_t)fr[1] * t.cf_in_frame;
 #pragma unroll 4
         for (int kk = 0; kk < T; ++kk) {
-            const float p0 = __ldg(x + (int64_t)row[0] * win + col[0]);
-            const float p1 = __ldg(x + (int64_t)row[1] * win + col[1]);
+            const float p0 = __ldg(x0 + (int64_t)row[0] * win + col[0]);
+            const float p1 = __ldg(x1 + (int64_t)row[1] * win + col[1]);
             row[0] = row[0] + 1u == hin ? 0u : row[0] + 1u;
             row[1] = row[1] + 1u == hin ? 0u : row[1] + 1u;
             float h[M];
@@ -345,14 +351,15 @@ __device__ __forceinline__ void col_fir_compute(const TaskDev& t, const float* h
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             if (a == 1 && i1 == i0) break;
-            const uint32_t c = lr[a] - r0[a] * C;
+            const uint32_t c = lr[a] - fast_div(lr[a], t.rep_div[3]) * C;
+            float* ya = y + (int64_t)fr[a] * t.cf_out_frame;
             const uint32_t vr = t.out.origin[0] + (uint32_t)M * r0[a];   // < 2^31: checked on the host
             uint32_t orow = vr - fast_div(vr, t.out.shape_div[0]) * hout;
             const uint32_t vc = t.out.origin[1] + c;
             const uint32_t ocol = vc - fast_div(vc, t.out.shape_div[1]) * wout;
 #pragma unroll
             for (int j = 0; j < M; ++j) {
-                y[(int64_t)orow * wout + ocol] = a == 0 ? acc0[j] : acc1[j];
+                ya[(int64_t)orow * wout + ocol] = a == 0 ? acc0[j] : acc1[j];
                 orow = orow + 1u == hout ? 0u : orow + 1u;
             }
         }
