@@ -388,11 +388,21 @@ def _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, kernel_name):
 
 
 def bench_chain_5to2(A, torch, stream, flush, reps, hbm):
-    """The 5-tap -> 2 step-4 downscaler chain on 64 x 1080 x 1920: the fused
-    separable chain kernel against the same chain stage by stage (a
+    """The 5-tap -> 2 step-4 downscaler chain on 64 x 1080 x 1920: the
+    streaming row-then-column kernel against the tile kernel (the streaming
+    kernel switched off for one chain) and the same chain stage by stage (a
     one-member batch: two launches, the intermediate through HBM)."""
     chain, xs = W.config1_5to2()
-    _, ms, out = _task_gbs(A, torch, stream, flush, reps, hbm, chain, xs, "sepchain_kernel")
+    _, ms, out = _task_gbs(A, torch, stream, flush, reps, hbm, chain, xs, "sepstream_kernel")
+    prev = os.environ.get("AROL_SEPSTREAM")
+    os.environ["AROL_SEPSTREAM"] = "off"
+    try:
+        _, out["tile_kernel_ms"], _ = _task_gbs(A, torch, stream, flush, reps, hbm, chain, xs, "sepchain_kernel")
+    finally:
+        if prev is None:
+            del os.environ["AROL_SEPSTREAM"]
+        else:
+            os.environ["AROL_SEPSTREAM"] = prev
     b = A.Batch([chain])
     ins = [torch.from_numpy(x).cuda() for x in xs]
     outs = b.empty_outputs()

@@ -124,7 +124,8 @@ typedef struct arol_batch_s* arol_batch;
 typedef struct {
     int32_t kind;              /* 0 single task, 1 chain */
     int32_t kernel;            /* 0 generic tiler, 1 fused separable downscaler (8 -> 3, step 8), 2 tcgen05 matmul,
-                                  3 unfused chain, 4 fused separable chain (any row and column passes) */
+                                  3 unfused chain, 4 fused separable chain (any row and column passes),
+                                  5 fused row-then-column chain (streaming rows) */
     int64_t reps;              /* repetitions of the task (sum over a chain's tasks) */
     int64_t gathered_elems;    /* pattern elements gathered over all inputs (and tasks) */
     int64_t scattered_elems;   /* elements scattered (sum over a chain's tasks) */
@@ -163,8 +164,13 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out);
  *  - any other f32 chain of 2 to 4 row passes (a fir along each row) and
  *    column passes (down each column), each identity on the other axis and
  *    the frames, with T <= 32, m <= 16, any step and input origin (wrap
- *    included), runs on the fused separable chain kernel (kernel 4): tiles of
- *    the last array, every pass in shared memory;
+ *    included), runs on a fused kernel: a row pass then a column pass on the
+ *    streaming kernel (kernel 5: rows of the input streamed through shared
+ *    memory, each intermediate column's last rows in a shared ring; T_v <= 29),
+ *    other chains on the tile kernel (kernel 4: tiles of the
+ *    last array, every pass in shared memory); the environment variable
+ *    AROL_SEPSTREAM=off (or 0), read here, keeps a row-then-column chain on
+ *    the tile kernel;
  * other chains run stage by stage through intermediates the chain owns. */
 arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out);
 

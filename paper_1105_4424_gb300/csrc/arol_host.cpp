@@ -749,9 +749,54 @@ bool match_sep_pass(const arol_task_desc& d, SepPassDev* p, int64_t* F, int64_t 
     return true;
 }
 
-// Plans a fused separable chain: the passes, the stage extents and the tile
-// of the last stage.  Region sizes separate into a row part (depending on
-// the tile row only) and a column part (tile column only), so the largest
+// Plans the streaming form of a chain of a row pass then a column pass
+// (host only): chunks of sepstream_chunk_cols() intermediate columns, the
+// widest input window of a chunk and the stages; refused when
+// the column pass's window outgrows the ring of intermediate rows or the
+// shared memory would not leave two CTAs per SM.  The bands are chosen at
+// the first run (sepstream_bands).
+constexpr size_t kSsSmemMax = 110 * 1024;
+
+bool plan_sepstream(const SepChainDev& c, SepChainDev* out, int* xw_max, int* nst) {
+    if (c.K != 2 || c.p[0].axis != 1 || c.p[1].axis != 0) return false;
+    const SepPassDev &ph = c.p[0], &pv = c.p[1];
+    if (pv.T > sepstream_max_taps()) return false;
+    const int cc = sepstream_chunk_cols();
+    const int64_t chunks = (c.W[1] + cc - 1) / cc;
+    int xw = 0;
+    for (int64_t k = 0; k < chunks; ++k) {
+        const int64_t q0 = k * cc, nq = std::min<int64_t>(cc, c.W[1] - q0);
+        const int64_t ra = q0 / ph.m, rb = (q0 + nq - 1) / ph.m;
+        xw = (int)std::max<int64_t>(xw, ph.S * (rb - ra) + ph.T);
+    }
+    const int ns = sepstream_stages(xw);
+    if (sepstream_smem(c, xw, ns) > kSsSmemMax || c.F * chunks * pv.R >= 2147483647LL) return false;
+    *out = c;
+    *xw_max = xw;
+    *nst = ns;
+    return true;
+}
+
+// Bands of column-pass repetitions for the streaming chain kernel on the
+// current device: the band height that minimises the rows the busiest CTA
+// walks (waves of resident CTAs times the rows of one band, halo included).
+void sepstream_bands(SepChainDev& d, int xw_max, int nst, int* units) {
+    const SepPassDev& pv = d.p[1];
+    const int cc = sepstream_chunk_cols();
+    const int64_t per = d.F * ((d.W[1] + cc - 1) / cc);
+    const int64_t cap = (int64_t)device_sm_count() * sepstream_ctas_per_sm(d, sepstream_smem(d, xw_max, nst));
+    int64_t best = -1, best_bh = pv.R;
+    for (int64_t nb = 1; nb <= std::min<int64_t>(pv.R, 4096); ++nb) {
+        const int64_t bh = (pv.R + nb - 1) / nb, u = per * ((pv.R + bh - 1) / bh);
+        const int64_t cost = ((u + cap - 1) / cap) * ((int64_t)pv.S * (bh - 1) + pv.T);
+        if (best < 0 || cost < best) best = cost, best_bh = bh;
+    }
+    d.BH = (int32_t)best_bh;
+    *units = (int)(per * ((pv.R + best_bh - 1) / best_bh));
+}
+
+// The tile kernel's plan: region sizes separate into a row part (depending
+// on the tile row only) and a column part (tile column only), so the largest
 // shared buffer and the total work of a tile shape take one pass over tile
 // rows and one over tile columns.  Among the shapes whose shared memory
 // (taps and two buffers) fits kSepSmemFloats, the one with the least work
@@ -762,7 +807,9 @@ bool match_sep_pass(const arol_task_desc& d, SepPassDev* p, int64_t* F, int64_t 
 constexpr int kSepSmemFloats = 14 * 1024;   // 56 KB: four CTAs per SM
 constexpr double kSepFillTiles = 4.0 * 152;  // four tiles per SM of a 152-SM GB300 (planning stays host-only)
 
-bool plan_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out) {
+// The passes and stage extents of a chain of 2 .. 4 row and column passes
+// (false for any other chain).
+bool describe_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out) {
     const int K = (int)descs.size();
     if (K < 2 || K > kSepMaxPasses) return false;
     SepChainDev d;
@@ -786,6 +833,14 @@ bool plan_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out) {
     }
     d.F = F0;
     d.ntaps = (int32_t)ntaps;
+    *out = d;
+    return true;
+}
+
+// Tiles of the last stage for the shared-memory tile kernel (false when no
+// tile's regions fit shared memory).
+bool plan_sepchain(const SepChainDev& d, SepChainDev* out) {
+    const int K = d.K;
     int max_m = 1;
     for (int k = 0; k < K; ++k) max_m = std::max(max_m, (int)d.p[k].m);
     const int taps4 = kSepMaxPasses * 32 * (max_m <= 4 ? 4 : 16);   // every pass's taps, transposed
@@ -891,6 +946,9 @@ struct arol_task_s {
     SepChainDev sc{};
     std::vector<int32_t> sc_tab;
     int32_t* sc_tab_dev = nullptr;
+    // streaming row-then-column chain (kernel 5)
+    SepChainDev ss{};
+    int ss_units = 0, ss_xw = 0, ss_nst = 2;
     unsigned* err_flag = nullptr;        // device word: bounded waits that gave up
     // backward scratch and inverse maps
     float* partials = nullptr;
@@ -1197,8 +1255,16 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     }
     // Any other chain of 2 .. 4 row and column passes (f32): the general
     // fused separable chain kernel, when a tile shape fits shared memory.
-    if (t->kernel == 3 && plan_sepchain(t->descs, &t->sc)) {
-        t->kernel = 4;
+    // A row pass then a column pass runs on the streaming kernel when its
+    // ring fits, unless AROL_SEPSTREAM is off.
+    SepChainDev sd;
+    const char* e = std::getenv("AROL_SEPSTREAM");
+    const bool stream = !(e && (!std::strcmp(e, "off") || !std::strcmp(e, "0")));
+    if (t->kernel == 3 && describe_sepchain(t->descs, &sd)) {
+        if (stream && plan_sepstream(sd, &t->ss, &t->ss_xw, &t->ss_nst)) t->kernel = 5;
+        else if (plan_sepchain(sd, &t->sc)) t->kernel = 4;
+    }
+    if (t->kernel == 4) {
         const SepChainDev& c = t->sc;
         const int K1 = c.K + 1;
         t->sc_tab.assign((size_t)2 * K1 * (c.tiles_y + c.tiles_x), 0);
@@ -1237,7 +1303,11 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     log_line("chain %p: %d tasks, %s", (void*)t, n,
              t->kernel == 1 ? "fused separable downscaler"
              : t->kernel == 4 ? "fused separable chain (shared-memory tiles)"
+             : t->kernel == 5 ? "fused row-then-column chain (streaming rows)"
                               : "stage by stage through a one-member batch");
+    if (t->kernel == 5)
+        log_line("chain %p: input windows of %d words, %d stages, %zu B of shared memory", (void*)t, t->ss_xw,
+                 t->ss_nst, sepstream_smem(t->ss, t->ss_xw, t->ss_nst));
     if (t->kernel == 4)
         log_line("chain %p: tiles of %d x %d, %lld tiles per frame, %zu B of shared memory", (void*)t, t->sc.BH,
                  t->sc.BW, (long long)t->sc.tiles_y * t->sc.tiles_x, sepchain_smem(t->sc));
@@ -1416,6 +1486,19 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
         p.x = (const float*)in[0];
         p.y = (float*)out[0];
         AROL_CUDA(launch_downscale_fwd(p, s), "downscale kernel launch");
+        return AROL_OK;
+    }
+    if (t->kernel == 5) {
+        if ((st = ensure_err(t, s)) != AROL_OK) return st;
+        if (!t->ss_units) {
+            sepstream_bands(t->ss, t->ss_xw, t->ss_nst, &t->ss_units);
+            log_line("chain %p: %d units, bands of %d repetitions", (void*)t, t->ss_units, t->ss.BH);
+        }
+        SepChainDev d = t->ss;
+        d.x = (const float*)in[0];
+        d.y = (float*)out[0];
+        d.taps = taps;
+        AROL_CUDA(launch_sepstream(d, t->ss_units, t->ss_xw, t->ss_nst, t->err_flag, s), "fused chain kernel launch");
         return AROL_OK;
     }
     if (t->kernel == 4) {

@@ -151,6 +151,15 @@ int downscale_bwd_partials(int sm_count, int W);   // per-CTA partial slots the 
 struct SepChainDev;
 cudaError_t launch_sepchain(const SepChainDev& d, cudaStream_t s);
 size_t sepchain_smem(const SepChainDev& d);
+// The streaming form of a row pass then a column pass (k_sepstream.cu):
+// d.BH is the band (column-pass repetitions per unit); xw_max the widest
+// input window of a column chunk; nst the stages (even).
+cudaError_t launch_sepstream(const SepChainDev& d, int units, int xw_max, int nst, unsigned* err, cudaStream_t s);
+size_t sepstream_smem(const SepChainDev& d, int xw_max, int nst);
+int sepstream_stages(int xw_max);
+int sepstream_chunk_cols();
+int sepstream_ctas_per_sm(const SepChainDev& d, size_t smem);
+int sepstream_max_taps();
 
 // tcgen05 matmul: C (M x N, f32) = A (M x K, bf16 row-major) . B (K x N, bf16 row-major).
 cudaError_t launch_matmul_tc(const void* A, const void* B, float* C, int M, int N, int K,

@@ -1,0 +1,404 @@
+// Streaming form of a fused two-pass separable chain: a row pass (taps
+// Hh: m_h x T_h, step S_h, origin o_h along the columns) then a column pass
+// (Hv: m_v x T_v, step S_v, origin o_v down the rows), on every frame
+// (Sec. 5 associatedParts: the intermediate never reaches HBM).
+//
+// Work unit: one frame, one chunk of 32 * kSsCWarps intermediate columns,
+// one band of column-pass repetitions [rb0, rb0 + nrb).  The band needs the
+// intermediate rows (o_v + S_v rb0 + i) mod H, i < S_v (nrb - 1) + T_v,
+// which are the row pass of the same input rows.  Producer warps copy those
+// input rows' windows (the row pass's input columns of the chunk, wrapped at
+// the row end), kSsRows rows per stage, into a ring of `nst` shared-memory
+// stages:
+// one cp.async.bulk per row for its 16-byte interior and 4-byte cp.async for
+// its ragged ends and wrapped words, all completing on the stage's mbarrier.
+//
+// Consumer warp w owns intermediate columns q0 + 32 w + lane.  For every
+// staged row it computes its 32 intermediate values (row pass; the rows of a
+// stage are independent, so their sums overlap), releases the stage, keeps
+// the values in its own ring of the last kSsRing rows (one column per lane:
+// no bank conflicts), and whenever the window of a column-pass repetition is
+// complete (T_v rows, every S_v rows), computes that repetition's m_v outputs
+// for its columns and stores them: consecutive lanes, consecutive columns.
+// Warps never wait on each other; each input row of a band is read from HBM
+// once (the halo rows that neighbouring bands share, T_v - S_v of them, twice).
+#include "arol_internal.h"
+#include "ptx.h"
+#include "sepchain.h"
+
+#ifndef AROL_SS_STAGES
+#define AROL_SS_STAGES 16
+#endif
+#ifndef AROL_SS_STAGE_KB
+#define AROL_SS_STAGE_KB 80
+#endif
+#ifndef AROL_SS_SLEEP_NS
+#define AROL_SS_SLEEP_NS 20000
+#endif
+
+namespace arol {
+namespace {
+
+constexpr int kSsCWarps = 8;                       // consumer warps (32 columns each)
+constexpr int kSsPWarps = 2;                       // producer warps (alternate stages)
+constexpr int kSsThreads = (kSsCWarps + kSsPWarps) * 32;
+constexpr int kSsMaxStages = AROL_SS_STAGES;       // stages (an even number, 2 .. this, set by the window)
+constexpr int kSsRows = 4;                         // input rows per stage
+// intermediate rows kept per column: a window of T_v rows plus the
+// kSsRows - 1 rows of its stage stored after its last one
+constexpr int kSsRing = 32;
+constexpr size_t kSsStageBudget = AROL_SS_STAGE_KB * 1024;   // bytes of stages aimed at
+static_assert(kSsPWarps == 2 && kSsRing % kSsRows == 0, "producers alternate stages; stages fill whole ring runs");
+
+__device__ __forceinline__ void flag(unsigned* err, unsigned bit) {
+    if (err) atomicOr(err, bit);
+}
+
+// One band unit's geometry, the same in every thread.
+struct SsUnit {
+    uint32_t f;       // frame
+    int q0, nq;       // intermediate columns q0 .. q0 + nq - 1
+    int ra;           // first row-pass repetition of the chunk
+    int c0, xw;       // input window: columns (c0 + w) mod W, w < xw
+    int rb0, nrb;     // column-pass repetitions rb0 .. rb0 + nrb - 1
+    int row0, nrows;  // intermediate (= input) rows (row0 + i) mod H, i < nrows
+};
+
+__device__ __forceinline__ SsUnit ss_unit(const SepChainDev& d, int u) {
+    const SepPassDev &ph = d.p[0], &pv = d.p[1];
+    const int chunks = (d.W[1] + 32 * kSsCWarps - 1) / (32 * kSsCWarps);
+    const int bands = (pv.R + d.BH - 1) / d.BH;
+    SsUnit s;
+    const int per_frame = chunks * bands;
+    s.f = (uint32_t)(u / per_frame);
+    const int v = u - (int)s.f * per_frame, band = v / chunks, chunk = v - band * chunks;
+    s.q0 = chunk * 32 * kSsCWarps;
+    s.nq = min(32 * kSsCWarps, d.W[1] - s.q0);
+    s.ra = s.q0 / ph.m;
+    const int rb = (s.q0 + s.nq - 1) / ph.m;
+    s.xw = ph.S * (rb - s.ra) + ph.T;
+    s.c0 = (int)(((int64_t)ph.o + (int64_t)ph.S * s.ra) % ph.n_in);
+    s.rb0 = band * d.BH;
+    s.nrb = min(d.BH, pv.R - s.rb0);
+    s.nrows = pv.S * (s.nrb - 1) + pv.T;
+    s.row0 = (int)(((int64_t)pv.o + (int64_t)pv.S * s.rb0) % pv.n_in);
+    return s;
+}
+
+// Copies one input row's window, columns (c0 + w) mod W for w < xw, into
+// `dst` (16-byte aligned) at dst[delta + w], delta the low two bits of the
+// window's first word's address; lane-parallel.  The 4-byte copies are
+// issued by every lane, the bulk copy by lane 0, which returns its bytes.
+__device__ __forceinline__ uint32_t ss_copy_row(const float* row, const float* xs, const float* xe, int W, int c0, int xw,
+                                                float* dst, uint32_t full, int lane) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(row + c0);
+    const int delta = (int)((a0 >> 2) & 3u);
+    const int L1 = min(xw, W - c0);                       // the run before the row's end
+    const uintptr_t a1 = a0 + 4u * (uintptr_t)L1;
+    uintptr_t gA = a0 & ~(uintptr_t)15;
+    if (gA < reinterpret_cast<uintptr_t>(xs)) gA += 16;
+    uintptr_t gB = (a1 + 15) & ~(uintptr_t)15;
+    if (L1 < xw || gB > reinterpret_cast<uintptr_t>(xe)) gB = a1 & ~(uintptr_t)15;
+    if (gB <= gA) gA = gB = a0;
+    // 4-byte copies: the run's words outside [gA, gB), then the wrapped words
+    const int nhead = (int)((gA > a0 ? gA - a0 : 0) >> 2);
+    const int tail0 = (int)(((gB > a0 ? gB : a0) - a0) >> 2);
+    for (int w = lane; w < nhead; w += 32) ptx::cp_async4(dst + delta + w, row + c0 + w);
+    for (int w = tail0 + lane; w < L1; w += 32) ptx::cp_async4(dst + delta + w, row + c0 + w);
+    for (int w = L1 + lane; w < xw; w += 32) {
+        int col = c0 + w - W;
+        while (col >= W) col -= W;
+        ptx::cp_async4(dst + delta + w, row + col);
+    }
+    const uint32_t bytes = (uint32_t)(gB - gA);
+    if (lane == 0 && bytes)
+        ptx::bulk_g2s(ptx::smem_addr(dst) + (uint32_t)(gA - (a0 & ~(uintptr_t)15)), reinterpret_cast<const void*>(gA),
+                      bytes, full);
+    return bytes;
+}
+
+// Row-pass sum of one intermediate value: TH > 0 taps in registers (T_h =
+// TH), TH = 0 any T_h with the taps read from shared memory.
+template <int TH>
+__device__ __forceinline__ float ss_dot(const float* hreg, const float* hrow, const float* src, int T) {
+    float acc = 0.f;
+    if (TH > 0) {
+#pragma unroll
+        for (int k = 0; k < TH; ++k) acc = fmaf(hreg[k], src[k], acc);
+    } else {
+#pragma unroll 4
+        for (int k = 0; k < T; ++k) acc = fmaf(hrow[k], src[k], acc);
+    }
+    return acc;
+}
+
+// Column-pass sum of one output: taps hvr[0 .. T), intermediate rows t ..
+// t + T - 1 of the lane's ring (slots mod kSsRing), in two runs that do not
+// wrap.
+__device__ __forceinline__ float ss_col(const float* hvr, const float* ring, int t, int T, int lane) {
+    const int s0 = t & (kSsRing - 1);
+    const int n1 = min(T, kSsRing - s0);
+    const float* a = ring + s0 * 32 + lane;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < n1; ++k) acc = fmaf(hvr[k], a[32 * k], acc);
+    const float* b = ring + lane;
+    const float* hb = hvr + n1;
+#pragma unroll 4
+    for (int k = 0; k < T - n1; ++k) acc = fmaf(hb[k], b[32 * k], acc);
+    return acc;
+}
+
+// Column pass of one repetition: the m_v outputs from intermediate rows t ..
+// t + T_v - 1 (ring slots mod kSsRing), stored at yo[j * ys] by active
+// lanes.  TV > 0: T_v = TV, the window loaded once into registers; TV = 0:
+// any T_v, one ring sweep per output.
+template <int TV>
+__device__ __forceinline__ void ss_column_pass(const float* hv, int m, int T, const float* ring, int t, int lane,
+                                               float* yo, int64_t ys, bool active) {
+    if (TV > 0) {
+        float rv[TV > 0 ? TV : 1];
+        const int s0 = t & (kSsRing - 1);
+        if (s0 + TV <= kSsRing) {
+            const float* a = ring + s0 * 32 + lane;
+#pragma unroll
+            for (int k = 0; k < TV; ++k) rv[k] = a[32 * k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < TV; ++k) rv[k] = ring[((s0 + k) & (kSsRing - 1)) * 32 + lane];
+        }
+        for (int j = 0; j < m; ++j) {
+            const float* h = hv + j * TV;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < TV; ++k) acc = fmaf(h[k], rv[k], acc);
+            if (active) yo[j * ys] = acc;
+        }
+    } else {
+        for (int j = 0; j < m; ++j) {
+            const float acc = ss_col(hv + j * T, ring, t, T, lane);
+            if (active) yo[j * ys] = acc;
+        }
+    }
+}
+
+template <int TH, int TV>
+__global__ void __launch_bounds__(kSsThreads, 2) sepstream_kernel(const SepChainDev d, int units, int xw_max, int nst,
+                                                                 unsigned* err) {
+    extern __shared__ __align__(128) float ssm[];
+    const int sr = (xw_max + 4 + 3) & ~3;                  // floats per staged row (window plus alignment slack)
+    const int sf = kSsRows * sr;                           // floats per stage
+    float* stages = ssm;
+    float* rings = stages + nst * sf;                      // kSsCWarps x kSsRing x 32
+    float* taps = rings + kSsCWarps * kSsRing * 32;        // Hh then Hv, row-major
+    uint64_t* bars = reinterpret_cast<uint64_t*>(taps + ((d.ntaps + 3) & ~3));
+    const uint32_t full0 = ptx::smem_addr(bars), empty0 = ptx::smem_addr(bars + nst);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SepPassDev &ph = d.p[0], &pv = d.p[1];
+    for (int i = threadIdx.x; i < d.ntaps; i += blockDim.x) taps[i] = __ldg(d.taps + i);
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < nst; ++st) {
+            ptx::mbar_init(full0 + 8 * st, 1);
+            ptx::mbar_init(empty0 + 8 * st, kSsCWarps);
+        }
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    const int H = d.H[0], W = d.W[0];
+    const int64_t frame_in = (int64_t)H * W, frame_out = (int64_t)d.H[2] * d.W[2];
+
+    if (warp >= kSsCWarps) {
+        // producers: stages g = pw, pw + kSsPWarps, ... of this CTA's stage
+        // sequence (nst is even, so each producer owns the stages of its parity)
+        const int pw = warp - kSsCWarps;
+        uint32_t g = 0;                                    // this CTA's stages so far (all units)
+        int st = 0;
+        uint32_t phase = 0;                                // parity of stage st's current use
+        bool ok = true;
+        for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+            const SsUnit s = ss_unit(d, u);
+            const float* xf = d.x + (int64_t)s.f * frame_in;
+            for (int base = 0; base < s.nrows; base += kSsRows) {
+                const bool mine = (int)(g & 1u) == pw;
+                if (mine) {
+                    if (g >= (uint32_t)nst && !ptx::mbar_wait_sleep(empty0 + 8 * st, phase ^ 1u, AROL_SS_SLEEP_NS)) {
+                        if (lane == 0) flag(err, 1u);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = full0 + 8 * st;
+                    const int n = min(kSsRows, s.nrows - base);
+                    int ir = (s.row0 + base) % H;
+                    uint32_t bytes = 0;
+                    for (int r = 0; r < n; ++r) {
+                        bytes += ss_copy_row(xf + (int64_t)ir * W, xf, xf + frame_in, W, s.c0, s.xw,
+                                             stages + st * sf + r * sr, full, lane);
+                        if (++ir == H) ir = 0;
+                    }
+                    // each lane's 4-byte copies arrive on the barrier when they
+                    // land (pending count raised now, lowered then); lane 0 then
+                    // arrives with the bulk bytes it issued (the transaction
+                    // count may dip below zero meanwhile: the phase cannot
+                    // complete before this arrival)
+                    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(full) : "memory");
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_expect_tx(full, bytes);
+                }
+                ++g;
+                if (++st == nst) st = 0, phase ^= 1u;
+            }
+        }
+        // every issued copy lands before the CTA's shared memory goes away:
+        // this producer's last use of stage t is the largest issued index
+        // congruent to t
+        for (int t = pw; t < nst; t += kSsPWarps) {
+            if (g <= (uint32_t)t) continue;
+            const uint32_t last = (uint32_t)t + (uint32_t)nst * ((g - 1 - (uint32_t)t) / (uint32_t)nst);
+            if (!ptx::mbar_wait(full0 + 8 * t, (last / (uint32_t)nst) & 1u) && lane == 0) flag(err, 4u);
+        }
+        ptx::cp_async_wait_all();
+        return;
+    }
+
+    // consumers
+    float* ring = rings + warp * kSsRing * 32;
+    const float* hv = taps + pv.tap_off;
+    int st = 0;
+    uint32_t phase = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const SsUnit s = ss_unit(d, u);
+        const int q = s.q0 + 32 * warp + lane;             // this lane's intermediate column
+        const bool active = 32 * warp + lane < s.nq;
+        const int rh = active ? q / ph.m : s.ra, jh = active ? q - rh * ph.m : 0;
+        const int xoff = ph.S * (rh - s.ra);               // window offset of the lane's row-pass repetition
+        const float* hrow = taps + ph.tap_off + jh * ph.T;
+        float hreg[TH > 0 ? TH : 1];
+#pragma unroll
+        for (int k = 0; k < (TH > 0 ? TH : 1); ++k) hreg[k] = TH > 0 ? hrow[k] : 0.f;
+        // the window's first word sits at the low two bits of its global word index
+        const uint32_t wbase = (uint32_t)(reinterpret_cast<uintptr_t>(d.x) >> 2) +
+                               (uint32_t)(s.f * (uint64_t)frame_in) + (uint32_t)s.c0;
+        float* yf = d.y + (int64_t)s.f * frame_out + q;
+        int ir = s.row0;
+        int due = pv.T - 1;                                // next row that completes a column-pass window
+        int64_t yrow = (int64_t)pv.m * s.rb0 * d.W[2];     // offset of that repetition's first output row
+        const int64_t ystep = (int64_t)pv.m * d.W[2];
+        for (int base = 0; base < s.nrows; base += kSsRows) {
+            if (!ptx::mbar_wait_sleep(full0 + 8 * st, phase, AROL_SS_SLEEP_NS)) {
+                if (lane == 0) flag(err, 2u);
+                return;
+            }
+            // row pass of the stage's rows (rows past the unit's end read
+            // stale words; their sums are dropped)
+            const float* sp = stages + st * sf + xoff;
+            float mid[kSsRows];
+            int irk = ir;
+#pragma unroll
+            for (int k = 0; k < kSsRows; ++k) {
+                const int delta = (int)((wbase + (uint32_t)irk * (uint32_t)W) & 3u);
+                mid[k] = ss_dot<TH>(hreg, hrow, sp + k * sr + delta, ph.T);
+                if (++irk == H) irk = 0;
+            }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(empty0 + 8 * st);
+            if (++st == nst) st = 0, phase ^= 1u;
+            const int n = min(kSsRows, s.nrows - base);
+            float* rp = ring + (base & (kSsRing - 1)) * 32 + lane;   // base is a multiple of kSsRows: no wrap
+            if (n == kSsRows) {
+#pragma unroll
+                for (int k = 0; k < kSsRows; ++k) rp[32 * k] = mid[k];
+                ir = irk;
+            } else {
+#pragma unroll
+                for (int k = 0; k < kSsRows; ++k)
+                    if (k < n) rp[32 * k] = mid[k];
+                ir += n;
+                while (ir >= H) ir -= H;
+            }
+            // column pass of every repetition whose window ends in this stage:
+            // rows S_v r .. S_v r + T_v - 1 of the band
+            for (; due < base + n; due += pv.S, yrow += ystep)
+                ss_column_pass<TV>(hv, pv.m, pv.T, ring, due - (pv.T - 1), lane, yf + yrow, d.W[2], active);
+        }
+    }
+}
+
+}  // namespace
+
+int sepstream_stages(int xw_max) {
+    const size_t stage = (size_t)kSsRows * ((xw_max + 4 + 3) & ~3) * sizeof(float);
+    size_t n = kSsStageBudget / stage;
+    n = n < 2 ? 2 : n > (size_t)kSsMaxStages ? (size_t)kSsMaxStages : n;
+    return (int)(n & ~(size_t)1);
+}
+
+size_t sepstream_smem(const SepChainDev& d, int xw_max, int nst) {
+    const int sr = (xw_max + 4 + 3) & ~3;
+    return ((size_t)nst * kSsRows * sr + (size_t)kSsCWarps * kSsRing * 32 + ((d.ntaps + 3) & ~3)) * sizeof(float) +
+           2 * (size_t)nst * sizeof(uint64_t);
+}
+
+int sepstream_chunk_cols() { return 32 * kSsCWarps; }
+int sepstream_max_taps() { return kSsRing - kSsRows + 1; }
+
+// The kernel for the passes' tap counts: both exact when T_h = T_v <= 8,
+// the row pass exact when T_h <= 8, else the shared-memory forms.
+using SsKernel = void (*)(const SepChainDev, int, int, int, unsigned*);
+
+template <int T>
+SsKernel ss_pick(int Tv) {
+    return Tv == T ? sepstream_kernel<T, T> : sepstream_kernel<T, 0>;
+}
+
+static SsKernel ss_kernel_for(int Th, int Tv) {
+    switch (Th) {
+        case 1: return ss_pick<1>(Tv);
+        case 2: return ss_pick<2>(Tv);
+        case 3: return ss_pick<3>(Tv);
+        case 4: return ss_pick<4>(Tv);
+        case 5: return ss_pick<5>(Tv);
+        case 6: return ss_pick<6>(Tv);
+        case 7: return ss_pick<7>(Tv);
+        case 8: return ss_pick<8>(Tv);
+        default: return sepstream_kernel<0, 0>;
+    }
+}
+
+// cudaFuncSetAttribute once per kernel and size (the largest so far).
+static cudaError_t ss_set_smem(SsKernel k, size_t smem) {
+    static SsKernel seen[17] = {};
+    static size_t attr[17] = {};
+    int i = 0;
+    while (i < 17 && seen[i] && seen[i] != k) ++i;
+    if (i == 17) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    seen[i] = k;
+    if (smem > attr[i]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr[i] = smem;
+    }
+    return cudaSuccess;
+}
+
+int sepstream_ctas_per_sm(const SepChainDev& d, size_t smem) {
+    int occ = 0;
+    const SsKernel k = ss_kernel_for(d.p[0].T, d.p[1].T);
+    if (ss_set_smem(k, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kSsThreads, smem) != cudaSuccess)
+        return 1;
+    return occ > 0 ? occ : 1;
+}
+
+cudaError_t launch_sepstream(const SepChainDev& d, int units, int xw_max, int nst, unsigned* err, cudaStream_t s) {
+    if (units <= 0) return cudaSuccess;
+    const size_t smem = sepstream_smem(d, xw_max, nst);
+    const SsKernel k = ss_kernel_for(d.p[0].T, d.p[1].T);
+    cudaError_t e = ss_set_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int cap = device_sm_count() * sepstream_ctas_per_sm(d, smem);
+    const int grid = units < cap ? units : cap;
+    k<<<grid, kSsThreads, smem, s>>>(d, units, xw_max, nst, err);
+    return cudaGetLastError();
+}
+
+}  // namespace arol

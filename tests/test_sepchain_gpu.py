@@ -1,5 +1,6 @@
-"""Parity of the fused separable chain kernel (kernel 4: 2 to 4 row and
-column passes fused through shared memory) with the C oracle: random chains
+"""Parity of the fused separable chain kernels (kernel 4: 2 to 4 row and
+column passes fused through shared-memory tiles; kernel 5: a row pass then a
+column pass streamed by rows) with the C oracle: random chains
 (any taps, outputs, step, origin, windows that wrap once or several times,
 frames), the 5-tap -> 2 step-4 downscaler at 64 x 1080 x 1920, a three-task
 chain, and the forward + backward entry on a general chain.  FIR outputs
@@ -28,7 +29,7 @@ def test_random_separable_chains(arol):
         chain, shape = W.random_separable_chain(g)
         x = g.standard_normal(shape).astype(np.float32)
         c = arol.Chain(chain)
-        fused += c.info["kernel"] == 4
+        fused += c.info["kernel"] in (4, 5)
         y = c.run([dev(x)])
         c.sync_status()
         assert_fir_close(host(y), C.run_chain(chain, [x])[0], fir_scale(chain, x, C.run_chain),
@@ -36,10 +37,14 @@ def test_random_separable_chains(arol):
     assert fused >= 45   # chains whose regions outgrow shared memory run stage by stage (checked all the same)
 
 
-def test_5to2_step4_downscaler_full_size(arol):
+@pytest.mark.parametrize("stream", ["on", "off"])
+def test_5to2_step4_downscaler_full_size(arol, monkeypatch, stream):
+    """64 frames of 1080 x 1920 through the streaming kernel and, with it
+    switched off, through the tile kernel."""
+    monkeypatch.setenv("AROL_SEPSTREAM", stream)
     chain, (x,) = W.config1_5to2()
     c = arol.Chain(chain)
-    assert c.info["kernel"] == 4
+    assert c.info["kernel"] == (5 if stream == "on" else 4)
     y = c.run([dev(x)])
     c.sync_status()
     assert_fir_close(host(y), C.run_chain(chain, [x])[0], fir_scale(chain, x, C.run_chain), what="5->2 step 4")

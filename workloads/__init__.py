@@ -467,3 +467,26 @@ def chain_batch(seed=0, n=128):
         chains.append(downscale_chain(1, h, w, _taps(g, 3, 8), _taps(g, 3, 8)))
         xs.append(x)
     return chains, xs
+
+
+def random_row_column_chain(g: np.random.Generator, max_rows=300, max_cols=1500, frames=None):
+    """A row pass then a column pass (the streaming kernel's case) of random
+    taps (T_h in 1..24, T_v in 1..32), outputs (m in 1..4), steps (S_h in
+    1..8, S_v in 1..24), origins and repetitions (ceil(n /
+    step), or up to twice the extent: windows that wrap), on frames x rows x
+    cols.  Draw order: frames, rows, cols, then per pass T, m, step, the
+    repetition rule, reps, origin, taps N(0,1)/T.  Returns (chain, input
+    shape)."""
+    F = int(g.integers(1, 4)) if frames is None else frames
+    shape = (F, int(g.integers(1, max_rows + 1)), int(g.integers(1, max_cols + 1)))
+    chain, cur = [], shape
+    for axis, tmax, smax in ((1, 24, 8), (0, 32, 24)):
+        n = cur[-1] if axis == 1 else cur[-2]
+        T, m = int(g.integers(1, tmax + 1)), int(g.integers(1, 5))
+        step = int(g.integers(1, smax + 1))
+        reps = -(-n // step) if g.random() < 0.7 else int(g.integers(1, 2 * n + 2))
+        origin = int(g.integers(0, n))
+        t = separable_pass(cur, axis, T, m, step, origin, reps, _taps(g, m, T))
+        chain.append(t)
+        cur = t["outputs"][0]["shape"]
+    return chain, shape
