@@ -3,7 +3,7 @@
 // (Hv: m_v x T_v, step S_v, origin o_v down the rows), on every frame
 // (Sec. 5 associatedParts: the intermediate never reaches HBM).
 //
-// Work unit: one frame, one chunk of 32 * kSsCWarps intermediate columns,
+// Work unit: one frame, one chunk of kSsChunk intermediate columns,
 // one band of column-pass repetitions [rb0, rb0 + nrb).  The band needs the
 // intermediate rows (o_v + S_v rb0 + i) mod H, i < S_v (nrb - 1) + T_v,
 // which are the row pass of the same input rows.  Producer warps copy those
@@ -13,13 +13,14 @@
 // one cp.async.bulk per row for its 16-byte interior and 4-byte cp.async for
 // its ragged ends and wrapped words, all completing on the stage's mbarrier.
 //
-// Consumer warp w owns intermediate columns q0 + 32 w + lane.  For every
-// staged row it computes its 32 intermediate values (row pass; the rows of a
-// stage are independent, so their sums overlap), releases the stage, keeps
-// the values in its own ring of the last kSsRing rows (one column per lane:
-// no bank conflicts), and whenever the window of a column-pass repetition is
-// complete (T_v rows, every S_v rows), computes that repetition's m_v outputs
-// for its columns and stores them: consecutive lanes, consecutive columns.
+// Consumer lane l of warp w owns intermediate columns q and q + 1, q = q0 +
+// 2 (32 w + l).  For every staged row it computes its two intermediate
+// values (row pass, paired FMAs; the rows of a stage are independent, so
+// their sums overlap), releases the stage, keeps the values in its warp's
+// ring of the last kSsRing rows (a float2 per lane: no bank conflicts), and
+// whenever the window of a column-pass repetition is complete (T_v rows,
+// every S_v rows), computes that repetition's m_v outputs for its columns
+// and stores them.
 // Warps never wait on each other; each input row of a band is read from HBM
 // once (the halo rows that neighbouring bands share, T_v - S_v of them, twice).
 #include "arol_internal.h"
@@ -30,16 +31,21 @@
 #define AROL_SS_STAGES 16
 #endif
 #ifndef AROL_SS_STAGE_KB
-#define AROL_SS_STAGE_KB 80
+#define AROL_SS_STAGE_KB 40
 #endif
 #ifndef AROL_SS_SLEEP_NS
 #define AROL_SS_SLEEP_NS 20000
+#endif
+#ifndef AROL_SS_MIN_CTAS
+#define AROL_SS_MIN_CTAS 3
 #endif
 
 namespace arol {
 namespace {
 
-constexpr int kSsCWarps = 8;                       // consumer warps (32 columns each)
+constexpr int kSsCWarps = 4;                       // consumer warps
+constexpr int kSsCols = 2;                         // intermediate columns per consumer lane
+constexpr int kSsChunk = 32 * kSsCWarps * kSsCols; // intermediate columns per unit
 constexpr int kSsPWarps = 2;                       // producer warps (alternate stages)
 constexpr int kSsThreads = (kSsCWarps + kSsPWarps) * 32;
 constexpr int kSsMaxStages = AROL_SS_STAGES;       // stages (an even number, 2 .. this, set by the window)
@@ -66,14 +72,14 @@ struct SsUnit {
 
 __device__ __forceinline__ SsUnit ss_unit(const SepChainDev& d, int u) {
     const SepPassDev &ph = d.p[0], &pv = d.p[1];
-    const int chunks = (d.W[1] + 32 * kSsCWarps - 1) / (32 * kSsCWarps);
+    const int chunks = (d.W[1] + kSsChunk - 1) / kSsChunk;
     const int bands = (pv.R + d.BH - 1) / d.BH;
     SsUnit s;
     const int per_frame = chunks * bands;
     s.f = (uint32_t)(u / per_frame);
     const int v = u - (int)s.f * per_frame, band = v / chunks, chunk = v - band * chunks;
-    s.q0 = chunk * 32 * kSsCWarps;
-    s.nq = min(32 * kSsCWarps, d.W[1] - s.q0);
+    s.q0 = chunk * kSsChunk;
+    s.nq = min(kSsChunk, d.W[1] - s.q0);
     s.ra = s.q0 / ph.m;
     const int rb = (s.q0 + s.nq - 1) / ph.m;
     s.xw = ph.S * (rb - s.ra) + ph.T;
@@ -117,50 +123,64 @@ __device__ __forceinline__ uint32_t ss_copy_row(const float* row, const float* x
     return bytes;
 }
 
-// Row-pass sum of one intermediate value: TH > 0 taps in registers (T_h =
-// TH), TH = 0 any T_h with the taps read from shared memory.
+// Row-pass sums of a lane's two intermediate values (paired FMAs, each an
+// IEEE fma rounded to nearest).  h2[k] holds the two columns' taps k.  One
+// window (`one`, both columns from the same repetition) or two (src0,
+// src1).  TH > 0: T_h = TH, taps in registers; TH = 0: any T_h, taps read
+// from shared memory (rows h0, h1).
 template <int TH>
-__device__ __forceinline__ float ss_dot(const float* hreg, const float* hrow, const float* src, int T) {
-    float acc = 0.f;
+__device__ __forceinline__ float2 ss_dot2(const float2* h2, const float* h0, const float* h1, const float* src0,
+                                          const float* src1, bool one, int T) {
+    float2 acc = make_float2(0.f, 0.f);
     if (TH > 0) {
+        if (one) {
 #pragma unroll
-        for (int k = 0; k < TH; ++k) acc = fmaf(hreg[k], src[k], acc);
+            for (int k = 0; k < TH; ++k) {
+                const float v = src0[k];
+                acc = __ffma2_rn(h2[k], make_float2(v, v), acc);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < TH; ++k) acc = __ffma2_rn(h2[k], make_float2(src0[k], src1[k]), acc);
+        }
     } else {
 #pragma unroll 4
-        for (int k = 0; k < T; ++k) acc = fmaf(hrow[k], src[k], acc);
+        for (int k = 0; k < T; ++k) acc = __ffma2_rn(make_float2(h0[k], h1[k]), make_float2(src0[k], src1[k]), acc);
     }
     return acc;
 }
 
-// Column-pass sum of one output: taps hvr[0 .. T), intermediate rows t ..
-// t + T - 1 of the lane's ring (slots mod kSsRing), in two runs that do not
-// wrap.
-__device__ __forceinline__ float ss_col(const float* hvr, const float* ring, int t, int T, int lane) {
-    const int s0 = t & (kSsRing - 1);
-    const int n1 = min(T, kSsRing - s0);
-    const float* a = ring + s0 * 32 + lane;
-    float acc = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < n1; ++k) acc = fmaf(hvr[k], a[32 * k], acc);
-    const float* b = ring + lane;
-    const float* hb = hvr + n1;
-#pragma unroll 4
-    for (int k = 0; k < T - n1; ++k) acc = fmaf(hb[k], b[32 * k], acc);
+// The same sums (TH in 1 .. 8, one window) from 16-byte loads: `src` is
+// 16-byte aligned and the staged row extends at least 8 words past it (the
+// words past the window are loaded and not used).
+template <int TH>
+__device__ __forceinline__ float2 ss_dot2_v4(const float2* h2, const float* src) {
+    float w[8];
+    const float4 a = *reinterpret_cast<const float4*>(src);
+    w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
+    if (TH > 4) {
+        const float4 b = *reinterpret_cast<const float4*>(src + 4);
+        w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
+    }
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < (TH > 0 && TH <= 8 ? TH : 1); ++k) acc = __ffma2_rn(h2[k], make_float2(w[k], w[k]), acc);
     return acc;
 }
 
-// Column pass of one repetition: the m_v outputs from intermediate rows t ..
-// t + T_v - 1 (ring slots mod kSsRing), stored at yo[j * ys] by active
+// Column pass of one repetition: the m_v outputs of the lane's two columns
+// from intermediate rows t .. t + T_v - 1 (ring slots mod kSsRing, a float2
+// per lane and row), stored at yo[j * ys] and yo[j * ys + 1] by active
 // lanes.  TV > 0: T_v = TV, the window loaded once into registers; TV = 0:
-// any T_v, one ring sweep per output.
+// any T_v, one ring sweep (in two runs that do not wrap) per output.
 template <int TV>
-__device__ __forceinline__ void ss_column_pass(const float* hv, int m, int T, const float* ring, int t, int lane,
-                                               float* yo, int64_t ys, bool active) {
+__device__ __forceinline__ void ss_column_pass(const float* hv, int m, int T, const float2* ring, int t, int lane,
+                                               float* yo, int64_t ys, bool act0, bool act1) {
+    const int s0 = t & (kSsRing - 1);
     if (TV > 0) {
-        float rv[TV > 0 ? TV : 1];
-        const int s0 = t & (kSsRing - 1);
+        float2 rv[TV > 0 ? TV : 1];
         if (s0 + TV <= kSsRing) {
-            const float* a = ring + s0 * 32 + lane;
+            const float2* a = ring + s0 * 32 + lane;
 #pragma unroll
             for (int k = 0; k < TV; ++k) rv[k] = a[32 * k];
         } else {
@@ -169,28 +189,39 @@ __device__ __forceinline__ void ss_column_pass(const float* hv, int m, int T, co
         }
         for (int j = 0; j < m; ++j) {
             const float* h = hv + j * TV;
-            float acc = 0.f;
+            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < TV; ++k) acc = fmaf(h[k], rv[k], acc);
-            if (active) yo[j * ys] = acc;
+            for (int k = 0; k < TV; ++k) acc = __ffma2_rn(make_float2(h[k], h[k]), rv[k], acc);
+            if (act0) yo[j * ys] = acc.x;
+            if (act1) yo[j * ys + 1] = acc.y;
         }
     } else {
+        const int n1 = min(T, kSsRing - s0);
         for (int j = 0; j < m; ++j) {
-            const float acc = ss_col(hv + j * T, ring, t, T, lane);
-            if (active) yo[j * ys] = acc;
+            const float* h = hv + j * T;
+            const float2* a = ring + s0 * 32 + lane;
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int k = 0; k < n1; ++k) acc = __ffma2_rn(make_float2(h[k], h[k]), a[32 * k], acc);
+            const float2* b = ring + lane;
+            const float* hb = h + n1;
+#pragma unroll 4
+            for (int k = 0; k < T - n1; ++k) acc = __ffma2_rn(make_float2(hb[k], hb[k]), b[32 * k], acc);
+            if (act0) yo[j * ys] = acc.x;
+            if (act1) yo[j * ys + 1] = acc.y;
         }
     }
 }
 
 template <int TH, int TV>
-__global__ void __launch_bounds__(kSsThreads, 2) sepstream_kernel(const SepChainDev d, int units, int xw_max, int nst,
+__global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel(const SepChainDev d, int units, int xw_max, int nst,
                                                                  unsigned* err) {
     extern __shared__ __align__(128) float ssm[];
     const int sr = (xw_max + 4 + 3) & ~3;                  // floats per staged row (window plus alignment slack)
     const int sf = kSsRows * sr;                           // floats per stage
     float* stages = ssm;
-    float* rings = stages + nst * sf;                      // kSsCWarps x kSsRing x 32
-    float* taps = rings + kSsCWarps * kSsRing * 32;        // Hh then Hv, row-major
+    float* rings = stages + nst * sf;                      // kSsCWarps x kSsRing x 32 x kSsCols
+    float* taps = rings + kSsCWarps * kSsRing * 32 * kSsCols;   // Hh then Hv, row-major
     uint64_t* bars = reinterpret_cast<uint64_t*>(taps + ((d.ntaps + 3) & ~3));
     const uint32_t full0 = ptx::smem_addr(bars), empty0 = ptx::smem_addr(bars + nst);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -260,25 +291,33 @@ __global__ void __launch_bounds__(kSsThreads, 2) sepstream_kernel(const SepChain
         return;
     }
 
-    // consumers
-    float* ring = rings + warp * kSsRing * 32;
+    // consumers: lane pair of columns q, q + 1
+    const float2* ring = reinterpret_cast<const float2*>(rings) + warp * kSsRing * 32;
+    float2* ringw = reinterpret_cast<float2*>(rings) + warp * kSsRing * 32;
     const float* hv = taps + pv.tap_off;
+    const bool one = (ph.m & 1) == 0;                      // q even: q and q + 1 share a repetition
     int st = 0;
     uint32_t phase = 0;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
         const SsUnit s = ss_unit(d, u);
-        const int q = s.q0 + 32 * warp + lane;             // this lane's intermediate column
-        const bool active = 32 * warp + lane < s.nq;
-        const int rh = active ? q / ph.m : s.ra, jh = active ? q - rh * ph.m : 0;
-        const int xoff = ph.S * (rh - s.ra);               // window offset of the lane's row-pass repetition
-        const float* hrow = taps + ph.tap_off + jh * ph.T;
-        float hreg[TH > 0 ? TH : 1];
+        const int c = kSsCols * (32 * warp + lane);        // column of the pair within the chunk
+        const int q = s.q0 + c;
+        const bool act0 = c < s.nq, act1 = c + 1 < s.nq;
+        const int rh0 = act0 ? q / ph.m : s.ra, jh0 = act0 ? q - rh0 * ph.m : 0;
+        const int rh1 = act1 ? (q + 1) / ph.m : rh0, jh1 = act1 ? q + 1 - rh1 * ph.m : jh0;
+        const int xoff0 = ph.S * (rh0 - s.ra), xoff1 = ph.S * (rh1 - s.ra);
+        const float* h0 = taps + ph.tap_off + jh0 * ph.T;
+        const float* h1 = taps + ph.tap_off + jh1 * ph.T;
+        float2 h2[TH > 0 ? TH : 1];
 #pragma unroll
-        for (int k = 0; k < (TH > 0 ? TH : 1); ++k) hreg[k] = TH > 0 ? hrow[k] : 0.f;
+        for (int k = 0; k < (TH > 0 ? TH : 1); ++k) h2[k] = TH > 0 ? make_float2(h0[k], h1[k]) : make_float2(0.f, 0.f);
         // the window's first word sits at the low two bits of its global word index
         const uint32_t wbase = (uint32_t)(reinterpret_cast<uintptr_t>(d.x) >> 2) +
                                (uint32_t)(s.f * (uint64_t)frame_in) + (uint32_t)s.c0;
         float* yf = d.y + (int64_t)s.f * frame_out + q;
+        // every row's window starts on a 16-byte boundary and each lane's
+        // repetition at a multiple of 4 words: 16-byte loads, no conflicts
+        const bool v4 = TH > 0 && TH <= 8 && one && (ph.S & 3) == 0 && (wbase & 3u) == 0 && (W & 3) == 0;
         int ir = s.row0;
         int due = pv.T - 1;                                // next row that completes a column-pass window
         int64_t yrow = (int64_t)pv.m * s.rb0 * d.W[2];     // offset of that repetition's first output row
@@ -290,20 +329,27 @@ __global__ void __launch_bounds__(kSsThreads, 2) sepstream_kernel(const SepChain
             }
             // row pass of the stage's rows (rows past the unit's end read
             // stale words; their sums are dropped)
-            const float* sp = stages + st * sf + xoff;
-            float mid[kSsRows];
+            const float* sp = stages + st * sf;
+            float2 mid[kSsRows];
             int irk = ir;
+            if (v4) {
 #pragma unroll
-            for (int k = 0; k < kSsRows; ++k) {
-                const int delta = (int)((wbase + (uint32_t)irk * (uint32_t)W) & 3u);
-                mid[k] = ss_dot<TH>(hreg, hrow, sp + k * sr + delta, ph.T);
-                if (++irk == H) irk = 0;
+                for (int k = 0; k < kSsRows; ++k) mid[k] = ss_dot2_v4<TH>(h2, sp + k * sr + xoff0);
+                irk += kSsRows;
+                while (irk >= H) irk -= H;
+            } else {
+#pragma unroll
+                for (int k = 0; k < kSsRows; ++k) {
+                    const float* row = sp + k * sr + (int)((wbase + (uint32_t)irk * (uint32_t)W) & 3u);
+                    mid[k] = ss_dot2<TH>(h2, h0, h1, row + xoff0, row + xoff1, one, ph.T);
+                    if (++irk == H) irk = 0;
+                }
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(empty0 + 8 * st);
             if (++st == nst) st = 0, phase ^= 1u;
             const int n = min(kSsRows, s.nrows - base);
-            float* rp = ring + (base & (kSsRing - 1)) * 32 + lane;   // base is a multiple of kSsRows: no wrap
+            float2* rp = ringw + (base & (kSsRing - 1)) * 32 + lane;   // base is a multiple of kSsRows: no wrap
             if (n == kSsRows) {
 #pragma unroll
                 for (int k = 0; k < kSsRows; ++k) rp[32 * k] = mid[k];
@@ -318,7 +364,7 @@ __global__ void __launch_bounds__(kSsThreads, 2) sepstream_kernel(const SepChain
             // column pass of every repetition whose window ends in this stage:
             // rows S_v r .. S_v r + T_v - 1 of the band
             for (; due < base + n; due += pv.S, yrow += ystep)
-                ss_column_pass<TV>(hv, pv.m, pv.T, ring, due - (pv.T - 1), lane, yf + yrow, d.W[2], active);
+                ss_column_pass<TV>(hv, pv.m, pv.T, ring, due - (pv.T - 1), lane, yf + yrow, d.W[2], act0, act1);
         }
     }
 }
@@ -334,11 +380,12 @@ int sepstream_stages(int xw_max) {
 
 size_t sepstream_smem(const SepChainDev& d, int xw_max, int nst) {
     const int sr = (xw_max + 4 + 3) & ~3;
-    return ((size_t)nst * kSsRows * sr + (size_t)kSsCWarps * kSsRing * 32 + ((d.ntaps + 3) & ~3)) * sizeof(float) +
+    return ((size_t)nst * kSsRows * sr + (size_t)kSsCWarps * kSsRing * 32 * kSsCols + ((d.ntaps + 3) & ~3)) *
+               sizeof(float) +
            2 * (size_t)nst * sizeof(uint64_t);
 }
 
-int sepstream_chunk_cols() { return 32 * kSsCWarps; }
+int sepstream_chunk_cols() { return kSsChunk; }
 int sepstream_max_taps() { return kSsRing - kSsRows + 1; }
 
 // The kernel for the passes' tap counts: both exact when T_h = T_v <= 8,
