@@ -174,7 +174,7 @@ __device__ __forceinline__ float2 ss_dot2_v4(const float2* h2, const float* src)
 // lanes.  TV > 0: T_v = TV, the window loaded once into registers; TV = 0:
 // any T_v, one ring sweep (in two runs that do not wrap) per output.
 template <int TV>
-__device__ __forceinline__ void ss_column_pass(const float* hv, int m, int T, const float2* ring, int t, int lane,
+__device__ __forceinline__ void ss_column_pass(const float2* hv, int m, int T, const float2* ring, int t, int lane,
                                                float* yo, int64_t ys, bool act0, bool act1) {
     const int s0 = t & (kSsRing - 1);
     if (TV > 0) {
@@ -188,25 +188,25 @@ __device__ __forceinline__ void ss_column_pass(const float* hv, int m, int T, co
             for (int k = 0; k < TV; ++k) rv[k] = ring[((s0 + k) & (kSsRing - 1)) * 32 + lane];
         }
         for (int j = 0; j < m; ++j) {
-            const float* h = hv + j * TV;
+            const float2* h = hv + j * TV;
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < TV; ++k) acc = __ffma2_rn(make_float2(h[k], h[k]), rv[k], acc);
+            for (int k = 0; k < TV; ++k) acc = __ffma2_rn(h[k], rv[k], acc);
             if (act0) yo[j * ys] = acc.x;
             if (act1) yo[j * ys + 1] = acc.y;
         }
     } else {
         const int n1 = min(T, kSsRing - s0);
         for (int j = 0; j < m; ++j) {
-            const float* h = hv + j * T;
+            const float2* h = hv + j * T;
             const float2* a = ring + s0 * 32 + lane;
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-            for (int k = 0; k < n1; ++k) acc = __ffma2_rn(make_float2(h[k], h[k]), a[32 * k], acc);
+            for (int k = 0; k < n1; ++k) acc = __ffma2_rn(h[k], a[32 * k], acc);
             const float2* b = ring + lane;
-            const float* hb = h + n1;
+            const float2* hb = h + n1;
 #pragma unroll 4
-            for (int k = 0; k < T - n1; ++k) acc = __ffma2_rn(make_float2(hb[k], hb[k]), b[32 * k], acc);
+            for (int k = 0; k < T - n1; ++k) acc = __ffma2_rn(hb[k], b[32 * k], acc);
             if (act0) yo[j * ys] = acc.x;
             if (act1) yo[j * ys + 1] = acc.y;
         }
@@ -222,11 +222,16 @@ __global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel
     float* stages = ssm;
     float* rings = stages + nst * sf;                      // kSsCWarps x kSsRing x 32 x kSsCols
     float* taps = rings + kSsCWarps * kSsRing * 32 * kSsCols;   // Hh then Hv, row-major
-    uint64_t* bars = reinterpret_cast<uint64_t*>(taps + ((d.ntaps + 3) & ~3));
+    float2* hv2 = reinterpret_cast<float2*>(taps + ((d.ntaps + 3) & ~3));   // Hv, each tap doubled
+    uint64_t* bars = reinterpret_cast<uint64_t*>(hv2 + ((d.p[1].m * d.p[1].T + 1) & ~1));
     const uint32_t full0 = ptx::smem_addr(bars), empty0 = ptx::smem_addr(bars + nst);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const SepPassDev &ph = d.p[0], &pv = d.p[1];
     for (int i = threadIdx.x; i < d.ntaps; i += blockDim.x) taps[i] = __ldg(d.taps + i);
+    for (int i = threadIdx.x; i < pv.m * pv.T; i += blockDim.x) {
+        const float h = __ldg(d.taps + pv.tap_off + i);
+        hv2[i] = make_float2(h, h);
+    }
     if (threadIdx.x == 0) {
         for (int st = 0; st < nst; ++st) {
             ptx::mbar_init(full0 + 8 * st, 1);
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel
     // consumers: lane pair of columns q, q + 1
     const float2* ring = reinterpret_cast<const float2*>(rings) + warp * kSsRing * 32;
     float2* ringw = reinterpret_cast<float2*>(rings) + warp * kSsRing * 32;
-    const float* hv = taps + pv.tap_off;
+
     const bool one = (ph.m & 1) == 0;                      // q even: q and q + 1 share a repetition
     int st = 0;
     uint32_t phase = 0;
@@ -364,7 +369,7 @@ __global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel
             // column pass of every repetition whose window ends in this stage:
             // rows S_v r .. S_v r + T_v - 1 of the band
             for (; due < base + n; due += pv.S, yrow += ystep)
-                ss_column_pass<TV>(hv, pv.m, pv.T, ring, due - (pv.T - 1), lane, yf + yrow, d.W[2], act0, act1);
+                ss_column_pass<TV>(hv2, pv.m, pv.T, ring, due - (pv.T - 1), lane, yf + yrow, d.W[2], act0, act1);
         }
     }
 }
@@ -380,7 +385,8 @@ int sepstream_stages(int xw_max) {
 
 size_t sepstream_smem(const SepChainDev& d, int xw_max, int nst) {
     const int sr = (xw_max + 4 + 3) & ~3;
-    return ((size_t)nst * kSsRows * sr + (size_t)kSsCWarps * kSsRing * 32 * kSsCols + ((d.ntaps + 3) & ~3)) *
+    return ((size_t)nst * kSsRows * sr + (size_t)kSsCWarps * kSsRing * 32 * kSsCols + ((d.ntaps + 3) & ~3) +
+            2 * (size_t)((d.p[1].m * d.p[1].T + 1) & ~1)) *
                sizeof(float) +
            2 * (size_t)nst * sizeof(uint64_t);
 }
