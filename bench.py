@@ -426,7 +426,7 @@ def bench_generic(A, torch, stream, flush, reps, hbm):
     """A tiler no specialised kernel takes (diagonal 8-element patterns) on
     64 x 1080 x 1920: the per-repetition walk."""
     tk, xs = W.diagonal_fir()
-    return _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, "tiler_generic_kernel")[2]
+    return _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, "tiler_tiled_kernel")[2]
 
 
 def bench_stencil(A, torch, stream, flush, reps, hbm):

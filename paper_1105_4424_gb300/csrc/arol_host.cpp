@@ -308,6 +308,20 @@ void make_port(const arol_array_desc& a, const arol_tiler& t, int rep_rank, Port
         p.pattern[1] = (int32_t)t.pattern[1];
     }
     for (int k = 0; k < 4; ++k) p.shape_div[k] = make_fastdiv((uint32_t)p.shape[k]);
+    // Linear walk: with every fitting reduced into [0, shape), a pattern whose
+    // base coordinate plus its largest step stays inside the array never
+    // wraps, and its elements sit at base + i0 lin[0] + i1 lin[1].
+    p.linear = 1;
+    for (int c = 0; c < 2; ++c) {
+        p.lin[c] = 0;
+        for (int k = 0; k < 4; ++k) p.lin[c] += (int64_t)p.fitting[k][c] * p.stride[k];
+    }
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t e = (uint64_t)p.fitting[k][0] * (uint64_t)(p.pattern[0] - 1) +
+                           (uint64_t)p.fitting[k][1] * (uint64_t)(p.pattern[1] - 1);
+        if (e >= 0x80000000ull) p.linear = 0;
+        p.ext[k] = (uint32_t)std::min<uint64_t>(e, 0xFFFFFFFFull);
+    }
     // Contiguous-row pattern: the whole pattern advances along the last array
     // dimension (stride 1) by one element per step, so the walk is an
     // increment with one wrap test.
@@ -1377,6 +1391,49 @@ arol_status arol_task_info(arol_task t, arol_task_info_t* info) {
 
 namespace {
 
+uint32_t pow2_at_least(uint32_t v) {
+    uint32_t p = 1;
+    while (p < v && p < (1u << 30)) p <<= 1;
+    return p;
+}
+
+// Block tiling of the generic walk over the last two repetition dims of
+// extent > 1 (db the last, da the one before): 256 threads, at most 8 rows
+// of repetitions along da, the rest along db, each thread R repetitions
+// 2^lb apart along db.
+bool gen_geom(const TaskDev& t, GenGeom* out) {
+    GenGeom g{};
+    g.db = 3;
+    while (g.db > 0 && t.rep[g.db] <= 1) --g.db;
+    g.da = g.db - 1;
+    while (g.da >= 0 && t.rep[g.da] <= 1) --g.da;
+    const uint32_t RB = (uint32_t)std::max(t.rep[g.db], 1), RA = g.da >= 0 ? (uint32_t)t.rep[g.da] : 1u;
+    const uint32_t rows = std::min<uint32_t>(8, pow2_at_least(RA));
+    const uint32_t tb = std::min<uint32_t>(pow2_at_least(RB), 256 / rows);
+    const uint32_t ta = std::min<uint32_t>(256 / tb, pow2_at_least(RA));
+    g.lb = 0;
+    while ((1u << g.lb) < tb) ++g.lb;
+    g.ta = (int32_t)ta;
+    const uint32_t R = (uint32_t)tiler_tiled_reps(t.elem == ELEM_FIR ? t.m : 1);
+    g.na = (RA + ta - 1) / ta;
+    g.nb = (RB + R * tb - 1) / (R * tb);
+    for (int k = 0; k < 4; ++k) {
+        g.istep[k] = t.in.shape[k] ? (uint32_t)(((uint64_t)tb * t.in.paving[k][g.db]) % (uint32_t)t.in.shape[k]) : 0u;
+        g.ostep[k] = t.out.shape[k] ? (uint32_t)(((uint64_t)tb * t.out.paving[k][g.db]) % (uint32_t)t.out.shape[k]) : 0u;
+    }
+    uint64_t outer = 1;
+    for (int q = 0; q < (g.da >= 0 ? g.da : g.db); ++q) outer *= (uint64_t)std::max(t.rep[q], 1);
+    const uint64_t nt = outer * g.na * g.nb;
+    if (nt >= 0x80000000ull) return false;
+    g.ntiles = (uint32_t)nt;
+    g.na_div = make_fastdiv(g.na);
+    g.nb_div = make_fastdiv(g.nb);
+    const int mx = tiler_tiled_maxm(t.elem == ELEM_FIR ? t.m : 1);
+    g.tap_floats = t.elem == ELEM_FIR && (int64_t)t.T * mx <= 12288 ? t.T * mx : 0;
+    *out = g;
+    return true;
+}
+
 arol_status run_generic(const arol_task_desc& d, const float* taps, const void* x, void* y, cudaStream_t s,
                         unsigned* err = nullptr) {
     TaskDev td = make_taskdev(d);
@@ -1386,6 +1443,11 @@ arol_status run_generic(const arol_task_desc& d, const float* taps, const void* 
     td.err = err;
     if (td.fir2d) {
         AROL_CUDA(launch_fir2d(td, s), "2-D FIR kernel launch");
+        return AROL_OK;
+    }
+    GenGeom g;
+    if (!td.wide && gen_geom(td, &g)) {
+        AROL_CUDA(launch_tiler_tiled(td, g, td.elem == ELEM_FIR ? td.m : 1, s), "tiler kernel launch");
         return AROL_OK;
     }
     AROL_CUDA(launch_tiler_generic(td, td.elem == ELEM_FIR ? td.m : 1, s), "tiler kernel launch");

@@ -25,6 +25,10 @@ struct PortDev {
     int32_t fast;           // 1: the pattern walks one contiguous dimension with step 1
     int32_t fdim;           // that dimension
     int64_t stride[4];      // row-major element strides; 0 for unused dims
+    int64_t lin[2];         // element offset of one step along pattern dim 0 / 1: sum_k fitting[k][c] stride[k]
+    uint32_t ext[4];        // largest coordinate a pattern adds along each array dim (fittings reduced)
+    int32_t linear;         // 1: ext < 2^31, so a pattern with base b and b + ext < shape never wraps
+    int32_t pad_;
     uint32_t origin[4];
     uint32_t paving[4][4];  // [array dim][repetition dim]
     uint32_t fitting[4][2]; // [array dim][pattern dim]
@@ -131,7 +135,24 @@ struct DownscaleDev {
 };
 
 // Launchers (return cudaGetLastError() of the launch).
+// Block tiling of the generic walk (tiler_tiled_kernel): a tile is R 2^lb
+// consecutive repetitions along dim db (lane l takes l, l + 2^lb, ...)
+// times ta along dim da (da = -1: none), so that the overlapping or
+// neighbouring patterns of nearby repetitions share cache lines within one
+// SM.
+struct GenGeom {
+    int32_t da, db;        // tiled repetition dims; every dim after da other than db has extent 1
+    int32_t lb, ta;        // log2 of the threads along db; threads along da
+    uint32_t na, nb;       // tiles along da and db
+    uint32_t ntiles;       // (repetitions before the tiled dims) x na x nb, < 2^31
+    int32_t tap_floats;    // taps staged in shared memory, transposed T x MAXM; 0: read from global memory
+    FastDiv na_div, nb_div;
+    uint32_t istep[4], ostep[4];   // base-coordinate step of 2^lb repetitions along db, reduced mod shape
+};
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s);
+cudaError_t launch_tiler_tiled(const TaskDev& t, const GenGeom& g, int max_m, cudaStream_t s);
+int tiler_tiled_maxm(int max_m);
+int tiler_tiled_reps(int max_m);   // repetitions per thread (R) of the tiled kernel for that bank size
 // CTA b takes tiles b, b + grid, ... (a static schedule; `counter` is unused).
 cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s);
 // A 2-D window task that launch_fir2d runs on the register-blocked stencil

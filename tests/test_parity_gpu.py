@@ -66,6 +66,40 @@ def test_random_fir_tilers(arol):
         assert_fir_close(y, O.run_task(tk, [x])[0], fir_scale(tk, x), what="random fir")
 
 
+def test_tiled_walk_long_repetition_rows(arol):
+    """Repetition spaces up to 300 along their last dimension on arrays up to
+    64 wide: the block-tiled walk gives each thread several repetitions 2^lb
+    apart, some of whose patterns wrap and some not.  Copies bit-exact (f32
+    and bf16 words), fir banks (m up to 16) against the C oracle."""
+    g = W.rng(110)
+    for n in range(40):
+        elem = "copy" if n % 2 == 0 else "fir"
+        tk = W.random_tiler_task(g, elem, max_side=64, max_rep=300)
+        if elem == "copy" and n % 4 == 0:
+            tk = dict(tk, inputs=[dict(tk["inputs"][0], dtype="bf16")], outputs=[dict(tk["outputs"][0], dtype="bf16")])
+            x = g.integers(0, 65536, size=tk["inputs"][0]["shape"], dtype=np.uint16)
+        elif elem == "copy":
+            x = g.random(tk["inputs"][0]["shape"], dtype=np.float32)
+        else:
+            x = g.standard_normal(tk["inputs"][0]["shape"]).astype(np.float32)
+        _, y = run1(arol, tk, [x])
+        ref = C.run_task(tk, [x])[0]
+        if elem == "copy":
+            np.testing.assert_array_equal(y.view(np.uint16 if x.dtype == np.uint16 else np.uint32),
+                                          ref.view(np.uint16 if x.dtype == np.uint16 else np.uint32))
+        else:
+            assert_fir_close(y, ref, fir_scale(tk, x, C.run_chain), what=f"long-row fir {n}")
+
+
+def test_diagonal_tiler_with_wrapping_rows(arol):
+    """The diagonal 8-element patterns of the generic bench case on 3 frames
+    of 40 x 256: the last 7 rows' patterns wrap to the top (the wrapping
+    walk), the rest take the linear walk."""
+    tk, (x,) = W.diagonal_fir(seed=2, frames=3, height=40, width=256)
+    _, y = run1(arol, tk, [x])
+    assert_fir_close(y, C.run_task(tk, [x])[0], fir_scale(tk, x, C.run_chain), what="diagonal")
+
+
 def test_fir_bank_sizes(arol):
     """m from 1 to 32 (every register-bank instantiation), T up to 64."""
     g = W.rng(104)

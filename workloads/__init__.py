@@ -249,10 +249,11 @@ def config4(seed=0, frames=16, height=1080, width=1920):
 
 
 def random_tiler_task(g: np.random.Generator, elem="copy", max_side=12,
-                      max_rank=3, max_abs=6, fir_pattern_rank=1):
+                      max_rank=3, max_abs=6, fir_pattern_rank=1, max_rep=5):
     """A random small task: random input tiler (negative origin, paving and
     fitting entries allowed, overlaps and wrap-around allowed) and an output
-    tiler that partitions its array by construction.
+    tiler that partitions its array by construction.  Repetition extents are
+    drawn in 1..max_rep.
 
     The output array's dimensions are a random permutation of the repetition
     dimensions and the output pattern dimensions; with probability 1/2 the
@@ -260,7 +261,7 @@ def random_tiler_task(g: np.random.Generator, elem="copy", max_side=12,
     one array dimension of size R*m (paving m, fitting 1), as in a downscaler.
     """
     q = int(g.integers(1, 3))
-    R = tuple(int(v) for v in g.integers(1, 6, size=q))
+    R = tuple(int(v) for v in g.integers(1, max_rep + 1, size=q))
     d = int(g.integers(1, max_rank + 1))
     shape = tuple(int(v) for v in g.integers(1, max_side + 1, size=d))
     p = fir_pattern_rank if elem == "fir" else int(g.integers(1, 3))
