@@ -471,9 +471,37 @@ def bench_backward(A, torch, stream, flush, reps):
     fb = statistics.median(time_each_flushed(both, reps, stream, flush))
     fused = statistics.median(time_each_flushed(lambda: c.fwd_bwd([xd], wd, y, gx, gt), reps, stream, flush))
     fb_bytes = 4 * (x.size + w.size) + 4 * x.size   # bwd reads X and dY, writes dX
-    return {"frames": 16, "fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_ms": fb, "ratio": fb / fwd,
-            "fused_fwd_bwd_ms": fused, "fused_ratio": fused / fwd,
-            "fwd_gbs": chain_bytes(16) / (fwd * 1e-3) / 1e9, "bwd_gbs": fb_bytes / (bwd * 1e-3) / 1e9}
+    out = {"frames": 16, "fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_ms": fb, "ratio": fb / fwd,
+           "fused_fwd_bwd_ms": fused, "fused_ratio": fused / fwd,
+           "fwd_gbs": chain_bytes(16) / (fwd * 1e-3) / 1e9, "bwd_gbs": fb_bytes / (bwd * 1e-3) / 1e9,
+           # the backward moves (X + dY + dX) / (X + Y) = 1.88x the forward's bytes, so
+           # separate calls at equal bandwidth take 2.88x the forward
+           "bytes_ratio_bwd_over_fwd": fb_bytes / chain_bytes(16)}
+    # the same at 64 frames, where the fixed costs of a launch weigh less
+    del xd, wd, gx, y
+    chain, (x,), w = W.config4(frames=64)
+    c = A.Chain(chain)
+    xd = torch.from_numpy(x).cuda()
+    wd = torch.from_numpy(w).cuda()
+    y = c.run([xd])
+    gx = torch.empty_like(xd)
+    for _ in range(3):
+        c.run([xd], y)
+        c.backward(wd, [xd], gx, gt)
+        c.fwd_bwd([xd], wd, y, gx, gt)
+    f64 = statistics.median(time_each_flushed(lambda: c.run([xd], y), reps, stream, flush))
+    b64 = statistics.median(time_each_flushed(lambda: c.backward(wd, [xd], gx, gt), reps, stream, flush))
+
+    def both64():
+        c.run([xd], y)
+        c.backward(wd, [xd], gx, gt)
+    fb64 = statistics.median(time_each_flushed(both64, reps, stream, flush))
+    fu64 = statistics.median(time_each_flushed(lambda: c.fwd_bwd([xd], wd, y, gx, gt), reps, stream, flush))
+    c.sync_status()
+    out["frames64"] = {"fwd_ms": f64, "bwd_ms": b64, "fwd_plus_bwd_ms": fb64, "ratio": fb64 / f64,
+                       "fused_fwd_bwd_ms": fu64, "fused_ratio": fu64 / f64,
+                       "bwd_gbs": (8 * x.size + 4 * w.size) / (b64 * 1e-3) / 1e9}
+    return out
 
 
 def bench_matmul(A, torch, stream, flush, reps, peak_tf):
