@@ -337,15 +337,28 @@ def bench_batched(A, torch, stream, flush, reps, tune=True):
             "launches_batched": 1, "launches_per_task": len(tasks), "autotuned": cfg}
 
 
-def bench_batched_chains(A, torch, stream, flush, reps):
-    """128 two-stage downscaler chains of uneven frame sizes in one batch
-    (one graph, one persistent launch per stage) against one launch per
-    stage task and against one fused chain launch per member."""
+def bench_batched_chains(A, torch, stream, flush, reps, hbm):
+    """128 two-stage 8 -> 3 downscaler chains of uneven frame sizes in one
+    batch: one launch of the batched downscaler over every member (the
+    intermediates stay on chip), against one launch per member, the batch
+    run stage by stage (the row-FIR kernel, then the persistent kernel's
+    column tiles, intermediates through HBM; inputs one float off a 16-byte
+    boundary route the members there) and one fused chain launch per
+    member."""
     chains, xs = W.chain_batch()
     b = A.Batch(chains)
     ins = [torch.from_numpy(x).cuda() for x in xs]
     outs = b.empty_outputs()
     run, run_per_task = b.prepare(ins, outs)
+    bs = A.Batch(chains)
+    # the same inputs one float past a 16-byte boundary: stage by stage
+    bufs = [torch.empty(x.size + 1, device="cuda") for x in xs]
+    sins = []
+    for buf, x in zip(bufs, ins):
+        buf[1:] = x.reshape(-1)
+        sins.append(buf[1:].view(x.shape))
+    souts = bs.empty_outputs()
+    run_staged, _ = bs.prepare(sins, souts)
     fused = [A.Chain(c) for c in chains]
     fouts = [torch.empty_like(o) for o in outs]
     fused_calls = [f.prepare([x], y) for f, x, y in zip(fused, ins, fouts)]
@@ -357,18 +370,22 @@ def bench_batched_chains(A, torch, stream, flush, reps):
     for _ in range(3):
         run()
         run_per_task()
+        run_staged()
         run_fused()
     tb = statistics.median(time_each_flushed(run, reps, stream, flush))
     tp = statistics.median(time_each_flushed(run_per_task, reps, stream, flush))
+    ts = statistics.median(time_each_flushed(run_staged, reps, stream, flush))
     tf = statistics.median(time_each_flushed(run_fused, reps, stream, flush))
+    b.sync_status()
+    bs.sync_status()
     mid = sum(4 * int(np.prod(c[0]["outputs"][0]["shape"])) for c in chains)
     nbytes = sum(4 * x.size for x in xs) + sum(4 * int(np.prod(c[-1]["outputs"][0]["shape"])) for c in chains)
+    gbs = nbytes / (tb * 1e-3) / 1e9
     return {"chains": len(chains), "unique_bytes": nbytes, "intermediate_bytes": mid,
-            "batched_ms": tb, "per_task_ms": tp, "fused_per_chain_ms": tf,
-            "speedup_vs_per_task": tp / tb, "speedup_vs_fused_per_chain": tf / tb,
-            "batched_gbs_unique": nbytes / (tb * 1e-3) / 1e9,
-            "batched_gbs_with_intermediate": (nbytes + 2 * mid) / (tb * 1e-3) / 1e9,
-            "launches": {"batched": 2, "per_task": 2 * len(chains), "fused_per_chain": len(chains)}}
+            "batched_ms": tb, "per_task_ms": tp, "staged_ms": ts, "fused_per_chain_ms": tf,
+            "speedup_vs_per_task": tp / tb, "speedup_vs_staged": ts / tb, "speedup_vs_fused_per_chain": tf / tb,
+            "batched_gbs_unique": gbs, "frac_of_hbm": gbs / hbm, "kernel": "downscale_batch_kernel",
+            "launches": {"batched": 1, "per_task": len(chains), "staged": 2, "fused_per_chain": len(chains)}}
 
 
 def _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, kernel_name):
@@ -403,7 +420,16 @@ def bench_chain_5to2(A, torch, stream, flush, reps, hbm):
             del os.environ["AROL_SEPSTREAM"]
         else:
             os.environ["AROL_SEPSTREAM"] = prev
-    b = A.Batch([chain])
+    # stage by stage: the chain made with the streaming kernel off, in a
+    # one-member batch
+    os.environ["AROL_SEPSTREAM"] = "off"
+    try:
+        b = A.Batch([chain])
+    finally:
+        if prev is None:
+            del os.environ["AROL_SEPSTREAM"]
+        else:
+            os.environ["AROL_SEPSTREAM"] = prev
     ins = [torch.from_numpy(x).cuda() for x in xs]
     outs = b.empty_outputs()
     run, _ = b.prepare(ins, outs)
@@ -759,7 +785,7 @@ def run_gpu(args):
         reps = max(5, min(args.steps, 20))
         line["config0"] = bench_config0(A, torch, stream, 200)
         line["batched"] = bench_batched(A, torch, stream, flush, reps)
-        line["batched_chains"] = bench_batched_chains(A, torch, stream, flush, reps)
+        line["batched_chains"] = bench_batched_chains(A, torch, stream, flush, reps, hbm)
         line["stencil"] = bench_stencil(A, torch, stream, flush, reps, hbm)
         line["chain_5to2"] = bench_chain_5to2(A, torch, stream, flush, reps, hbm)
         line["config0_scaled"] = bench_config0_scaled(A, torch, stream, flush, reps, hbm)
@@ -803,7 +829,7 @@ def run_case(args):
     elif args.case == "stencil":
         out = bench_stencil(A, torch, stream, flush, reps, hbm)
     elif args.case == "chains":
-        out = bench_batched_chains(A, torch, stream, flush, reps)
+        out = bench_batched_chains(A, torch, stream, flush, reps, hbm)
     elif args.case == "chain5to2":
         out = bench_chain_5to2(A, torch, stream, flush, reps, hbm)
     elif args.case == "config0_scaled":

@@ -256,13 +256,18 @@ arol_status arol_selftest_wait_timeout(void* stream);
 
 /* Build a batch of n independent members (uneven shapes allowed).  A member
  * is a single-input copy/fir task or a chain of them from arol_chain_create
- * (Sec. 5: tasks linked through shared arrays), which enters as its tasks,
- * one per stage, without the fused chain kernels.  The batch copies the
- * descriptors and host taps (the handles may be destroyed afterwards), owns
- * one device arena for every chain intermediate, a device work list of
- * tiles grouped by stage, built on first run, and a CUDA graph that launches
- * the persistent kernels of each stage: stage k of every chain runs after
- * stage k - 1 of every chain.  Row-FIR tasks (one row per repetition row,
+ * (Sec. 5: tasks linked through shared arrays).  Chain members keep their
+ * intermediates on chip when a fused form serves them all in one launch:
+ * chains the fused 8 -> 3 downscaler takes (f32) run on its batched form
+ * while their input is 16-byte aligned (checked every run; a change of that
+ * set rebuilds the work lists and the graph), row-then-column chains (kernel
+ * 5 of arol_task_info) on the batched streaming chain kernel.  Other chains
+ * enter as their tasks, one per stage.  The batch copies the descriptors and
+ * host taps (the handles may be destroyed afterwards), owns one device arena
+ * for the staged chain intermediates, a device work list of tiles grouped by
+ * stage, built on first run, and a CUDA graph that launches the fused chain
+ * kernels, then the persistent kernels of each stage: stage k of every chain
+ * runs after stage k - 1 of every chain.  Row-FIR tasks (one row per repetition row,
  * step <= 32 along it, T <= 32, m <= 16, f32) run as tiles of whole rows or
  * row pieces on the row-FIR kernel; the others as repetition ranges on the
  * general persistent kernel.  Matmul tasks and tasks whose
@@ -276,8 +281,9 @@ arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out);
  * previous call the device table is refreshed (one copy) before the launch. */
 arol_status arol_batch_run(arol_batch b, const void* const* in, void* const* out, void* stream);
 
-/* The same tasks with one kernel launch per task (each stage of a chain is a
- * task), in order, on `stream`:
+/* The same tasks with one kernel launch per task (each stage of a staged
+ * chain is a task; a chain on a fused kernel is one launch), in order, on
+ * `stream`:
  * the same kernel over each task's own tiles, without the graph or the shared
  * tile counter (for comparison with arol_batch_run). */
 arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* const* out, void* stream);

@@ -765,48 +765,43 @@ bool match_sep_pass(const arol_task_desc& d, SepPassDev* p, int64_t* F, int64_t 
 
 // Plans the streaming form of a chain of a row pass then a column pass
 // (host only): chunks of sepstream_chunk_cols() intermediate columns, the
-// widest input window of a chunk and the stages; refused when
-// the column pass's window outgrows the ring of intermediate rows or the
-// shared memory would not leave two CTAs per SM.  The bands are chosen at
-// the first run (sepstream_bands).
+// widest input window of a chunk, the stages and the shared taps per warp;
+// refused when the column pass's window outgrows the ring of intermediate
+// rows or the shared memory would not leave two CTAs per SM.  The bands
+// are chosen at the first run (sepstream_bands).
 constexpr size_t kSsSmemMax = 110 * 1024;
 
-bool plan_sepstream(const SepChainDev& c, SepChainDev* out, int* xw_max, int* nst) {
-    if (c.K != 2 || c.p[0].axis != 1 || c.p[1].axis != 0) return false;
-    const SepPassDev &ph = c.p[0], &pv = c.p[1];
-    if (pv.T > sepstream_max_taps()) return false;
-    const int cc = sepstream_chunk_cols();
-    const int64_t chunks = (c.W[1] + cc - 1) / cc;
-    int xw = 0;
-    for (int64_t k = 0; k < chunks; ++k) {
-        const int64_t q0 = k * cc, nq = std::min<int64_t>(cc, c.W[1] - q0);
-        const int64_t ra = q0 / ph.m, rb = (q0 + nq - 1) / ph.m;
-        xw = (int)std::max<int64_t>(xw, ph.S * (rb - ra) + ph.T);
-    }
-    const int ns = sepstream_stages(xw);
-    if (sepstream_smem(c, xw, ns) > kSsSmemMax || c.F * chunks * pv.R >= 2147483647LL) return false;
+bool plan_sepstream(const SepChainDev& d, SsChain* out, int* xw_max, int* nst, int* tapw) {
+    if (d.K != 2 || d.p[0].axis != 1 || d.p[1].axis != 0) return false;
+    if (d.p[1].T > sepstream_max_taps()) return false;
+    SepChainDev one = d;
+    one.BH = d.p[1].R;
+    const SsChain c = ss_chain_of(one);
+    const int xw = sepstream_window(c), ns = sepstream_stages(xw), tw = sepstream_tap_floats(c);
+    if (sepstream_smem(xw, ns, tw) > kSsSmemMax || c.F * c.chunks * c.Rv >= 2147483647LL) return false;
     *out = c;
     *xw_max = xw;
     *nst = ns;
+    *tapw = tw;
     return true;
 }
 
 // Bands of column-pass repetitions for the streaming chain kernel on the
 // current device: the band height that minimises the rows the busiest CTA
 // walks (waves of resident CTAs times the rows of one band, halo included).
-void sepstream_bands(SepChainDev& d, int xw_max, int nst, int* units) {
-    const SepPassDev& pv = d.p[1];
-    const int cc = sepstream_chunk_cols();
-    const int64_t per = d.F * ((d.W[1] + cc - 1) / cc);
-    const int64_t cap = (int64_t)device_sm_count() * sepstream_ctas_per_sm(d, sepstream_smem(d, xw_max, nst));
-    int64_t best = -1, best_bh = pv.R;
-    for (int64_t nb = 1; nb <= std::min<int64_t>(pv.R, 4096); ++nb) {
-        const int64_t bh = (pv.R + nb - 1) / nb, u = per * ((pv.R + bh - 1) / bh);
-        const int64_t cost = ((u + cap - 1) / cap) * ((int64_t)pv.S * (bh - 1) + pv.T);
+void sepstream_bands(SsChain& c, int xw_max, int nst, int tapw, int* units) {
+    const int64_t per = c.F * c.chunks;
+    const int64_t cap =
+        (int64_t)device_sm_count() * sepstream_ctas_per_sm(c.Th, c.Tv, false, sepstream_smem(xw_max, nst, tapw));
+    int64_t best = -1, best_bh = c.Rv;
+    for (int64_t nb = 1; nb <= std::min<int64_t>(c.Rv, 4096); ++nb) {
+        const int64_t bh = (c.Rv + nb - 1) / nb, u = per * ((c.Rv + bh - 1) / bh);
+        const int64_t cost = ((u + cap - 1) / cap) * ((int64_t)c.Sv * (bh - 1) + c.Tv);
         if (best < 0 || cost < best) best = cost, best_bh = bh;
     }
-    d.BH = (int32_t)best_bh;
-    *units = (int)(per * ((pv.R + best_bh - 1) / best_bh));
+    c.BH = (int32_t)best_bh;
+    c.bands = (c.Rv + c.BH - 1) / c.BH;
+    *units = (int)(per * c.bands);
 }
 
 // The tile kernel's plan: region sizes separate into a row part (depending
@@ -961,8 +956,8 @@ struct arol_task_s {
     std::vector<int32_t> sc_tab;
     int32_t* sc_tab_dev = nullptr;
     // streaming row-then-column chain (kernel 5)
-    SepChainDev ss{};
-    int ss_units = 0, ss_xw = 0, ss_nst = 2;
+    SsChain ss{};
+    int ss_units = 0, ss_xw = 0, ss_nst = 2, ss_tapw = 0;
     unsigned* err_flag = nullptr;        // device word: bounded waits that gave up
     // backward scratch and inverse maps
     float* partials = nullptr;
@@ -1275,7 +1270,7 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     const char* e = std::getenv("AROL_SEPSTREAM");
     const bool stream = !(e && (!std::strcmp(e, "off") || !std::strcmp(e, "0")));
     if (t->kernel == 3 && describe_sepchain(t->descs, &sd)) {
-        if (stream && plan_sepstream(sd, &t->ss, &t->ss_xw, &t->ss_nst)) t->kernel = 5;
+        if (stream && plan_sepstream(sd, &t->ss, &t->ss_xw, &t->ss_nst, &t->ss_tapw)) t->kernel = 5;
         else if (plan_sepchain(sd, &t->sc)) t->kernel = 4;
     }
     if (t->kernel == 4) {
@@ -1321,7 +1316,7 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
                               : "stage by stage through a one-member batch");
     if (t->kernel == 5)
         log_line("chain %p: input windows of %d words, %d stages, %zu B of shared memory", (void*)t, t->ss_xw,
-                 t->ss_nst, sepstream_smem(t->ss, t->ss_xw, t->ss_nst));
+                 t->ss_nst, sepstream_smem(t->ss_xw, t->ss_nst, t->ss_tapw));
     if (t->kernel == 4)
         log_line("chain %p: tiles of %d x %d, %lld tiles per frame, %zu B of shared memory", (void*)t, t->sc.BH,
                  t->sc.BW, (long long)t->sc.tiles_y * t->sc.tiles_x, sepchain_smem(t->sc));
@@ -1553,14 +1548,17 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
     if (t->kernel == 5) {
         if ((st = ensure_err(t, s)) != AROL_OK) return st;
         if (!t->ss_units) {
-            sepstream_bands(t->ss, t->ss_xw, t->ss_nst, &t->ss_units);
+            sepstream_bands(t->ss, t->ss_xw, t->ss_nst, t->ss_tapw, &t->ss_units);
             log_line("chain %p: %d units, bands of %d repetitions", (void*)t, t->ss_units, t->ss.BH);
         }
-        SepChainDev d = t->ss;
-        d.x = (const float*)in[0];
-        d.y = (float*)out[0];
-        d.taps = taps;
-        AROL_CUDA(launch_sepstream(d, t->ss_units, t->ss_xw, t->ss_nst, t->err_flag, s), "fused chain kernel launch");
+        SsChain c = t->ss;
+        c.x = (const float*)in[0];
+        c.y = (float*)out[0];
+        c.hh = taps;
+        c.hv = taps + (size_t)c.mh * c.Th;
+        AROL_CUDA(launch_sepstream(c, nullptr, nullptr, 1, t->ss_units, c.Th, c.Tv, t->ss_xw, t->ss_nst, t->ss_tapw,
+                                   t->err_flag, s),
+                  "fused chain kernel launch");
         return AROL_OK;
     }
     if (t->kernel == 4) {
@@ -1983,6 +1981,32 @@ struct arol_batch_s {
     int64_t tile_reps = 2048;
     int threads = kBatchThreads;
     int ctas_per_sm = 4;
+    // members that are a row pass then a column pass run on the streaming
+    // chain kernel, all in one launch: their plans (pointers set per run),
+    // the unit prefix over them, and the common launch shape
+    std::vector<char> streamed;           // per internal task: its member is streamed
+    std::vector<int> ss_members;
+    std::vector<SsChain> ss_chains;
+    std::vector<int> ss_ustart;
+    int ss_xw = 0, ss_nst = 2, ss_tapw = 0, ss_th = 0, ss_tv = 0, ss_units = 0;
+    SsChain* dev_ss = nullptr;
+    SsChain* pinned_ss = nullptr;
+    int* dev_ss_ustart = nullptr;
+    // chain members the fused 8 -> 3 kernel would run alone (f32): one
+    // launch of its batched form over those whose input is 16-byte aligned
+    // (checked every run; a change of the set rebuilds tiles and graph)
+    std::vector<char> ds_ok;              // per member: eligible
+    std::vector<char> ds_on;              // per member: on the batched kernel in the current tables
+    std::vector<int> ds_members;
+    std::vector<DsMember> ds_geom;        // per member: frames, H, W and chunks (eligible members)
+    std::vector<DsMember> ds_mem;
+    float* ds_taps = nullptr;             // per eligible member: its 48 taps back to back
+    std::vector<int> ds_ustart;
+    int ds_units = 0, ds_ws = 0;
+    DsMember* dev_ds = nullptr;
+    DsMember* pinned_ds = nullptr;
+    int* dev_ds_ustart = nullptr;
+    std::vector<char> skip;               // per internal task: no tiles (its member runs on a chain kernel)
     // graph
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -2188,6 +2212,7 @@ arol_status build_tiles(arol_batch b) {
         std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
         b->rstage_off[stage] = (int)std::min<size_t>(rtiles.size(), 2147483647);
         for (int i : order) {
+            if (b->skip[i]) continue;
             const TaskDev& t = b->host_tasks[i];
             if (t.rowfir) {
                 build_row_tiles(t, i, b->row_budget, rtiles);
@@ -2262,6 +2287,89 @@ arol_status build_tiles(arol_batch b) {
     return AROL_OK;
 }
 
+// Bands of the streamed chain members, sized for about four units per
+// resident CTA over the whole batch (16 to 1024 rows per unit), the unit
+// prefix, and the device chain table.
+arol_status batch_stream_plan(arol_batch b) {
+    const size_t ns = b->ss_members.size();
+    if (!ns || b->dev_ss) return AROL_OK;
+    const size_t smem = sepstream_smem(b->ss_xw, b->ss_nst, b->ss_tapw);
+    const double cap = (double)device_sm_count() * sepstream_ctas_per_sm(b->ss_th, b->ss_tv, true, smem);
+    double rows = 0;
+    for (const SsChain& c : b->ss_chains) rows += (double)c.F * c.chunks * c.H;
+    const double target = std::min(1024.0, std::max(16.0, rows / (4.0 * cap)));
+    b->ss_ustart.assign(ns + 1, 0);
+    int64_t units = 0;
+    for (size_t k = 0; k < ns; ++k) {
+        SsChain& c = b->ss_chains[k];
+        const int64_t bh = std::max<int64_t>(1, std::min<int64_t>(c.Rv, (int64_t)((target - c.Tv) / c.Sv) + 1));
+        c.BH = (int32_t)bh;
+        c.bands = (int32_t)((c.Rv + bh - 1) / bh);
+        b->ss_ustart[k] = (int)units;
+        units += c.F * c.chunks * c.bands;
+        if (units >= 2147483647LL) return fail(AROL_ERR_UNSUPPORTED, "batch: too many streamed chain units");
+    }
+    b->ss_ustart[ns] = (int)units;
+    b->ss_units = (int)units;
+    AROL_CUDA(arol_malloc((void**)&b->dev_ss, ns * sizeof(SsChain)), "cudaMalloc(chain table)");
+    AROL_CUDA(arol_malloc((void**)&b->dev_ss_ustart, (ns + 1) * sizeof(int)), "cudaMalloc(chain units)");
+    AROL_CUDA(cudaMallocHost((void**)&b->pinned_ss, ns * sizeof(SsChain)), "cudaMallocHost(chain table)");
+    AROL_CUDA(cudaMemcpy(b->dev_ss_ustart, b->ss_ustart.data(), (ns + 1) * sizeof(int), cudaMemcpyHostToDevice),
+              "upload chain units");
+    log_line("batch %p: %lld streamed chain units (%.0f rows per unit aimed at)", (void*)b, (long long)units, target);
+    return AROL_OK;
+}
+
+// The members on the batched 8 -> 3 kernel (ds_on), their column chunks,
+// the unit prefix, and device tables sized for every eligible member.
+arol_status batch_ds_plan(arol_batch b) {
+    b->ds_members.clear();
+    b->ds_mem.clear();
+    b->ds_ustart.assign(1, 0);
+    b->ds_ws = 32;
+    int64_t units = 0;
+    size_t cap = 0;
+    for (char e : b->ds_ok) cap += e ? 1 : 0;
+    if (cap && !b->dev_ds) {
+        AROL_CUDA(arol_malloc((void**)&b->dev_ds, cap * sizeof(DsMember)), "cudaMalloc(chain table)");
+        AROL_CUDA(arol_malloc((void**)&b->dev_ds_ustart, (cap + 1) * sizeof(int)), "cudaMalloc(chain units)");
+        AROL_CUDA(cudaMallocHost((void**)&b->pinned_ds, cap * sizeof(DsMember)), "cudaMallocHost(chain table)");
+        AROL_CUDA(arol_malloc((void**)&b->ds_taps, cap * 48 * sizeof(float)), "cudaMalloc(chain taps)");
+        std::vector<float> h;
+        for (size_t i = 0; i < b->ds_ok.size(); ++i) {
+            if (!b->ds_ok[i]) continue;
+            const int f = b->first_of[i];
+            h.insert(h.end(), b->taps[f].begin(), b->taps[f].end());
+            h.insert(h.end(), b->taps[f + 1].begin(), b->taps[f + 1].end());
+        }
+        if (h.size() != cap * 48) return fail(AROL_ERR_INVALID, "batch: 8 -> 3 chain taps");
+        AROL_CUDA(cudaMemcpy(b->ds_taps, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice), "upload chain taps");
+    }
+    int e = 0;   // eligible members so far: their taps' slot
+    for (size_t i = 0; i < b->ds_on.size(); ++i) {
+        if (!b->ds_ok[i]) continue;
+        const int slot = e++;
+        if (!b->ds_on[i]) continue;
+        DsMember d = b->ds_geom[i];
+        d.taps = b->ds_taps + (size_t)48 * slot;
+        b->ds_members.push_back((int)i);
+        b->ds_mem.push_back(d);
+        b->ds_ws = std::max(b->ds_ws, d.Wc);
+        units += d.frames * (d.H / 8) * d.nch;
+        if (units >= 2147483647LL) return fail(AROL_ERR_UNSUPPORTED, "batch: too many chain units");
+        b->ds_ustart.push_back((int)units);
+    }
+    b->ds_units = (int)units;
+    if (!b->ds_members.empty()) {
+        AROL_CUDA(cudaMemcpy(b->dev_ds_ustart, b->ds_ustart.data(), b->ds_ustart.size() * sizeof(int),
+                             cudaMemcpyHostToDevice),
+                  "upload chain units");
+        log_line("batch %p: %zu 8 -> 3 chain members on the batched downscaler, %d units", (void*)b,
+                 b->ds_members.size(), b->ds_units);
+    }
+    return AROL_OK;
+}
+
 arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out, cudaStream_t s) {
     const size_t n = b->descs.size(), nm = b->first_of.size();
     int dev = 0;
@@ -2273,7 +2381,26 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
         if (!in[i] && b->host_tasks[f].nreps > 0) return fail(AROL_ERR_INVALID, "null input pointer for task %zu", i);
         if (!out[i] && b->host_tasks[l].nreps > 0) return fail(AROL_ERR_INVALID, "null output pointer for task %zu", i);
     }
+    // the batched 8 -> 3 kernel takes the eligible members whose input is
+    // 16-byte aligned now; another set than the tables were built for
+    // rebuilds them
+    {
+        bool same = true;
+        std::vector<char> on(nm, 0);
+        for (size_t i = 0; i < nm; ++i) {
+            on[i] = b->ds_ok[i] && aligned16(in[i]);
+            same = same && on[i] == b->ds_on[i];
+        }
+        if (!same) {
+            b->ds_on = on;
+            b->tables_built = false;
+        }
+    }
     if (!b->tables_built) {
+        b->skip = b->streamed;
+        for (size_t i = 0; i < nm; ++i)
+            if (b->ds_on[i])
+                for (int k = 0; k < b->len_of[i]; ++k) b->skip[b->first_of[i] + k] = 1;
         // each task's taps, then (row-FIR tasks) the same taps transposed and
         // zero padded to T x 16 for the row-tile path
         size_t ntaps = 0;
@@ -2329,7 +2456,7 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
         b->mid_off.assign(n, 0);
         for (size_t j = 0; j < n; ++j) {
             const int m = b->member_of[j];
-            if (b->stage_of[j] == b->len_of[m] - 1) continue;
+            if (b->stage_of[j] == b->len_of[m] - 1 || b->streamed[j]) continue;
             b->mid_off[j] = arena;
             const arol_array_desc& o = b->descs[j].out[0];
             arena += ((size_t)elems_of(o) * esize_of(o.dtype) + 255) / 256 * 256;
@@ -2338,6 +2465,8 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
         if (!b->cap_stream) AROL_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         arol_status st = build_tiles(b);
         if (st != AROL_OK) return st;
+        if ((st = batch_stream_plan(b)) != AROL_OK) return st;
+        if ((st = batch_ds_plan(b)) != AROL_OK) return st;
         b->tables_built = true;
         b->last_in.assign(nm, (const void*)1);   // force the first table upload
         b->last_out.assign(nm, (void*)1);
@@ -2366,6 +2495,32 @@ arol_status batch_prepare(arol_batch b, const void* const* in, void* const* out,
         AROL_CUDA(cudaStreamWaitEvent(s, b->launched, 0), "wait for previous launches");
         AROL_CUDA(cudaMemcpyAsync(b->dev_tasks, b->pinned_tasks, n * sizeof(TaskDev), cudaMemcpyHostToDevice, s),
                   "upload task table");
+        const size_t ns = b->ss_members.size();
+        if (ns) {
+            for (size_t k = 0; k < ns; ++k) {
+                const int m = b->ss_members[k], f = b->first_of[m];
+                SsChain c = b->ss_chains[k];
+                c.x = (const float*)in[m];
+                c.y = (float*)out[m];
+                c.hh = b->host_tasks[f].taps;
+                c.hv = b->host_tasks[f + 1].taps;
+                b->pinned_ss[k] = c;
+            }
+            AROL_CUDA(cudaMemcpyAsync(b->dev_ss, b->pinned_ss, ns * sizeof(SsChain), cudaMemcpyHostToDevice, s),
+                      "upload chain table");
+        }
+        const size_t nd = b->ds_members.size();
+        if (nd) {
+            for (size_t k = 0; k < nd; ++k) {
+                const int m = b->ds_members[k];
+                DsMember d = b->ds_mem[k];
+                d.x = (const float*)in[m];
+                d.y = (float*)out[m];
+                b->pinned_ds[k] = d;
+            }
+            AROL_CUDA(cudaMemcpyAsync(b->dev_ds, b->pinned_ds, nd * sizeof(DsMember), cudaMemcpyHostToDevice, s),
+                      "upload chain table");
+        }
         if (nr) {
             AROL_CUDA(cudaMemcpyAsync(b->dev_rtiles, b->pinned_rtiles, nr * sizeof(RowTileDev), cudaMemcpyHostToDevice, s),
                       "upload row tiles");
@@ -2385,6 +2540,12 @@ arol_status batch_capture(arol_batch b) {
     // one launch per chain stage; stage k reads what stage k - 1 wrote
     cudaError_t le = cudaSuccess;
     const int rgrid = b->row_ctas > 0 ? device_sm_count() * b->row_ctas : 0;
+    if (b->ss_units > 0)
+        le = launch_sepstream(SsChain{}, b->dev_ss, b->dev_ss_ustart, (int)b->ss_members.size(), b->ss_units, b->ss_th,
+                              b->ss_tv, b->ss_xw, b->ss_nst, b->ss_tapw, b->err, b->cap_stream);
+    if (b->ds_units > 0 && le == cudaSuccess)
+        le = launch_downscale_batch(b->dev_ds, b->dev_ds_ustart, (int)b->ds_members.size(), b->ds_units, b->ds_ws,
+                                    b->err, b->cap_stream);
     for (int k = 0; k < b->nstages && le == cudaSuccess; ++k) {
         if (b->rstage_cnt[k] > 0)
             le = launch_rowfir_batch(b->dev_rtiles + b->rstage_off[k], b->rstage_cnt[k], rgrid, b->err, b->cap_stream);
@@ -2441,6 +2602,52 @@ arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out) {
             if (d.elem == AROL_ELEM_FIR) b->max_m = std::max(b->max_m, d.fir_m);
         }
     }
+    // Members that are a row pass then a column pass run together on the
+    // streaming chain kernel when its common launch shape (widest window,
+    // most taps) fits shared memory; their tasks get no tiles and no
+    // intermediates.
+    b->streamed.assign(b->descs.size(), 0);
+    {
+        std::vector<int> mem;
+        int xw = 0, tapw = 0, th = -1, tv = -1;
+        for (int i = 0; i < n; ++i) {
+            const arol_task t = tasks[i];
+            if (t->kind != 1 || t->kernel != 5) continue;
+            mem.push_back(i);
+            xw = std::max(xw, t->ss_xw);
+            tapw = std::max(tapw, t->ss_tapw);
+            th = th == -1 || th == t->ss.Th ? t->ss.Th : 0;
+            tv = tv == -1 || tv == t->ss.Tv ? t->ss.Tv : 0;
+        }
+        const int nst = sepstream_stages(std::max(xw, 1));
+        if (!mem.empty() && sepstream_smem(xw, nst, tapw) <= kSsSmemMax) {
+            b->ss_members = mem;
+            b->ss_xw = xw;
+            b->ss_nst = nst;
+            b->ss_tapw = tapw;
+            b->ss_th = th;
+            b->ss_tv = tv;
+            for (int i : mem) {
+                b->ss_chains.push_back(tasks[i]->ss);
+                for (int k = 0; k < b->len_of[i]; ++k) b->streamed[b->first_of[i] + k] = 1;
+            }
+        }
+    }
+    b->ds_ok.assign(n, 0);
+    b->ds_on.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const arol_task t = tasks[i];
+        b->ds_ok[i] = t->kind == 1 && t->kernel == 1 && !t->ds_in16 && !t->ds_mid16 && !t->ds_out16;
+        DsMember d{};
+        if (b->ds_ok[i]) {
+            d.frames = t->ds_frames;
+            d.H = t->ds_H;
+            d.W = t->ds_W;
+            d.Wc = downscale_chunk(d.W);
+            d.nch = (d.W + d.Wc - 1) / d.Wc;
+        }
+        b->ds_geom.push_back(d);
+    }
     // The persistent kernel's column-FIR path serves output counts up to 16;
     // a batch with a larger m runs other tiles on the per-repetition walk,
     // which needs every task's full ports: frame-stripped column FIRs go back
@@ -2456,6 +2663,9 @@ arol_status arol_batch_create(const arol_task* tasks, int n, arol_batch* out) {
         }
         log_line("batch %p: %d members, %zu tasks in %d stage(s): %d row FIR, %d column FIR, %zu per-repetition",
                  (void*)b, n, b->host_tasks.size(), b->nstages, rows, cols, b->host_tasks.size() - rows - cols);
+        if (!b->ss_members.empty())
+            log_line("batch %p: %zu chain members on the streaming chain kernel (windows of %d words, %d stages)",
+                     (void*)b, b->ss_members.size(), b->ss_xw, b->ss_nst);
     }
     *out = b;
     return AROL_OK;
@@ -2482,6 +2692,26 @@ arol_status arol_batch_run_per_task(arol_batch b, const void* const* in, void* c
     // one launch of the batch kernel per task, over that task's tiles only
     const int cap = device_sm_count() * b->ctas_per_sm;
     const int rgrid = b->row_ctas > 0 ? device_sm_count() * b->row_ctas : 0;
+    // 8 -> 3 chain members: one launch of the fused downscaler each
+    for (size_t k = 0; k < b->ds_members.size(); ++k) {
+        const DsMember& d = b->pinned_ds[k];
+        DownscaleDev p{};
+        p.x = d.x;
+        p.y = d.y;
+        p.taps = d.taps;
+        p.err = b->err;
+        p.frames = d.frames;
+        p.H = d.H;
+        p.W = d.W;
+        AROL_CUDA(launch_downscale_fwd(p, s), "downscale kernel launch");
+    }
+    // streamed chain members: one launch of the streaming kernel each
+    for (size_t k = 0; k < b->ss_members.size(); ++k) {
+        const SsChain& c = b->pinned_ss[k];
+        AROL_CUDA(launch_sepstream(c, nullptr, nullptr, 1, b->ss_ustart[k + 1] - b->ss_ustart[k], c.Th, c.Tv, b->ss_xw,
+                                   b->ss_nst, b->ss_tapw, b->err, s),
+                  "fused chain kernel launch");
+    }
     for (size_t i = 0; i < b->host_tasks.size(); ++i) {
         if (b->rpt_cnt[i] > 0)
             AROL_CUDA(launch_rowfir_batch(b->dev_rtiles_pt + b->rpt_off[i], b->rpt_cnt[i], rgrid, b->err, s),
@@ -2649,6 +2879,13 @@ void arol_batch_destroy(arol_batch b) {
         free_dev(b->counter);
         free_dev(b->taps_dev);
         free_dev(b->arena);
+        free_dev(b->dev_ss);
+        free_dev(b->dev_ss_ustart);
+        if (b->pinned_ss) cudaFreeHost(b->pinned_ss);
+        free_dev(b->dev_ds);
+        free_dev(b->dev_ds_ustart);
+        free_dev(b->ds_taps);
+        if (b->pinned_ds) cudaFreeHost(b->pinned_ds);
         if (cur != b->device) cudaSetDevice(cur);
     }
     delete b;

@@ -134,6 +134,22 @@ struct DownscaleDev {
     int32_t H, W;
 };
 
+// One member of a batch of separable 8 -> 3 chains (k_downscale.cu): f32
+// frames (frames x H x W, 16-byte aligned), taps 3x8 horizontal then 3x8
+// vertical, column chunks of Wc (downscale_chunk), nch of them.
+struct DsMember {
+    const float* x;
+    float* y;
+    const float* taps;
+    int64_t frames;
+    int32_t H, W, Wc, nch;
+};
+int downscale_chunk(int W);
+// One launch over the units of nmem members (unit prefix ustart[0 .. nmem],
+// staged row stride Ws >= every member's Wc).
+cudaError_t launch_downscale_batch(const DsMember* mem, const int* ustart, int nmem, int units, int Ws, unsigned* err,
+                                   cudaStream_t s);
+
 // Launchers (return cudaGetLastError() of the launch).
 // Block tiling of the generic walk (tiler_tiled_kernel): a tile is R 2^lb
 // consecutive repetitions along dim db (lane l takes l, l + 2^lb, ...)
@@ -172,15 +188,38 @@ int downscale_bwd_partials(int sm_count, int W);   // per-CTA partial slots the 
 struct SepChainDev;
 cudaError_t launch_sepchain(const SepChainDev& d, cudaStream_t s);
 size_t sepchain_smem(const SepChainDev& d);
-// The streaming form of a row pass then a column pass (k_sepstream.cu):
-// d.BH is the band (column-pass repetitions per unit); xw_max the widest
-// input window of a column chunk; nst the stages (even).
-cudaError_t launch_sepstream(const SepChainDev& d, int units, int xw_max, int nst, unsigned* err, cudaStream_t s);
-size_t sepstream_smem(const SepChainDev& d, int xw_max, int nst);
+// One chain of the streaming row-then-column kernel (k_sepstream.cu): a row
+// pass (taps hh, m_h x T_h, step S_h, origin o_h) then a column pass (hv,
+// m_v x T_v, S_v, o_v) on F frames of H x W, intermediate and output W1
+// columns, H2 = m_v R_v output rows; units of one frame, one chunk of
+// sepstream_chunk_cols() intermediate columns and one band of BH column-pass
+// repetitions.
+struct SsChain {
+    const float* x;
+    float* y;
+    const float* hh;
+    const float* hv;
+    int64_t F;
+    int32_t H, W, W1, H2;
+    int32_t Th, mh, Sh, oh;   // oh in [0, W)
+    int32_t Tv, mv, Sv, ov;   // ov in [0, H)
+    int32_t Rv, BH;
+    int32_t chunks, bands;
+};
+SsChain ss_chain_of(const SepChainDev& d);           // BH, chunks and bands from d.BH; pointers left null
+int sepstream_window(const SsChain& c);               // widest input window of a chunk, words
+int sepstream_tap_floats(const SsChain& c);           // shared taps per consumer warp
+size_t sepstream_smem(int xw_max, int nst, int tap_floats);
 int sepstream_stages(int xw_max);
 int sepstream_chunk_cols();
-int sepstream_ctas_per_sm(const SepChainDev& d, size_t smem);
 int sepstream_max_taps();
+int sepstream_ctas_per_sm(int Th, int Tv, bool batch, size_t smem);
+// One launch over the units of one chain (chains = nullptr: `one`) or of
+// nchains chains in device memory (unit prefix ustart[0 .. nchains]).  Th,
+// Tv pick the exact-tap variant when every chain has those tap counts
+// (0: any).
+cudaError_t launch_sepstream(const SsChain& one, const SsChain* chains, const int* ustart, int nchains, int units,
+                             int Th, int Tv, int xw_max, int nst, int tap_floats, unsigned* err, cudaStream_t s);
 
 // tcgen05 matmul: C (M x N, f32) = A (M x K, bf16 row-major) . B (K x N, bf16 row-major).
 cudaError_t launch_matmul_tc(const void* A, const void* B, float* C, int M, int N, int K,

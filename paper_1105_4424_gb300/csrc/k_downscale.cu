@@ -683,6 +683,135 @@ cudaError_t launch_bulk(const DownscaleDev& p, int grid, cudaStream_t s) {
 // sizes (1.5 * columns) are multiples of 16 only when W is a multiple of 32.
 bool bulk_backward_ok(int W) { return W % 32 == 0; }
 
+// ---------------------------------------------------------------------------
+// Batches of 8 -> 3 chains (Sec. 5 chains inside one batch): the forward
+// bulk-copy ring over the units of every member in one launch.  Member c's
+// units (frame, stripe, chunk of Wc_c columns) follow member c - 1's; staged
+// rows keep the stride Ws of the widest chunk; each consumer warp reloads
+// the taps when its unit's member changes.  Inputs are 16-byte aligned (the
+// host routes other members elsewhere).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ds_find(const int* ustart, int n, int u, int c) {
+    while (c + 1 < n && __ldg(ustart + c + 1) <= u) ++c;
+    return c;
+}
+
+__global__ void __launch_bounds__(BulkCfg<0>::kThreads, BulkCfg<0>::kMinCtas)
+    downscale_batch_kernel(const DsMember* mem, const int* ustart, int nmem, int units, int Ws, unsigned* err) {
+    constexpr int kCWarps = BulkCfg<0>::kCWarps;
+    constexpr int kStages = BulkCfg<0>::kStages;
+    extern __shared__ __align__(128) float sm[];
+    const int sf = 8 * Ws;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kStages * sf);
+    const uint32_t full0 = ptx::smem_addr(bars), empty0 = ptx::smem_addr(bars + kStages);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            ptx::mbar_init(full0 + 8 * st, 1);
+            ptx::mbar_init(empty0 + 8 * st, kCWarps);
+        }
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == kCWarps) {
+        // ---------------- producer
+        if (lane == 0) {
+            int last[kStages];
+#pragma unroll
+            for (int st = 0; st < kStages; ++st) last[st] = -1;
+            uint32_t i = 0;
+            int c = 0;
+            for (int u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+                const int st = (int)(i % kStages);
+                if (i >= (uint32_t)kStages && !ptx::mbar_wait(empty0 + 8 * st, ((i / kStages) & 1u) ^ 1u)) {
+                    if (err) atomicOr(err, 1u);
+                    break;
+                }
+                c = ds_find(ustart, nmem, u, c);
+                const DsMember m = mem[c];
+                const uint32_t v = (uint32_t)(u - __ldg(ustart + c)), HB = (uint32_t)m.H >> 3;
+                const uint32_t ch = v % (uint32_t)m.nch, stripe = v / (uint32_t)m.nch;
+                const uint32_t f = stripe / HB, sy = stripe - f * HB;
+                const int c0 = (int)ch * m.Wc;
+                const int wc = min(m.Wc, m.W - c0);
+                const uint32_t xrow = (uint32_t)wc * 4u, fb = full0 + 8 * st;
+                ptx::mbar_expect_tx(fb, 8u * xrow);
+                float* dst = sm + st * sf;
+                const float* xs = m.x + ((int64_t)f * m.H + 8 * sy) * (int64_t)m.W + c0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) ptx::bulk_g2s(ptx::smem_addr(dst + r * Ws), xs + (int64_t)r * m.W, xrow, fb);
+                last[st] = (int)i;
+            }
+            // every issued copy lands before the CTA (and its shared memory) goes away
+#pragma unroll
+            for (int st = 0; st < kStages; ++st)
+                if (last[st] >= 0) ptx::mbar_wait(full0 + 8 * st, ((uint32_t)last[st] / kStages) & 1u);
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    const int half = lane & 1;
+    Taps tp;
+    uint32_t i = 0;
+    int c = 0, cur = -1;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+        const int st = (int)(i % kStages);
+        if (!ptx::mbar_wait(full0 + 8 * st, (i / kStages) & 1u)) {
+            if (err && lane == 0) atomicOr(err, 2u);
+            break;
+        }
+        c = ds_find(ustart, nmem, u, c);
+        const DsMember m = mem[c];
+        if (c != cur) {
+            load_taps(m.taps, half, tp);
+            cur = c;
+        }
+        DownscaleDev p{};
+        p.y = m.y;
+        p.H = m.H;
+        p.W = m.W;
+        const uint32_t v = (uint32_t)(u - __ldg(ustart + c)), HB = (uint32_t)m.H >> 3;
+        const uint32_t ch = v % (uint32_t)m.nch, stripe = v / (uint32_t)m.nch;
+        const uint32_t f = stripe / HB, sy = stripe - f * HB;
+        const int c0 = (int)ch * m.Wc;
+        const int nq = min(m.Wc, m.W - c0) >> 2;
+        const float* src = sm + st * sf;
+        for (int qb = warp * 32; qb < nq; qb += kCWarps * 32) {
+            const int q = qb + lane;
+            Item it;
+            it.valid = q < nq;
+            it.half = half;
+            it.f = f;
+            it.sy = sy;
+            it.c4 = (uint32_t)(c0 >> 2) + (uint32_t)q;
+            // lanes past the chunk's end read column 0; their results are discarded
+            const float* row0 = src + 4 * (it.valid ? q : 0);
+            float y[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int ii = 0; ii < 3; ++ii) y[j][ii] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float4 vk = *reinterpret_cast<const float4*>(row0 + k * Ws);
+                float mh[3];
+                horiz(tp, vk, mh);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int ii = 0; ii < 3; ++ii) y[j][ii] = fmaf(tp.hv[j][k], mh[ii], y[j][ii]);
+            }
+            store_block(p, it, y);
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(empty0 + 8 * st);
+    }
+}
+
+size_t ds_batch_smem(int Ws) { return (size_t)BulkCfg<0>::kStages * 8 * Ws * 4 + 2 * BulkCfg<0>::kStages * 8; }
+
 bool use_register_variant() {
     static int v = -1;
     if (v < 0) {
@@ -922,6 +1051,27 @@ cudaError_t launch_downscale_fwd(const DownscaleDev& p, cudaStream_t s) {
         return launch_bulk<0>(p, (int)(units < cap ? units : cap), s);
     }
     downscale_fwd_kernel<<<fwd_grid(items), kThr, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+int downscale_chunk(int W) { return bulk_chunk(W); }
+
+cudaError_t launch_downscale_batch(const DsMember* mem, const int* ustart, int nmem, int units, int Ws, unsigned* err,
+                                   cudaStream_t s) {
+    if (units <= 0) return cudaSuccess;
+    const size_t smem = ds_batch_smem(Ws);
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(downscale_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, downscale_batch_kernel, BulkCfg<0>::kThreads, smem);
+    const int cap = device_sm_count() * (occ > 0 ? occ : 1);
+    downscale_batch_kernel<<<units < cap ? units : cap, BulkCfg<0>::kThreads, smem, s>>>(mem, ustart, nmem, units, Ws,
+                                                                                         err);
     return cudaGetLastError();
 }
 

@@ -70,24 +70,21 @@ struct SsUnit {
     int row0, nrows;  // intermediate (= input) rows (row0 + i) mod H, i < nrows
 };
 
-__device__ __forceinline__ SsUnit ss_unit(const SepChainDev& d, int u) {
-    const SepPassDev &ph = d.p[0], &pv = d.p[1];
-    const int chunks = (d.W[1] + kSsChunk - 1) / kSsChunk;
-    const int bands = (pv.R + d.BH - 1) / d.BH;
+__host__ __device__ __forceinline__ SsUnit ss_unit(const SsChain& c, int u) {
     SsUnit s;
-    const int per_frame = chunks * bands;
+    const int per_frame = c.chunks * c.bands;
     s.f = (uint32_t)(u / per_frame);
-    const int v = u - (int)s.f * per_frame, band = v / chunks, chunk = v - band * chunks;
+    const int v = u - (int)s.f * per_frame, band = v / c.chunks, chunk = v - band * c.chunks;
     s.q0 = chunk * kSsChunk;
-    s.nq = min(kSsChunk, d.W[1] - s.q0);
-    s.ra = s.q0 / ph.m;
-    const int rb = (s.q0 + s.nq - 1) / ph.m;
-    s.xw = ph.S * (rb - s.ra) + ph.T;
-    s.c0 = (int)(((int64_t)ph.o + (int64_t)ph.S * s.ra) % ph.n_in);
-    s.rb0 = band * d.BH;
-    s.nrb = min(d.BH, pv.R - s.rb0);
-    s.nrows = pv.S * (s.nrb - 1) + pv.T;
-    s.row0 = (int)(((int64_t)pv.o + (int64_t)pv.S * s.rb0) % pv.n_in);
+    s.nq = c.W1 - s.q0 < kSsChunk ? c.W1 - s.q0 : kSsChunk;
+    s.ra = s.q0 / c.mh;
+    const int rb = (s.q0 + s.nq - 1) / c.mh;
+    s.xw = c.Sh * (rb - s.ra) + c.Th;
+    s.c0 = (int)(((int64_t)c.oh + (int64_t)c.Sh * s.ra) % c.W);
+    s.rb0 = band * c.BH;
+    s.nrb = c.Rv - s.rb0 < c.BH ? c.Rv - s.rb0 : c.BH;
+    s.nrows = c.Sv * (s.nrb - 1) + c.Tv;
+    s.row0 = (int)(((int64_t)c.ov + (int64_t)c.Sv * s.rb0) % c.H);
     return s;
 }
 
@@ -213,25 +210,26 @@ __device__ __forceinline__ void ss_column_pass(const float2* hv, int m, int T, c
     }
 }
 
-template <int TH, int TV>
-__global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel(const SepChainDev d, int units, int xw_max, int nst,
-                                                                 unsigned* err) {
+// The chain of unit u: the last chain whose first unit is <= u, searched
+// forward from the previous one (a CTA's units increase).
+__device__ __forceinline__ int ss_find(const int* ustart, int nchains, int u, int c) {
+    while (c + 1 < nchains && __ldg(ustart + c + 1) <= u) ++c;
+    return c;
+}
+
+template <int TH, int TV, bool BATCH>
+__global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS)
+    sepstream_kernel(const SsChain one, const SsChain* chains, const int* ustart, int nchains, int units, int xw_max,
+                     int nst, int tapw, unsigned* err) {
     extern __shared__ __align__(128) float ssm[];
     const int sr = (xw_max + 4 + 3) & ~3;                  // floats per staged row (window plus alignment slack)
     const int sf = kSsRows * sr;                           // floats per stage
     float* stages = ssm;
     float* rings = stages + nst * sf;                      // kSsCWarps x kSsRing x 32 x kSsCols
-    float* taps = rings + kSsCWarps * kSsRing * 32 * kSsCols;   // Hh then Hv, row-major
-    float2* hv2 = reinterpret_cast<float2*>(taps + ((d.ntaps + 3) & ~3));   // Hv, each tap doubled
-    uint64_t* bars = reinterpret_cast<uint64_t*>(hv2 + ((d.p[1].m * d.p[1].T + 1) & ~1));
+    float* wtaps = rings + kSsCWarps * kSsRing * 32 * kSsCols;   // per consumer warp: Hh, then Hv doubled
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wtaps + kSsCWarps * tapw);
     const uint32_t full0 = ptx::smem_addr(bars), empty0 = ptx::smem_addr(bars + nst);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const SepPassDev &ph = d.p[0], &pv = d.p[1];
-    for (int i = threadIdx.x; i < d.ntaps; i += blockDim.x) taps[i] = __ldg(d.taps + i);
-    for (int i = threadIdx.x; i < pv.m * pv.T; i += blockDim.x) {
-        const float h = __ldg(d.taps + pv.tap_off + i);
-        hv2[i] = make_float2(h, h);
-    }
     if (threadIdx.x == 0) {
         for (int st = 0; st < nst; ++st) {
             ptx::mbar_init(full0 + 8 * st, 1);
@@ -240,8 +238,6 @@ __global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel
         ptx::fence_barrier_init();
     }
     __syncthreads();
-    const int H = d.H[0], W = d.W[0];
-    const int64_t frame_in = (int64_t)H * W, frame_out = (int64_t)d.H[2] * d.W[2];
 
     if (warp >= kSsCWarps) {
         // producers: stages g = pw, pw + kSsPWarps, ... of this CTA's stage
@@ -251,9 +247,14 @@ __global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel
         int st = 0;
         uint32_t phase = 0;                                // parity of stage st's current use
         bool ok = true;
+        int c = 0;
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-            const SsUnit s = ss_unit(d, u);
-            const float* xf = d.x + (int64_t)s.f * frame_in;
+            if (BATCH) c = ss_find(ustart, nchains, u, c);
+            const SsChain ch = BATCH ? chains[c] : one;
+            const SsUnit s = ss_unit(ch, BATCH ? u - __ldg(ustart + c) : u);
+            const int H = ch.H, W = ch.W;
+            const int64_t frame_in = (int64_t)H * W;
+            const float* xf = ch.x + (int64_t)s.f * frame_in;
             for (int base = 0; base < s.nrows; base += kSsRows) {
                 const bool mine = (int)(g & 1u) == pw;
                 if (mine) {
@@ -299,34 +300,52 @@ __global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel
     // consumers: lane pair of columns q, q + 1
     const float2* ring = reinterpret_cast<const float2*>(rings) + warp * kSsRing * 32;
     float2* ringw = reinterpret_cast<float2*>(rings) + warp * kSsRing * 32;
-
-    const bool one = (ph.m & 1) == 0;                      // q even: q and q + 1 share a repetition
+    float* wt = wtaps + warp * tapw;                       // this warp's copy of its chain's taps
     int st = 0;
     uint32_t phase = 0;
+    int c = 0, cur = -1;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        const SsUnit s = ss_unit(d, u);
-        const int c = kSsCols * (32 * warp + lane);        // column of the pair within the chunk
-        const int q = s.q0 + c;
-        const bool act0 = c < s.nq, act1 = c + 1 < s.nq;
-        const int rh0 = act0 ? q / ph.m : s.ra, jh0 = act0 ? q - rh0 * ph.m : 0;
-        const int rh1 = act1 ? (q + 1) / ph.m : rh0, jh1 = act1 ? q + 1 - rh1 * ph.m : jh0;
-        const int xoff0 = ph.S * (rh0 - s.ra), xoff1 = ph.S * (rh1 - s.ra);
-        const float* h0 = taps + ph.tap_off + jh0 * ph.T;
-        const float* h1 = taps + ph.tap_off + jh1 * ph.T;
+        if (BATCH) c = ss_find(ustart, nchains, u, c);
+        const SsChain ch = BATCH ? chains[c] : one;
+        const SsUnit s = ss_unit(ch, BATCH ? u - __ldg(ustart + c) : u);
+        if (c != cur) {
+            // the chain's taps: Hh (m_h x T_h), then Hv with each tap doubled
+            __syncwarp();
+            const int nh = ch.mh * ch.Th, hoff = (nh + 1) & ~1, nv = ch.mv * ch.Tv;
+            for (int i = lane; i < nh; i += 32) wt[i] = __ldg(ch.hh + i);
+            for (int i = lane; i < nv; i += 32) {
+                const float h = __ldg(ch.hv + i);
+                reinterpret_cast<float2*>(wt + hoff)[i] = make_float2(h, h);
+            }
+            __syncwarp();
+            cur = c;
+        }
+        const float2* hv2 = reinterpret_cast<const float2*>(wt + ((ch.mh * ch.Th + 1) & ~1));
+        const int H = ch.H, W = ch.W;
+        const bool one2 = (ch.mh & 1) == 0;                // q even: q and q + 1 share a repetition
+        const int cc = kSsCols * (32 * warp + lane);       // column of the pair within the chunk
+        const int q = s.q0 + cc;
+        const bool act0 = cc < s.nq, act1 = cc + 1 < s.nq;
+        const int rh0 = act0 ? q / ch.mh : s.ra, jh0 = act0 ? q - rh0 * ch.mh : 0;
+        const int rh1 = act1 ? (q + 1) / ch.mh : rh0, jh1 = act1 ? q + 1 - rh1 * ch.mh : jh0;
+        const int xoff0 = ch.Sh * (rh0 - s.ra), xoff1 = ch.Sh * (rh1 - s.ra);
+        const float* h0 = wt + jh0 * ch.Th;
+        const float* h1 = wt + jh1 * ch.Th;
         float2 h2[TH > 0 ? TH : 1];
 #pragma unroll
         for (int k = 0; k < (TH > 0 ? TH : 1); ++k) h2[k] = TH > 0 ? make_float2(h0[k], h1[k]) : make_float2(0.f, 0.f);
         // the window's first word sits at the low two bits of its global word index
-        const uint32_t wbase = (uint32_t)(reinterpret_cast<uintptr_t>(d.x) >> 2) +
+        const int64_t frame_in = (int64_t)H * W;
+        const uint32_t wbase = (uint32_t)(reinterpret_cast<uintptr_t>(ch.x) >> 2) +
                                (uint32_t)(s.f * (uint64_t)frame_in) + (uint32_t)s.c0;
-        float* yf = d.y + (int64_t)s.f * frame_out + q;
+        float* yf = ch.y + (int64_t)s.f * ch.H2 * ch.W1 + q;
         // every row's window starts on a 16-byte boundary and each lane's
         // repetition at a multiple of 4 words: 16-byte loads, no conflicts
-        const bool v4 = TH > 0 && TH <= 8 && one && (ph.S & 3) == 0 && (wbase & 3u) == 0 && (W & 3) == 0;
+        const bool v4 = TH > 0 && TH <= 8 && one2 && (ch.Sh & 3) == 0 && (wbase & 3u) == 0 && (W & 3) == 0;
         int ir = s.row0;
-        int due = pv.T - 1;                                // next row that completes a column-pass window
-        int64_t yrow = (int64_t)pv.m * s.rb0 * d.W[2];     // offset of that repetition's first output row
-        const int64_t ystep = (int64_t)pv.m * d.W[2];
+        int due = ch.Tv - 1;                               // next row that completes a column-pass window
+        int64_t yrow = (int64_t)ch.mv * s.rb0 * ch.W1;     // offset of that repetition's first output row
+        const int64_t ystep = (int64_t)ch.mv * ch.W1;
         for (int base = 0; base < s.nrows; base += kSsRows) {
             if (!ptx::mbar_wait_sleep(full0 + 8 * st, phase, AROL_SS_SLEEP_NS)) {
                 if (lane == 0) flag(err, 2u);
@@ -346,7 +365,7 @@ __global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel
 #pragma unroll
                 for (int k = 0; k < kSsRows; ++k) {
                     const float* row = sp + k * sr + (int)((wbase + (uint32_t)irk * (uint32_t)W) & 3u);
-                    mid[k] = ss_dot2<TH>(h2, h0, h1, row + xoff0, row + xoff1, one, ph.T);
+                    mid[k] = ss_dot2<TH>(h2, h0, h1, row + xoff0, row + xoff1, one2, ch.Th);
                     if (++irk == H) irk = 0;
                 }
             }
@@ -368,13 +387,42 @@ __global__ void __launch_bounds__(kSsThreads, AROL_SS_MIN_CTAS) sepstream_kernel
             }
             // column pass of every repetition whose window ends in this stage:
             // rows S_v r .. S_v r + T_v - 1 of the band
-            for (; due < base + n; due += pv.S, yrow += ystep)
-                ss_column_pass<TV>(hv2, pv.m, pv.T, ring, due - (pv.T - 1), lane, yf + yrow, d.W[2], act0, act1);
+            for (; due < base + n; due += ch.Sv, yrow += ystep)
+                ss_column_pass<TV>(hv2, ch.mv, ch.Tv, ring, due - (ch.Tv - 1), lane, yf + yrow, ch.W1, act0, act1);
         }
     }
 }
 
 }  // namespace
+
+SsChain ss_chain_of(const SepChainDev& d) {
+    SsChain c{};
+    const SepPassDev &ph = d.p[0], &pv = d.p[1];
+    c.F = d.F;
+    c.H = d.H[0];
+    c.W = d.W[0];
+    c.W1 = d.W[1];
+    c.H2 = d.H[2];
+    c.Th = ph.T, c.mh = ph.m, c.Sh = ph.S, c.oh = ph.o;
+    c.Tv = pv.T, c.mv = pv.m, c.Sv = pv.S, c.ov = pv.o;
+    c.Rv = pv.R;
+    c.BH = d.BH > 0 ? d.BH : pv.R;
+    c.chunks = (c.W1 + kSsChunk - 1) / kSsChunk;
+    c.bands = (c.Rv + c.BH - 1) / c.BH;
+    return c;
+}
+
+int sepstream_window(const SsChain& c) {
+    int xw = 0;
+    for (int k = 0; k < c.chunks; ++k) {
+        const int64_t q0 = (int64_t)k * kSsChunk, nq = std::min<int64_t>(kSsChunk, c.W1 - q0);
+        const int64_t ra = q0 / c.mh, rb = (q0 + nq - 1) / c.mh;
+        xw = (int)std::max<int64_t>(xw, c.Sh * (rb - ra) + c.Th);
+    }
+    return xw;
+}
+
+int sepstream_tap_floats(const SsChain& c) { return (((c.mh * c.Th + 1) & ~1) + 2 * c.mv * c.Tv + 3) & ~3; }
 
 int sepstream_stages(int xw_max) {
     const size_t stage = (size_t)kSsRows * ((xw_max + 4 + 3) & ~3) * sizeof(float);
@@ -383,10 +431,9 @@ int sepstream_stages(int xw_max) {
     return (int)(n & ~(size_t)1);
 }
 
-size_t sepstream_smem(const SepChainDev& d, int xw_max, int nst) {
+size_t sepstream_smem(int xw_max, int nst, int tap_floats) {
     const int sr = (xw_max + 4 + 3) & ~3;
-    return ((size_t)nst * kSsRows * sr + (size_t)kSsCWarps * kSsRing * 32 * kSsCols + ((d.ntaps + 3) & ~3) +
-            2 * (size_t)((d.p[1].m * d.p[1].T + 1) & ~1)) *
+    return ((size_t)nst * kSsRows * sr + (size_t)kSsCWarps * kSsRing * 32 * kSsCols + (size_t)kSsCWarps * tap_floats) *
                sizeof(float) +
            2 * (size_t)nst * sizeof(uint64_t);
 }
@@ -394,36 +441,40 @@ size_t sepstream_smem(const SepChainDev& d, int xw_max, int nst) {
 int sepstream_chunk_cols() { return kSsChunk; }
 int sepstream_max_taps() { return kSsRing - kSsRows + 1; }
 
+namespace {
+
 // The kernel for the passes' tap counts: both exact when T_h = T_v <= 8,
-// the row pass exact when T_h <= 8, else the shared-memory forms.
-using SsKernel = void (*)(const SepChainDev, int, int, int, unsigned*);
+// the row pass exact when T_h <= 8 (one chain), else the general forms.
+using SsKernel = void (*)(const SsChain, const SsChain*, const int*, int, int, int, int, int, unsigned*);
 
 template <int T>
-SsKernel ss_pick(int Tv) {
-    return Tv == T ? sepstream_kernel<T, T> : sepstream_kernel<T, 0>;
+SsKernel ss_pick(int Tv, bool batch) {
+    if (batch) return Tv == T ? sepstream_kernel<T, T, true> : sepstream_kernel<0, 0, true>;
+    return Tv == T ? sepstream_kernel<T, T, false> : sepstream_kernel<T, 0, false>;
 }
 
-static SsKernel ss_kernel_for(int Th, int Tv) {
+SsKernel ss_kernel_for(int Th, int Tv, bool batch) {
     switch (Th) {
-        case 1: return ss_pick<1>(Tv);
-        case 2: return ss_pick<2>(Tv);
-        case 3: return ss_pick<3>(Tv);
-        case 4: return ss_pick<4>(Tv);
-        case 5: return ss_pick<5>(Tv);
-        case 6: return ss_pick<6>(Tv);
-        case 7: return ss_pick<7>(Tv);
-        case 8: return ss_pick<8>(Tv);
-        default: return sepstream_kernel<0, 0>;
+        case 1: return ss_pick<1>(Tv, batch);
+        case 2: return ss_pick<2>(Tv, batch);
+        case 3: return ss_pick<3>(Tv, batch);
+        case 4: return ss_pick<4>(Tv, batch);
+        case 5: return ss_pick<5>(Tv, batch);
+        case 6: return ss_pick<6>(Tv, batch);
+        case 7: return ss_pick<7>(Tv, batch);
+        case 8: return ss_pick<8>(Tv, batch);
+        default: return batch ? sepstream_kernel<0, 0, true> : sepstream_kernel<0, 0, false>;
     }
 }
 
 // cudaFuncSetAttribute once per kernel and size (the largest so far).
-static cudaError_t ss_set_smem(SsKernel k, size_t smem) {
-    static SsKernel seen[17] = {};
-    static size_t attr[17] = {};
+cudaError_t ss_set_smem(SsKernel k, size_t smem) {
+    constexpr int kMax = 32;
+    static SsKernel seen[kMax] = {};
+    static size_t attr[kMax] = {};
     int i = 0;
-    while (i < 17 && seen[i] && seen[i] != k) ++i;
-    if (i == 17) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    while (i < kMax && seen[i] && seen[i] != k) ++i;
+    if (i == kMax) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     seen[i] = k;
     if (smem > attr[i]) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -433,24 +484,28 @@ static cudaError_t ss_set_smem(SsKernel k, size_t smem) {
     return cudaSuccess;
 }
 
-int sepstream_ctas_per_sm(const SepChainDev& d, size_t smem) {
+}  // namespace
+
+int sepstream_ctas_per_sm(int Th, int Tv, bool batch, size_t smem) {
     int occ = 0;
-    const SsKernel k = ss_kernel_for(d.p[0].T, d.p[1].T);
+    const SsKernel k = ss_kernel_for(Th, Tv, batch);
     if (ss_set_smem(k, smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kSsThreads, smem) != cudaSuccess)
         return 1;
     return occ > 0 ? occ : 1;
 }
 
-cudaError_t launch_sepstream(const SepChainDev& d, int units, int xw_max, int nst, unsigned* err, cudaStream_t s) {
+cudaError_t launch_sepstream(const SsChain& one, const SsChain* chains, const int* ustart, int nchains, int units,
+                             int Th, int Tv, int xw_max, int nst, int tap_floats, unsigned* err, cudaStream_t s) {
     if (units <= 0) return cudaSuccess;
-    const size_t smem = sepstream_smem(d, xw_max, nst);
-    const SsKernel k = ss_kernel_for(d.p[0].T, d.p[1].T);
+    const bool batch = chains != nullptr;
+    const size_t smem = sepstream_smem(xw_max, nst, tap_floats);
+    const SsKernel k = ss_kernel_for(Th, Tv, batch);
     cudaError_t e = ss_set_smem(k, smem);
     if (e != cudaSuccess) return e;
-    const int cap = device_sm_count() * sepstream_ctas_per_sm(d, smem);
+    const int cap = device_sm_count() * sepstream_ctas_per_sm(Th, Tv, batch, smem);
     const int grid = units < cap ? units : cap;
-    k<<<grid, kSsThreads, smem, s>>>(d, units, xw_max, nst, err);
+    k<<<grid, kSsThreads, smem, s>>>(one, chains, ustart, nchains, units, xw_max, nst, tap_floats, err);
     return cudaGetLastError();
 }
 
