@@ -1423,7 +1423,7 @@ bool gen_geom(const TaskDev& t, GenGeom* out) {
     g.ntiles = (uint32_t)nt;
     g.na_div = make_fastdiv(g.na);
     g.nb_div = make_fastdiv(g.nb);
-    const int mx = tiler_tiled_maxm(t.elem == ELEM_FIR ? t.m : 1);
+    const int mx = (tiler_tiled_maxm(t.elem == ELEM_FIR ? t.m : 1) + 3) & ~3;   // taps staged in 16-byte rows
     g.tap_floats = t.elem == ELEM_FIR && (int64_t)t.T * mx <= 12288 ? t.T * mx : 0;
     *out = g;
     return true;

@@ -399,7 +399,7 @@ __device__ __forceinline__ void tiled_reps(const TaskDev& t, const GenGeom& g, c
     for (int k = 0; k < n; ++k) {
         float h[MAXM];
         if (ht) {
-            load_taps<MAXM>(ht + k * MAXM, h);
+            load_taps<MAXM>(ht + k * ((MAXM + 3) & ~3), h);
         } else {
 #pragma unroll
             for (int j = 0; j < MAXM; ++j) h[j] = j < m ? __ldg(t.taps + (int64_t)j * n + k) : 0.f;
@@ -442,13 +442,17 @@ __device__ __forceinline__ void tiled_reps(const TaskDev& t, const GenGeom& g, c
     }
 }
 
+// Blocks per SM the launch bound asks for: larger banks need more registers.
+constexpr int gen_min_blocks(int maxm) { return maxm <= 4 ? AROL_GEN_MINB : maxm <= 8 ? 2 : 1; }
+
 template <int MAXM, int R, bool F32>
-__global__ void __launch_bounds__(kThreads, AROL_GEN_MINB) tiler_tiled_kernel(const TaskDev t, const GenGeom g) {
+__global__ void __launch_bounds__(kThreads, gen_min_blocks(MAXM)) tiler_tiled_kernel(const TaskDev t, const GenGeom g) {
     extern __shared__ __align__(16) float ht[];
     if (g.tap_floats) {
         const int n = t.T, m = t.m;
         for (int i = threadIdx.x; i < g.tap_floats; i += blockDim.x) {
-            const int k = i / MAXM, j = i - k * MAXM;
+            constexpr int kHs = (MAXM + 3) & ~3;   // 16-byte rows of taps
+            const int k = i / kHs, j = i - k * kHs;
             ht[i] = j < m ? __ldg(t.taps + (int64_t)j * n + k) : 0.f;
         }
         __syncthreads();
@@ -1135,7 +1139,9 @@ cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int tiler_tiled_maxm(int max_m) { return max_m <= 4 ? 4 : max_m <= 8 ? 8 : max_m <= 16 ? 16 : 32; }
+int tiler_tiled_maxm(int max_m) {
+    return max_m <= 3 ? (max_m < 1 ? 1 : max_m) : max_m <= 4 ? 4 : max_m <= 8 ? 8 : max_m <= 16 ? 16 : 32;
+}
 int tiler_tiled_reps(int max_m) { return max_m <= 8 ? AROL_GEN_R : max_m <= 16 ? 2 : 1; }
 
 template <int MAXM, bool F32>
@@ -1168,6 +1174,9 @@ static cudaError_t launch_tiled_dt(const TaskDev& t, const GenGeom& g, cudaStrea
 cudaError_t launch_tiler_tiled(const TaskDev& t, const GenGeom& g, int max_m, cudaStream_t s) {
     if (t.nreps == 0 || g.ntiles == 0) return cudaSuccess;
     switch (tiler_tiled_maxm(max_m)) {
+        case 1: return launch_tiled_dt<1>(t, g, s);
+        case 2: return launch_tiled_dt<2>(t, g, s);
+        case 3: return launch_tiled_dt<3>(t, g, s);
         case 4: return launch_tiled_dt<4>(t, g, s);
         case 8: return launch_tiled_dt<8>(t, g, s);
         case 16: return launch_tiled_dt<16>(t, g, s);
