@@ -438,6 +438,24 @@ def bench_chain_5to2(A, torch, stream, flush, reps, hbm):
     out["staged_ms"] = statistics.median(time_each_flushed(run, reps, stream, flush))
     out["fused_speedup"] = out["staged_ms"] / ms
     out["roofline"] = {"bound": "hbm", "achieved": out["gbs"], "peak": hbm, "unit": "GB/s", "frac": out["frac_of_hbm"]}
+    # the chain's backward (recomputed intermediate, then the adjoint task by
+    # task) on 16 frames: loss sum(G * Y)
+    chain16, xs16 = W.config1_5to2(frames=16)
+    c = A.Chain(chain16)
+    x16 = torch.from_numpy(xs16[0]).cuda()
+    g16 = torch.from_numpy(W.rng(7).standard_normal(chain16[-1]["outputs"][0]["shape"]).astype(np.float32)).cuda()
+    gx = torch.empty_like(x16)
+    gt = torch.empty(20, device="cuda")
+    y16 = c.run([x16])
+    for _ in range(3):
+        c.backward(g16, [x16], gx, gt)
+    fwd16 = statistics.median(time_each_flushed(lambda: c.run([x16], y16), reps, stream, flush))
+    bwd16 = statistics.median(time_each_flushed(lambda: c.backward(g16, [x16], gx, gt), reps, stream, flush))
+    c.sync_status()
+    bbytes = 4 * (2 * x16.numel() + g16.numel())   # reads X and dY, writes dX
+    out["backward_16_frames"] = {"fwd_ms": fwd16, "bwd_ms": bwd16, "ratio": (fwd16 + bwd16) / fwd16,
+                                 "bwd_gbs": bbytes / (bwd16 * 1e-3) / 1e9,
+                                 "bwd_frac_of_hbm": bbytes / (bwd16 * 1e-3) / 1e9 / hbm}
     return out
 
 

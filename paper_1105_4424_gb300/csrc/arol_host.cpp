@@ -28,7 +28,7 @@ namespace arol {
 cudaError_t launch_tiler_bwd(const TaskDev& t, const int64_t* inv_start, const int32_t* inv_list,
                              float* gx, const float* gy, float* grad_taps, float* partials, int nblocks,
                              int64_t chunk, cudaStream_t s);
-int tiler_bwd_blocks(int64_t nreps, int64_t* chunk);
+int tiler_bwd_blocks(int64_t nreps, int m, int T, int64_t* chunk);
 }  // namespace arol
 
 namespace {
@@ -956,6 +956,8 @@ struct arol_task_s {
     std::vector<int32_t> sc_tab;
     int32_t* sc_tab_dev = nullptr;
     // streaming row-then-column chain (kernel 5)
+    SepChainDev sd{};     // the chain as separable passes (sd_ok), for the backward
+    bool sd_ok = false;
     SsChain ss{};
     int ss_units = 0, ss_xw = 0, ss_nst = 2, ss_tapw = 0;
     unsigned* err_flag = nullptr;        // device word: bounded waits that gave up
@@ -1267,6 +1269,7 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     // A row pass then a column pass runs on the streaming kernel when its
     // ring fits, unless AROL_SEPSTREAM is off.
     SepChainDev sd;
+    t->sd_ok = describe_sepchain(t->descs, &t->sd);
     const char* e = std::getenv("AROL_SEPSTREAM");
     const bool stream = !(e && (!std::strcmp(e, "off") || !std::strcmp(e, "0")));
     if (t->kernel == 3 && describe_sepchain(t->descs, &sd)) {
@@ -1774,7 +1777,7 @@ arol_status backward_generic_task(arol_task t, size_t i, const float* taps, cons
     td.taps = taps;
     td.x = x;
     int64_t chunk = 0;
-    const int nb = tiler_bwd_blocks(td.nreps, &chunk);
+    const int nb = tiler_bwd_blocks(td.nreps, td.m, td.T, &chunk);
     if (gtaps && d.elem == AROL_ELEM_FIR && (st = ensure_partials(t, (int64_t)nb * td.m * td.T, s)) != AROL_OK) return st;
     AROL_CUDA(launch_tiler_bwd(td, gx ? t->inv_start[i] : nullptr, gx ? t->inv_list[i] : nullptr, gx, gy,
                                d.elem == AROL_ELEM_FIR ? gtaps : nullptr, t->partials, nb, chunk, s),
@@ -1842,6 +1845,14 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
         if (reps_of(t->descs[ii]) == 0) {
             if (gx) AROL_CUDA(cudaMemsetAsync(gx, 0, array_bytes(t->descs[ii].in[0]), s), "zero gradient");
             if (gt) AROL_CUDA(cudaMemsetAsync(gt, 0, sizeof(float) * t->descs[ii].fir_m * t->descs[ii].fir_T, s), "zero gradient");
+        } else if (t->sd_ok) {
+            // separable passes: dX by the pass's transposed tiler as a
+            // gather (no inverse map), the tap gradients as for any task
+            const SepChainDev& c = t->sd;
+            if (gx)
+                AROL_CUDA(launch_sep_adjoint(c.p[ii], c.F, c.H[ii], c.W[ii], c.H[ii + 1], c.W[ii + 1], tp, g, gx, s),
+                          "chain backward launch");
+            if (gt && (st = backward_generic_task(t, ii, tp, xin, g, nullptr, gt, s)) != AROL_OK) return st;
         } else if ((st = backward_generic_task(t, ii, tp, xin, g, gx, gt, s)) != AROL_OK) {
             return st;
         }

@@ -186,7 +186,12 @@ int downscale_bwd_partials(int sm_count, int W);   // per-CTA partial slots the 
 
 // Fused chains of separable FIR passes (sepchain.h).
 struct SepChainDev;
+struct SepPassDev;
 cudaError_t launch_sepchain(const SepChainDev& d, cudaStream_t s);
+// dL/dIn of one pass of a separable chain (k_sepchain.cu): input F x Hin x
+// Win, output F x Hout x Wout, taps the pass's m x T block.
+cudaError_t launch_sep_adjoint(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const float* taps,
+                               const float* gy, float* gx, cudaStream_t s);
 size_t sepchain_smem(const SepChainDev& d);
 // One chain of the streaming row-then-column kernel (k_sepstream.cu): a row
 // pass (taps hh, m_h x T_h, step S_h, origin o_h) then a column pass (hv,

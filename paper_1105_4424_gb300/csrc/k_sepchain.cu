@@ -28,11 +28,6 @@ namespace {
 
 constexpr int kSepThreads = 256;
 
-__device__ __forceinline__ int wrap_pos(int v, int n) {
-    while (v >= n) v -= n;
-    return v;
-}
-
 // Row stride (floats) of a region of `cols` columns in shared memory: odd,
 // so lanes that walk down a column of the region hit distinct banks.
 __device__ __forceinline__ int ld_of(int cols) { return cols | 1; }
@@ -257,6 +252,73 @@ cudaError_t launch_sepchain_m(const SepChainDev& d, int64_t work, cudaStream_t s
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sepchain_kernel<kMaxM>, kSepThreads, smem);
     const int64_t cap = (int64_t)device_sm_count() * (occ > 0 ? occ : 1);
     sepchain_kernel<kMaxM><<<(int)(work < cap ? work : cap), kSepThreads, smem, s>>>(d);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of one pass of a separable chain with respect to its input (Sec. 5
+// chains, differentiated: the transposed tiler), as a gather: input position
+// c along the pass's axis receives, for every repetition r whose window
+// (o + S r + k) mod n_in, k < T, covers it, sum_j H[j, k] dY[m r + j].  With
+// u = (c - o) mod n_in, the windows that reach c start at S r <= u + q n_in
+// < S r + T for q = 0, 1, ... (windows that wrap once or more); no inverse
+// map is needed.  One thread per input element, the non-axis index fastest
+// for a column pass and the axis index for a row pass: coalesced loads and
+// stores either way.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Rows of the input (frame, row) go to blocks, columns to threads; the
+// windows that reach a position depend only on that position.
+__device__ __forceinline__ float sep_adjoint_sum(const SepPassDev& p, int pos, const float* __restrict__ h,
+                                                 const float* __restrict__ gy, int64_t o0, int64_t ostep) {
+    int u = pos - p.o;
+    if (u < 0) u += p.n_in;
+    float acc = 0.f;
+    // S R + T + n_in < 2^31 (host-checked), so v stays in 32 bits
+    for (int v = u;; v += p.n_in) {
+        const int lo = v - p.T + 1;
+        const int rlo = lo <= 0 ? 0 : (lo + p.S - 1) / p.S;
+        if (rlo >= p.R) break;
+        int rhi = v / p.S;
+        if (rhi >= p.R) rhi = p.R - 1;
+        for (int r = rlo; r <= rhi; ++r) {
+            const int k = v - p.S * r;
+            const float* g = gy + o0 + ((int64_t)p.m * r) * ostep;
+            for (int j = 0; j < p.m; ++j) acc = fmaf(__ldg(h + j * p.T + k), __ldg(g + (int64_t)j * ostep), acc);
+        }
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) sep_adjoint_kernel(const SepPassDev p, int64_t F, int Hin, int Win, int Hout,
+                                                          int Wout, const float* __restrict__ h,
+                                                          const float* __restrict__ gy, float* __restrict__ gx) {
+    const int64_t rows = F * Hin;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int64_t f = row / Hin;
+        const int i = (int)(row - f * Hin);
+        float* gxr = gx + row * Win;
+        if (p.axis == 1) {
+            // row pass: position c along the row; dY row (f, i), column m r + j
+            const int64_t o0 = (f * Hout + i) * (int64_t)Wout;
+            for (int c = threadIdx.x; c < Win; c += blockDim.x) gxr[c] = sep_adjoint_sum(p, c, h, gy, o0, 1);
+        } else {
+            // column pass: position i down the column; dY rows m r + j, column c
+            const int64_t o0 = f * Hout * (int64_t)Wout;
+            for (int c = threadIdx.x; c < Win; c += blockDim.x) gxr[c] = sep_adjoint_sum(p, i, h, gy, o0 + c, Wout);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sep_adjoint(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const float* taps,
+                               const float* gy, float* gx, cudaStream_t s) {
+    const int64_t n = F * Hin * (int64_t)Win;
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>(F * Hin, (int64_t)device_sm_count() * 16);
+    sep_adjoint_kernel<<<(int)blocks, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, taps, gy, gx);
     return cudaGetLastError();
 }
 

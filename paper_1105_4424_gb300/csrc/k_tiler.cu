@@ -999,6 +999,15 @@ __device__ __forceinline__ int64_t pattern_offset(const PortDev& p, const uint32
     return off;
 }
 
+// The same offset when the pattern cannot wrap (pattern_fits; `base` its
+// first element's offset): the linear walk, no modulo.
+__device__ __forceinline__ int64_t pattern_off(const PortDev& p, const uint32_t b[4], bool fits, int64_t base, int j) {
+    if (!fits) return pattern_offset(p, b, j);
+    const uint32_t i0 = (uint32_t)j / (uint32_t)p.pattern[1];
+    const uint32_t i1 = (uint32_t)j - i0 * (uint32_t)p.pattern[1];
+    return base + (int64_t)i0 * p.lin[0] + (int64_t)i1 * p.lin[1];
+}
+
 // dL/dX by owner computes: input element e sums, over the (r, k) pairs whose
 // gather visited it (inverse map, increasing order), sum_j H[j,k] g[e_out(r,j)]
 // (fir) or g[e_out(r,k)] (copy).  Each element is written once: no atomics.
@@ -1011,17 +1020,20 @@ __global__ void __launch_bounds__(kThreads) tiler_bwd_dx_kernel(const TaskDev t,
         float acc = 0.f;
         const int64_t a = start[e], z = start[e + 1];
         for (int64_t idx = a; idx < z; ++idx) {
-            const int64_t rk = list[idx];
-            const int64_t lr = rk / t.T;
-            const int k = (int)(rk - lr * t.T);
+            // r * T + k < 2^31 (the host checks): 32-bit division
+            const uint32_t rk = (uint32_t)list[idx];
+            const uint32_t lr = rk / (uint32_t)t.T;
+            const int k = (int)(rk - lr * (uint32_t)t.T);
             uint32_t r[4], b[4];
             decode_rep(t, lr, wide, r);
             base_index(t.out, r, wide, b);
+            const bool fo = pattern_fits(t.out, b);
+            const int64_t bo = fo ? offset_of(t.out, b) : 0;
             if (t.elem == ELEM_FIR) {
                 for (int j = 0; j < t.m; ++j)
-                    acc = fmaf(__ldg(t.taps + (int64_t)j * t.T + k), __ldg(gy + pattern_offset(t.out, b, j)), acc);
+                    acc = fmaf(__ldg(t.taps + (int64_t)j * t.T + k), __ldg(gy + pattern_off(t.out, b, fo, bo, j)), acc);
             } else {
-                acc += __ldg(gy + pattern_offset(t.out, b, k));
+                acc += __ldg(gy + pattern_off(t.out, b, fo, bo, k));
             }
         }
         gx[e] = acc;
@@ -1052,13 +1064,72 @@ __global__ void __launch_bounds__(kThreads) tiler_bwd_dh_kernel(const TaskDev t,
     }
 }
 
+// The same partials with every thread of the block at work: thread t takes
+// repetitions r0 + t, r0 + t + blockDim, ... and keeps all m x T pair sums
+// in registers (m <= MM, T <= TT), then the block adds them in a fixed order
+// (warp shuffles, then warps in order), so the result is the same every run.
+template <int MM, int TT>
+__global__ void __launch_bounds__(kThreads) tiler_bwd_dh_regs_kernel(const TaskDev t, const float* __restrict__ gy,
+                                                                     float* __restrict__ partials, int64_t chunk) {
+    const bool wide = t.wide != 0;
+    const float* x = static_cast<const float*>(t.x);
+    const int64_t r0 = (int64_t)blockIdx.x * chunk;
+    const int64_t r1 = r0 + chunk < t.nreps ? r0 + chunk : t.nreps;
+    const int m = t.m, T = t.T;
+    float acc[MM][TT];
+#pragma unroll
+    for (int j = 0; j < MM; ++j)
+#pragma unroll
+        for (int k = 0; k < TT; ++k) acc[j][k] = 0.f;
+    for (int64_t lr = r0 + threadIdx.x; lr < r1; lr += blockDim.x) {
+        uint32_t r[4], bi[4], bo[4];
+        decode_rep(t, lr, wide, r);
+        base_index(t.in, r, wide, bi);
+        base_index(t.out, r, wide, bo);
+        const bool fi = pattern_fits(t.in, bi), fo = pattern_fits(t.out, bo);
+        const int64_t oi = fi ? offset_of(t.in, bi) : 0, oo = fo ? offset_of(t.out, bo) : 0;
+        float xv[TT], gv[MM];
+#pragma unroll
+        for (int k = 0; k < TT; ++k) xv[k] = k < T ? __ldg(x + pattern_off(t.in, bi, fi, oi, k)) : 0.f;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) gv[j] = j < m ? __ldg(gy + pattern_off(t.out, bo, fo, oo, j)) : 0.f;
+#pragma unroll
+        for (int j = 0; j < MM; ++j)
+#pragma unroll
+            for (int k = 0; k < TT; ++k) acc[j][k] = fmaf(gv[j], xv[k], acc[j][k]);
+    }
+    __shared__ float red[kThreads / 32][MM * TT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < MM; ++j)
+#pragma unroll
+        for (int k = 0; k < TT; ++k) {
+            float v = acc[j][k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) red[warp][j * TT + k] = v;
+        }
+    __syncthreads();
+    const int npairs = m * T, nw = (int)(blockDim.x >> 5);
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        const int j = p / T, k = p - j * T;
+        float v = 0.f;
+        for (int w = 0; w < nw; ++w) v += red[w][j * TT + k];
+        partials[(int64_t)blockIdx.x * npairs + p] = v;
+    }
+}
+
+// One warp per tap pair: lane l adds the partials of blocks l, l + 32, ...
+// in order, then the lanes' sums meet in a fixed shuffle tree.
 __global__ void __launch_bounds__(kThreads) tiler_bwd_reduce_kernel(const float* __restrict__ partials, int nblocks,
                                                                     int npairs, float* __restrict__ out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (p >= npairs) return;
     float s = 0.f;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * npairs + p];
-    out[p] = s;
+    for (int b = lane; b < nblocks; b += 32) s += partials[(int64_t)b * npairs + p];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) out[p] = s;
 }
 
 int grid_for(int64_t work, int threads) {
@@ -1235,9 +1306,12 @@ cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, 
     return launch_batch_m<32>(tasks, tiles, ntiles, grid, threads, s);
 }
 
-int tiler_bwd_blocks(int64_t nreps, int64_t* chunk) {
-    int64_t nb = (nreps + 63) / 64;
-    const int64_t cap = (int64_t)device_sm_count() * 8;
+int tiler_bwd_blocks(int64_t nreps, int m, int T, int64_t* chunk) {
+    // the register kernel keeps every thread busy: two blocks per SM; the
+    // per-pair kernel runs one thread per pair, so it wants more blocks
+    const bool regs = (m <= 4 && T <= 16) || (m <= 8 && T <= 16);
+    int64_t nb = regs ? (nreps + 255) / 256 : (nreps + 63) / 64;
+    const int64_t cap = (int64_t)device_sm_count() * (regs ? 2 : 8);
     if (nb > cap) nb = cap;
     if (nb < 1) nb = 1;
     *chunk = (nreps + nb - 1) / nb;
@@ -1257,10 +1331,14 @@ cudaError_t launch_tiler_bwd(const TaskDev& t, const int64_t* inv_start, const i
     }
     if (grad_taps) {
         const int npairs = t.m * t.T;
-        tiler_bwd_dh_kernel<<<nblocks, kThreads, 0, s>>>(t, gy, partials, chunk);
+        if (t.m <= 4 && t.T <= 8) tiler_bwd_dh_regs_kernel<4, 8><<<nblocks, kThreads, 0, s>>>(t, gy, partials, chunk);
+        else if (t.m <= 4 && t.T <= 16) tiler_bwd_dh_regs_kernel<4, 16><<<nblocks, kThreads, 0, s>>>(t, gy, partials, chunk);
+        else if (t.m <= 8 && t.T <= 16) tiler_bwd_dh_regs_kernel<8, 16><<<nblocks, kThreads, 0, s>>>(t, gy, partials, chunk);
+        else tiler_bwd_dh_kernel<<<nblocks, kThreads, 0, s>>>(t, gy, partials, chunk);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        tiler_bwd_reduce_kernel<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, s>>>(partials, nblocks, npairs, grad_taps);
+        tiler_bwd_reduce_kernel<<<(npairs * 32 + kThreads - 1) / kThreads, kThreads, 0, s>>>(partials, nblocks, npairs,
+                                                                                             grad_taps);
         return cudaGetLastError();
     }
     return cudaSuccess;
