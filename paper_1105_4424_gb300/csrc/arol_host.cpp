@@ -1852,7 +1852,14 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
             if (gx)
                 AROL_CUDA(launch_sep_adjoint(c.p[ii], c.F, c.H[ii], c.W[ii], c.H[ii + 1], c.W[ii + 1], tp, g, gx, s),
                           "chain backward launch");
-            if (gt && (st = backward_generic_task(t, ii, tp, xin, g, nullptr, gt, s)) != AROL_OK) return st;
+            if (gt && sep_dh_supported(c.p[ii])) {
+                if ((st = ensure_partials(t, (int64_t)sep_dh_blocks() * c.p[ii].m * c.p[ii].T, s)) != AROL_OK) return st;
+                AROL_CUDA(launch_sep_dh(c.p[ii], c.F, c.H[ii], c.W[ii], c.H[ii + 1], c.W[ii + 1], (const float*)xin, g,
+                                        t->partials, gt, s),
+                          "chain backward launch");
+            } else if (gt && (st = backward_generic_task(t, ii, tp, xin, g, nullptr, gt, s)) != AROL_OK) {
+                return st;
+            }
         } else if ((st = backward_generic_task(t, ii, tp, xin, g, gx, gt, s)) != AROL_OK) {
             return st;
         }

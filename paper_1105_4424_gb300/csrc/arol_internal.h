@@ -192,6 +192,14 @@ cudaError_t launch_sepchain(const SepChainDev& d, cudaStream_t s);
 // Win, output F x Hout x Wout, taps the pass's m x T block.
 cudaError_t launch_sep_adjoint(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const float* taps,
                                const float* gy, float* gx, cudaStream_t s);
+// dL/dH of one pass (m <= 8, T <= 16; false otherwise, nothing launched):
+// per-block partials (sep_dh_blocks() x m T floats) reduced into grad_taps.
+int sep_dh_blocks();
+bool sep_dh_supported(const SepPassDev& p);
+cudaError_t launch_sep_dh(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const float* x,
+                          const float* gy, float* partials, float* grad_taps, cudaStream_t s);
+// Sum of nblocks rows of npairs partials, in a fixed order (k_tiler.cu).
+cudaError_t launch_tap_reduce(const float* partials, int nblocks, int npairs, float* out, cudaStream_t s);
 size_t sepchain_smem(const SepChainDev& d);
 // One chain of the streaming row-then-column kernel (k_sepstream.cu): a row
 // pass (taps hh, m_h x T_h, step S_h, origin o_h) then a column pass (hv,

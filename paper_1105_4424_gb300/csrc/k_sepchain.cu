@@ -268,19 +268,37 @@ cudaError_t launch_sepchain_m(const SepChainDev& d, int64_t work, cudaStream_t s
 // ---------------------------------------------------------------------------
 namespace {
 
+// Division by S of values below 2^31: multiply by ceil(2^(31 + l) / S),
+// l = ceil(log2 S), and shift (the multiply-shift division the host uses for
+// the tilers, set up once per thread here).
+struct SDiv {
+    uint64_t m;
+    uint32_t s;
+};
+__device__ __forceinline__ SDiv sdiv_of(uint32_t d) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    SDiv f;
+    f.s = 31 + l;
+    f.m = ((1ull << f.s) + d - 1) / d;
+    return f;
+}
+__device__ __forceinline__ int sdiv(int v, const SDiv& f) { return (int)(((uint64_t)(uint32_t)v * f.m) >> f.s); }
+
 // Rows of the input (frame, row) go to blocks, columns to threads; the
 // windows that reach a position depend only on that position.
-__device__ __forceinline__ float sep_adjoint_sum(const SepPassDev& p, int pos, const float* __restrict__ h,
-                                                 const float* __restrict__ gy, int64_t o0, int64_t ostep) {
+__device__ __forceinline__ float sep_adjoint_sum(const SepPassDev& p, const SDiv& ds, int pos,
+                                                 const float* __restrict__ h, const float* __restrict__ gy, int64_t o0,
+                                                 int64_t ostep) {
     int u = pos - p.o;
     if (u < 0) u += p.n_in;
     float acc = 0.f;
     // S R + T + n_in < 2^31 (host-checked), so v stays in 32 bits
     for (int v = u;; v += p.n_in) {
         const int lo = v - p.T + 1;
-        const int rlo = lo <= 0 ? 0 : (lo + p.S - 1) / p.S;
+        const int rlo = lo <= 0 ? 0 : sdiv(lo + p.S - 1, ds);
         if (rlo >= p.R) break;
-        int rhi = v / p.S;
+        int rhi = sdiv(v, ds);
         if (rhi >= p.R) rhi = p.R - 1;
         for (int r = rlo; r <= rhi; ++r) {
             const int k = v - p.S * r;
@@ -295,6 +313,7 @@ __global__ void __launch_bounds__(256) sep_adjoint_kernel(const SepPassDev p, in
                                                           int Wout, const float* __restrict__ h,
                                                           const float* __restrict__ gy, float* __restrict__ gx) {
     const int64_t rows = F * Hin;
+    const SDiv ds = sdiv_of((uint32_t)p.S);
     for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
         const int64_t f = row / Hin;
         const int i = (int)(row - f * Hin);
@@ -302,16 +321,110 @@ __global__ void __launch_bounds__(256) sep_adjoint_kernel(const SepPassDev p, in
         if (p.axis == 1) {
             // row pass: position c along the row; dY row (f, i), column m r + j
             const int64_t o0 = (f * Hout + i) * (int64_t)Wout;
-            for (int c = threadIdx.x; c < Win; c += blockDim.x) gxr[c] = sep_adjoint_sum(p, c, h, gy, o0, 1);
+            for (int c = threadIdx.x; c < Win; c += blockDim.x) gxr[c] = sep_adjoint_sum(p, ds, c, h, gy, o0, 1);
         } else {
             // column pass: position i down the column; dY rows m r + j, column c
             const int64_t o0 = f * Hout * (int64_t)Wout;
-            for (int c = threadIdx.x; c < Win; c += blockDim.x) gxr[c] = sep_adjoint_sum(p, i, h, gy, o0 + c, Wout);
+            for (int c = threadIdx.x; c < Win; c += blockDim.x) gxr[c] = sep_adjoint_sum(p, ds, i, h, gy, o0 + c, Wout);
         }
     }
 }
 
+// Tap gradients of one pass: dH[j, k] = sum over repetitions of
+// dY[m r + j] X[(o + S r + k) mod n_in] (the other indices passing through).
+// Row pass: blocks take input rows, threads the repetitions along them;
+// column pass: blocks take (frame, repetition) lines, threads the columns.
+// Every thread keeps all m x T sums in registers; the block adds them in a
+// fixed order (warp shuffles, then warps in order) into its partials.
+constexpr int kDhBlocksPerSm = 2;
+
+template <int MM, int TT>
+__global__ void __launch_bounds__(256) sep_dh_kernel(const SepPassDev p, int64_t F, int Hin, int Win, int Hout, int Wout,
+                                                     const float* __restrict__ x, const float* __restrict__ gy,
+                                                     float* __restrict__ partials) {
+    const int m = p.m, T = p.T;
+    float acc[MM][TT];
+#pragma unroll
+    for (int j = 0; j < MM; ++j)
+#pragma unroll
+        for (int k = 0; k < TT; ++k) acc[j][k] = 0.f;
+    const int64_t lines = p.axis == 1 ? F * Hin : F * p.R;
+    const int width = p.axis == 1 ? p.R : Win;
+    for (int64_t line = blockIdx.x; line < lines; line += gridDim.x) {
+        for (int q = threadIdx.x; q < width; q += blockDim.x) {
+            float xv[TT], gv[MM];
+            if (p.axis == 1) {
+                // row (f, i) = line, repetition r = q
+                const int64_t f = line / Hin, i = line - f * Hin;
+                const float* xr = x + line * Win;
+                const float* gr = gy + (f * Hout + i) * (int64_t)Wout + (int64_t)m * q;
+                int col = (int)(((int64_t)p.o + (int64_t)p.S * q) % p.n_in);
+#pragma unroll
+                for (int k = 0; k < TT; ++k) {
+                    xv[k] = k < T ? __ldg(xr + col) : 0.f;
+                    if (++col == p.n_in) col = 0;
+                }
+#pragma unroll
+                for (int j = 0; j < MM; ++j) gv[j] = j < m ? __ldg(gr + j) : 0.f;
+            } else {
+                // (f, r) = line, column c = q
+                const int64_t f = line / p.R;
+                const int r = (int)(line - f * p.R);
+                const float* xf = x + f * Hin * (int64_t)Win + q;
+                const float* gf = gy + (f * Hout + (int64_t)m * r) * (int64_t)Wout + q;
+                int row = (int)(((int64_t)p.o + (int64_t)p.S * r) % p.n_in);
+#pragma unroll
+                for (int k = 0; k < TT; ++k) {
+                    xv[k] = k < T ? __ldg(xf + (int64_t)row * Win) : 0.f;
+                    if (++row == p.n_in) row = 0;
+                }
+#pragma unroll
+                for (int j = 0; j < MM; ++j) gv[j] = j < m ? __ldg(gf + (int64_t)j * Wout) : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < MM; ++j)
+#pragma unroll
+                for (int k = 0; k < TT; ++k) acc[j][k] = fmaf(gv[j], xv[k], acc[j][k]);
+        }
+    }
+    __shared__ float red[8][MM * TT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < MM; ++j)
+#pragma unroll
+        for (int k = 0; k < TT; ++k) {
+            float v = acc[j][k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) red[warp][j * TT + k] = v;
+        }
+    __syncthreads();
+    const int npairs = m * T;
+    for (int pp = threadIdx.x; pp < npairs; pp += blockDim.x) {
+        const int j = pp / T, k = pp - j * T;
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w) v += red[w][j * TT + k];
+        partials[(int64_t)blockIdx.x * npairs + pp] = v;
+    }
+}
+
 }  // namespace
+
+int sep_dh_blocks() { return device_sm_count() * kDhBlocksPerSm; }
+
+bool sep_dh_supported(const SepPassDev& p) { return p.m <= 8 && p.T <= 16; }
+
+cudaError_t launch_sep_dh(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const float* x,
+                          const float* gy, float* partials, float* grad_taps, cudaStream_t s) {
+    const int nb = sep_dh_blocks();
+    if (p.m <= 4 && p.T <= 8) sep_dh_kernel<4, 8><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, gy, partials);
+    else if (p.m <= 4 && p.T <= 16) sep_dh_kernel<4, 16><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, gy, partials);
+    else if (p.m <= 8 && p.T <= 16) sep_dh_kernel<8, 16><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, gy, partials);
+    else return cudaErrorInvalidValue;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_tap_reduce(partials, nb, p.m * p.T, grad_taps, s);
+}
 
 cudaError_t launch_sep_adjoint(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const float* taps,
                                const float* gy, float* gx, cudaStream_t s) {

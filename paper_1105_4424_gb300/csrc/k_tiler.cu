@@ -1306,6 +1306,11 @@ cudaError_t launch_batch_persistent(const TaskDev* tasks, const TileDev* tiles, 
     return launch_batch_m<32>(tasks, tiles, ntiles, grid, threads, s);
 }
 
+cudaError_t launch_tap_reduce(const float* partials, int nblocks, int npairs, float* out, cudaStream_t s) {
+    tiler_bwd_reduce_kernel<<<(npairs * 32 + kThreads - 1) / kThreads, kThreads, 0, s>>>(partials, nblocks, npairs, out);
+    return cudaGetLastError();
+}
+
 int tiler_bwd_blocks(int64_t nreps, int m, int T, int64_t* chunk) {
     // the register kernel keeps every thread busy: two blocks per SM; the
     // per-pair kernel runs one thread per pair, so it wants more blocks
