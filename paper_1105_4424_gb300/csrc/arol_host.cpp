@@ -1817,6 +1817,26 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
         return AROL_OK;
     }
     if (t->kind == 0) {
+        // a row or column FIR pass: the separable adjoint and tap-gradient
+        // kernels (no inverse map); any other tiler: owner computes
+        SepPassDev pass;
+        int64_t F = 0, ihw[2], ohw[2];
+        if (match_sep_pass(t->descs[0], &pass, &F, ihw, ohw)) {
+            pass.tap_off = 0;
+            if (grad_in)
+                AROL_CUDA(launch_sep_adjoint(pass, F, (int)ihw[0], (int)ihw[1], (int)ohw[0], (int)ohw[1], taps,
+                                             (const float*)grad_out, (float*)grad_in, s),
+                          "backward launch");
+            if (grad_taps && sep_dh_supported(pass)) {
+                if ((st = ensure_partials(t, (int64_t)sep_dh_blocks() * pass.m * pass.T, s)) != AROL_OK) return st;
+                AROL_CUDA(launch_sep_dh(pass, F, (int)ihw[0], (int)ihw[1], (int)ohw[0], (int)ohw[1],
+                                        (const float*)saved_in[0], (const float*)grad_out, t->partials, grad_taps, s),
+                          "backward launch");
+            } else if (grad_taps) {
+                return backward_generic_task(t, 0, taps, saved_in[0], (const float*)grad_out, nullptr, grad_taps, s);
+            }
+            return AROL_OK;
+        }
         return backward_generic_task(t, 0, taps, saved_in[0], (const float*)grad_out, (float*)grad_in, grad_taps, s);
     }
     // Unfused chain: recompute the intermediates, then reverse task by task.

@@ -203,3 +203,19 @@ def test_misaligned_gradient_buffer_falls_back(arol):
     assert_fir_close(host(gx), host(gx2).astype(np.float64), sX, RTOL, "misaligned dL/dY")
     assert_fir_close(host(gt), host(gt2).astype(np.float64),
                      np.concatenate([sHh.reshape(-1), sHv.reshape(-1)]), RTOL, "misaligned dL/dY taps")
+
+
+@pytest.mark.parametrize("axis,T,m,S,reps_mul", [(1, 5, 2, 4, 1), (0, 7, 3, 2, 3), (1, 20, 10, 6, 2), (0, 1, 1, 1, 1)])
+def test_backward_separable_pass_tasks(arol, axis, T, m, S, reps_mul):
+    """Single row or column FIR passes (the separable adjoint and tap-gradient
+    kernels; m = 10 > 8 takes the owner-computes tap gradients), windows that
+    wrap once or several times (reps_mul times the covering repetitions),
+    against the C oracle's adjoint."""
+    g = W.rng(206 + T)
+    shape = (3, 37, 50)
+    n = shape[2] if axis == 1 else shape[1]
+    reps = reps_mul * -(-n // S)
+    tk = W.separable_pass(shape, axis, T, m, S, 3 % n, reps, (g.standard_normal((m, T)) / T).astype(np.float32))
+    x = g.standard_normal(shape).astype(np.float32)
+    G = g.standard_normal(tk["outputs"][0]["shape"])
+    check_chain_grads(arol, [tk], x, G)
