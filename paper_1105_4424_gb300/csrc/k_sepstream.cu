@@ -9,9 +9,14 @@
 // which are the row pass of the same input rows.  Producer warps copy those
 // input rows' windows (the row pass's input columns of the chunk, wrapped at
 // the row end), kSsRows rows per stage, into a ring of `nst` shared-memory
-// stages:
-// one cp.async.bulk per row for its 16-byte interior and 4-byte cp.async for
-// its ragged ends and wrapped words, all completing on the stage's mbarrier.
+// stages: one cp.async.bulk per row for its 16-byte interior and 4-byte
+// cp.async for its ragged ends and wrapped words, all completing on the
+// stage's mbarrier.
+//
+// One launch serves one chain or, in a batch, many: the units of chain c
+// follow those of chain c - 1 (a unit prefix in device memory), and each
+// consumer warp copies its unit's chain taps into its own shared area when
+// the chain changes.
 //
 // Consumer lane l of warp w owns intermediate columns q and q + 1, q = q0 +
 // 2 (32 w + l).  For every staged row it computes its two intermediate
@@ -39,17 +44,23 @@
 #ifndef AROL_SS_MIN_CTAS
 #define AROL_SS_MIN_CTAS 3
 #endif
+#ifndef AROL_SS_CWARPS
+#define AROL_SS_CWARPS 4
+#endif
+#ifndef AROL_SS_ROWS
+#define AROL_SS_ROWS 4
+#endif
 
 namespace arol {
 namespace {
 
-constexpr int kSsCWarps = 4;                       // consumer warps
+constexpr int kSsCWarps = AROL_SS_CWARPS;          // consumer warps
 constexpr int kSsCols = 2;                         // intermediate columns per consumer lane
 constexpr int kSsChunk = 32 * kSsCWarps * kSsCols; // intermediate columns per unit
 constexpr int kSsPWarps = 2;                       // producer warps (alternate stages)
 constexpr int kSsThreads = (kSsCWarps + kSsPWarps) * 32;
 constexpr int kSsMaxStages = AROL_SS_STAGES;       // stages (an even number, 2 .. this, set by the window)
-constexpr int kSsRows = 4;                         // input rows per stage
+constexpr int kSsRows = AROL_SS_ROWS;              // input rows per stage
 // intermediate rows kept per column: a window of T_v rows plus the
 // kSsRows - 1 rows of its stage stored after its last one
 constexpr int kSsRing = 32;
