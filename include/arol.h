@@ -62,8 +62,10 @@ typedef enum {
 /* Element storage (Sec. 5 typeAllocation).  FIR arithmetic is f32 for every
  * storage type: 16-bit inputs are widened exactly, 16-bit outputs (and a
  * 16-bit chain intermediate) are rounded to nearest even.  Copy tasks move
- * raw bits of any type; matmul inputs are bfloat16 only; backward passes take
- * float32 storage only. */
+ * raw bits of any type; matmul inputs are bfloat16 only; backward passes of
+ * fir tasks read saved inputs of any storage (widened exactly) and take and
+ * give gradients in float32; a chain's intermediates must be float32 there;
+ * copy tasks differentiate on float32 only. */
 typedef enum {
     AROL_F32 = 0,    /* IEEE binary32 */
     AROL_BF16 = 1,   /* bfloat16: the upper 16 bits of a binary32 */
@@ -214,9 +216,11 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
  * should be page-locked for full bandwidth. */
 arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* const* host_out, void* stream);
 
-/* Reverse mode of a fir task or chain for a loss L with dL/d(out) = grad_out.
- * saved_in: the forward inputs (device).  grad_in (nullable, device, input
- * shape) is OVERWRITTEN with dL/d(in): the transposed-tiler scatter-add, which
+/* Reverse mode of a fir task or chain for a loss L with dL/d(out) = grad_out
+ * (float32, output shape).  saved_in: the forward inputs (device, their own
+ * storage: 16-bit inputs are widened exactly).  grad_in (nullable, device,
+ * float32, input shape) is OVERWRITTEN with dL/d(in): the transposed-tiler
+ * scatter-add, which
  * sums over every (r, i) whose gather visited an element (overlaps and modulo
  * wrap included).  grad_taps (nullable, device, m x T floats, a chain's blocks
  * concatenated) is OVERWRITTEN with dL/dH.  Deterministic: no atomics. */

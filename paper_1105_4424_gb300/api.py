@@ -89,11 +89,13 @@ class Task:
         return out
 
     def backward(self, grad_out, saved_in, grad_in=None, grad_taps=None, stream=None):
-        _check_tensor(grad_out, self.out_port, "grad_out")
+        """Gradients are float32 whatever the arrays' storage: grad_out has
+        the output's shape, grad_in the input's; saved_in keeps its storage."""
+        _check_tensor(grad_out, dict(self.out_port, dtype="f32"), "grad_out")
         for t, p in zip(saved_in, self.in_ports):
             _check_tensor(t, p, "saved input")
         if grad_in is not None:
-            _check_tensor(grad_in, self.in_ports[0], "grad_in")
+            _check_tensor(grad_in, dict(self.in_ports[0], dtype="f32"), "grad_in")
         if isinstance(grad_taps, torch.Tensor) and grad_taps.dtype != torch.float32:
             raise TypeError("grad_taps must be float32")
         B.arol_task_backward(self.handle, grad_out, list(saved_in), grad_in, grad_taps, stream)
@@ -230,11 +232,11 @@ class TaskFunction(torch.autograd.Function):
         x, taps = ctx.saved_tensors
         task = ctx.task
         task.set_taps(taps)
-        gx = torch.empty_like(x) if ctx.needs_input_grad[1] else None
+        gx = torch.empty(x.shape, dtype=torch.float32, device=x.device) if ctx.needs_input_grad[1] else None
         gt = torch.empty_like(taps) if ctx.needs_input_grad[2] else None
         if gx is not None or gt is not None:
-            task.backward(grad_out.contiguous(), [x], gx, gt)
-        return None, gx, gt
+            task.backward(grad_out.float().contiguous(), [x], gx, gt)
+        return None, (gx.to(x.dtype) if gx is not None else None), gt
 
 
 def apply_task(task, x, taps):

@@ -715,10 +715,11 @@ bool match_pass(const arol_task_desc& d, int axis, Pass* ps) {
 // paving S, fitting 1, any origin, output paving m, fitting 1, origin 0; the
 // other axis and the frames identity.  Fills the pass (taps offset left 0)
 // and the frame count and input/output extents.
-bool match_sep_pass(const arol_task_desc& d, SepPassDev* p, int64_t* F, int64_t in_hw[2], int64_t out_hw[2]) {
+bool match_sep_pass(const arol_task_desc& d, SepPassDev* p, int64_t* F, int64_t in_hw[2], int64_t out_hw[2],
+                    bool any_storage = false) {
     if (d.elem != AROL_ELEM_FIR || d.n_in != 1) return false;
     const arol_array_desc &a = d.in[0], &o = d.out[0];
-    if (a.dtype != AROL_F32 || o.dtype != AROL_F32) return false;
+    if (!any_storage && (a.dtype != AROL_F32 || o.dtype != AROL_F32)) return false;
     const int r = a.rank;
     if ((r != 2 && r != 3) || o.rank != r || d.rep_rank != r) return false;
     const arol_tiler &ti = d.in_tiler[0], &to = d.out_tiler[0];
@@ -818,7 +819,7 @@ constexpr double kSepFillTiles = 4.0 * 152;  // four tiles per SM of a 152-SM GB
 
 // The passes and stage extents of a chain of 2 .. 4 row and column passes
 // (false for any other chain).
-bool describe_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out) {
+bool describe_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* out, bool any_storage = false) {
     const int K = (int)descs.size();
     if (K < 2 || K > kSepMaxPasses) return false;
     SepChainDev d;
@@ -827,7 +828,7 @@ bool describe_sepchain(const std::vector<arol_task_desc>& descs, SepChainDev* ou
     int64_t F0 = -1, ntaps = 0;
     for (int k = 0; k < K; ++k) {
         int64_t F, ihw[2], ohw[2];
-        if (!match_sep_pass(descs[k], &d.p[k], &F, ihw, ohw)) return false;
+        if (!match_sep_pass(descs[k], &d.p[k], &F, ihw, ohw, any_storage)) return false;
         if (k == 0) {
             F0 = F;
             d.H[0] = (int32_t)ihw[0];
@@ -1269,7 +1270,7 @@ arol_status arol_chain_create(const arol_task* tasks, int n, arol_task* out) {
     // A row pass then a column pass runs on the streaming kernel when its
     // ring fits, unless AROL_SEPSTREAM is off.
     SepChainDev sd;
-    t->sd_ok = describe_sepchain(t->descs, &t->sd);
+    t->sd_ok = describe_sepchain(t->descs, &t->sd, true);   // the backward reads any storage
     const char* e = std::getenv("AROL_SEPSTREAM");
     const bool stream = !(e && (!std::strcmp(e, "off") || !std::strcmp(e, "0")));
     if (t->kernel == 3 && describe_sepchain(t->descs, &sd)) {
@@ -1794,16 +1795,20 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
     AROL_TRACE();
     if (!t || !grad_out || !saved_in || !saved_in[0]) return fail(AROL_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
-    for (const arol_task_desc& d : t->descs) {
+    for (size_t i = 0; i < t->descs.size(); ++i) {
+        const arol_task_desc& d = t->descs[i];
         if (d.elem == AROL_ELEM_MATMUL) return fail(AROL_ERR_UNSUPPORTED, "backward of matmul tasks is not implemented");
-        if (d.in[0].dtype != AROL_F32 || d.out[0].dtype != AROL_F32)
-            return fail(AROL_ERR_UNSUPPORTED, "backward: float32 storage only");
+        if (d.elem == AROL_ELEM_COPY && (d.in[0].dtype != AROL_F32 || d.out[0].dtype != AROL_F32))
+            return fail(AROL_ERR_UNSUPPORTED, "backward: copy tasks on float32 only");
+        if (i + 1 < t->descs.size() && d.out[0].dtype != AROL_F32)
+            return fail(AROL_ERR_UNSUPPORTED, "backward: chain intermediates must be float32");
     }
     arol_status st = remember_device(t);
     if (st != AROL_OK) return st;
     const float* taps = nullptr;
     if ((st = ensure_taps(t, s, &taps)) != AROL_OK) return st;
-    if (t->kind == 1 && t->kernel == 1 && aligned16(saved_in[0]) && aligned16(grad_in) && aligned16(grad_out)) {
+    if (t->kind == 1 && t->kernel == 1 && !t->ds_in16 && !t->ds_mid16 && !t->ds_out16 && aligned16(saved_in[0]) &&
+        aligned16(grad_in) && aligned16(grad_out)) {
         const int nparts = downscale_bwd_partials(device_sm_count(), t->ds_W);
         if ((st = ensure_partials(t, (int64_t)nparts * 48, s)) != AROL_OK) return st;
         if ((st = ensure_err(t, s)) != AROL_OK) return st;
@@ -1821,7 +1826,7 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
         // kernels (no inverse map); any other tiler: owner computes
         SepPassDev pass;
         int64_t F = 0, ihw[2], ohw[2];
-        if (match_sep_pass(t->descs[0], &pass, &F, ihw, ohw)) {
+        if (match_sep_pass(t->descs[0], &pass, &F, ihw, ohw, true)) {
             pass.tap_off = 0;
             if (grad_in)
                 AROL_CUDA(launch_sep_adjoint(pass, F, (int)ihw[0], (int)ihw[1], (int)ohw[0], (int)ohw[1], taps,
@@ -1829,8 +1834,8 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
                           "backward launch");
             if (grad_taps && sep_dh_supported(pass)) {
                 if ((st = ensure_partials(t, (int64_t)sep_dh_blocks() * pass.m * pass.T, s)) != AROL_OK) return st;
-                AROL_CUDA(launch_sep_dh(pass, F, (int)ihw[0], (int)ihw[1], (int)ohw[0], (int)ohw[1],
-                                        (const float*)saved_in[0], (const float*)grad_out, t->partials, grad_taps, s),
+                AROL_CUDA(launch_sep_dh(pass, F, (int)ihw[0], (int)ihw[1], (int)ohw[0], (int)ohw[1], saved_in[0],
+                                        t->descs[0].in[0].dtype, (const float*)grad_out, t->partials, grad_taps, s),
                           "backward launch");
             } else if (grad_taps) {
                 return backward_generic_task(t, 0, taps, saved_in[0], (const float*)grad_out, nullptr, grad_taps, s);
@@ -1863,7 +1868,7 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
         const float* tp = taps ? taps + t->tap_off[ii] : nullptr;
         float* gt = grad_taps ? grad_taps + t->tap_off[ii] : nullptr;
         if (reps_of(t->descs[ii]) == 0) {
-            if (gx) AROL_CUDA(cudaMemsetAsync(gx, 0, array_bytes(t->descs[ii].in[0]), s), "zero gradient");
+            if (gx) AROL_CUDA(cudaMemsetAsync(gx, 0, (size_t)elems_of(t->descs[ii].in[0]) * sizeof(float), s), "zero gradient");
             if (gt) AROL_CUDA(cudaMemsetAsync(gt, 0, sizeof(float) * t->descs[ii].fir_m * t->descs[ii].fir_T, s), "zero gradient");
         } else if (t->sd_ok) {
             // separable passes: dX by the pass's transposed tiler as a
@@ -1874,8 +1879,8 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
                           "chain backward launch");
             if (gt && sep_dh_supported(c.p[ii])) {
                 if ((st = ensure_partials(t, (int64_t)sep_dh_blocks() * c.p[ii].m * c.p[ii].T, s)) != AROL_OK) return st;
-                AROL_CUDA(launch_sep_dh(c.p[ii], c.F, c.H[ii], c.W[ii], c.H[ii + 1], c.W[ii + 1], (const float*)xin, g,
-                                        t->partials, gt, s),
+                AROL_CUDA(launch_sep_dh(c.p[ii], c.F, c.H[ii], c.W[ii], c.H[ii + 1], c.W[ii + 1], xin,
+                                        t->descs[ii].in[0].dtype, g, t->partials, gt, s),
                           "chain backward launch");
             } else if (gt && (st = backward_generic_task(t, ii, tp, xin, g, nullptr, gt, s)) != AROL_OK) {
                 return st;

@@ -196,8 +196,8 @@ cudaError_t launch_sep_adjoint(const SepPassDev& p, int64_t F, int Hin, int Win,
 // per-block partials (sep_dh_blocks() x m T floats) reduced into grad_taps.
 int sep_dh_blocks();
 bool sep_dh_supported(const SepPassDev& p);
-cudaError_t launch_sep_dh(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const float* x,
-                          const float* gy, float* partials, float* grad_taps, cudaStream_t s);
+cudaError_t launch_sep_dh(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const void* x, int x_dt,
+                          const float* gy, float* partials, float* grad_taps, cudaStream_t s);   // x_dt: arol_dtype
 // Sum of nblocks rows of npairs partials, in a fixed order (k_tiler.cu).
 cudaError_t launch_tap_reduce(const float* partials, int nblocks, int npairs, float* out, cudaStream_t s);
 size_t sepchain_smem(const SepChainDev& d);

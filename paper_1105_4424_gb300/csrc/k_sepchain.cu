@@ -19,6 +19,8 @@
 // passes store consecutive columns from consecutive lanes.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "arol_internal.h"
 #include "ptx.h"
 #include "sepchain.h"
@@ -338,9 +340,16 @@ __global__ void __launch_bounds__(256) sep_adjoint_kernel(const SepPassDev p, in
 // fixed order (warp shuffles, then warps in order) into its partials.
 constexpr int kDhBlocksPerSm = 2;
 
+// An input element in its storage (0 f32, 1 bfloat16, 2 IEEE half), widened.
+__device__ __forceinline__ float ld_x(const void* x, int64_t i, int dt) {
+    if (dt == 1) return __uint_as_float((uint32_t)__ldg(static_cast<const unsigned short*>(x) + i) << 16);
+    if (dt == 2) return __half2float(__ushort_as_half(__ldg(static_cast<const unsigned short*>(x) + i)));
+    return __ldg(static_cast<const float*>(x) + i);
+}
+
 template <int MM, int TT>
 __global__ void __launch_bounds__(256) sep_dh_kernel(const SepPassDev p, int64_t F, int Hin, int Win, int Hout, int Wout,
-                                                     const float* __restrict__ x, const float* __restrict__ gy,
+                                                     const void* __restrict__ x, int x_dt, const float* __restrict__ gy,
                                                      float* __restrict__ partials) {
     const int m = p.m, T = p.T;
     float acc[MM][TT];
@@ -356,12 +365,12 @@ __global__ void __launch_bounds__(256) sep_dh_kernel(const SepPassDev p, int64_t
             if (p.axis == 1) {
                 // row (f, i) = line, repetition r = q
                 const int64_t f = line / Hin, i = line - f * Hin;
-                const float* xr = x + line * Win;
+                const int64_t xr = line * Win;
                 const float* gr = gy + (f * Hout + i) * (int64_t)Wout + (int64_t)m * q;
                 int col = (int)(((int64_t)p.o + (int64_t)p.S * q) % p.n_in);
 #pragma unroll
                 for (int k = 0; k < TT; ++k) {
-                    xv[k] = k < T ? __ldg(xr + col) : 0.f;
+                    xv[k] = k < T ? ld_x(x, xr + col, x_dt) : 0.f;
                     if (++col == p.n_in) col = 0;
                 }
 #pragma unroll
@@ -370,12 +379,12 @@ __global__ void __launch_bounds__(256) sep_dh_kernel(const SepPassDev p, int64_t
                 // (f, r) = line, column c = q
                 const int64_t f = line / p.R;
                 const int r = (int)(line - f * p.R);
-                const float* xf = x + f * Hin * (int64_t)Win + q;
+                const int64_t xf = f * Hin * (int64_t)Win + q;
                 const float* gf = gy + (f * Hout + (int64_t)m * r) * (int64_t)Wout + q;
                 int row = (int)(((int64_t)p.o + (int64_t)p.S * r) % p.n_in);
 #pragma unroll
                 for (int k = 0; k < TT; ++k) {
-                    xv[k] = k < T ? __ldg(xf + (int64_t)row * Win) : 0.f;
+                    xv[k] = k < T ? ld_x(x, xf + (int64_t)row * Win, x_dt) : 0.f;
                     if (++row == p.n_in) row = 0;
                 }
 #pragma unroll
@@ -414,12 +423,15 @@ int sep_dh_blocks() { return device_sm_count() * kDhBlocksPerSm; }
 
 bool sep_dh_supported(const SepPassDev& p) { return p.m <= 8 && p.T <= 16; }
 
-cudaError_t launch_sep_dh(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const float* x,
+cudaError_t launch_sep_dh(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const void* x, int x_dt,
                           const float* gy, float* partials, float* grad_taps, cudaStream_t s) {
     const int nb = sep_dh_blocks();
-    if (p.m <= 4 && p.T <= 8) sep_dh_kernel<4, 8><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, gy, partials);
-    else if (p.m <= 4 && p.T <= 16) sep_dh_kernel<4, 16><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, gy, partials);
-    else if (p.m <= 8 && p.T <= 16) sep_dh_kernel<8, 16><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, gy, partials);
+    if (p.m <= 4 && p.T <= 8)
+        sep_dh_kernel<4, 8><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, x_dt, gy, partials);
+    else if (p.m <= 4 && p.T <= 16)
+        sep_dh_kernel<4, 16><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, x_dt, gy, partials);
+    else if (p.m <= 8 && p.T <= 16)
+        sep_dh_kernel<8, 16><<<nb, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, x, x_dt, gy, partials);
     else return cudaErrorInvalidValue;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -1058,7 +1058,7 @@ __global__ void __launch_bounds__(kThreads) tiler_bwd_dh_kernel(const TaskDev t,
             decode_rep(t, lr, wide, r);
             base_index(t.in, r, wide, bi);
             base_index(t.out, r, wide, bo);
-            acc = fmaf(__ldg(gy + pattern_offset(t.out, bo, j)), __ldg(x + pattern_offset(t.in, bi, k)), acc);
+            acc = fmaf(__ldg(gy + pattern_offset(t.out, bo, j)), load_value(t, pattern_offset(t.in, bi, k)), acc);
         }
         partials[(int64_t)blockIdx.x * npairs + p] = acc;
     }
@@ -1090,7 +1090,7 @@ __global__ void __launch_bounds__(kThreads) tiler_bwd_dh_regs_kernel(const TaskD
         const int64_t oi = fi ? offset_of(t.in, bi) : 0, oo = fo ? offset_of(t.out, bo) : 0;
         float xv[TT], gv[MM];
 #pragma unroll
-        for (int k = 0; k < TT; ++k) xv[k] = k < T ? __ldg(x + pattern_off(t.in, bi, fi, oi, k)) : 0.f;
+        for (int k = 0; k < TT; ++k) xv[k] = k < T ? load_value(t, pattern_off(t.in, bi, fi, oi, k)) : 0.f;
 #pragma unroll
         for (int j = 0; j < MM; ++j) gv[j] = j < m ? __ldg(gy + pattern_off(t.out, bo, fo, oo, j)) : 0.f;
 #pragma unroll

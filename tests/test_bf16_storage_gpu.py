@@ -14,7 +14,7 @@ import torch
 import workloads as W
 from oracle import cpu_ref as C
 from oracle import tiler as O
-from tests.gpu_helpers import FIR_RTOL, dev, fir_scale, host
+from tests.gpu_helpers import FIR_RTOL, assert_fir_close, dev, fir_scale, host
 
 pytestmark = pytest.mark.gpu
 
@@ -76,10 +76,33 @@ def test_bf16_chain_full_size(arol):
     check(y, C.run_chain(chain, [xv])[0], fir_scale(chain, xv, C.run_chain), False, True, "bf16 chain 64x1080x1920")
 
 
-def test_bf16_backward_is_rejected(arol):
-    chain, (x,) = W.config1_bf16(seed=20, frames=1, height=8, width=64)
+def test_bf16_backward_against_oracle(arol):
+    """bfloat16 frames with a float32 intermediate: the backward reads X in
+    its storage (widened exactly) and gives float32 dX and tap gradients,
+    against the oracle's adjoint on the widened values."""
+    chain, (x,) = W.config1_bf16(seed=20, frames=2, height=24, width=96, mid="f32", out="bf16")
+    c = arol.Chain(chain)
+    xv = to_f64(x)
+    f32_chain = [dict(t, inputs=[dict(t["inputs"][0], dtype="f32")], outputs=[dict(t["outputs"][0], dtype="f32")])
+                 for t in chain]
+    G = W.rng(122).standard_normal(chain[-1]["outputs"][0]["shape"]).astype(np.float32)
+    gx = torch.empty(x.shape, device="cuda")
+    gt = torch.empty(48, device="cuda")
+    c.backward(dev(G), [dev(x)], gx, gt)
+    c.sync_status()
+    g64 = G.astype(np.float64)
+    dX, (dHh, dHv) = C.chain_vjp(f32_chain, [xv], g64)
+    absc = [dict(t, taps=np.abs(np.asarray(t["taps"], np.float64))) for t in f32_chain]
+    sX, (sHh, sHv) = C.chain_vjp(absc, [np.abs(xv)], np.abs(g64))
+    assert_fir_close(host(gx), dX, sX, 1e-5, "bf16 dX")
+    got = host(gt)
+    assert_fir_close(got[:24].reshape(3, 8), dHh, sHh, 1e-5, "bf16 dHh")
+    assert_fir_close(got[24:].reshape(3, 8), dHv, sHv, 1e-5, "bf16 dHv")
+
+
+def test_bf16_intermediate_backward_is_rejected(arol):
+    chain, (x,) = W.config1_bf16(seed=21, frames=1, height=8, width=64, mid="bf16", out="f32")
     c = arol.Chain(chain)
     with pytest.raises(arol.ArolError) as e:
-        c.backward(torch.zeros(1, 3, 24, device="cuda", dtype=torch.bfloat16), [dev(x)],
-                   torch.empty(1, 8, 64, device="cuda", dtype=torch.bfloat16), None)
+        c.backward(torch.zeros(1, 3, 24, device="cuda"), [dev(x)], torch.empty(1, 8, 64, device="cuda"), None)
     assert e.value.status == 3

@@ -17,7 +17,7 @@ import torch
 import workloads as W
 from oracle import cpu_ref as C
 from oracle import tiler as O
-from tests.gpu_helpers import FIR_RTOL, dev, fir_scale, host
+from tests.gpu_helpers import FIR_RTOL, assert_fir_close, dev, fir_scale, host
 
 pytestmark = pytest.mark.gpu
 
@@ -137,10 +137,25 @@ def test_batch_with_f16_member(arol):
     check(host(outs[-1]), O.run_task(tv, [xv])[0], fir_scale(tv, xv), True, "f16 member of a batch")
 
 
-def test_f16_backward_is_rejected(arol):
-    chain, (x,) = W.config1_f16(seed=31, frames=1, height=8, width=64)
+def test_f16_backward_against_oracle(arol):
+    """IEEE half frames and output with a float32 intermediate: dX and the
+    tap gradients in float32 against the oracle's adjoint on the widened
+    values (the backward reads X in its storage)."""
+    chain, (x,) = W.config1_f16(seed=31, frames=2, height=16, width=128, mid="f32", out="f16")
     c = arol.Chain(chain)
-    with pytest.raises(arol.ArolError) as e:
-        c.backward(torch.zeros(1, 3, 24, device="cuda", dtype=torch.float16), [dev(x)],
-                   torch.empty(1, 8, 64, device="cuda", dtype=torch.float16), None)
-    assert e.value.status == 3
+    xv = x.astype(np.float64)
+    f32_chain = [dict(t, inputs=[dict(t["inputs"][0], dtype="f32")], outputs=[dict(t["outputs"][0], dtype="f32")])
+                 for t in chain]
+    G = W.rng(131).standard_normal(chain[-1]["outputs"][0]["shape"]).astype(np.float32)
+    gx = torch.empty(x.shape, device="cuda")
+    gt = torch.empty(48, device="cuda")
+    c.backward(dev(G), [dev(x)], gx, gt)
+    c.sync_status()
+    g64 = G.astype(np.float64)
+    dX, (dHh, dHv) = C.chain_vjp(f32_chain, [xv], g64)
+    absc = [dict(t, taps=np.abs(np.asarray(t["taps"], np.float64))) for t in f32_chain]
+    sX, (sHh, sHv) = C.chain_vjp(absc, [np.abs(xv)], np.abs(g64))
+    assert_fir_close(host(gx), dX, sX, 1e-5, "f16 dX")
+    got = host(gt)
+    assert_fir_close(got[:24].reshape(3, 8), dHh, sHh, 1e-5, "f16 dHh")
+    assert_fir_close(got[24:].reshape(3, 8), dHv, sHv, 1e-5, "f16 dHv")
