@@ -417,6 +417,73 @@ __global__ void __launch_bounds__(256) sep_dh_kernel(const SepPassDev p, int64_t
     }
 }
 
+// The adjoint when the repetitions tile the axis exactly (S R = n_in):
+// input position (o + S r + d) mod n_in, d < S, is the "home" of repetition
+// r, and the windows that reach it are those of repetitions (r - q) mod R
+// with tap index d + S q < T.  One thread per (line, r) keeps the Q x m
+// gradients dY[m ((r - q) mod R) + j] in registers (Q = ceil(T / S) <= QQ,
+// m <= MM) and writes its S home elements: no division per element.
+template <int QQ, int MM>
+__global__ void __launch_bounds__(256) sep_adjoint_poly_kernel(const SepPassDev p, int64_t F, int Hin, int Win,
+                                                               int Hout, int Wout, const float* __restrict__ taps,
+                                                               const float* __restrict__ gy, float* __restrict__ gx) {
+    __shared__ float h[32 * 16];
+    const int m = p.m, T = p.T, S = p.S, R = p.R;
+    for (int i = threadIdx.x; i < m * T; i += blockDim.x) h[i] = __ldg(taps + i);
+    __syncthreads();
+    const int Q = (T + S - 1) / S;
+    const int64_t lines = p.axis == 1 ? F * Hin : F * R;
+    const int width = p.axis == 1 ? R : Win;
+    for (int64_t line = blockIdx.x; line < lines; line += gridDim.x) {
+        for (int q0 = threadIdx.x; q0 < width; q0 += blockDim.x) {
+            int r;
+            const float* gb;       // dY of repetition 0 for this thread's line or column
+            int64_t gs;            // dY step between outputs j (and, times m, between repetitions)
+            float* xb;             // dX of position 0
+            int64_t xs;            // dX step between positions
+            if (p.axis == 1) {
+                const int64_t f = line / Hin, i = line - f * Hin;
+                r = q0;
+                gb = gy + (f * Hout + i) * (int64_t)Wout;
+                gs = 1;
+                xb = gx + line * Win;
+                xs = 1;
+            } else {
+                const int64_t f = line / R;
+                r = (int)(line - f * R);
+                gb = gy + f * Hout * (int64_t)Wout + q0;
+                gs = Wout;
+                xb = gx + f * Hin * (int64_t)Win + q0;
+                xs = Win;
+            }
+            float g[QQ][MM];
+#pragma unroll
+            for (int q = 0; q < QQ; ++q) {
+                int rq = r - q;
+                while (rq < 0) rq += R;
+#pragma unroll
+                for (int j = 0; j < MM; ++j)
+                    g[q][j] = q < Q && j < m ? __ldg(gb + ((int64_t)m * rq + j) * gs) : 0.f;
+            }
+            int pos = (int)(((int64_t)p.o + (int64_t)S * r) % p.n_in);
+            for (int d = 0; d < S; ++d) {
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < QQ; ++q) {
+                    const int k = d + S * q;
+                    if (q < Q && k < T) {
+#pragma unroll
+                        for (int j = 0; j < MM; ++j)
+                            if (j < m) acc = fmaf(h[j * T + k], g[q][j], acc);
+                    }
+                }
+                xb[(int64_t)pos * xs] = acc;
+                if (++pos == p.n_in) pos = 0;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 int sep_dh_blocks() { return device_sm_count() * kDhBlocksPerSm; }
@@ -442,6 +509,17 @@ cudaError_t launch_sep_adjoint(const SepPassDev& p, int64_t F, int Hin, int Win,
                                const float* gy, float* gx, cudaStream_t s) {
     const int64_t n = F * Hin * (int64_t)Win;
     if (n <= 0) return cudaSuccess;
+    // repetitions that tile the axis exactly: the per-repetition form
+    const int Q = (p.T + p.S - 1) / p.S;
+    if ((int64_t)p.S * p.R == p.n_in && p.m * p.T <= 32 * 16 && Q <= 4 && p.m <= 8) {
+        const int64_t lines = p.axis == 1 ? F * Hin : F * p.R;
+        const int64_t blocks = std::min<int64_t>(lines, (int64_t)device_sm_count() * 16);
+        if (Q <= 2 && p.m <= 4)
+            sep_adjoint_poly_kernel<2, 4><<<(int)blocks, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, taps, gy, gx);
+        else
+            sep_adjoint_poly_kernel<4, 8><<<(int)blocks, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, taps, gy, gx);
+        return cudaGetLastError();
+    }
     const int64_t blocks = std::min<int64_t>(F * Hin, (int64_t)device_sm_count() * 16);
     sep_adjoint_kernel<<<(int)blocks, 256, 0, s>>>(p, F, Hin, Win, Hout, Wout, taps, gy, gx);
     return cudaGetLastError();

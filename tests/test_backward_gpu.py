@@ -219,3 +219,17 @@ def test_backward_separable_pass_tasks(arol, axis, T, m, S, reps_mul):
     x = g.standard_normal(shape).astype(np.float32)
     G = g.standard_normal(tk["outputs"][0]["shape"])
     check_chain_grads(arol, [tk], x, G)
+
+
+@pytest.mark.parametrize("axis,T,m,S", [(1, 9, 2, 5), (0, 7, 3, 2), (0, 12, 4, 4), (1, 16, 8, 4)])
+def test_backward_separable_pass_exact_tiling(arol, axis, T, m, S):
+    """Repetitions that tile the axis exactly (S R = n): dX by the
+    per-repetition adjoint, windows overlapping up to four repetitions and
+    wrapping at the end, origin 5."""
+    g = W.rng(230 + T)
+    shape = (2, 36, 60)
+    n = shape[2] if axis == 1 else shape[1]
+    tk = W.separable_pass(shape, axis, T, m, S, 5, n // S, (g.standard_normal((m, T)) / T).astype(np.float32))
+    x = g.standard_normal(shape).astype(np.float32)
+    G = g.standard_normal(tk["outputs"][0]["shape"])
+    check_chain_grads(arol, [tk], x, G)
