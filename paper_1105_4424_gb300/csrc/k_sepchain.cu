@@ -338,7 +338,10 @@ __global__ void __launch_bounds__(256) sep_adjoint_kernel(const SepPassDev p, in
 // column pass: blocks take (frame, repetition) lines, threads the columns.
 // Every thread keeps all m x T sums in registers; the block adds them in a
 // fixed order (warp shuffles, then warps in order) into its partials.
-constexpr int kDhBlocksPerSm = 2;
+#ifndef AROL_DH_BLOCKS
+#define AROL_DH_BLOCKS 4
+#endif
+constexpr int kDhBlocksPerSm = AROL_DH_BLOCKS;
 
 // An input element in its storage (0 f32, 1 bfloat16, 2 IEEE half), widened.
 __device__ __forceinline__ float ld_x(const void* x, int64_t i, int dt) {
@@ -360,6 +363,7 @@ __global__ void __launch_bounds__(256) sep_dh_kernel(const SepPassDev p, int64_t
     const int64_t lines = p.axis == 1 ? F * Hin : F * p.R;
     const int width = p.axis == 1 ? p.R : Win;
     for (int64_t line = blockIdx.x; line < lines; line += gridDim.x) {
+#pragma unroll 2
         for (int q = threadIdx.x; q < width; q += blockDim.x) {
             float xv[TT], gv[MM];
             if (p.axis == 1) {
