@@ -290,3 +290,57 @@ def test_info_reports_the_kernel_path(B):
     assert B.arol_task_info(h)["path"] == -1
     for x in subs + [h]:
         B.arol_task_destroy(x)
+
+
+def _chain_kernel(B, chain):
+    parts = [B.arol_task_create(t) for t in chain]
+    ch = B.arol_chain_create(parts)
+    k = B.arol_task_info(ch)["kernel"]
+    for h in parts + [ch]:
+        B.arol_task_destroy(h)
+    return k
+
+
+def test_row_then_column_chains_choose_the_streaming_kernel(B, monkeypatch):
+    """Chain creation is host-only: a row pass then a column pass takes the
+    streaming kernel (kernel 5) when the column window fits its ring (T_v <=
+    29), the tile kernel (4) with AROL_SEPSTREAM=off or a longer window, and
+    a column pass first always takes the tile kernel."""
+    chain, _ = W.config1_5to2(frames=2, height=64, width=96)
+    assert _chain_kernel(B, chain) == 5
+    monkeypatch.setenv("AROL_SEPSTREAM", "off")
+    assert _chain_kernel(B, chain) == 4
+    monkeypatch.delenv("AROL_SEPSTREAM")
+    g = W.rng(9)
+    t1 = W.separable_pass((1, 64, 64), 1, 3, 1, 2, 0, 32, np.ones((1, 3), np.float32))
+    t2 = W.separable_pass(t1["outputs"][0]["shape"], 0, 30, 1, 2, 0, 32, (g.standard_normal((1, 30)) / 30).astype(np.float32))
+    assert _chain_kernel(B, [t1, t2]) == 4
+    c1 = W.separable_pass((1, 64, 64), 0, 3, 1, 2, 0, 32, np.ones((1, 3), np.float32))
+    c2 = W.separable_pass(c1["outputs"][0]["shape"], 1, 3, 1, 2, 0, 32, np.ones((1, 3), np.float32))
+    assert _chain_kernel(B, [c1, c2]) == 4
+
+
+def test_batch_with_streamed_and_fused_chain_members(B):
+    """A batch mixing 8 -> 3 chains (the batched downscaler), row-then-column
+    chains (the batched streaming kernel), a three-pass chain and single
+    tasks is created on the host without device work."""
+    members = []
+    chain, _ = W.config1(seed=2, frames=1, height=16, width=64)
+    members.append(chain)
+    chain, _ = W.config1_5to2(seed=3, frames=1, height=32, width=96)
+    members.append(chain)
+    g = W.rng(10)
+    for _ in range(3):
+        c, _ = W.random_separable_chain(g)
+        members.append(c)
+    single, _ = W.config0()
+    handles, made = [], []
+    for m in members:
+        parts = [B.arol_task_create(t) for t in m]
+        made += parts
+        handles.append(B.arol_chain_create(parts))
+    handles.append(B.arol_task_create(single))
+    b = B.arol_batch_create(handles)
+    B.arol_batch_destroy(b)
+    for h in made + handles:
+        B.arol_task_destroy(h)
