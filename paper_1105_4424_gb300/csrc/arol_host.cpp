@@ -1416,9 +1416,12 @@ bool gen_geom(const TaskDev& t, GenGeom* out) {
     const uint32_t R = (uint32_t)tiler_tiled_reps(t.elem == ELEM_FIR ? t.m : 1);
     g.na = (RA + ta - 1) / ta;
     g.nb = (RB + R * tb - 1) / (R * tb);
+    g.idelta = g.odelta = 0;
     for (int k = 0; k < 4; ++k) {
         g.istep[k] = t.in.shape[k] ? (uint32_t)(((uint64_t)tb * t.in.paving[k][g.db]) % (uint32_t)t.in.shape[k]) : 0u;
         g.ostep[k] = t.out.shape[k] ? (uint32_t)(((uint64_t)tb * t.out.paving[k][g.db]) % (uint32_t)t.out.shape[k]) : 0u;
+        g.idelta += (int64_t)g.istep[k] * t.in.stride[k];
+        g.odelta += (int64_t)g.ostep[k] * t.out.stride[k];
     }
     uint64_t outer = 1;
     for (int q = 0; q < (g.da >= 0 ? g.da : g.db); ++q) outer *= (uint64_t)std::max(t.rep[q], 1);

@@ -164,6 +164,7 @@ struct GenGeom {
     int32_t tap_floats;    // taps staged in shared memory, transposed T x MAXM; 0: read from global memory
     FastDiv na_div, nb_div;
     uint32_t istep[4], ostep[4];   // base-coordinate step of 2^lb repetitions along db, reduced mod shape
+    int64_t idelta, odelta;        // the element offsets of those steps when no coordinate wraps
 };
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s);
 cudaError_t launch_tiler_tiled(const TaskDev& t, const GenGeom& g, int max_m, cudaStream_t s);

@@ -343,8 +343,27 @@ __device__ __forceinline__ void tiled_reps(const TaskDev& t, const GenGeom& g, c
     base_index(t.out, r, false, bo);
     int64_t oi[R], oo[R];
     bool lin[R];
+    // The common case: no base of the thread's repetitions and no pattern
+    // wraps, so their offsets step by a constant.
+    bool all = t.in.linear && t.out.linear;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t span = (uint64_t)(nr - 1);
+        all = all && (uint64_t)b[k] + span * g.istep[k] + t.in.ext[k] < (uint64_t)(uint32_t)t.in.shape[k];
+        all = all && (uint64_t)bo[k] + span * g.ostep[k] + t.out.ext[k] < (uint64_t)(uint32_t)t.out.shape[k];
+    }
+    if (all) {
+        const int64_t i0 = offset_of(t.in, b), o0 = offset_of(t.out, bo);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            lin[q] = q < nr;
+            oi[q] = i0 + q * g.idelta;
+            oo[q] = o0 + q * g.odelta;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < R; ++q) {
+        if (all) break;
         lin[q] = false;
         oi[q] = oo[q] = 0;
         if (q < nr) {
