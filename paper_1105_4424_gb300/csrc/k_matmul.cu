@@ -280,7 +280,14 @@ __global__ void __launch_bounds__(192, 1) matmul_tc_kernel(const __grid_constant
 // epilogue warps of the pair arrive on the even CTA's accumulator-free
 // barriers.  Every wait is bounded as in the one-SM kernel.
 // ---------------------------------------------------------------------------
-constexpr int STAGES2 = 6;
+// k-depth of a stage of the pair kernel (64 or 128: one or two 64-deep A
+// boxes per stage, one barrier round trip per stage) and the stages.
+#ifndef AROL_MM_BK2
+#define AROL_MM_BK2 128
+#endif
+constexpr int BK2 = AROL_MM_BK2;
+constexpr int STAGES2 = 6 * 64 / BK2;
+static_assert(BK2 == 64 || BK2 == 128, "one or two 64-deep boxes of A per stage");
 
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -360,8 +367,8 @@ __device__ __forceinline__ PairItem pair_item(int i, int full, int tiles_n) {
 }
 
 struct Cfg2 {
-    static constexpr int kABytes = BM * BK * 2;            // 128 x 64 of A
-    static constexpr int kBBytes = BK * 128 * 2;           // 64 x 128 of B (this CTA's half)
+    static constexpr int kABytes = BM * BK2 * 2;           // 128 x BK2 of A (BK2 / 64 boxes of 128 x 64)
+    static constexpr int kBBytes = BK2 * 128 * 2;          // BK2 x 128 of B (this CTA's half)
     static constexpr int kStageBytes = kABytes + kBBytes;
     static constexpr int kOutBytes = 32 * 32 * 4;          // one 32 x 32 f32 block of C, 128-byte swizzled
     static constexpr int kSmem = STAGES2 * kStageBytes + 4 * 2 * kOutBytes + 1024 + 256;
@@ -389,7 +396,7 @@ __global__ void __launch_bounds__(192, 1) matmul_tc2_kernel(const __grid_constan
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
     const bool leader = rank == 0;
-    const int nkb = K / BK;
+    const int nkb = K / BK2;
     const int tiles_n = N / 256;
     const int ntiles = total;
     const int cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
@@ -434,7 +441,7 @@ __global__ void __launch_bounds__(192, 1) matmul_tc2_kernel(const __grid_constan
                 const int m0 = it.m0 + (int)rank * 128;
                 const int chunks = it.wide ? 2 : 1;                  // 64-column B chunks of this CTA's half
                 const int n0 = it.n0 + (int)rank * 64 * chunks;
-                const uint32_t bytes = 2u * (uint32_t)(G::kABytes + chunks * BK * 128);
+                const uint32_t bytes = 2u * (uint32_t)(G::kABytes + chunks * BK2 * 128);
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int st = (int)(g % STAGES2);
                     if (g >= (uint32_t)STAGES2 && !mbar_wait(empty0 + 8 * st, ((g / STAGES2) & 1u) ^ 1u)) {
@@ -445,10 +452,13 @@ __global__ void __launch_bounds__(192, 1) matmul_tc2_kernel(const __grid_constan
                     const uint32_t fb = full0 + 8 * st;
                     if (leader) mbar_expect_tx(fb, bytes);
                     const uint32_t fb_pair = map_to(fb, 0);
-                    tma_load_2d_pair(smem_addr(sA + st * G::kABytes), &tmA, kb * BK, m0, fb_pair);
+#pragma unroll
+                    for (int hb = 0; hb < BK2 / 64; ++hb)
+                        tma_load_2d_pair(smem_addr(sA + st * G::kABytes + hb * (BM * 64 * 2)), &tmA, kb * BK2 + 64 * hb,
+                                         m0, fb_pair);
                     for (int c = 0; c < chunks; ++c)
-                        tma_load_2d_pair(smem_addr(sB + st * G::kBBytes + c * (BK * 128)), &tmB, n0 + 64 * c, kb * BK,
-                                         fb_pair);
+                        tma_load_2d_pair(smem_addr(sB + st * G::kBBytes + c * (BK2 * 128)), &tmB, n0 + 64 * c,
+                                         kb * BK2, fb_pair);
                 }
             }
             progress[0] = (int)g;
@@ -480,9 +490,10 @@ __global__ void __launch_bounds__(192, 1) matmul_tc2_kernel(const __grid_constan
                     const uint32_t a0 = smem_addr(sA + st * G::kABytes);
                     const uint32_t b0 = smem_addr(sB + st * G::kBBytes);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t ad = smem_desc(a0 + kk * 32, 16, 1024);
-                        const uint64_t bd = smem_desc(b0 + kk * 16 * 128, BK * 128, 1024);
+                    for (int kk = 0; kk < BK2 / 16; ++kk) {
+                        // A: box kk / 4 of the stage, 32 bytes per 16-deep step in its swizzle atom
+                        const uint64_t ad = smem_desc(a0 + (kk >> 2) * (BM * 64 * 2) + (kk & 3) * 32, 16, 1024);
+                        const uint64_t bd = smem_desc(b0 + kk * 16 * 128, BK2 * 128, 1024);
                         mma_bf16_pair(d, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
                     }
                     mma_commit_pair(empty0 + 8 * st);
@@ -691,9 +702,9 @@ cudaError_t launch_matmul_tc(const void* A, const void* B, float* C, int M, int 
     if (!make_map(&mb, B, (uint64_t)K, (uint64_t)N, BK)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(err_flag, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    if (M % 256 == 0 && N % 256 == 0 && pair_enabled()) {
+    if (M % 256 == 0 && N % 256 == 0 && K % BK2 == 0 && pair_enabled()) {
         CUtensorMap mb2;
-        if (!make_map(&mb2, B, (uint64_t)K, (uint64_t)N, BK)) return cudaErrorInvalidValue;
+        if (!make_map(&mb2, B, (uint64_t)K, (uint64_t)N, BK2)) return cudaErrorInvalidValue;
         return launch_pair(ma, mb2, C, M, N, K, err_flag, s);
     }
     if (N % 256 == 0) return launch_bn<256>(ma, mb, C, M, N, K, err_flag, s);
