@@ -82,15 +82,6 @@ __device__ __forceinline__ void flag(unsigned* err, unsigned bit) {
 // never overlap (a tile's slots span nrows * ss + 28 floats).
 __device__ __forceinline__ int slot_offset(int k, int ss) { return k * ss + 4 * (k >> 2); }
 
-__device__ __forceinline__ RowTileDev load_tile(const RowTileDev* p) {
-    RowTileDev r;
-    const uint4* s = reinterpret_cast<const uint4*>(p);
-    uint4* d = reinterpret_cast<uint4*>(&r);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) d[i] = __ldg(s + i);
-    return r;
-}
-
 // Per-tile constants of a consumer warp.
 struct TileGeom {
     int la;        // a = 2^la rows per unit

@@ -12,261 +12,11 @@
 
 #include "arol_internal.h"
 #include "ptx.h"
+#include "tiler_dev.h"
 
-#ifndef AROL_GEN_UNROLL
-#define AROL_GEN_UNROLL 2
-#endif
-#ifndef AROL_GEN_MINB
-#define AROL_GEN_MINB 3
-#endif
-#ifndef AROL_GEN_R
-#define AROL_GEN_R 4
-#endif
 
 namespace arol {
 namespace {
-
-constexpr int kThreads = 256;
-constexpr int kGenUnroll = AROL_GEN_UNROLL;   // tap indices of the block-tiled walk in flight together
-
-// n / d for n < 2^31 by multiply-shift (host-prepared reciprocal).
-__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
-    return (uint32_t)(((uint64_t)n * f.m) >> f.s);
-}
-
-__device__ __forceinline__ void base_index(const PortDev& p, const uint32_t r[4], bool wide, uint32_t e[4]) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (wide) {
-            uint64_t v = p.origin[k];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v += (uint64_t)p.paving[k][q] * r[q];
-            e[k] = (uint32_t)(v % (uint64_t)(uint32_t)p.shape[k]);
-        } else {
-            // the host guarantees v < 2^31 on this path
-            uint32_t v = p.origin[k];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v += p.paving[k][q] * r[q];
-            e[k] = v - fast_div(v, p.shape_div[k]) * (uint32_t)p.shape[k];
-        }
-    }
-}
-
-__device__ __forceinline__ uint32_t pick(const uint32_t c[4], int k) {
-    return k == 0 ? c[0] : k == 1 ? c[1] : k == 2 ? c[2] : c[3];
-}
-
-// c += fitting column `col`, modulo the shape (every term already in [0, s)).
-__device__ __forceinline__ void advance(const PortDev& p, int col, uint32_t c[4]) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        uint32_t v = c[k] + p.fitting[k][col];
-        c[k] = v >= (uint32_t)p.shape[k] ? v - (uint32_t)p.shape[k] : v;
-    }
-}
-
-__device__ __forceinline__ int64_t offset_of(const PortDev& p, const uint32_t c[4]) {
-    return (int64_t)c[0] * p.stride[0] + (int64_t)c[1] * p.stride[1] +
-           (int64_t)c[2] * p.stride[2] + (int64_t)c[3] * p.stride[3];
-}
-
-// Walks a pattern in row-major order: pattern dim 1 is the fast one.
-struct PatternWalk {
-    uint32_t row[4], cur[4];
-    int i1;
-    __device__ __forceinline__ void start(const uint32_t b[4]) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) row[k] = cur[k] = b[k];
-        i1 = 0;
-    }
-    __device__ __forceinline__ void next(const PortDev& p) {
-        if (++i1 == p.pattern[1]) {
-            i1 = 0;
-            advance(p, 0, row);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cur[k] = row[k];
-        } else {
-            advance(p, 1, cur);
-        }
-    }
-};
-
-__device__ __forceinline__ void decode_rep(const TaskDev& t, int64_t lr, bool wide, uint32_t r[4]) {
-    if (wide) {
-#pragma unroll
-        for (int q = 3; q >= 0; --q) {
-            int64_t d = t.rep[q];
-            int64_t qq = lr / d;
-            r[q] = (uint32_t)(lr - qq * d);
-            lr = qq;
-        }
-    } else {
-        uint32_t l = (uint32_t)lr;   // < 2^31 on this path
-#pragma unroll
-        for (int q = 3; q >= 0; --q) {
-            const uint32_t qq = fast_div(l, t.rep_div[q]);
-            r[q] = l - qq * (uint32_t)t.rep[q];
-            l = qq;
-        }
-    }
-}
-
-// One repetition of a copy or fir task: gather, elementary task, scatter.
-// FIR storage: f32, bfloat16 or IEEE half; 16-bit values are widened
-// exactly on load and rounded to nearest even on store; the arithmetic is f32
-// either way.
-__device__ __forceinline__ float load_value(const TaskDev& t, int64_t off) {
-    if (t.in_dt == kStBf16) return __uint_as_float((uint32_t)__ldg(static_cast<const unsigned short*>(t.x) + off) << 16);
-    if (t.in_dt == kStF16) return __half2float(__ushort_as_half(__ldg(static_cast<const unsigned short*>(t.x) + off)));
-    return __ldg(static_cast<const float*>(t.x) + off);
-}
-
-__device__ __forceinline__ void store_value(const TaskDev& t, int64_t off, float v) {
-    if (t.out_dt == kStBf16) static_cast<__nv_bfloat16*>(t.y)[off] = __float2bfloat16_rn(v);
-    else if (t.out_dt == kStF16) static_cast<__half*>(t.y)[off] = __float2half_rn(v);
-    else static_cast<float*>(t.y)[off] = v;
-}
-
-// Contiguous-row pattern walk: offset of the row start plus a coordinate
-// along the last dimension that wraps to 0 at its extent.
-struct RowWalk {
-    int64_t base;
-    uint32_t c, extent;
-    __device__ __forceinline__ void start(const PortDev& p, const uint32_t b[4]) {
-        c = pick(b, p.fdim);
-        extent = (uint32_t)p.shape[p.fdim];
-        base = offset_of(p, b) - (int64_t)c;
-    }
-    __device__ __forceinline__ int64_t off() const { return base + (int64_t)c; }
-    __device__ __forceinline__ void next() { c = (c + 1u == extent) ? 0u : c + 1u; }
-};
-
-// AROL_DEBUG builds check every index the per-repetition walk computes
-// against its array before the access; an index out of range is skipped and
-// recorded in *t.err, bit 0x100 (input) or 0x200 (output), which
-// arol_task_sync_status reports as AROL_ERR_OOB.
-// Release builds compile the checks away.
-#ifdef AROL_DEBUG
-__device__ __forceinline__ bool in_ok(const TaskDev& t, int64_t off) {
-    if ((uint64_t)off < (uint64_t)t.in_elems) return true;
-    if (t.err) atomicOr(t.err, 0x100u);
-    return false;
-}
-__device__ __forceinline__ bool out_ok(const TaskDev& t, int64_t off) {
-    if ((uint64_t)off < (uint64_t)t.out_elems) return true;
-    if (t.err) atomicOr(t.err, 0x200u);
-    return false;
-}
-#else
-__device__ __forceinline__ constexpr bool in_ok(const TaskDev&, int64_t) { return true; }
-__device__ __forceinline__ constexpr bool out_ok(const TaskDev&, int64_t) { return true; }
-#endif
-
-template <int MAXM>
-__device__ __forceinline__ void process_rep_rows(const TaskDev& t, const uint32_t bi[4], const uint32_t bo[4]) {
-    RowWalk wi, wo;
-    wi.start(t.in, bi);
-    wo.start(t.out, bo);
-    const int n = t.T;
-    if (t.elem == ELEM_COPY) {
-        if (t.esize == 4) {
-            const uint32_t* x = static_cast<const uint32_t*>(t.x);
-            uint32_t* y = static_cast<uint32_t*>(t.y);
-            for (int k = 0; k < n; ++k) {
-                if (in_ok(t, wi.off()) && out_ok(t, wo.off())) y[wo.off()] = __ldg(x + wi.off());
-                wi.next();
-                wo.next();
-            }
-        } else {
-            const uint16_t* x = static_cast<const uint16_t*>(t.x);
-            uint16_t* y = static_cast<uint16_t*>(t.y);
-            for (int k = 0; k < n; ++k) {
-                if (in_ok(t, wi.off()) && out_ok(t, wo.off())) y[wo.off()] = __ldg(x + wi.off());
-                wi.next();
-                wo.next();
-            }
-        }
-        return;
-    }
-    const int m = t.m;
-    float acc[MAXM];
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) acc[j] = 0.f;
-    for (int k = 0; k < n; ++k) {
-        const float p = in_ok(t, wi.off()) ? load_value(t, wi.off()) : 0.f;
-        wi.next();
-        const float* h = t.taps + k;
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-            if (j < m) acc[j] = fmaf(__ldg(h + j * n), p, acc[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-        if (j < m) {
-            if (out_ok(t, wo.off())) store_value(t, wo.off(), acc[j]);
-            wo.next();
-        }
-    }
-}
-
-// One repetition from its input and output base coordinates b, bo: the
-// pattern walks with a wrap test per step (PatternWalk), or with one per
-// row pattern (process_rep_rows).
-template <int MAXM>
-__device__ __forceinline__ void process_rep_at(const TaskDev& t, const uint32_t b[4], const uint32_t bo[4]) {
-    if (t.in.fast && t.out.fast) {
-        process_rep_rows<MAXM>(t, b, bo);
-        return;
-    }
-    PatternWalk wi, wo;
-    wi.start(b);
-    wo.start(bo);
-    const int n = t.T;
-    if (t.elem == ELEM_COPY) {
-        if (t.esize == 4) {
-            const uint32_t* x = static_cast<const uint32_t*>(t.x);
-            uint32_t* y = static_cast<uint32_t*>(t.y);
-            for (int k = 0; k < n; ++k) {
-                const int64_t oi = offset_of(t.in, wi.cur), oo = offset_of(t.out, wo.cur);
-                if (in_ok(t, oi) && out_ok(t, oo)) y[oo] = __ldg(x + oi);
-                wi.next(t.in);
-                wo.next(t.out);
-            }
-        } else {
-            const uint16_t* x = static_cast<const uint16_t*>(t.x);
-            uint16_t* y = static_cast<uint16_t*>(t.y);
-            for (int k = 0; k < n; ++k) {
-                const int64_t oi = offset_of(t.in, wi.cur), oo = offset_of(t.out, wo.cur);
-                if (in_ok(t, oi) && out_ok(t, oo)) y[oo] = __ldg(x + oi);
-                wi.next(t.in);
-                wo.next(t.out);
-            }
-        }
-        return;
-    }
-    // FIR bank: y[j] = sum_k H[j,k] p[k], accumulated in k order with fma.
-    const int m = t.m;
-    float acc[MAXM];
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) acc[j] = 0.f;
-    for (int k = 0; k < n; ++k) {
-        const int64_t oi = offset_of(t.in, wi.cur);
-        const float p = in_ok(t, oi) ? load_value(t, oi) : 0.f;
-        wi.next(t.in);
-        const float* h = t.taps + k;
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-            if (j < m) acc[j] = fmaf(__ldg(h + (int64_t)j * n), p, acc[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-        if (j < m) {
-            const int64_t oo = offset_of(t.out, wo.cur);
-            if (out_ok(t, oo)) store_value(t, oo, acc[j]);
-            wo.next(t.out);
-        }
-    }
-}
 
 template <int MAXM>
 __device__ __forceinline__ void process_rep(const TaskDev& t, int64_t lr) {
@@ -285,228 +35,6 @@ __global__ void __launch_bounds__(kThreads) tiler_generic_kernel(const TaskDev t
         process_rep<MAXM>(t, lr);
 }
 
-// Taps of one tap index k for M outputs, from the transposed block
-// ht[k * 16 + j] = H[j, k], as float4 / float2 / float pieces.
-template <int M>
-__device__ __forceinline__ void load_taps(const float* hrow, float (&h)[M]) {
-#pragma unroll
-    for (int j = 0; j + 4 <= M; j += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(hrow + j);
-        h[j] = v.x;
-        h[j + 1] = v.y;
-        h[j + 2] = v.z;
-        h[j + 3] = v.w;
-    }
-    constexpr int j0 = M / 4 * 4;
-    if (M - j0 >= 2) {
-        const float2 v = *reinterpret_cast<const float2*>(hrow + j0);
-        h[j0] = v.x;
-        h[j0 + 1] = v.y;
-    }
-    if ((M - j0) & 1) h[M - 1] = hrow[M - 1];
-}
-
-// ---------------------------------------------------------------------------
-// Generic walk, block-tiled.  A pattern whose base coordinates b satisfy
-// b + ext < shape on every array dimension never wraps (fittings are reduced
-// into [0, shape)), so its elements sit at offset(b) + i0 lin[0] + i1
-// lin[1]: one add per element instead of a wrap test per dimension.  Other
-// patterns take the wrapping walk.  FIR taps are staged once per block in
-// shared memory, transposed (T x MAXM) for 16-byte loads of a tap index's
-// MAXM taps.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool pattern_fits(const PortDev& p, const uint32_t b[4]) {
-    bool ok = p.linear != 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) ok = ok && b[k] + p.ext[k] < (uint32_t)p.shape[k];
-    return ok;
-}
-
-// Up to R repetitions of one thread along the lane dimension db, 2^lb
-// apart, their base coordinates stepped by g.istep / g.ostep (reduced).  Repetitions whose input and output patterns
-// both stay inside their arrays run the linear walk together (one load of a
-// tap index's taps for all of them, one add per element and repetition);
-// the others take the wrapping walk one by one.
-__device__ __forceinline__ void step_base(const PortDev& p, const uint32_t st[4], uint32_t b[4]) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t v = b[k] + st[k];
-        b[k] = v >= (uint32_t)p.shape[k] ? v - (uint32_t)p.shape[k] : v;
-    }
-}
-
-template <int MAXM, int R, bool F32>
-__device__ __forceinline__ void tiled_reps(const TaskDev& t, const GenGeom& g, const uint32_t r[4], int nr,
-                                           const float* ht) {
-    uint32_t b[4], bo[4];
-    base_index(t.in, r, false, b);
-    base_index(t.out, r, false, bo);
-    int64_t oi[R], oo[R];
-    bool lin[R];
-    // The common case: no base of the thread's repetitions and no pattern
-    // wraps, so their offsets step by a constant.
-    bool all = t.in.linear && t.out.linear;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint64_t span = (uint64_t)(nr - 1);
-        all = all && (uint64_t)b[k] + span * g.istep[k] + t.in.ext[k] < (uint64_t)(uint32_t)t.in.shape[k];
-        all = all && (uint64_t)bo[k] + span * g.ostep[k] + t.out.ext[k] < (uint64_t)(uint32_t)t.out.shape[k];
-    }
-    if (all) {
-        const int64_t i0 = offset_of(t.in, b), o0 = offset_of(t.out, bo);
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            lin[q] = q < nr;
-            oi[q] = i0 + q * g.idelta;
-            oo[q] = o0 + q * g.odelta;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-        if (all) break;
-        lin[q] = false;
-        oi[q] = oo[q] = 0;
-        if (q < nr) {
-            if (pattern_fits(t.in, b) && pattern_fits(t.out, bo)) {
-                lin[q] = true;
-                oi[q] = offset_of(t.in, b);
-                oo[q] = offset_of(t.out, bo);
-            } else {
-                process_rep_at<MAXM>(t, b, bo);
-            }
-            step_base(t.in, g.istep, b);
-            step_base(t.out, g.ostep, bo);
-        }
-    }
-    const int n = t.T;
-    // every repetition's walk takes the same steps: lin[1] within a pattern
-    // row, lin[0] - (pattern[1] - 1) lin[1] from a row's end to the next
-    const int pi1 = t.in.pattern[1], po1 = t.out.pattern[1];
-    const int64_t si1 = t.in.lin[1], si0 = t.in.lin[0] - (int64_t)(pi1 - 1) * si1;
-    const int64_t so1 = t.out.lin[1], so0 = t.out.lin[0] - (int64_t)(po1 - 1) * so1;
-    if (t.elem == ELEM_COPY) {
-        int ii = 0, io = 0;
-#pragma unroll 4
-        for (int k = 0; k < n; ++k) {
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                if (lin[q] && in_ok(t, oi[q]) && out_ok(t, oo[q])) {
-                    if (t.esize == 4) static_cast<uint32_t*>(t.y)[oo[q]] = __ldg(static_cast<const uint32_t*>(t.x) + oi[q]);
-                    else static_cast<uint16_t*>(t.y)[oo[q]] = __ldg(static_cast<const uint16_t*>(t.x) + oi[q]);
-                }
-            }
-            const bool wi = ++ii == pi1, wo = ++io == po1;
-            const int64_t di = wi ? si0 : si1, dout = wo ? so0 : so1;
-            if (wi) ii = 0;
-            if (wo) io = 0;
-#pragma unroll
-            for (int q = 0; q < R; ++q) oi[q] += di, oo[q] += dout;
-        }
-        return;
-    }
-    // FIR bank: y[j] = sum_k H[j,k] p[k], accumulated in k order with fma
-    const int m = t.m;
-    float acc[R][MAXM];
-#pragma unroll
-    for (int q = 0; q < R; ++q)
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j) acc[q][j] = 0.f;
-    const float* xf = static_cast<const float*>(t.x);
-    int ii = 0;
-    // unrolled: the loads of several tap indices are in flight together
-#pragma unroll kGenUnroll
-    for (int k = 0; k < n; ++k) {
-        float h[MAXM];
-        if (ht) {
-            load_taps<MAXM>(ht + k * ((MAXM + 3) & ~3), h);
-        } else {
-#pragma unroll
-            for (int j = 0; j < MAXM; ++j) h[j] = j < m ? __ldg(t.taps + (int64_t)j * n + k) : 0.f;
-        }
-        float p[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            if (F32) p[q] = lin[q] && in_ok(t, oi[q]) ? __ldg(xf + oi[q]) : 0.f;
-            else p[q] = lin[q] && in_ok(t, oi[q]) ? load_value(t, oi[q]) : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < R; ++q)
-#pragma unroll
-            for (int j = 0; j < MAXM; ++j)
-                if (j < m) acc[q][j] = fmaf(h[j], p[q], acc[q][j]);
-        const bool wi = ++ii == pi1;
-        if (wi) ii = 0;
-        const int64_t di = wi ? si0 : si1;
-#pragma unroll
-        for (int q = 0; q < R; ++q) oi[q] += di;
-    }
-    float* yf = static_cast<float*>(t.y);
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-        if (!lin[q]) continue;
-        int64_t cur = oo[q];
-        int io = 0;
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-            if (j < m) {
-                if (out_ok(t, cur)) {
-                    if (F32) yf[cur] = acc[q][j];
-                    else store_value(t, cur, acc[q][j]);
-                }
-                const bool wo = ++io == po1;
-                if (wo) io = 0;
-                cur += wo ? so0 : so1;
-            }
-        }
-    }
-}
-
-// Blocks per SM the launch bound asks for: larger banks need more registers.
-constexpr int gen_min_blocks(int maxm) { return maxm <= 4 ? AROL_GEN_MINB : maxm <= 8 ? 2 : 1; }
-
-template <int MAXM, int R, bool F32>
-__global__ void __launch_bounds__(kThreads, gen_min_blocks(MAXM)) tiler_tiled_kernel(const TaskDev t, const GenGeom g) {
-    extern __shared__ __align__(16) float ht[];
-    if (g.tap_floats) {
-        const int n = t.T, m = t.m;
-        for (int i = threadIdx.x; i < g.tap_floats; i += blockDim.x) {
-            constexpr int kHs = (MAXM + 3) & ~3;   // 16-byte rows of taps
-            const int k = i / kHs, j = i - k * kHs;
-            ht[i] = j < m ? __ldg(t.taps + (int64_t)j * n + k) : 0.f;
-        }
-        __syncthreads();
-    }
-    const float* hts = g.tap_floats ? ht : nullptr;
-    const uint32_t tb = 1u << g.lb;
-    const uint32_t tx = threadIdx.x & (tb - 1u), ty = threadIdx.x >> g.lb;
-    const uint32_t RA = g.da >= 0 ? (uint32_t)t.rep[g.da] : 1u, RB = (uint32_t)t.rep[g.db];
-    const int qlim = g.da >= 0 ? g.da : g.db;   // dims below qlim come from the outer index
-    for (uint32_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
-        const uint32_t q1 = fast_div(tile, g.nb_div), ib = tile - q1 * g.nb;
-        const uint32_t o = fast_div(q1, g.na_div), ia = q1 - o * g.na;
-        // a tile covers R * tb repetitions along db: this thread's are bb, bb + tb, ...
-        const uint32_t a = ia * (uint32_t)g.ta + ty, bb = ib * (uint32_t)R * tb + tx;
-        if (a >= RA || bb >= RB) continue;
-        const int nr = (int)min((uint32_t)R, (RB - bb + tb - 1u) >> g.lb);
-        uint32_t r[4];
-        uint32_t l = o;
-#pragma unroll
-        for (int q = 3; q >= 0; --q) {
-            if (q == g.db) {
-                r[q] = bb;
-            } else if (q == g.da) {
-                r[q] = a;
-            } else if (q < qlim) {
-                const uint32_t qq = fast_div(l, t.rep_div[q]);
-                r[q] = l - qq * (uint32_t)t.rep[q];
-                l = qq;
-            } else {
-                r[q] = 0;
-            }
-        }
-        tiled_reps<MAXM, R, F32>(t, g, r, nr, hts);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Column FIR tile (repetitions start .. start + count - 1 of a column-FIR
@@ -1065,7 +593,6 @@ __global__ void __launch_bounds__(kThreads) tiler_bwd_dx_kernel(const TaskDev t,
 __global__ void __launch_bounds__(kThreads) tiler_bwd_dh_kernel(const TaskDev t, const float* __restrict__ gy,
                                                                 float* __restrict__ partials, int64_t chunk) {
     const bool wide = t.wide != 0;
-    const float* x = static_cast<const float*>(t.x);
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
     const int64_t r1 = r0 + chunk < t.nreps ? r0 + chunk : t.nreps;
     const int npairs = t.m * t.T;
@@ -1091,7 +618,6 @@ template <int MM, int TT>
 __global__ void __launch_bounds__(kThreads) tiler_bwd_dh_regs_kernel(const TaskDev t, const float* __restrict__ gy,
                                                                      float* __restrict__ partials, int64_t chunk) {
     const bool wide = t.wide != 0;
-    const float* x = static_cast<const float*>(t.x);
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
     const int64_t r1 = r0 + chunk < t.nreps ? r0 + chunk : t.nreps;
     const int m = t.m, T = t.T;
@@ -1227,51 +753,6 @@ cudaError_t launch_fir2d(const TaskDev& t, cudaStream_t s) {
     if (t.m <= 4) fir2d_kernel<4><<<grid, kFir2dThreads, smem, s>>>(t, (int)tiles_x);
     else fir2d_kernel<16><<<grid, kFir2dThreads, smem, s>>>(t, (int)tiles_x);
     return cudaGetLastError();
-}
-
-int tiler_tiled_maxm(int max_m) {
-    return max_m <= 3 ? (max_m < 1 ? 1 : max_m) : max_m <= 4 ? 4 : max_m <= 8 ? 8 : max_m <= 16 ? 16 : 32;
-}
-int tiler_tiled_reps(int max_m) { return max_m <= 8 ? AROL_GEN_R : max_m <= 16 ? 2 : 1; }
-
-template <int MAXM, bool F32>
-static cudaError_t launch_tiled_m(const TaskDev& t, const GenGeom& g, cudaStream_t s) {
-    constexpr int R = MAXM <= 8 ? AROL_GEN_R : MAXM <= 16 ? 2 : 1;
-    const size_t smem = (size_t)g.tap_floats * sizeof(float);
-    static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(tiler_tiled_kernel<MAXM, R, F32>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = smem;
-    }
-    const int threads = g.ta << g.lb;
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tiler_tiled_kernel<MAXM, R, F32>, threads, smem);
-    const int64_t cap = (int64_t)device_sm_count() * (occ > 0 ? occ : 1);
-    const int grid = (int)std::min<int64_t>(g.ntiles, cap);
-    tiler_tiled_kernel<MAXM, R, F32><<<grid, threads, smem, s>>>(t, g);
-    return cudaGetLastError();
-}
-
-template <int MAXM>
-static cudaError_t launch_tiled_dt(const TaskDev& t, const GenGeom& g, cudaStream_t s) {
-    // f32 storage on both sides (or a copy): plain loads and stores
-    if (t.elem == ELEM_COPY || (t.in_dt == kStF32 && t.out_dt == kStF32)) return launch_tiled_m<MAXM, true>(t, g, s);
-    return launch_tiled_m<MAXM, false>(t, g, s);
-}
-
-cudaError_t launch_tiler_tiled(const TaskDev& t, const GenGeom& g, int max_m, cudaStream_t s) {
-    if (t.nreps == 0 || g.ntiles == 0) return cudaSuccess;
-    switch (tiler_tiled_maxm(max_m)) {
-        case 1: return launch_tiled_dt<1>(t, g, s);
-        case 2: return launch_tiled_dt<2>(t, g, s);
-        case 3: return launch_tiled_dt<3>(t, g, s);
-        case 4: return launch_tiled_dt<4>(t, g, s);
-        case 8: return launch_tiled_dt<8>(t, g, s);
-        case 16: return launch_tiled_dt<16>(t, g, s);
-        default: return launch_tiled_dt<32>(t, g, s);
-    }
 }
 
 cudaError_t launch_tiler_generic(const TaskDev& t, int max_m, cudaStream_t s) {
