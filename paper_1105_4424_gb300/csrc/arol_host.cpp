@@ -968,6 +968,11 @@ struct arol_task_s {
     std::vector<int64_t*> inv_start;
     std::vector<int32_t*> inv_list;
     std::vector<float*> grad_mids;
+    // chain backward: per intermediate, a one-pass task over the same tiler
+    // and taps that recomputes it on the batch engine (row- and column-FIR
+    // passes); null where the per-repetition walk recomputes it
+    std::vector<arol_task> rc;
+    bool rc_checked = false;
     // host-buffer staging
     void* stage_in[2] = {nullptr, nullptr};
     void* stage_out = nullptr;
@@ -1369,6 +1374,11 @@ arol_status arol_task_set_taps(arol_task t, const float* taps, int on_device) {
         t->ib = nullptr;
     }
     t->ib_checked = false;
+    for (arol_task& r : t->rc) {
+        arol_task_destroy(r);
+        r = nullptr;
+    }
+    t->rc_checked = false;
     if (on_device) {
         t->taps_borrowed = taps;
     } else {
@@ -1789,6 +1799,52 @@ arol_status backward_generic_task(arol_task t, size_t i, const float* taps, cons
     return AROL_OK;
 }
 
+// Backward of one separable pass (task ii of t): the one-sweep kernel when
+// the repetitions tile the axis and the data fit its forms, else the adjoint
+// gather and the tap-gradient walk (no inverse map); tap gradients of larger
+// banks by the owner-computes walk.  gx and gt may be null.
+arol_status sep_pass_backward(arol_task t, size_t ii, const SepPassDev& p, int64_t F, const int64_t ihw[2],
+                              const int64_t ohw[2], const float* tp, const void* x, const float* g, float* gx, float* gt,
+                              cudaStream_t s) {
+    const int x_dt = t->descs[ii].in[0].dtype;
+    const int Hin = (int)ihw[0], Win = (int)ihw[1], Hout = (int)ohw[0], Wout = (int)ohw[1];
+    arol_status st = AROL_OK;
+    if (!gx && !gt) return AROL_OK;
+    if (sep_bwd_supported(p, F, Hin, Win, x_dt, x, g, gx, gt != nullptr)) {
+        const int nb = sep_bwd_blocks(p, x_dt, gt != nullptr);
+        if (gt && (st = ensure_partials(t, (int64_t)nb * p.m * p.T, s)) != AROL_OK) return st;
+        AROL_CUDA(launch_sep_bwd(p, F, Hin, Win, tp, x, x_dt, g, gx, t->partials, nb, gt, s), "backward launch");
+        return AROL_OK;
+    }
+    if (gx) AROL_CUDA(launch_sep_adjoint(p, F, Hin, Win, Hout, Wout, tp, g, gx, s), "backward launch");
+    if (gt && sep_dh_supported(p)) {
+        if ((st = ensure_partials(t, (int64_t)sep_dh_blocks() * p.m * p.T, s)) != AROL_OK) return st;
+        AROL_CUDA(launch_sep_dh(p, F, Hin, Win, Hout, Wout, x, x_dt, g, t->partials, gt, s), "backward launch");
+    } else if (gt) {
+        return backward_generic_task(t, ii, tp, x, g, nullptr, gt, s);
+    }
+    return AROL_OK;
+}
+
+// The chain backward's recompute tasks: one single-pass task per
+// intermediate whose pass is a row or column FIR with host taps (it runs as a
+// one-member batch: staged row tiles or column tiles); the others stay null.
+void build_recompute_tasks(arol_task t) {
+    t->rc_checked = true;
+    t->rc.assign(t->descs.size(), nullptr);
+    if (t->taps_borrowed || !t->taps_ready) return;
+    for (size_t i = 0; i + 1 < t->descs.size(); ++i) {
+        const arol_task_desc& d = t->descs[i];
+        if (d.elem != AROL_ELEM_FIR || d.n_in != 1) continue;
+        const TaskDev td = make_taskdev(d, true);
+        if (!td.rowfir && !td.colfir) continue;
+        arol_task_desc di = d;
+        di.fir_taps_host = t->taps_host.data() + t->tap_off[i];
+        arol_task sub = nullptr;
+        if (arol_task_create(&di, &sub) == AROL_OK) t->rc[i] = sub;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1831,30 +1887,28 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
         int64_t F = 0, ihw[2], ohw[2];
         if (match_sep_pass(t->descs[0], &pass, &F, ihw, ohw, true)) {
             pass.tap_off = 0;
-            if (grad_in)
-                AROL_CUDA(launch_sep_adjoint(pass, F, (int)ihw[0], (int)ihw[1], (int)ohw[0], (int)ohw[1], taps,
-                                             (const float*)grad_out, (float*)grad_in, s),
-                          "backward launch");
-            if (grad_taps && sep_dh_supported(pass)) {
-                if ((st = ensure_partials(t, (int64_t)sep_dh_blocks() * pass.m * pass.T, s)) != AROL_OK) return st;
-                AROL_CUDA(launch_sep_dh(pass, F, (int)ihw[0], (int)ihw[1], (int)ohw[0], (int)ohw[1], saved_in[0],
-                                        t->descs[0].in[0].dtype, (const float*)grad_out, t->partials, grad_taps, s),
-                          "backward launch");
-            } else if (grad_taps) {
-                return backward_generic_task(t, 0, taps, saved_in[0], (const float*)grad_out, nullptr, grad_taps, s);
-            }
-            return AROL_OK;
+            return sep_pass_backward(t, 0, pass, F, ihw, ohw, taps, saved_in[0], (const float*)grad_out,
+                                     (float*)grad_in, grad_taps, s);
         }
         return backward_generic_task(t, 0, taps, saved_in[0], (const float*)grad_out, (float*)grad_in, grad_taps, s);
     }
     // Unfused chain: recompute the intermediates, then reverse task by task.
     const size_t n = t->descs.size();
+    if (!t->rc_checked) build_recompute_tasks(t);
     const void* cur = saved_in[0];
     for (size_t i = 0; i + 1 < n; ++i) {
         if ((st = dev_alloc(t, &t->mids[i], array_bytes(t->descs[i].out[0]), "cudaMalloc(chain intermediate)")) != AROL_OK)
             return st;
-        if (reps_of(t->descs[i]) > 0 && (st = run_generic(t->descs[i], taps ? taps + t->tap_off[i] : nullptr, cur, t->mids[i], s)) != AROL_OK)
-            return st;
+        if (reps_of(t->descs[i]) > 0) {
+            if (t->rc[i]) {
+                const void* rin[1] = {cur};
+                void* rout[1] = {t->mids[i]};
+                if ((st = arol_task_run(t->rc[i], rin, rout, stream)) != AROL_OK) return st;
+            } else if ((st = run_generic(t->descs[i], taps ? taps + t->tap_off[i] : nullptr, cur, t->mids[i], s)) !=
+                       AROL_OK) {
+                return st;
+            }
+        }
         cur = t->mids[i];
     }
     if (t->grad_mids.size() < n) t->grad_mids.resize(n, nullptr);
@@ -1877,17 +1931,8 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
             // separable passes: dX by the pass's transposed tiler as a
             // gather (no inverse map), the tap gradients as for any task
             const SepChainDev& c = t->sd;
-            if (gx)
-                AROL_CUDA(launch_sep_adjoint(c.p[ii], c.F, c.H[ii], c.W[ii], c.H[ii + 1], c.W[ii + 1], tp, g, gx, s),
-                          "chain backward launch");
-            if (gt && sep_dh_supported(c.p[ii])) {
-                if ((st = ensure_partials(t, (int64_t)sep_dh_blocks() * c.p[ii].m * c.p[ii].T, s)) != AROL_OK) return st;
-                AROL_CUDA(launch_sep_dh(c.p[ii], c.F, c.H[ii], c.W[ii], c.H[ii + 1], c.W[ii + 1], xin,
-                                        t->descs[ii].in[0].dtype, g, t->partials, gt, s),
-                          "chain backward launch");
-            } else if (gt && (st = backward_generic_task(t, ii, tp, xin, g, nullptr, gt, s)) != AROL_OK) {
-                return st;
-            }
+            const int64_t ihw[2] = {c.H[ii], c.W[ii]}, ohw[2] = {c.H[ii + 1], c.W[ii + 1]};
+            if ((st = sep_pass_backward(t, ii, c.p[ii], c.F, ihw, ohw, tp, xin, g, gx, gt, s)) != AROL_OK) return st;
         } else if ((st = backward_generic_task(t, ii, tp, xin, g, gx, gt, s)) != AROL_OK) {
             return st;
         }
@@ -1934,6 +1979,11 @@ arol_status arol_task_sync_status(arol_task t, void* stream) {
         const arol_status bs = arol_batch_sync_status(t->ib, stream);
         if (bs != AROL_OK) return bs;
     }
+    for (arol_task r : t->rc)
+        if (r) {
+            const arol_status rs = arol_task_sync_status(r, stream);
+            if (rs != AROL_OK) return rs;
+        }
     if (t->err_flag) {
         unsigned flag = 0;
         AROL_CUDA(cudaMemcpy(&flag, t->err_flag, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
@@ -1951,6 +2001,7 @@ arol_status arol_task_sync_status(arol_task t, void* stream) {
 void arol_task_destroy(arol_task t) {
     if (!t) return;
     if (t->ib) arol_batch_destroy(t->ib);
+    for (arol_task r : t->rc) arol_task_destroy(r);
     if (t->device >= 0) {
         int cur = 0;
         cudaGetDevice(&cur);

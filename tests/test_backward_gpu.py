@@ -233,3 +233,46 @@ def test_backward_separable_pass_exact_tiling(arol, axis, T, m, S):
     x = g.standard_normal(shape).astype(np.float32)
     G = g.standard_normal(tk["outputs"][0]["shape"])
     check_chain_grads(arol, [tk], x, G)
+
+
+@pytest.mark.parametrize("axis,T,m,S,width,dt", [
+    (0, 5, 2, 4, 60, "f32"), (0, 8, 3, 4, 60, "f32"), (0, 5, 2, 4, 62, "f32"), (0, 6, 2, 3, 60, "bf16"),
+    (1, 5, 2, 4, 60, "f32"), (1, 3, 1, 3, 60, "f16"), (1, 12, 4, 6, 60, "f32"), (1, 5, 2, 2, 62, "bf16"),
+    (1, 4, 2, 2, 62, "f32"), (1, 8, 3, 8, 64, "f32")])
+def test_backward_one_sweep_pass(arol, axis, T, m, S, width, dt):
+    """Passes whose repetitions tile the axis (S R = n) with at most 4 outputs
+    and 16 taps: dX and the tap gradients in one sweep over the data (column
+    passes four columns at a time when the width is a multiple of 4, else the
+    adjoint and tap-gradient kernels; row passes staged a row at a time, rows
+    of 30 or 62 words alternating the 16-byte and the word-by-word staging;
+    steps 2, 4 and 8 in their step-specialised forms), origin 5, inputs in
+    f32, bfloat16 or IEEE half, against the oracle.  A
+    call asking for dX alone or the tap gradients alone gives the same bits."""
+    g = W.rng(250 + T + width)
+    shape = (2, 36, width)
+    n = shape[2] if axis == 1 else shape[1]
+    tk = W.separable_pass(shape, axis, T, m, S, 5, n // S, (g.standard_normal((m, T)) / T).astype(np.float32))
+    xf = g.standard_normal(shape).astype(np.float32)
+    if dt == "bf16":
+        x = W.bf16_round(xf)
+        xv = W.bf16_bits_to_f32(x)
+    elif dt == "f16":
+        x = xf.astype(np.float16)
+        xv = x.astype(np.float32)
+    else:
+        x = xv = xf
+    G = g.standard_normal(tk["outputs"][0]["shape"]).astype(np.float32)
+    t = arol.Task(dict(tk, inputs=[dict(tk["inputs"][0], dtype=dt)]))
+    gx, gx1 = torch.empty(shape, device="cuda"), torch.empty(shape, device="cuda")
+    gt, gt1 = torch.empty(m * T, device="cuda"), torch.empty(m * T, device="cuda")
+    t.backward(dev(G), [dev(x)], gx, gt)
+    t.backward(dev(G), [dev(x)], gx1, None)
+    t.backward(dev(G), [dev(x)], None, gt1)
+    t.sync_status()
+    g64 = G.astype(np.float64)
+    dX, dH = O.task_vjp(tk, [xv], g64)
+    sX, sH = O.task_vjp(_abs_chain([tk])[0], [np.abs(xv)], np.abs(g64))
+    assert_fir_close(host(gx), dX, sX, RTOL, "dX")
+    assert_fir_close(host(gt).reshape(m, T), dH, sH, RTOL, "dH")
+    np.testing.assert_array_equal(host(gx1), host(gx))
+    np.testing.assert_array_equal(host(gt1), host(gt))
