@@ -1810,10 +1810,10 @@ arol_status sep_pass_backward(arol_task t, size_t ii, const SepPassDev& p, int64
     const int Hin = (int)ihw[0], Win = (int)ihw[1], Hout = (int)ohw[0], Wout = (int)ohw[1];
     arol_status st = AROL_OK;
     if (!gx && !gt) return AROL_OK;
-    if (sep_bwd_supported(p, F, Hin, Win, x_dt, x, g, gx, gt != nullptr)) {
-        const int nb = sep_bwd_blocks(p, x_dt, gt != nullptr);
-        if (gt && (st = ensure_partials(t, (int64_t)nb * p.m * p.T, s)) != AROL_OK) return st;
-        AROL_CUDA(launch_sep_bwd(p, F, Hin, Win, tp, x, x_dt, g, gx, t->partials, nb, gt, s), "backward launch");
+    SepBwdPlan plan;
+    if (sep_bwd_plan(p, F, Hin, Win, x_dt, x, g, gx, gt != nullptr, &plan)) {
+        if (gt && (st = ensure_partials(t, (int64_t)plan.blocks * p.m * p.T, s)) != AROL_OK) return st;
+        AROL_CUDA(launch_sep_bwd(plan, p, F, Hin, Win, tp, x, x_dt, g, gx, t->partials, gt, s), "backward launch");
         return AROL_OK;
     }
     if (gx) AROL_CUDA(launch_sep_adjoint(p, F, Hin, Win, Hout, Wout, tp, g, gx, s), "backward launch");

@@ -200,14 +200,23 @@ bool sep_dh_supported(const SepPassDev& p);
 cudaError_t launch_sep_dh(const SepPassDev& p, int64_t F, int Hin, int Win, int Hout, int Wout, const void* x, int x_dt,
                           const float* gy, float* partials, float* grad_taps, cudaStream_t s);   // x_dt: arol_dtype
 // Backward of one separable pass in one sweep (k_sepbwd.cu): dX (gx, may be
-// null) and the tap gradients (grad_taps, may be null; nblocks x m T
-// partials, nblocks = sep_bwd_blocks(p)), for repetitions that tile the axis
-// and data that fit the kernels' forms (sep_bwd_supported).
-bool sep_bwd_supported(const SepPassDev& p, int64_t F, int Hin, int Win, int x_dt, const void* x, const float* gy,
-                       const float* gx, bool want_taps);
-int sep_bwd_blocks(const SepPassDev& p, int x_dt, bool want_taps);
-cudaError_t launch_sep_bwd(const SepPassDev& p, int64_t F, int Hin, int Win, const float* taps, const void* x,
-                           int x_dt, const float* gy, float* gx, float* partials, int nblocks, float* grad_taps,
+// null) and the tap gradients (grad_taps, may be null; plan.blocks x m T
+// partials), for repetitions that tile the axis and data that fit one of the
+// kernels' forms (sep_bwd_plan false otherwise).
+struct SepBwdPlan {
+    int form;       // 0 column passes; 1 row passes, staged rows; 2 row passes in 16-word regions
+    int bin;        // the kernel's (windows, outputs, taps) bank
+    int ss;         // compile-time step (0: the pass's)
+    int mm;         // outputs bank of form 2
+    bool async;     // form 1: rows copied ahead
+    size_t smem;    // dynamic shared memory per block
+    int threads;
+    int blocks;     // grid: one row of tap-gradient partials per block
+};
+bool sep_bwd_plan(const SepPassDev& p, int64_t F, int Hin, int Win, int x_dt, const void* x, const float* gy,
+                  const float* gx, bool want_taps, SepBwdPlan* plan);
+cudaError_t launch_sep_bwd(const SepBwdPlan& plan, const SepPassDev& p, int64_t F, int Hin, int Win, const float* taps,
+                           const void* x, int x_dt, const float* gy, float* gx, float* partials, float* grad_taps,
                            cudaStream_t s);
 // Sum of nblocks rows of npairs partials, in a fixed order (k_tiler.cu).
 cudaError_t launch_tap_reduce(const float* partials, int nblocks, int npairs, float* out, cudaStream_t s);

@@ -96,9 +96,10 @@ __device__ __forceinline__ void unstage_row(float* dst, const float* src, int n)
 
 // The block's m x T tap sums into its row of partials, in a fixed order
 // (lanes by shuffles, then warps in order).
-template <int MM, int TT>
+template <int MM, int TT, int NT = kBwThreads>
 __device__ __forceinline__ void block_taps(const float (&acc)[MM][TT], int m, int T, float* partials) {
-    __shared__ float red[kBwThreads / 32][MM * TT];
+    static_assert(NT % 32 == 0, "whole warps");
+    __shared__ float red[NT / 32][MM * TT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
 #pragma unroll
@@ -114,7 +115,7 @@ __device__ __forceinline__ void block_taps(const float (&acc)[MM][TT], int m, in
     for (int pp = threadIdx.x; pp < m * T; pp += blockDim.x) {
         const int j = pp / T, k = pp - j * T;
         float v = 0.f;
-        for (int w = 0; w < kBwThreads / 32; ++w) v += red[w][j * TT + k];
+        for (int w = 0; w < NT / 32; ++w) v += red[w][j * TT + k];
         partials[(int64_t)blockIdx.x * (m * T) + pp] = v;
     }
 }
@@ -277,6 +278,149 @@ __global__ void __launch_bounds__(kBwThreads) sep_row_bwd_kernel(const SepPassDe
     if (partials) block_taps<MM, TT>(acc, m, T, partials);
 }
 
+// Row pass in 16-word regions: step SS in {2, 4, 8}, rows of n_in = 16 k
+// words, origin o = 16 k', X in f32, dY rows 16-byte aligned.  Thread t of a
+// row takes the home region of words h0 .. h0 + 15, h0 = (o + 16 t) mod n_in:
+// repetitions NR t .. NR t + NR - 1 (NR = 16 / SS), their windows (XW words
+// from h0) and their dY words (plus those of the QQ - 1 repetitions before,
+// whose windows also reach the region).  Every index below a region's start
+// is a compile-time constant: the window and the 16 dX words move as 16-byte
+// shared loads and stores, the taps sit in registers.
+//
+// Staged X and dX rows are swizzled by 16-byte units: unit f of a row lives
+// at unit (f & ~3) | ((f & 3) ^ ((f >> 3) & 3)), so the 8 lanes of a
+// quarter-warp that read unit v of 8 consecutive regions (a stride of 64
+// bytes) hit 8 distinct 16-byte bank groups.  The dY row is stored plainly
+// after 16 halo words holding the row's last m (Q - 1) words (the windows of
+// repetitions 0 .. Q - 2 that wrap to the row's end), and 16 halo words after
+// the X row repeat its first 16 words (windows that run past the row's end).
+constexpr int kVecThreads = 128;
+__device__ __forceinline__ int swz(int f) { return (f & ~3) | ((f & 3) ^ ((f >> 3) & 3)); }
+
+template <int SS, int MM, int TT>
+__global__ void __launch_bounds__(kVecThreads) sep_row_bwd_vec_kernel(const SepPassDev p, int64_t rows,
+                                                                      const float* __restrict__ taps,
+                                                                      const float* __restrict__ x,
+                                                                      const float* __restrict__ gy,
+                                                                      float* __restrict__ gx,
+                                                                      float* __restrict__ partials) {
+    constexpr int NR = 16 / SS;                     // repetitions per region
+    constexpr int QQ = (TT + SS - 1) / SS;          // repetitions whose windows reach a word, at most
+    constexpr int NG = NR + QQ - 1;                 // repetitions whose dY a region reads
+    constexpr int XW = (16 - SS + TT + 3) & ~3;     // window words of a region
+    static_assert(XW <= 32 && MM * (QQ - 1) <= 16, "a window within two regions, the dY halo within 16 words");
+    extern __shared__ __align__(16) float vsm[];
+    const int m = p.m, T = p.T, Win = p.n_in, Wout = p.n_out;
+    const int Q = (T + SS - 1) / SS;
+    const int nreg = Win >> 4, W4 = Win >> 2, Wo4 = Wout >> 2;
+    const int halo = m * (Q - 1);                   // dY words before the row
+    float* hs = vsm;                                // taps, m x T
+    const int gsz = 16 + Wout, stage = gsz + Win + 16;
+    float* const st0 = hs + kBwTaps;                // kBwStages stages: [16 | dY row] [X row | 16]
+    float* const ds = st0 + kBwStages * stage;      // the dX row
+    for (int i = threadIdx.x; i < m * T; i += blockDim.x) hs[i] = __ldg(taps + i);
+    float acc[MM][TT];
+#pragma unroll
+    for (int j = 0; j < MM; ++j)
+#pragma unroll
+        for (int k = 0; k < TT; ++k) acc[j][k] = 0.f;
+    const int64_t G = gridDim.x;
+    auto stage_rows = [&](int64_t rr, float* st) {
+        const float* gr = gy + rr * Wout;
+        float* gs = st + 16;
+        for (int f = threadIdx.x; f < Wo4; f += blockDim.x) ptx::cp_async16(gs + 4 * f, gr + 4 * f);
+        for (int e = threadIdx.x; e < halo; e += blockDim.x) ptx::cp_async4(gs - halo + e, gr + Wout - halo + e);
+        if (partials) {
+            const float* xr = x + rr * Win;
+            float* xs = st + gsz;
+            for (int f = threadIdx.x; f < W4 + 4; f += blockDim.x)
+                ptx::cp_async16(xs + 4 * swz(f), xr + 4 * (f < W4 ? f : f - W4));
+        }
+    };
+    for (int i = 0; i < kBwStages - 1; ++i) {
+        const int64_t rr = blockIdx.x + i * G;
+        if (rr < rows) stage_rows(rr, st0 + i * stage);
+        ptx::cp_async_commit();
+    }
+    __syncthreads();   // the taps
+    float hr[MM][TT];  // zero past m and T
+#pragma unroll
+    for (int j = 0; j < MM; ++j)
+#pragma unroll
+        for (int k = 0; k < TT; ++k) hr[j][k] = j < m && k < T ? hs[j * T + k] : 0.f;
+    int b = 0;
+    for (int64_t row = blockIdx.x; row < rows; row += G) {
+        const int64_t ahead = row + (kBwStages - 1) * G;
+        if (ahead < rows) stage_rows(ahead, st0 + (b == 0 ? kBwStages - 1 : b - 1) * stage);
+        ptx::cp_async_commit();
+        ptx::cp_async_wait_group<kBwStages - 1>();
+        __syncthreads();
+        const float* gs = st0 + b * stage + 16;
+        const float* xs = st0 + b * stage + gsz;
+        if (++b == kBwStages) b = 0;
+        for (int t = threadIdx.x; t < nreg; t += blockDim.x) {
+            int h0 = p.o + 16 * t;
+            if (h0 >= Win) h0 -= Win;
+            const int u0 = h0 >> 2;                 // the region's first 16-byte unit
+            // dY of repetitions NR t - (QQ - 1) + i (below -(Q - 1): unused, zero)
+            float g[NG][MM];
+            const float* gb = gs + m * (NR * t - (QQ - 1));
+#pragma unroll
+            for (int i = 0; i < NG; ++i)
+#pragma unroll
+                for (int j = 0; j < MM; ++j) g[i][j] = j < m && i >= QQ - Q ? gb[m * i + j] : 0.f;
+            if (gx) {
+                // home word w = SS i + d gets taps k = d + SS q < T against
+                // the dY of repetition i - q
+                float o4[16];
+#pragma unroll
+                for (int i = 0; i < NR; ++i)
+#pragma unroll
+                    for (int d = 0; d < SS; ++d) {
+                        float a = 0.f;
+#pragma unroll
+                        for (int q = 0; q < QQ; ++q) {
+                            const int k = d + SS * q;
+                            if (k < TT && k < T) {
+#pragma unroll
+                                for (int j = 0; j < MM; ++j) a = fmaf(hr[j][k < TT ? k : 0], g[i + QQ - 1 - q][j], a);
+                            }
+                        }
+                        o4[SS * i + d] = a;
+                    }
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    *reinterpret_cast<float4*>(ds + 4 * swz(u0 + v)) =
+                        make_float4(o4[4 * v], o4[4 * v + 1], o4[4 * v + 2], o4[4 * v + 3]);
+            }
+            if (partials) {
+                float xw[XW];
+#pragma unroll
+                for (int v = 0; v < XW / 4; ++v) {
+                    const float4 q4 = *reinterpret_cast<const float4*>(xs + 4 * swz(u0 + v));
+                    xw[4 * v] = q4.x;
+                    xw[4 * v + 1] = q4.y;
+                    xw[4 * v + 2] = q4.z;
+                    xw[4 * v + 3] = q4.w;
+                }
+#pragma unroll
+                for (int i = 0; i < NR; ++i)
+#pragma unroll
+                    for (int j = 0; j < MM; ++j)
+#pragma unroll
+                        for (int k = 0; k < TT; ++k) acc[j][k] = fmaf(g[i + QQ - 1][j], xw[SS * i + k], acc[j][k]);
+            }
+        }
+        __syncthreads();
+        if (gx) {
+            float4* dst = reinterpret_cast<float4*>(gx + row * Win);
+            for (int f = threadIdx.x; f < W4; f += blockDim.x) dst[f] = *reinterpret_cast<const float4*>(ds + 4 * swz(f));
+        }
+    }
+    ptx::cp_async_wait_all();
+    if (partials) block_taps<MM, TT, kVecThreads>(acc, m, T, partials);
+}
+
 // Division by d of values below 2^31 by multiply and shift.
 struct BDiv {
     uint64_t mul;
@@ -397,14 +541,19 @@ size_t row_smem(const SepPassDev& p, bool async) {
     return sizeof(float) * ((size_t)kBwTaps + (async ? kBwStages : 1) * pair + spad_len(p.n_in));
 }
 
+size_t vec_smem(const SepPassDev& p) {
+    return sizeof(float) * ((size_t)kBwTaps + (size_t)kBwStages * (32 + p.n_out + p.n_in) + p.n_in);
+}
+
 template <typename K>
-int blocks_of(K kernel, size_t smem) {
+int blocks_of(K kernel, int threads, size_t smem) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kBwThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem);
     return device_sm_count() * (n > 0 ? n : 1);
 }
 
 using RowKernel = void (*)(const SepPassDev, int64_t, const float*, const void*, int, const float*, float*, float*);
+using VecKernel = void (*)(const SepPassDev, int64_t, const float*, const float*, const float*, float*, float*);
 using ColKernel = void (*)(const SepPassDev, uint32_t, int, BDiv, BDiv, const float*, const void*, int, const float*,
                            float*, float*);
 
@@ -427,75 +576,114 @@ RowKernel row_kernel(int bin, bool async, int ss) {
     return bin == 0 ? sep_row_bwd_kernel<2, 2, 8, false, 0>
                     : bin == 1 ? sep_row_bwd_kernel<2, 4, 8, false, 0> : sep_row_bwd_kernel<4, 4, 16, false, 0>;
 }
+
+// The 16-word-region forms: (step, bank) = (2, m <= 2), (4 or 8, m <= 4), T <= 8.
+VecKernel vec_kernel(int ss, int mm) {
+    if (ss == 2) return sep_row_bwd_vec_kernel<2, 2, 8>;
+    if (ss == 4) return mm == 2 ? sep_row_bwd_vec_kernel<4, 2, 8> : sep_row_bwd_vec_kernel<4, 4, 8>;
+    return mm == 2 ? sep_row_bwd_vec_kernel<8, 2, 8> : sep_row_bwd_vec_kernel<8, 4, 8>;
+}
 ColKernel col_kernel(int bin) { return bin == 0 ? sep_col_bwd_kernel<2, 2, 8> : sep_col_bwd_kernel<2, 4, 8>; }
 
 constexpr size_t kRowSmemMax = 96 * 1024;
 
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+
+void opt_in_smem() {
+    static bool done = false;
+    if (done) return;
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 2; ++a)
+            for (int ss : {0, 2, 4, 8})
+                cudaFuncSetAttribute(row_kernel(b, a == 1, ss), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRowSmemMax);
+    for (int ss : {2, 4, 8})
+        for (int mm : {2, 4})
+            cudaFuncSetAttribute(vec_kernel(ss, mm), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmemMax);
+    done = true;
+}
+
 }  // namespace
 
-bool sep_bwd_supported(const SepPassDev& p, int64_t F, int Hin, int Win, int x_dt, const void* x, const float* gy,
-                       const float* gx, bool want_taps) {
+bool sep_bwd_plan(const SepPassDev& p, int64_t F, int Hin, int Win, int x_dt, const void* x, const float* gy,
+                  const float* gx, bool want_taps, SepBwdPlan* plan) {
     if ((int64_t)p.S * p.R != p.n_in || F < 1) return false;
     const int bin = bwd_bin(p, p.axis == 0);
     if (bin < 0) return false;
-    if (p.axis == 1) return row_smem(p, row_async(x_dt, want_taps)) <= kRowSmemMax;
+    SepBwdPlan pl{};
+    pl.bin = bin;
+    if (p.axis == 1) {
+        opt_in_smem();
+        const bool vec = (p.S == 2 ? p.m <= 2 : (p.S == 4 || p.S == 8) && p.m <= 4) && p.T <= 8 && p.n_in % 16 == 0 &&
+                         p.o % 16 == 0 && p.n_out % 4 == 0 && (x_dt == 0 || !want_taps) && aligned16(gy) &&
+                         aligned16(gx) && (!want_taps || aligned16(x)) && vec_smem(p) <= kRowSmemMax;
+        if (vec) {
+            pl.form = 2;
+            pl.ss = p.S;
+            pl.mm = p.m <= 2 ? 2 : 4;
+            pl.smem = vec_smem(p);
+            pl.threads = kVecThreads;
+            static int cache[9][5] = {};
+            static size_t cache_smem[9][5] = {};
+            int& c = cache[pl.ss][pl.mm];
+            if (!c || cache_smem[pl.ss][pl.mm] != pl.smem) {
+                c = blocks_of(vec_kernel(pl.ss, pl.mm), kVecThreads, pl.smem);
+                cache_smem[pl.ss][pl.mm] = pl.smem;
+            }
+            pl.blocks = c;
+        } else {
+            pl.form = 1;
+            pl.async = row_async(x_dt, want_taps);
+            pl.ss = row_step(bin, pl.async, p.S);
+            pl.smem = row_smem(p, pl.async);
+            if (pl.smem > kRowSmemMax) return false;
+            pl.threads = kBwThreads;
+            static int cache[3][2][9] = {};
+            static size_t cache_smem[3][2][9] = {};
+            int& c = cache[bin][pl.async][pl.ss];
+            if (!c || cache_smem[bin][pl.async][pl.ss] != pl.smem) {
+                c = blocks_of(row_kernel(bin, pl.async, pl.ss), kBwThreads, pl.smem);
+                cache_smem[bin][pl.async][pl.ss] = pl.smem;
+            }
+            pl.blocks = c;
+        }
+        *plan = pl;
+        return true;
+    }
     // column pass: 16-byte rows of 4-column groups
     const uintptr_t xa = x_dt == 0 ? 15 : 7;
-    if (Win % 4 || (reinterpret_cast<uintptr_t>(gy) & 15) || (reinterpret_cast<uintptr_t>(gx) & 15) ||
-        (want_taps && (reinterpret_cast<uintptr_t>(x) & xa)))
+    if (Win % 4 || !aligned16(gy) || !aligned16(gx) || (want_taps && (reinterpret_cast<uintptr_t>(x) & xa)))
         return false;
-    return F * p.R * (Win / 4) < (int64_t)1 << 31 && F * (int64_t)Hin * Win < (int64_t)1 << 40;
-}
-
-int sep_bwd_blocks(const SepPassDev& p, int x_dt, bool want_taps) {
-    const int bin = bwd_bin(p, p.axis == 0);
-    if (bin < 0) return 0;
-    if (p.axis == 1) {
-        static bool opted = false;
-        if (!opted) {
-            for (int b = 0; b < 3; ++b)
-                for (int a = 0; a < 2; ++a)
-                    for (int ss : {0, 2, 4, 8})
-                        cudaFuncSetAttribute(row_kernel(b, a == 1, ss), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kRowSmemMax);
-            opted = true;
-        }
-        // per (bin, async, step form): the occupancy at this shared-memory size
-        static int cache[3][2][9] = {};
-        static size_t cache_smem[3][2][9] = {};
-        const bool async = row_async(x_dt, want_taps);
-        const int ss = row_step(bin, async, p.S);
-        const size_t smem = row_smem(p, async);
-        if (!cache[bin][async][ss] || cache_smem[bin][async][ss] != smem) {
-            cache[bin][async][ss] = blocks_of(row_kernel(bin, async, ss), smem);
-            cache_smem[bin][async][ss] = smem;
-        }
-        return cache[bin][async][ss];
-    }
+    if (F * p.R * (Win / 4) >= (int64_t)1 << 31 || F * (int64_t)Hin * Win >= (int64_t)1 << 40) return false;
+    pl.form = 0;
+    pl.threads = kBwThreads;
     static int ccache[2] = {0, 0};
-    if (!ccache[bin]) ccache[bin] = blocks_of(col_kernel(bin), 0);
-    return ccache[bin];
+    if (!ccache[bin]) ccache[bin] = blocks_of(col_kernel(bin), kBwThreads, 0);
+    pl.blocks = ccache[bin];
+    *plan = pl;
+    return true;
 }
 
-cudaError_t launch_sep_bwd(const SepPassDev& p, int64_t F, int Hin, int Win, const float* taps, const void* x,
-                           int x_dt, const float* gy, float* gx, float* partials, int nblocks, float* grad_taps,
+cudaError_t launch_sep_bwd(const SepBwdPlan& pl, const SepPassDev& p, int64_t F, int Hin, int Win, const float* taps,
+                           const void* x, int x_dt, const float* gy, float* gx, float* partials, float* grad_taps,
                            cudaStream_t s) {
-    const int bin = bwd_bin(p, p.axis == 0);
-    if (bin < 0 || nblocks < 1) return cudaErrorInvalidValue;
+    if (pl.blocks < 1) return cudaErrorInvalidValue;
     float* part = grad_taps ? partials : nullptr;
-    if (p.axis == 1) {
-        const bool async = row_async(x_dt, grad_taps != nullptr);
-        row_kernel(bin, async, row_step(bin, async, p.S))<<<nblocks, kBwThreads, row_smem(p, async), s>>>(p, F * Hin, taps, x, x_dt, gy, gx,
-                                                                               part);
+    if (pl.form == 2) {
+        vec_kernel(pl.ss, pl.mm)<<<pl.blocks, kVecThreads, pl.smem, s>>>(p, F * Hin, taps,
+                                                                         static_cast<const float*>(x), gy, gx, part);
+    } else if (pl.form == 1) {
+        row_kernel(pl.bin, pl.async, pl.ss)<<<pl.blocks, kBwThreads, pl.smem, s>>>(p, F * Hin, taps, x, x_dt, gy, gx,
+                                                                                   part);
     } else {
         const uint32_t W4 = (uint32_t)(Win / 4);
         const uint32_t items = (uint32_t)(F * p.R * (int64_t)W4);
-        col_kernel(bin)<<<nblocks, kBwThreads, 0, s>>>(p, items, Win, bdiv_of(W4), bdiv_of((uint32_t)p.R), taps, x,
-                                                       x_dt, gy, gx, part);
+        col_kernel(pl.bin)<<<pl.blocks, kBwThreads, 0, s>>>(p, items, Win, bdiv_of(W4), bdiv_of((uint32_t)p.R), taps,
+                                                            x, x_dt, gy, gx, part);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !grad_taps) return e;
-    return launch_tap_reduce(partials, nblocks, p.m * p.T, grad_taps, s);
+    return launch_tap_reduce(partials, pl.blocks, p.m * p.T, grad_taps, s);
 }
 
 }  // namespace arol

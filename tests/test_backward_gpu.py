@@ -248,10 +248,26 @@ def test_backward_one_sweep_pass(arol, axis, T, m, S, width, dt):
     steps 2, 4 and 8 in their step-specialised forms), origin 5, inputs in
     f32, bfloat16 or IEEE half, against the oracle.  A
     call asking for dX alone or the tap gradients alone gives the same bits."""
+    _one_sweep_case(arol, axis, T, m, S, width, dt, 5)
+
+
+@pytest.mark.parametrize("T,m,S,width,origin,dt", [
+    (5, 2, 4, 64, 16, "f32"), (8, 3, 8, 128, 0, "f32"), (6, 2, 2, 96, 32, "f32"), (7, 4, 4, 48, 0, "f32"),
+    (5, 2, 4, 64, 0, "bf16")])
+def test_backward_row_pass_regions(arol, T, m, S, width, origin, dt):
+    """Row passes on rows of a multiple of 16 words, origin a multiple of 16,
+    steps 2, 4 and 8: the 16-word-region form (swizzled 16-byte shared loads
+    and stores, halos for the windows that wrap at either end of a row),
+    against the oracle.  bfloat16 X: the tap gradients take the staged-row
+    form and dX alone the region form, with the same dX bits."""
+    _one_sweep_case(arol, 1, T, m, S, width, dt, origin)
+
+
+def _one_sweep_case(arol, axis, T, m, S, width, dt, origin):
     g = W.rng(250 + T + width)
     shape = (2, 36, width)
     n = shape[2] if axis == 1 else shape[1]
-    tk = W.separable_pass(shape, axis, T, m, S, 5, n // S, (g.standard_normal((m, T)) / T).astype(np.float32))
+    tk = W.separable_pass(shape, axis, T, m, S, origin, n // S, (g.standard_normal((m, T)) / T).astype(np.float32))
     xf = g.standard_normal(shape).astype(np.float32)
     if dt == "bf16":
         x = W.bf16_round(xf)
