@@ -438,8 +438,9 @@ def bench_chain_5to2(A, torch, stream, flush, reps, hbm):
     out["staged_ms"] = statistics.median(time_each_flushed(run, reps, stream, flush))
     out["fused_speedup"] = out["staged_ms"] / ms
     out["roofline"] = {"bound": "hbm", "achieved": out["gbs"], "peak": hbm, "unit": "GB/s", "frac": out["frac_of_hbm"]}
-    # the chain's backward (recomputed intermediate, then the adjoint task by
-    # task) on 16 frames: loss sum(G * Y)
+    # the chain's backward on 16 frames (the intermediate recomputed by the
+    # row pass, then one sweep per pass for dX and the tap gradients): loss
+    # sum(G * Y)
     chain16, xs16 = W.config1_5to2(frames=16)
     c = A.Chain(chain16)
     x16 = torch.from_numpy(xs16[0]).cuda()
