@@ -1893,10 +1893,14 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
         return backward_generic_task(t, 0, taps, saved_in[0], (const float*)grad_out, (float*)grad_in, grad_taps, s);
     }
     // Unfused chain: recompute the intermediates, then reverse task by task.
+    // Separable passes read a pass's input only for its tap gradients, so
+    // without tap gradients nothing is recomputed.
     const size_t n = t->descs.size();
     if (!t->rc_checked) build_recompute_tasks(t);
+    if (t->grad_mids.size() < n) t->grad_mids.resize(n, nullptr);
+    const bool need_mids = !(t->sd_ok && !grad_taps);
     const void* cur = saved_in[0];
-    for (size_t i = 0; i + 1 < n; ++i) {
+    for (size_t i = 0; need_mids && i + 1 < n; ++i) {
         if ((st = dev_alloc(t, &t->mids[i], array_bytes(t->descs[i].out[0]), "cudaMalloc(chain intermediate)")) != AROL_OK)
             return st;
         if (reps_of(t->descs[i]) > 0) {
@@ -1911,10 +1915,9 @@ arol_status arol_task_backward(arol_task t, const void* grad_out, const void* co
         }
         cur = t->mids[i];
     }
-    if (t->grad_mids.size() < n) t->grad_mids.resize(n, nullptr);
     const float* g = (const float*)grad_out;
     for (size_t ii = n; ii-- > 0;) {
-        const void* xin = ii == 0 ? saved_in[0] : t->mids[ii - 1];
+        const void* xin = ii == 0 ? saved_in[0] : need_mids ? t->mids[ii - 1] : nullptr;
         float* gx = nullptr;
         if (ii == 0) gx = (float*)grad_in;
         else {

@@ -114,3 +114,36 @@ def test_backward_of_random_separable_chains(arol):
         for dH, sH in zip(dHs, sHs):
             assert_fir_close(got[off:off + dH.size].reshape(dH.shape), dH, sH, RTOL, f"chain {n} dH")
             off += dH.size
+
+
+@pytest.mark.parametrize("mh,Th,Sh,oh", [(1, 3, 2, 0), (2, 5, 4, 3), (4, 8, 4, 1), (2, 8, 3, 39)])
+def test_row_column_chain_backward_partial_requests(arol, mh, Th, Sh, oh):
+    """A row pass (1, 2 or 4 outputs per repetition, windows that wrap) then
+    a column pass whose repetitions tile the rows, against the C oracle's
+    adjoint.  dX alone (no tap gradients: the intermediate is not
+    recomputed) and the tap gradients alone give the same bits as the call
+    asking for both."""
+    g = W.rng(420 + mh + Th)
+    F, H, Wx, Rh = 2, 48, 40, 12
+    row = W.separable_pass((F, H, Wx), 1, Th, mh, Sh, oh, Rh, (g.standard_normal((mh, Th)) / Th).astype(np.float32))
+    col = W.separable_pass((F, H, mh * Rh), 0, 5, 2, 4, 4, H // 4, (g.standard_normal((2, 5)) / 5).astype(np.float32))
+    chain = [row, col]
+    x = g.standard_normal((F, H, Wx)).astype(np.float32)
+    G = g.standard_normal(col["outputs"][0]["shape"]).astype(np.float32)
+    c = arol.Chain(chain)
+    ntaps = mh * Th + 10
+    gx, gx1 = torch.empty(x.shape, device="cuda"), torch.empty(x.shape, device="cuda")
+    gt, gt1 = torch.empty(ntaps, device="cuda"), torch.empty(ntaps, device="cuda")
+    c.backward(dev(G), [dev(x)], gx, gt)
+    c.backward(dev(G), [dev(x)], gx1, None)
+    c.backward(dev(G), [dev(x)], None, gt1)
+    c.sync_status()
+    g64 = G.astype(np.float64)
+    dX, dHs = C.chain_vjp(chain, [x], g64)
+    sX, sHs = C.chain_vjp(_abs_chain(chain), [np.abs(x)], np.abs(g64))
+    assert_fir_close(host(gx), dX, sX, RTOL, "dX")
+    got = host(gt)
+    assert_fir_close(got[:mh * Th].reshape(mh, Th), dHs[0], sHs[0], RTOL, "dH row pass")
+    assert_fir_close(got[mh * Th:].reshape(2, 5), dHs[1], sHs[1], RTOL, "dH column pass")
+    np.testing.assert_array_equal(host(gx1), host(gx))
+    np.testing.assert_array_equal(host(gt1), got)
