@@ -462,9 +462,20 @@ def bench_chain_5to2(A, torch, stream, flush, reps, hbm):
 
 def bench_config0_scaled(A, torch, stream, flush, reps, hbm):
     """The 64 x 64 task's step-4 wrapping 8 -> 3 tiler on 64 x 1080 x 1920 (a
-    row-FIR task: the row-FIR batch kernel, as a one-member batch)."""
+    row-FIR task: the library's choice, the row FIR in 16-word regions), and
+    the same task as a one-member batch (the row-FIR tile kernel)."""
     tk, xs = W.config0_scaled()
-    return _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, "rowfir_batch_kernel")[2]
+    _, _, out = _task_gbs(A, torch, stream, flush, reps, hbm, tk, xs, "rowfir_region_kernel")
+    b = A.Batch([tk])
+    ins = [torch.from_numpy(x).cuda() for x in xs]
+    outs = b.empty_outputs()
+    for _ in range(3):
+        b.run(ins, outs)
+    out["tiles_ms"] = statistics.median(time_each_flushed(lambda: b.run(ins, outs), reps, stream, flush))
+    b.sync_status()
+    out["tiles_frac_of_hbm"] = out["unique_bytes"] / (out["tiles_ms"] * 1e-3) / 1e9 / hbm
+    out["roofline"] = {"bound": "hbm", "achieved": out["gbs"], "peak": hbm, "unit": "GB/s", "frac": out["frac_of_hbm"]}
+    return out
 
 
 def bench_generic(A, torch, stream, flush, reps, hbm):

@@ -136,7 +136,11 @@ typedef struct {
     double flops;              /* arithmetic of the elementary tasks (2 per multiply-add) */
     int32_t path;              /* a single task with kernel 0 and taps given on the host: 0 per-repetition
                                   walk, 1 row-FIR tiles, 2 column-FIR tiles, 3 2-D window tiles,
-                                  4 register-blocked stencil (3x3 or 5x5, steps 1, one output); -1 otherwise */
+                                  4 register-blocked stencil (3x3 or 5x5, steps 1, one output),
+                                  5 row FIR in 16-word regions (repetitions tiling each row, step 2, 4
+                                  or 8, T <= 8, m <= 4, rows of a multiple of 16 words, origin a
+                                  multiple of 16, output columns from 0; row-FIR tiles when a buffer
+                                  is not 16-byte aligned); -1 otherwise */
     int32_t reserved_;
 } arol_task_info_t;
 

@@ -945,6 +945,10 @@ struct arol_task_s {
     // row/column-FIR tasks and unfused chains run as a one-member batch
     arol_batch ib = nullptr;
     bool ib_checked = false;
+    // a row-FIR task in 16-word regions (rr_ok)
+    bool rr_ok = false;
+    int rr_S = 0, rr_T = 0, rr_M = 0, rr_W = 0, rr_o = 0;
+    int64_t rr_rows = 0;
     // fused downscaler
     int64_t ds_frames = 0;
     int ds_H = 0, ds_W = 0;
@@ -1095,6 +1099,29 @@ arol_status validate_desc(const arol_task_desc& d) {
     return check_partition(d.out[0], d.out_tiler[0], d.rep_rank, d.rep);
 }
 
+// A single row-FIR task that the region kernel takes (host only): one output
+// row per input row, repetitions tiling the rows, output columns from 0.
+void plan_row_region(arol_task t) {
+    t->rr_ok = false;
+    const arol_task_desc& d = t->descs[0];
+    if (d.elem != AROL_ELEM_FIR || d.n_in != 1) return;
+    const TaskDev td = make_taskdev(d, true);
+    if (!td.rowfir || td.in_dt != kStF32 || td.out_dt != kStF32) return;
+    const int64_t H = td.in.shape[0], W = td.in.shape[1], Ho = td.out.shape[0], Wo = td.out.shape[1];
+    const int64_t R0 = td.rep[2], R1 = td.rep[3];
+    if (R0 != H || Ho != H || td.in.origin[0] != 0 || td.out.origin[0] != 0 || td.out.origin[1] != 0) return;
+    if ((int64_t)td.step * R1 != W) return;
+    const int64_t o = td.in.origin[1];
+    if (!rowfir_region_supported(td.step, td.T, td.m, W, Wo, o, R0)) return;
+    t->rr_ok = true;
+    t->rr_S = td.step;
+    t->rr_T = td.T;
+    t->rr_M = td.m;
+    t->rr_W = (int)W;
+    t->rr_o = (int)o;
+    t->rr_rows = R0;
+}
+
 void fill_info_single(arol_task t) {
     const arol_task_desc& d = t->descs[0];
     arol_task_info_t& in = t->info;
@@ -1116,7 +1143,7 @@ void fill_info_single(arol_task t) {
     in.path = -1;
     if (t->kernel == 0 && d.elem != AROL_ELEM_MATMUL) {
         const TaskDev td = make_taskdev(d, true);
-        in.path = td.rowfir ? 1 : td.colfir ? 2 : td.fir2d ? (fir2d_uses_stencil(td) ? 4 : 3) : 0;
+        in.path = t->rr_ok ? 5 : td.rowfir ? 1 : td.colfir ? 2 : td.fir2d ? (fir2d_uses_stencil(td) ? 4 : 3) : 0;
     }
     in.reserved_ = 0;
 }
@@ -1208,10 +1235,12 @@ arol_status arol_task_create(const arol_task_desc* desc, arol_task* out) {
         t->mm_N = N;
         t->mm_K = K;
     }
+    if (t->kernel == 0) plan_row_region(t);
     fill_info_single(t);
     if (log_enabled()) {
         const TaskDev td = make_taskdev(t->descs[0], true);
         const char* path = t->kernel == 2 ? (M % 256 == 0 && N % 256 == 0 ? "tcgen05 matmul, CTA pairs" : "tcgen05 matmul")
+                           : t->rr_ok ? "row FIR (16-word regions)"
                            : td.rowfir ? "row FIR (staged row tiles)"
                            : td.colfir ? "column FIR (column tiles)"
                            : td.fir2d ? (fir2d_uses_stencil(td) ? "register-blocked stencil" : "2-D window FIR")
@@ -1546,6 +1575,12 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
             if ((st = ensure_err(t, s)) != AROL_OK) return st;
             AROL_CUDA(launch_matmul_tc(in[0], in[1], (float*)out[0], t->mm_M, t->mm_N, t->mm_K, t->err_flag, s),
                       "matmul kernel launch");
+            return AROL_OK;
+        }
+        if (t->rr_ok && aligned16(in[0]) && aligned16(out[0])) {
+            AROL_CUDA(launch_rowfir_region(t->rr_S, t->rr_T, t->rr_M, t->rr_rows, t->rr_W, t->rr_o, taps,
+                                           (const float*)in[0], (float*)out[0], s),
+                      "row-FIR region kernel launch");
             return AROL_OK;
         }
         bool used = false;

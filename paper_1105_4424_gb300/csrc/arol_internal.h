@@ -218,6 +218,13 @@ bool sep_bwd_plan(const SepPassDev& p, int64_t F, int Hin, int Win, int x_dt, co
 cudaError_t launch_sep_bwd(const SepBwdPlan& plan, const SepPassDev& p, int64_t F, int Hin, int Win, const float* taps,
                            const void* x, int x_dt, const float* gy, float* gx, float* partials, float* grad_taps,
                            cudaStream_t s);
+// Row FIR in 16-word regions (k_rowregion.cu): repetitions that tile each row
+// (S R = W), S in {2, 4, 8}, T <= 8, M <= 4 (2 for S = 2), W a multiple of
+// 16, origin o a multiple of 16, output rows of M R words from column 0, one
+// per input row; x and y 16-byte aligned.
+bool rowfir_region_supported(int S, int T, int M, int64_t W, int64_t Wout, int64_t o, int64_t rows);
+cudaError_t launch_rowfir_region(int S, int T, int M, int64_t rows, int W, int o, const float* taps, const float* x,
+                                 float* y, cudaStream_t s);
 // Sum of nblocks rows of npairs partials, in a fixed order (k_tiler.cu).
 cudaError_t launch_tap_reduce(const float* partials, int nblocks, int npairs, float* out, cudaStream_t s);
 size_t sepchain_smem(const SepChainDev& d);

@@ -24,6 +24,7 @@
 
 #include "arol_internal.h"
 #include "ptx.h"
+#include "region.h"
 #include "sepchain.h"
 
 namespace arol {
@@ -294,8 +295,7 @@ __global__ void __launch_bounds__(kBwThreads) sep_row_bwd_kernel(const SepPassDe
 // after 16 halo words holding the row's last m (Q - 1) words (the windows of
 // repetitions 0 .. Q - 2 that wrap to the row's end), and 16 halo words after
 // the X row repeat its first 16 words (windows that run past the row's end).
-constexpr int kVecThreads = 128;
-__device__ __forceinline__ int swz(int f) { return (f & ~3) | ((f & 3) ^ ((f >> 3) & 3)); }
+constexpr int kVecThreads = kRegionThreads;
 
 template <int SS, int MM, int TT>
 __global__ void __launch_bounds__(kVecThreads) sep_row_bwd_vec_kernel(const SepPassDev p, int64_t rows,
@@ -330,12 +330,7 @@ __global__ void __launch_bounds__(kVecThreads) sep_row_bwd_vec_kernel(const SepP
         float* gs = st + 16;
         for (int f = threadIdx.x; f < Wo4; f += blockDim.x) ptx::cp_async16(gs + 4 * f, gr + 4 * f);
         for (int e = threadIdx.x; e < halo; e += blockDim.x) ptx::cp_async4(gs - halo + e, gr + Wout - halo + e);
-        if (partials) {
-            const float* xr = x + rr * Win;
-            float* xs = st + gsz;
-            for (int f = threadIdx.x; f < W4 + 4; f += blockDim.x)
-                ptx::cp_async16(xs + 4 * swz(f), xr + 4 * (f < W4 ? f : f - W4));
-        }
+        if (partials) stage_region_row(st + gsz, x + rr * Win, Win);
     };
     for (int i = 0; i < kBwStages - 1; ++i) {
         const int64_t rr = blockIdx.x + i * G;
@@ -390,14 +385,14 @@ __global__ void __launch_bounds__(kVecThreads) sep_row_bwd_vec_kernel(const SepP
                     }
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
-                    *reinterpret_cast<float4*>(ds + 4 * swz(u0 + v)) =
+                    *reinterpret_cast<float4*>(ds + 4 * region_unit(u0 + v)) =
                         make_float4(o4[4 * v], o4[4 * v + 1], o4[4 * v + 2], o4[4 * v + 3]);
             }
             if (partials) {
                 float xw[XW];
 #pragma unroll
                 for (int v = 0; v < XW / 4; ++v) {
-                    const float4 q4 = *reinterpret_cast<const float4*>(xs + 4 * swz(u0 + v));
+                    const float4 q4 = *reinterpret_cast<const float4*>(xs + 4 * region_unit(u0 + v));
                     xw[4 * v] = q4.x;
                     xw[4 * v + 1] = q4.y;
                     xw[4 * v + 2] = q4.z;
@@ -414,7 +409,7 @@ __global__ void __launch_bounds__(kVecThreads) sep_row_bwd_vec_kernel(const SepP
         __syncthreads();
         if (gx) {
             float4* dst = reinterpret_cast<float4*>(gx + row * Win);
-            for (int f = threadIdx.x; f < W4; f += blockDim.x) dst[f] = *reinterpret_cast<const float4*>(ds + 4 * swz(f));
+            for (int f = threadIdx.x; f < W4; f += blockDim.x) dst[f] = *reinterpret_cast<const float4*>(ds + 4 * region_unit(f));
         }
     }
     ptx::cp_async_wait_all();

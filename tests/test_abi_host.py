@@ -262,12 +262,17 @@ def _fir2d(n0, n1, p0, p1, s0=1, s1=1, m=1, dtype="f32"):
 
 
 def test_info_reports_the_kernel_path(B):
-    """Which kernel a single task takes, decided on the host: the staged row
-    and column FIR tiles, the 2-D window tiles and the register-blocked
-    stencil are f32-only paths; 16-bit storage, copies and anything else take
-    the per-repetition walk."""
+    """Which kernel a single task takes, decided on the host: the row FIR in
+    16-word regions, the staged row and column FIR tiles, the 2-D window
+    tiles and the register-blocked stencil are f32-only paths; 16-bit
+    storage, copies and anything else take the per-repetition walk."""
     tk, _ = W.config0()
-    assert _path(B, tk) == 1                                              # row FIR, step 4, wrap
+    assert _path(B, tk) == 5                                              # row FIR, step 4, wrap: regions
+    shifted = dict(tk, inputs=[dict(tk["inputs"][0], origin=(0, 8))])
+    assert _path(B, shifted) == 1                                         # origin not a multiple of 16: tiles
+    wide = W.config0_scaled(frames=2, height=8, width=1920)[0]
+    assert _path(B, wide) == 5
+    assert _path(B, W.config0_scaled(frames=2, height=8, width=1928)[0]) == 1   # rows not a multiple of 16
     assert _path(B, dict(tk, inputs=[dict(tk["inputs"][0], dtype="f16")])) == 0
     assert _path(B, dict(tk, outputs=[dict(tk["outputs"][0], dtype="bf16")])) == 0
     col = W.task((16, 64), "fir", [W.port((64, 64), (0, 0), ((4, 0), (0, 1)), ((1,), (0,)), (8,))],

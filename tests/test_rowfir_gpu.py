@@ -107,3 +107,42 @@ def test_rowfir_results_do_not_depend_on_the_launch_shape(arol, monkeypatch):
     b.sync_status()
     for a, c in zip(o1, o2):
         assert torch.equal(a, c)
+
+
+@pytest.mark.parametrize("S", [2, 4, 8])
+def test_rowfir_regions(arol, S):
+    """Single row-FIR tasks in 16-word regions: every output count the form
+    takes, 1 to 8 taps, origin 0 or a multiple of 16 (windows that wrap at
+    the row's end), against the C oracle.  The same task on views one float
+    past a 16-byte boundary takes the row-FIR tiles, within the same bound."""
+    g = W.rng(310 + S)
+    for M in range(1, (2 if S == 2 else 4) + 1):
+        for T in sorted({1, S, 8, int(g.integers(1, 9))}):
+            Wd = 16 * int(g.integers(1, 40))
+            H = int(g.integers(1, 50))
+            o1 = 16 * int(g.integers(0, Wd // 16))
+            tk = row_task(g, H, Wd, T, M, S, R1=Wd // S, o=(0, o1))
+            x = g.standard_normal((H, Wd)).astype(np.float32)
+            ref = C.run_task(tk, [x])[0]
+            scale = fir_scale(tk, x, C.run_chain)
+            t = arol.Task(tk)
+            assert t.info["path"] == 5
+            y = t.run([dev(x)])
+            xb = torch.zeros(x.size + 1, device="cuda")
+            xb[1:] = dev(x).reshape(-1)
+            y1 = t.run([xb[1:].view(x.shape)])
+            t.sync_status()
+            assert_fir_close(host(y), ref, scale, what=f"S {S} M {M} T {T} W {Wd} o {o1}")
+            assert_fir_close(host(y1), ref, scale, what=f"S {S} M {M} T {T} W {Wd} o {o1}, unaligned")
+
+
+def test_rowfir_regions_config0_scaled_full_size(arol):
+    """The 64 x 64 task's tiler (8 taps, 3 outputs, step 4, windows wrapping
+    at the row end) on 64 x 1080 x 1920 float32, as the bench runs it,
+    against the C oracle element by element."""
+    tk, (x,) = W.config0_scaled()
+    t = arol.Task(tk)
+    assert t.info["path"] == 5
+    y = t.run([dev(x)])
+    t.sync_status()
+    assert_fir_close(host(y), C.run_task(tk, [x])[0], fir_scale(tk, x, C.run_chain), what="config0 scaled")
