@@ -7,7 +7,7 @@
 // T <= 8, rows of a multiple of 16 words, origin o a multiple of 16, output
 // rows of M R words starting at column 0, one output row per input row.
 //
-// One block of kRegionThreads threads takes a row at a time; the rows reach
+// One block of kRrThreads threads takes a row at a time; the rows reach
 // shared memory by 16-byte cp.async copies in a ring of kRrStages stages
 // (swizzled, with the 16-word halo of region.h).  Thread t owns the home
 // region h0 = (o + 16 t) mod W: the windows of repetitions NR t .. NR t + NR -
@@ -24,11 +24,18 @@
 namespace arol {
 namespace {
 
-constexpr int kRrStages = 3;
+#ifndef AROL_RR_STAGES
+#define AROL_RR_STAGES 4
+#endif
+#ifndef AROL_RR_THREADS
+#define AROL_RR_THREADS kRegionThreads
+#endif
+constexpr int kRrStages = AROL_RR_STAGES;
+constexpr int kRrThreads = AROL_RR_THREADS;
 constexpr int kRrTaps = 64;
 
 template <int SS, int M>
-__global__ void __launch_bounds__(kRegionThreads) rowfir_region_kernel(int64_t rows, int W, int o, int T,
+__global__ void __launch_bounds__(kRrThreads) rowfir_region_kernel(int64_t rows, int W, int o, int T,
                                                                        const float* __restrict__ taps,
                                                                        const float* __restrict__ x,
                                                                        float* __restrict__ y) {
@@ -140,10 +147,10 @@ cudaError_t launch_rowfir_region(int S, int T, int M, int64_t rows, int W, int o
     const size_t smem = region_smem(W);
     const RegionKernel k = region_kernel(S, M);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegionThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRrThreads, smem);
     const int64_t cap = (int64_t)device_sm_count() * (n > 0 ? n : 1);
     const int grid = (int)(rows < cap ? rows : cap);
-    k<<<grid, kRegionThreads, smem, s>>>(rows, W, o, T, taps, x, y);
+    k<<<grid, kRrThreads, smem, s>>>(rows, W, o, T, taps, x, y);
     return cudaGetLastError();
 }
 
