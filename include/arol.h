@@ -207,10 +207,12 @@ arol_status arol_task_set_taps(arol_task t, const float* taps, int on_device);
 
 /* Run the task: in[k] is the device pointer of input port k, out[0] of the
  * output port.  Inputs are read-only (Sec. 6.3); they must not overlap the
- * output.  Row- and column-FIR tasks and chains outside the fused kernel run
- * on the batch engine as a one-member batch the handle owns (built at the
- * first run, rebuilt after arol_task_set_taps); with taps on the device they
- * take the per-repetition kernel.  A handle may be used from several streams:
+ * output.  Row-FIR tasks that the 16-word-region kernel takes (info path 5)
+ * run there when both buffers are 16-byte aligned.  Other row- and
+ * column-FIR tasks and chains outside the fused kernel run on the batch
+ * engine as a one-member batch the handle owns (built at the first run,
+ * rebuilt after arol_task_set_taps); with taps on the device they take the
+ * per-repetition kernel.  A handle may be used from several streams:
  * a change of buffers is ordered after its launches on any stream. */
 arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, void* stream);
 
@@ -227,7 +229,11 @@ arol_status arol_task_run_host(arol_task t, const void* const* host_in, void* co
  * scatter-add, which
  * sums over every (r, i) whose gather visited an element (overlaps and modulo
  * wrap included).  grad_taps (nullable, device, m x T floats, a chain's blocks
- * concatenated) is OVERWRITTEN with dL/dH.  Deterministic: no atomics. */
+ * concatenated) is OVERWRITTEN with dL/dH.  Deterministic: no atomics.
+ * Row and column FIR passes (single tasks and the passes of a separable
+ * chain) whose repetitions tile their axis take one sweep per pass for dX and
+ * the tap gradients; a chain recomputes its intermediates from saved_in, and
+ * a separable chain does so only when grad_taps is given. */
 arol_status arol_task_backward(arol_task t, const void* grad_out, const void* const* saved_in,
                                void* grad_in, float* grad_taps, void* stream);
 

@@ -6,14 +6,20 @@
 // the "home" of repetition r, and the windows that reach it are those of
 // repetitions (r - q) mod R with tap index d + S q < T, q < Q = ceil(T / S).
 //
-//  * Row pass: one block per input row at a time.  The row of dY and the row
-//    of X are staged in shared memory by 16-byte loads (one padding word per
-//    32, so lanes reading at a stride of S words spread over the banks); each
+//  * Row pass, 16-word regions (steps 2, 4, 8; rows and origin multiples of
+//    16; X in f32): rows staged swizzled (region.h), each thread owning the
+//    16 home words of 16 / S repetitions with every index a compile-time
+//    offset: 16-byte shared loads and stores, taps in registers.
+//  * Row pass, staged rows (the other shapes): one block per input row at a
+//    time.  The row of dY and the row of X are staged in shared memory (one
+//    padding word per 32, so lanes reading at a stride of S words spread over
+//    the banks; 4-byte cp.async copies a few rows ahead when X is f32); each
 //    thread takes repetitions, writes their S home elements of dX into a
 //    staged row and adds its m x T tap products in registers; the staged dX
 //    row leaves by 16-byte stores.
 //  * Column pass: one thread per (frame, repetition, 4 columns): Q m rows of
-//    dY and T rows of X as 16-byte loads, S rows of dX as 16-byte stores.
+//    dY and T rows of X as 16-byte loads (the X window before any dX store),
+//    S rows of dX as 16-byte stores.
 //
 // Tap gradients: every thread keeps its m x T sums in registers; the block
 // adds them in a fixed order into its partials (one row of m T floats per
