@@ -294,13 +294,10 @@ __global__ void __launch_bounds__(kBwThreads) sep_row_bwd_kernel(const SepPassDe
 // is a compile-time constant: the window and the 16 dX words move as 16-byte
 // shared loads and stores, the taps sit in registers.
 //
-// Staged X and dX rows are swizzled by 16-byte units: unit f of a row lives
-// at unit (f & ~3) | ((f & 3) ^ ((f >> 3) & 3)), so the 8 lanes of a
-// quarter-warp that read unit v of 8 consecutive regions (a stride of 64
-// bytes) hit 8 distinct 16-byte bank groups.  The dY row is stored plainly
-// after 16 halo words holding the row's last m (Q - 1) words (the windows of
-// repetitions 0 .. Q - 2 that wrap to the row's end), and 16 halo words after
-// the X row repeat its first 16 words (windows that run past the row's end).
+// Staged X and dX rows take the swizzled layout of region.h (X with its 16
+// halo words for the windows that run past the row's end).  The dY row is
+// stored plainly after 16 halo words holding the row's last m (Q - 1) words
+// (the windows of repetitions 0 .. Q - 2 that wrap to the row's end).
 constexpr int kVecThreads = kRegionThreads;
 
 template <int SS, int MM, int TT>
