@@ -1578,8 +1578,9 @@ arol_status arol_task_run(arol_task t, const void* const* in, void* const* out, 
             return AROL_OK;
         }
         if (t->rr_ok && aligned16(in[0]) && aligned16(out[0])) {
+            if ((st = ensure_err(t, s)) != AROL_OK) return st;
             AROL_CUDA(launch_rowfir_region(t->rr_S, t->rr_T, t->rr_M, t->rr_rows, t->rr_W, t->rr_o, taps,
-                                           (const float*)in[0], (float*)out[0], s),
+                                           (const float*)in[0], (float*)out[0], t->err_flag, s),
                       "row-FIR region kernel launch");
             return AROL_OK;
         }

@@ -224,7 +224,7 @@ cudaError_t launch_sep_bwd(const SepBwdPlan& plan, const SepPassDev& p, int64_t 
 // per input row; x and y 16-byte aligned.
 bool rowfir_region_supported(int S, int T, int M, int64_t W, int64_t Wout, int64_t o, int64_t rows);
 cudaError_t launch_rowfir_region(int S, int T, int M, int64_t rows, int W, int o, const float* taps, const float* x,
-                                 float* y, cudaStream_t s);
+                                 float* y, unsigned* err, cudaStream_t s);
 // Sum of nblocks rows of npairs partials, in a fixed order (k_tiler.cu).
 cudaError_t launch_tap_reduce(const float* partials, int nblocks, int npairs, float* out, cudaStream_t s);
 size_t sepchain_smem(const SepChainDev& d);
