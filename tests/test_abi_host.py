@@ -254,6 +254,14 @@ def _path(B, spec):
         B.arol_task_destroy(h)
 
 
+def _row(g, Wd, T, m, S, R1, o=(0, 0), oo=(0, 0), H=8):
+    """A row FIR on an H x Wd array: R1 repetitions per row at step S from
+    origin o, m outputs per repetition from output origin oo."""
+    inp = W.port((H, Wd), o, ((1, 0), (0, S)), ((0,), (1,)), (T,))
+    out = W.port((H, m * R1), oo, ((1, 0), (0, m)), ((0,), (1,)), (m,))
+    return W.task((H, R1), "fir", [inp], [out], (g.standard_normal((m, T)) / T).astype(np.float32))
+
+
 def _fir2d(n0, n1, p0, p1, s0=1, s1=1, m=1, dtype="f32"):
     R0, R1 = -(-n0 // s0), -(-n1 // s1)
     inp = W.port((n0, n1), (-(p0 // 2), -(p1 // 2)), ((s0, 0), (0, s1)), ((1, 0), (0, 1)), (p0, p1), dtype)
@@ -273,6 +281,14 @@ def test_info_reports_the_kernel_path(B):
     wide = W.config0_scaled(frames=2, height=8, width=1920)[0]
     assert _path(B, wide) == 5
     assert _path(B, W.config0_scaled(frames=2, height=8, width=1928)[0]) == 1   # rows not a multiple of 16
+    g = W.rng(1)
+    assert _path(B, _row(g, 64, 5, 2, 4, 16, o=(0, 16))) == 5              # origin a multiple of 16
+    assert _path(B, _row(g, 64, 8, 4, 8, 8)) == 5                          # step 8, 4 outputs
+    assert _path(B, _row(g, 64, 5, 3, 2, 32)) == 1                         # step 2 takes at most 2 outputs
+    assert _path(B, _row(g, 64, 9, 2, 4, 16)) == 1                         # more than 8 taps
+    assert _path(B, _row(g, 64, 5, 2, 4, 16, oo=(0, 4))) == 1              # output columns not from 0
+    assert _path(B, _row(g, 64, 5, 2, 4, 16, o=(3, 0))) == 1               # rows shifted
+    assert _path(B, _row(g, 64, 5, 2, 4, 15)) == 1                         # repetitions short of the row
     assert _path(B, dict(tk, inputs=[dict(tk["inputs"][0], dtype="f16")])) == 0
     assert _path(B, dict(tk, outputs=[dict(tk["outputs"][0], dtype="bf16")])) == 0
     col = W.task((16, 64), "fir", [W.port((64, 64), (0, 0), ((4, 0), (0, 1)), ((1,), (0,)), (8,))],
